@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark: path solves/s to 1e-5 m stationarity, forward + implicit backward.
+
+Workload (one step): the urban canyon -- 32 vertical facades (5-30 m) on a
+200 x 200 m grid plus their 128 edges, a 32-object alphabet (16 facades, 16
+edges), TX at (100, 100, 10) m and a 32 x 32 RX grid at 1.5 m; every order-3
+sequence for every RX: 32^3 * 1024 = 33,554,432 paths.  A step enumerates,
+solves (plain init, FP32 BFGS with Eq. 6 step sizes, FP64-gradient Newton
+polish, validity), and back-propagates the sum of the valid solved paths'
+lengths to TX, RX and every vertex by implicit differentiation.  A path
+counts as solved when its stationarity residual is <= 1e-5 m.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the workload (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "path solves/s to 1e-5 m stationarity, fwd+implicit bwd; learned vs plain init"
+UNIT = "solves/s"
+WORKLOAD = ("urban canyon: 32 facades + 128 edges, 32-object alphabet (16 R + 16 D), order 3, "
+            "1 TX x 32x32 RX = 33,554,432 paths; plain init; FP32 BFGS + Eq.6 fixed point, FP64-gradient "
+            "Newton polish, validity, implicit backward of the sum of valid path lengths")
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work (FP32 flops, FMA = 2) of the BFGS kernel, per path
+# ---------------------------------------------------------------------------
+def bfgs_flops_per_iter(n: int, fp: int) -> int:
+    """Static op count of one BFGS step of order n with fp rounds of Eq. 6 (k_solve.cu)."""
+    m, s = 2 * n, n + 1
+    hp = m * (m + 1) // 2
+    direction = 2 * m * m + m              # p = -H g
+    world = 15 * n                         # A_i p_i and |A_i p_i|^2
+    segs = 3 * (n - 1) + 10 * s            # q_j, q_j.z_j, q_j.q_j
+    fixed = fp * (9 * s + 1)               # Eq. 6 rounds
+    step = 2 * m                           # s = alpha p, t += s
+    grad = 28 * n + 9 * s                  # z_j, |z_j|, u_j, g
+    curv = 7 * m + 4                       # y, s.y, s.s, y.y, guard
+    update = 1 + 2 * m * m + 2 * m + 3 + 4 * m + 4 * hp  # inverse-Hessian update
+    conv = 2 + n
+    return direction + world + segs + fixed + step + grad + curv + update + conv
+
+
+def bfgs_flops_init(n: int) -> int:
+    return 28 * n + 9 * (n + 1)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_identifier(torch, dev) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("k_solve.cu", "k_polish.cu", "blocktri.cuh", "fpt_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2510_16172_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+# DRAM traffic per launch from an ncu capture (profiles/), valid for the kernel sources with this hash.
+NCU_TRAFFIC = {}
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(sc, n_paths, seed, target_s=None, max_paths=None):
+    """Oracle fwd+bwd on a seeded uniform sample of the workload: (solved/s, sample size, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    threads = os.cpu_count() or 1
+
+    def run(m):
+        g = np.sort(rng.choice(n_paths, m, replace=False))
+        ids, order, ti, ri = oracle.exhaustive_paths(sc, 3, 3, g)
+        t0 = time.perf_counter()
+        out = oracle.solve(sc, ids, order, ti, ri, dL=np.ones(m), n_threads=threads)
+        dt = time.perf_counter() - t0
+        return int(((out["status"] & oracle.SOLVED) > 0).sum()), dt
+
+    m = 20000
+    solved, dt = run(m)
+    if target_s:
+        m = int(min(max_paths or 4_000_000, max(m, m * target_s / max(dt, 1e-3))))
+        solved, dt = run(m)
+    return solved / dt, m, dt, threads
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle on the machine's host cores, rank 0 only."""
+    if rank != 0:
+        return
+    from paper_2510_16172_gb300 import scenes
+
+    sc = scenes.urban_canyon(0)
+    n_paths = 32 ** 3 * len(sc.rx)
+    rate0, m0, dt0, threads = oracle_rate(sc, n_paths, 1)
+    per_step = int(min(2_000_000, max(20000, rate0 * 4.0)))  # about 4 s of CPU work per step
+    import numpy as np
+
+    import oracle
+
+    rng = np.random.default_rng(2)
+    times, solved = [], 0
+    for k in range(args.warmup + args.steps):
+        g = np.sort(rng.choice(n_paths, per_step, replace=False))
+        ids, order, ti, ri = oracle.exhaustive_paths(sc, 3, 3, g)
+        t0 = time.perf_counter()
+        out = oracle.solve(sc, ids, order, ti, ri, dL=np.ones(per_step), n_threads=threads)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            solved += int(((out["status"] & oracle.SOLVED) > 0).sum())
+    total = sum(times)
+    value = solved / total
+    sample = f"{per_step} uniformly sampled paths of the workload per step (seeded), FP64 damped Newton + VJP"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_paths_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, world, rank, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2510_16172_gb300 import build, fpt, scenes
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    sc = scenes.urban_canyon(0)
+    ctx = fpt.Context(local_rank)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    batch = fpt.Batch.exhaustive(ctx, scene, 3, 3, sc.alphabet)
+    N = batch.n_paths
+    params = fpt.default_params()
+    out = fpt.alloc_outputs(ctx, batch, with_X=False, with_rho=False, with_iters=True)
+    grads = (torch.empty((scene.n_tx, 3), device=dev), torch.empty((scene.n_rx, 3), device=dev),
+             torch.empty((scene.n_obj, 3, 3), device=dev))
+    mask = fpt.ST_VALID | fpt.ST_SOLVED
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fpt.solve(ctx, scene, batch, params, out)
+        fpt.backward(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask, out=grads)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    torch.cuda.synchronize(dev)
+
+    fpt.profile_enable(ctx, True)
+    fpt.profile_read(ctx, reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(gpu_identifier(torch, dev)) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.zero_()  # write 512 MB between steps: evict L2 (129 MB)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kms, klaunch = fpt.profile_read(ctx, reset=True)
+    fpt.profile_enable(ctx, False)
+    total_ms = sum(step_ms)
+    solved = fpt.count_status(ctx, out["status"], fpt.ST_SOLVED)
+    iters = out["iters"].to(torch.int64)
+    total_iters = int(iters.sum().item())
+    run_paths = N - fpt.count_status(ctx, out["status"], fpt.ST_REPEAT)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        s = torch.tensor([solved], device=dev, dtype=torch.float64)
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        solved_all = float(s.item())
+    else:
+        solved_all = float(solved)
+    value = solved_all * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (device time per launch from the library's event timing)
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    per_launch = {k: (kms[k] / klaunch[k] if klaunch[k] else 0.0) for k in range(fpt.K_COUNT)}
+    bfgs_flops = bfgs_flops_init(3) * run_paths + bfgs_flops_per_iter(3, params.fp_iters) * total_iters
+    names = {fpt.K_BFGS: "bfgs_kernel<3>", fpt.K_POLISH: "polish_kernel<3>", fpt.K_BACKWARD: "backward_kernel<3>",
+             fpt.K_OTHER: "backward_finalize_kernel"}
+    dom = max(range(fpt.K_COUNT), key=lambda k: kms[k])
+    clocks = clk.summary()
+    roof_bfgs = {"kernel": names[fpt.K_BFGS], "bound": "alu", "achieved": bfgs_flops / (per_launch[0] * 1e-3) / 1e12,
+                 "peak": fp32_peak, "unit": "TFLOP/s",
+                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured peaks)",
+                 "traffic": NCU_TRAFFIC.get((kernel_source_hash(), "bfgs"))}
+    roof_bfgs["frac"] = roof_bfgs["achieved"] / roof_bfgs["peak"]
+    if clocks.get("sm_mhz"):
+        roof_bfgs["frac_at_measured_clock"] = roof_bfgs["achieved"] / (fp32_peak * clocks["sm_mhz"] / sm_max)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_paths": N, "init": "plain (learned init not built)",
+                       "polish": "1 Newton step, FP64 gradient", "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "solved_per_step": solved, "solved_fraction": solved / N, "mean_bfgs_iters": total_iters / max(1, run_paths),
+            "kernel_ms_per_step": {names[k]: kms[k] / args.steps for k in range(fpt.K_COUNT)},
+            "dominant_kernel": names[dom],
+            "roofline": roof_bfgs,
+            "gpu_launches": int(sum(klaunch)),
+            "clocks": clocks}
+    if dom != fpt.K_BFGS:
+        line["roofline_note"] = f"dominant kernel is {names[dom]}; roofline reported for the FP32 solver kernel"
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, sc, ctx, dev, torch, fpt)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, m, dt, threads = oracle_rate(sc, N, 1, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{m} seeded uniformly sampled paths of the workload, FP64 damped Newton "
+                                          f"+ implicit VJP, {dt:.1f} s on {threads} threads"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def e2e(args, sc, ctx, dev, torch, fpt):
+    """Same metric through the public API: host scene/endpoints in, host lengths/status/gradients out."""
+    import numpy as np
+
+    types = torch.from_numpy(sc.types).pin_memory()
+    verts = torch.from_numpy(sc.verts).pin_memory()
+    tx = torch.from_numpy(sc.tx).pin_memory()
+    rx = torch.from_numpy(sc.rx).pin_memory()
+    alphabet = sc.alphabet
+    N = 32 ** 3 * len(sc.rx)
+    L_h = torch.empty(N, dtype=torch.float32).pin_memory()
+    st_h = torch.empty(N, dtype=torch.uint8).pin_memory()
+    gv_h = torch.empty((len(sc.types), 3, 3), dtype=torch.float32).pin_memory()
+    gtx_h = torch.empty((len(sc.tx), 3), dtype=torch.float32).pin_memory()
+    grx_h = torch.empty((len(sc.rx), 3), dtype=torch.float32).pin_memory()
+    mask = fpt.ST_VALID | fpt.ST_SOLVED
+    out = None
+    times, solved = [], 0
+    h2d = types.numel() + verts.numel() * 8 + tx.numel() * 8 + rx.numel() * 8 + alphabet.size * 4
+    d2h = N * 4 + N + gv_h.numel() * 4 + gtx_h.numel() * 4 + grx_h.numel() * 4
+    for k in range(args.warmup + max(3, args.steps // 2)):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        scene = fpt.Scene(ctx, types.numpy(), verts.numpy(), tx.numpy(), rx.numpy())
+        batch = fpt.Batch.exhaustive(ctx, scene, 3, 3, alphabet)
+        if out is None:
+            out = fpt.alloc_outputs(ctx, batch, with_X=False, with_rho=False, with_iters=False)
+        fpt.solve(ctx, scene, batch, None, out)
+        g = fpt.backward(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask)
+        L_h.copy_(out["L"], non_blocking=True)
+        st_h.copy_(out["status"], non_blocking=True)
+        gtx_h.copy_(g[0], non_blocking=True)
+        grx_h.copy_(g[1], non_blocking=True)
+        gv_h.copy_(g[2], non_blocking=True)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            solved += int(((st_h.numpy() & fpt.ST_SOLVED) > 0).sum())
+        batch.close()
+        scene.close()
+    return {"value": solved / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": 1e3 * sum(times) / len(times)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, world, rank, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

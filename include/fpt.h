@@ -1,0 +1,210 @@
+/*
+ * fpt.h -- C ABI of the batched Fermat path library (CUDA, sm_103a).
+ *
+ * The library finds ray paths between transmitters (TX) and receivers (RX)
+ * that interact, in a given order, with planar reflectors and straight
+ * diffraction edges.  For every candidate interaction sequence it minimises
+ * the total path length (Fermat's principle) over one point per object,
+ * following "Fast, Differentiable, GPU-Accelerated Ray Tracing for Multiple
+ * Diffraction and Reflection Paths" (arXiv 2510.16172):
+ *
+ *   - candidate sequences: all ordered sequences of n objects, n = lo..hi
+ *     (Sec. III, first paragraph);
+ *   - unified parameterisation x_i = A_i t_i + b_i with t_i in R^2; an edge
+ *     uses a zero second basis vector (Sec. III-B, Eq. 3);
+ *   - objective: L(T; A, B) = sum_i |x_{i+1} - x_i|, x_0 = TX, x_{n+1} = RX
+ *     (Sec. III-B, Eq. 4-5);
+ *   - solver: BFGS on the inverse Hessian with the fixed-point step-size
+ *     update of Eq. 6 (Sec. III-C), in FP32;
+ *   - validity: each point inside its object (Sec. I, Sec. III);
+ *   - gradients: implicit differentiation at grad_T L = 0 (Sec. III-D,
+ *     Eq. 8-13).
+ *
+ * Conventions.
+ *   - All calls are asynchronous on the context's CUDA stream unless stated.
+ *     Device pointers are caller-owned and must stay valid until the stream
+ *     reaches the call.  Host pointers are read before the call returns.
+ *   - Objects: type FPT_QUAD (planar reflector) is the parallelogram with
+ *     corners v0, v1, v1 + v3 - v0, v3, given as verts = (v0, v1, v3); its
+ *     record is b = v0, A = [v1 - v0, v3 - v0] and t in [0,1]^2 is inside.
+ *     Type FPT_EDGE (straight edge e0 -> e1) is given as verts = (e0, e1, *);
+ *     b = e0, A = [e1 - e0, 0] and t_1 in [0,1] is inside.
+ *   - Path index g (uint64) enumerates a batch; per-path arrays are indexed
+ *     by g.  n_max is the batch's largest order; per-path slot arrays have
+ *     n_max slots and unused slots are written as zero.
+ *   - No call traps or faults on bad data: invalid per-path input gets the
+ *     FPT_ST_INVALID_INPUT status bit.  Launch or argument errors are
+ *     returned as fpt_status; fpt_last_error() gives a message.
+ */
+#ifndef FPT_H
+#define FPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility push(default) /* the library is built with -fvisibility=hidden */
+#endif
+
+typedef enum {
+  FPT_OK = 0,
+  FPT_EINVAL = 1,       /* bad argument (null pointer, size, degenerate object, ...) */
+  FPT_ENOMEM = 2,       /* device or host allocation failed */
+  FPT_ECUDA = 3,        /* a CUDA runtime call failed */
+  FPT_EDEVICE = 4,      /* a kernel reported an error through the device error word */
+  FPT_EUNSUPPORTED = 5  /* valid request outside what this build supports */
+} fpt_status;
+
+enum { FPT_QUAD = 0, FPT_EDGE = 1 };
+
+/* per-path status bits (uint8) */
+enum {
+  FPT_ST_VALID = 1,         /* every point lies inside its object (closed test) */
+  FPT_ST_CONVERGED = 2,     /* BFGS stopped on its world-space step tolerance */
+  FPT_ST_SOLVED = 4,        /* stationarity residual <= solved_tol and not DEGENERATE/REPEAT/NONFINITE */
+  FPT_ST_FP64 = 8,          /* the Hessian solve was redone in FP64 (ill-conditioned) */
+  FPT_ST_DEGENERATE = 16,   /* a segment shorter than deg_tol at the solution (kink of L) */
+  FPT_ST_REPEAT = 32,       /* the same object twice in a row: not solved */
+  FPT_ST_NONFINITE = 64,    /* NaN/Inf met */
+  FPT_ST_INVALID_INPUT = 128 /* object id, order or TX/RX index out of range */
+};
+
+/* Solver parameters.  fpt_default_params() fills the defaults shown. */
+typedef struct {
+  int32_t max_iters;   /* BFGS step cap (64).  Sec. III-C runs a fixed count; see fixed_iters. */
+  int32_t fp_iters;    /* rounds of the Eq. 6 fixed point per BFGS step (1; the paper also uses 64) */
+  int32_t polish;      /* Newton steps with an FP64 gradient after BFGS (1; 0..2) */
+  int32_t fixed_iters; /* 1: every path runs exactly max_iters steps (Sec. III-C); 0: stop on tol_step (0) */
+  float tol_step;      /* BFGS stops when max_i |A_i s_i| <= tol_step metres (1e-4) */
+  float solved_tol;    /* stationarity residual bound for FPT_ST_SOLVED, metres (1e-5) */
+  float deg_tol;       /* a solution segment shorter than this (metres) is DEGENERATE (1e-3) */
+  float cond_fp64;     /* Hessian pivot ratio below which the solve is redone in FP64 (1e-4) */
+  int32_t init_mode;   /* 0: plain init, t = 1/2 (object centroid).  1: learned init (unsupported here) */
+  int32_t reserved[7]; /* must be zero */
+} fpt_solve_params;
+
+typedef struct fpt_ctx fpt_ctx;
+typedef struct fpt_scene fpt_scene;
+typedef struct fpt_batch fpt_batch;
+
+/* Defaults listed in fpt_solve_params. */
+void fpt_default_params(fpt_solve_params* p);
+
+/* Create a context on CUDA device `device`, launching on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  The context owns its
+ * device workspace.  Returns FPT_ECUDA if the device cannot be used. */
+fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream);
+void fpt_destroy(fpt_ctx* ctx);
+fpt_status fpt_set_stream(fpt_ctx* ctx, void* cuda_stream);
+/* Message for the last error on this context (static storage, never NULL). */
+const char* fpt_last_error(const fpt_ctx* ctx);
+/* Wait for the stream, then check the device error word: FPT_EDEVICE if a
+ * kernel flagged an error since the last check (the word is then cleared). */
+fpt_status fpt_sync(fpt_ctx* ctx);
+
+/* Scene upload (Sec. III-B, Eq. 3).  types: host uint8 [n_obj] (FPT_QUAD /
+ * FPT_EDGE); verts: host double [n_obj][3][3].  The library builds object
+ * records in FP32 (hi + lo parts) and FP64 on the device, relative to the
+ * scene centre.  FPT_EINVAL on non-finite vertices, a zero-area plane or a
+ * zero-length edge (< 1e-9 m), or n_obj outside [1, 65535].  Synchronous. */
+fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* verts, int32_t n_obj,
+                            fpt_scene** out);
+void fpt_scene_free(fpt_scene* scene);
+/* TX and RX positions (x_0 and x_{n+1} of Eq. 2): host double [n][3].
+ * Copied to the device.  FPT_EINVAL on non-finite input or n < 1. */
+fpt_status fpt_set_endpoints(fpt_scene* scene, const double* tx, int32_t n_tx, const double* rx, int32_t n_rx);
+
+/* Candidate sequences (Sec. III).
+ * Exhaustive: for every (tx, rx) pair, every ordered sequence over the
+ *   alphabet (host int32 object ids; NULL = all objects) of order lo..hi.
+ *   g = (tx * n_rx + rx) * per_pair + r; r runs over order lo first, each
+ *   order in lexicographic order with the first interaction most significant.
+ * Seeded: per_pair sequences for each pair; sequence g has order
+ *   lo + h(g,0) mod (hi-lo+1), first object h(g,1) mod K and each next object
+ *   (prev + 1 + h(g,j+1) mod (K-1)) mod K (no immediate repeats), where
+ *   h(g,s) is splitmix64's output function applied to
+ *   seed + 0x9E3779B97F4A7C15 * (8 g + s + 1).
+ * Explicit: caller-owned device arrays ids [n][n_max] (object ids),
+ *   order [n], tx_idx [n], rx_idx [n].
+ * FPT_EINVAL on lo < 1, hi > 5, lo > hi, empty alphabet or ids out of range
+ * (host-checked arrays only). */
+fpt_status fpt_batch_exhaustive(fpt_ctx* ctx, const fpt_scene* scene, const int32_t* alphabet, int32_t n_alpha,
+                                int32_t order_lo, int32_t order_hi, fpt_batch** out);
+fpt_status fpt_batch_seeded(fpt_ctx* ctx, const fpt_scene* scene, const int32_t* alphabet, int32_t n_alpha,
+                            uint64_t seed, uint64_t per_pair, int32_t order_lo, int32_t order_hi, fpt_batch** out);
+fpt_status fpt_batch_explicit(fpt_ctx* ctx, const fpt_scene* scene, const int32_t* ids_dev, const uint8_t* order_dev,
+                              const int32_t* tx_idx_dev, const int32_t* rx_idx_dev, uint64_t n, int32_t n_max,
+                              fpt_batch** out);
+/* Number of paths and slots per path of a batch. */
+fpt_status fpt_batch_size(const fpt_batch* batch, uint64_t* n_paths, int32_t* n_max);
+void fpt_batch_free(fpt_batch* batch);
+/* Write the batch's sequences (device outputs: ids [N][n_max] int32, order
+ * [N] uint8, tx_idx [N], rx_idx [N] int32; any may be NULL). */
+fpt_status fpt_enumerate(fpt_ctx* ctx, const fpt_batch* batch, int32_t* ids_out, uint8_t* order_out,
+                         int32_t* tx_idx_out, int32_t* rx_idx_out);
+
+/* Solve every path of the batch (Sec. III-C): plain init t = 1/2, BFGS with
+ * Eq. 6 step sizes in FP32, then `polish` Newton steps whose gradient is
+ * formed in FP64 and whose block-tridiagonal Hessian system is solved in
+ * FP32 (FP64 when ill-conditioned), then the validity test and the
+ * stationarity residual rho = max_i |A_i delta_i| of the Newton step at the
+ * returned T.  Device outputs (caller-owned; any but status_out may be NULL):
+ *   T_out [N][n_max][2] float   parameters t_i (edges: t_i2 stays 1/2)
+ *   X_out [N][n_max][3] float   world points x_i
+ *   L_out [N] float             path length
+ *   status_out [N] uint8        FPT_ST_* bits (required)
+ *   iters_out [N] uint8         BFGS steps taken (saturates at 255)
+ *   rho_out [N] float           stationarity residual, metres (inf if undefined) */
+fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* batch, const fpt_solve_params* params,
+                     float* T_out, float* X_out, float* L_out, uint8_t* status_out, uint8_t* iters_out,
+                     float* rho_out);
+
+/* Validity and stationarity at caller-given parameters T [N][n_max][2]
+ * (device).  Outputs (device, any may be NULL): mask [N] uint8 (1 = inside),
+ * bdist [N] float (signed in-plane distance to the nearest side line,
+ * metres, minimised over the path; positive inside), rho [N] float. */
+fpt_status fpt_validity(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* batch, const float* T,
+                        uint8_t* mask_out, float* bdist_out, float* rho_out);
+
+/* Implicit-differentiation backward (Sec. III-D, Eq. 8-13) at solutions T
+ * [N][n_max][2] (device).  Cotangents (device, may be NULL = zero):
+ * dX [N][n_max][3] for the points, dL [N] for the lengths.  When dL is NULL
+ * and dL_status_mask is non-zero, the length cotangent of a path is 1 if its
+ * status holds every bit of the mask and 0 otherwise (e.g. FPT_ST_VALID |
+ * FPT_ST_SOLVED differentiates the sum of the valid paths' lengths).  Per
+ * path: v = A^T dX + dL grad_T L, solve H u = -v with the block-tridiagonal
+ * Hessian H (FP32; FP64 if ill-conditioned), then u^T d(grad_T L)/dtheta plus
+ * the explicit terms.  Paths with status REPEAT/DEGENERATE/NONFINITE/
+ * INVALID_INPUT in `status` (device [N], may be NULL) contribute nothing.
+ * Gradients are summed over paths into device outputs that the call
+ * overwrites (any may be NULL): g_tx [n_tx][3], g_rx [n_rx][3],
+ * g_vertices [n_obj][3][3] (plane: v0, v1, v3; edge: e0, e1, zeros).
+ * Uses a context-owned FP64 accumulator of 9 n_obj + 3 (n_tx + n_rx) values. */
+fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* batch, const float* T,
+                        const uint8_t* status, const float* dX, const float* dL, uint8_t dL_status_mask,
+                        float* g_tx, float* g_rx, float* g_vertices);
+
+/* Number of paths whose status has all bits of `mask` set (device status
+ * [n]; result written to *count on the host after a stream sync). */
+fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uint8_t mask, uint64_t* count);
+
+/* Kernel timing.  While enabled, every kernel the context launches is
+ * bracketed by CUDA events on the context's stream, and fpt_profile_read()
+ * returns, per kernel class, the summed device time in milliseconds and the
+ * number of launches (it synchronises the stream; reset != 0 clears the sums). */
+enum { FPT_K_BFGS = 0, FPT_K_POLISH = 1, FPT_K_BACKWARD = 2, FPT_K_OTHER = 3, FPT_K_COUNT = 4 };
+fpt_status fpt_profile_enable(fpt_ctx* ctx, int on);
+fpt_status fpt_profile_read(fpt_ctx* ctx, double* ms, uint64_t* launches, int reset);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPT_H */

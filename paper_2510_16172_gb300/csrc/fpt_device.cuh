@@ -1,0 +1,196 @@
+// fpt_device.cuh -- device-side data layout and helpers shared by the kernels.
+//
+// Scene records live in HBM as flat arrays and are staged into shared memory
+// per CTA (a scene of K objects costs K * 48 B in FP32 and K * 72 B in FP64).
+// Coordinates are relative to the scene centre, which keeps FP32 ulps small.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fpt {
+
+constexpr int kMaxOrder = 5;        // longest sequence solved on the GPU
+constexpr int kRec32 = 12;          // floats per FP32 object record: b_hi[3], b_lo[3], a1[3], a2[3]
+constexpr int kRec64 = 9;           // doubles per FP64 object record: b[3], a1[3], a2[3]
+constexpr int kAux = 4;             // floats per object: side heights h1, h2 (metres), type, pad
+constexpr int kEnd32 = 6;           // floats per endpoint: hi[3], lo[3]
+
+// status bits (same values as the public header)
+constexpr uint8_t ST_VALID = 1, ST_CONVERGED = 2, ST_SOLVED = 4, ST_FP64 = 8, ST_DEGENERATE = 16,
+                  ST_REPEAT = 32, ST_NONFINITE = 64, ST_INVALID = 128;
+constexpr uint8_t ST_SKIP = ST_REPEAT | ST_INVALID;  // never solved
+
+// device error word codes
+constexpr int ERR_NONE = 0, ERR_BAD_ORDER = 1, ERR_SMEM = 2;
+
+struct SceneDev {
+  int n_obj;
+  const float* rec32;    // [n_obj][12]
+  const double* rec64;   // [n_obj][9]
+  const float* aux;      // [n_obj][4]
+  int n_tx, n_rx;
+  const float* tx32;     // [n_tx][6]
+  const float* rx32;     // [n_rx][6]
+  const double* tx64;    // [n_tx][3]
+  const double* rx64;    // [n_rx][3]
+  double centre[3];
+};
+
+enum BatchMode { BATCH_EXHAUSTIVE = 0, BATCH_SEEDED = 1, BATCH_EXPLICIT = 2 };
+
+struct BatchDev {
+  int mode;
+  int n_alpha;
+  const int32_t* alphabet;  // device [n_alpha]
+  int lo, hi, n_max;
+  int n_tx, n_rx;
+  uint64_t per_pair;        // sequences per (tx, rx) pair (exhaustive, seeded)
+  uint64_t n_paths;
+  uint64_t seed;
+  uint64_t kpow[kMaxOrder + 1];    // n_alpha^n
+  uint64_t offset[kMaxOrder + 2];  // exhaustive: first r of order n inside a pair
+  const int32_t* ids;       // explicit [n][n_max]
+  const uint8_t* order;     // explicit [n]
+  const int32_t* tx_idx;    // explicit [n]
+  const int32_t* rx_idx;    // explicit [n]
+};
+
+// One candidate sequence, decoded.
+struct PathDesc {
+  uint64_t g;
+  int n;
+  int ids[kMaxOrder];
+  int tx, rx;
+  uint8_t flags;  // ST_REPEAT / ST_INVALID
+};
+
+// splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014).
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// counter-based draw s of sequence g: state number 8 g + s + 1 of a splitmix64 stream
+__device__ __forceinline__ uint64_t seeded_draw(uint64_t seed, uint64_t g, int s) {
+  return sm64_mix(seed + 0x9E3779B97F4A7C15ULL * (8ULL * g + (uint64_t)s + 1ULL));
+}
+
+__device__ __forceinline__ void finish_desc(const BatchDev& B, const int* digits, PathDesc& d) {
+  d.flags = 0;
+  for (int j = 0; j < d.n; ++j) {
+    int o = B.alphabet[digits[j]];
+    d.ids[j] = o;
+    if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
+  }
+}
+
+// Exhaustive batch, order n known: local index j over n_pairs * K^n paths.
+__device__ __forceinline__ void decode_exhaustive_order(const BatchDev& B, int n, uint64_t j, PathDesc& d) {
+  uint64_t kn = B.kpow[n];
+  uint64_t pair = j / kn;
+  uint64_t r = j - pair * kn;
+  d.g = pair * B.per_pair + B.offset[n] + r;
+  d.n = n;
+  d.tx = (int)(pair / (uint64_t)B.n_rx);
+  d.rx = (int)(pair - (uint64_t)d.tx * (uint64_t)B.n_rx);
+  int digits[kMaxOrder];
+  const uint64_t K = (uint64_t)B.n_alpha;
+  if (kn <= 0xFFFFFFFFull) {  // 32-bit digit extraction
+    uint32_t r32 = (uint32_t)r, K32 = (uint32_t)K;
+#pragma unroll
+    for (int q = kMaxOrder - 1; q >= 0; --q)
+      if (q < n) {
+        uint32_t qq = r32 / K32;
+        digits[q] = (int)(r32 - qq * K32);
+        r32 = qq;
+      }
+  } else {
+#pragma unroll
+    for (int q = kMaxOrder - 1; q >= 0; --q)
+      if (q < n) {
+        uint64_t qq = r / K;
+        digits[q] = (int)(r - qq * K);
+        r = qq;
+      }
+  }
+  finish_desc(B, digits, d);
+}
+
+// Any batch: decode global index g.
+__device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, PathDesc& d) {
+  d.g = g;
+  if (B.mode == BATCH_EXPLICIT) {
+    int n = B.order[g];
+    d.n = n;
+    d.tx = B.tx_idx[g];
+    d.rx = B.rx_idx[g];
+    d.flags = 0;
+    if (n < 1 || n > B.n_max || n > kMaxOrder || d.tx < 0 || d.tx >= B.n_tx || d.rx < 0 || d.rx >= B.n_rx) {
+      d.flags = ST_INVALID;
+      const int cap = B.n_max < kMaxOrder ? B.n_max : kMaxOrder;
+      d.n = n < 1 ? 1 : (n > cap ? cap : n);
+      for (int j = 0; j < kMaxOrder; ++j) d.ids[j] = 0;
+      if (d.tx < 0 || d.tx >= B.n_tx) d.tx = 0;
+      if (d.rx < 0 || d.rx >= B.n_rx) d.rx = 0;
+      return;
+    }
+    for (int j = 0; j < n; ++j) {
+      int o = B.ids[g * (uint64_t)B.n_max + j];
+      d.ids[j] = o;
+      if (o < 0 || o >= B.n_alpha) {  // for explicit batches n_alpha holds the object count
+        d.flags |= ST_INVALID;
+        d.ids[j] = 0;
+      }
+      if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
+    }
+    return;
+  }
+  uint64_t pair = g / B.per_pair;
+  uint64_t r = g - pair * B.per_pair;
+  d.tx = (int)(pair / (uint64_t)B.n_rx);
+  d.rx = (int)(pair - (uint64_t)d.tx * (uint64_t)B.n_rx);
+  int digits[kMaxOrder];
+  const uint64_t K = (uint64_t)B.n_alpha;
+  if (B.mode == BATCH_SEEDED) {
+    int n = B.lo + (int)(seeded_draw(B.seed, g, 0) % (uint64_t)(B.hi - B.lo + 1));
+    d.n = n;
+    digits[0] = (int)(seeded_draw(B.seed, g, 1) % K);
+    for (int j = 1; j < n; ++j)
+      digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + seeded_draw(B.seed, g, j + 1) % (K - 1)) % K);
+  } else {
+    int n = B.lo;
+    while (n < B.hi && r >= B.offset[n + 1]) ++n;
+    d.n = n;
+    r -= B.offset[n];
+    for (int q = n - 1; q >= 0; --q) {
+      uint64_t qq = r / K;
+      digits[q] = (int)(r - qq * K);
+      r = qq;
+    }
+  }
+  finish_desc(B, digits, d);
+}
+
+// Path source for one per-order launch: exhaustive batches need no list; other
+// batches pass the list of global indices that have this order.
+__device__ __forceinline__ void fetch_path(const BatchDev& B, int n, const uint64_t* list, uint64_t j,
+                                           PathDesc& d) {
+  if (list == nullptr)
+    decode_exhaustive_order(B, n, j, d);
+  else
+    decode_global(B, list[j], d);
+}
+
+// Stage `count` elements of T from global to shared memory (whole CTA).
+template <typename T>
+__device__ __forceinline__ void stage(T* dst, const T* src, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+}
+
+__device__ __forceinline__ void raise_error(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+}  // namespace fpt

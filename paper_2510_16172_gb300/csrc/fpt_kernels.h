@@ -1,0 +1,61 @@
+// fpt_kernels.h -- launch wrappers of the CUDA kernels (host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fpt_device.cuh"
+
+namespace fpt {
+
+constexpr int kThreads = 128;  // threads per CTA for all path kernels
+
+struct SolveCfg {
+  int max_iters;    // BFGS step cap
+  int fp_iters;     // Eq. 6 rounds per step
+  int fixed_iters;  // 1: run every path for max_iters steps
+  float tol2;       // (world-space step tolerance)^2
+  float stop2;      // a segment shorter than sqrt(stop2) stops BFGS (the path runs into a kink)
+};
+
+enum PolishMode { POLISH_SOLVE = 0, POLISH_VALIDITY = 1 };
+
+struct PolishCfg {
+  int mode;          // PolishMode
+  int steps;         // Newton steps applied (solve mode)
+  float solved_tol;  // residual bound for ST_SOLVED
+  float deg_tol;     // shortest segment of a regular solution
+  float cond_fp64;   // pivot ratio that triggers the FP64 Hessian solve
+};
+
+struct BackwardCfg {
+  float cond_fp64;
+  float deg_tol;
+  int acc_in_smem;   // accumulate per CTA in shared memory before the FP64 global sum
+  int flush_tiles;   // flush the shared accumulators every this many CTA tiles
+  uint8_t dl_mask;   // with no dL array: dL = 1 where (status & dl_mask) == dl_mask (0 = no length term)
+};
+
+// Per-order launches (n = 1..kMaxOrder).  `list` = nullptr for exhaustive batches.
+cudaError_t launch_bfgs(int n, const SceneDev& S, const BatchDev& B, const SolveCfg& cfg, uint64_t n_local,
+                        const uint64_t* list, float* T, uint8_t* status, uint8_t* iters, cudaStream_t stream,
+                        int n_sm, int* err);
+cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
+                          const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
+                          uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, int* err);
+cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,
+                            const uint64_t* list, const float* T, const uint8_t* status, const float* dX,
+                            const float* dL, double* gacc, cudaStream_t stream, int n_sm, int* err);
+cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
+                                     float* g_rx, float* g_vertices, cudaStream_t stream);
+
+// Batch utilities.
+cudaError_t launch_enumerate(const BatchDev& B, int32_t* ids, uint8_t* order, int32_t* tx_idx, int32_t* rx_idx,
+                             cudaStream_t stream, int n_sm);
+cudaError_t launch_order_histogram(const BatchDev& B, unsigned long long* counts, cudaStream_t stream, int n_sm);
+cudaError_t launch_order_scatter(const BatchDev& B, unsigned long long* cursors, uint64_t* lists,
+                                 cudaStream_t stream, int n_sm);
+cudaError_t launch_count_status(const uint8_t* status, uint64_t n, uint8_t mask, unsigned long long* out,
+                                cudaStream_t stream, int n_sm);
+
+}  // namespace fpt

@@ -1,0 +1,364 @@
+// k_backward.cu -- implicit-differentiation backward and the theta-gradient sum.
+//
+// Sec. III-D: at a solution grad_T L = 0 (Eq. 8), so for a loss
+// l = sum_i dX_i . x_i + dL L the vector-Jacobian product through T*(theta)
+// is u^T d(grad_T L)/dtheta with H u = -v, v = dl/dT = A^T dX + dL grad_T L
+// (Eq. 11-13; H symmetric).  With w_i = A_i u_i, Dw_j = w_j - w_{j-1} (zero
+// beyond the ends) and q_j = M_j Dw_j (M_j = (I - u_j u_j^T)/|z_j|), the
+// per-path gradient, including the explicit dependence of l on theta, is
+//   e_i        = dX_i + dL (u_i - u_{i+1}) + (q_i - q_{i+1})
+//   dl/db_i    = e_i
+//   dl/da_ik   = e_i t_ik + (u_i - u_{i+1}) u_ik       (k = 1, 2)
+//   dl/dTX     = -dL u_0 - q_0,     dl/dRX = dL u_N + q_N
+// The per-path terms are summed over paths (per CTA in shared memory, then in
+// FP64 in global memory) and mapped to vertices by the chain rule of the
+// object records (plane: b = v0, a1 = v1 - v0, a2 = v3 - v0; edge: b = e0,
+// a1 = e1 - e0).
+#include "blocktri.cuh"
+#include "fpt_kernels.h"
+
+namespace fpt {
+
+// Warp-aggregated accumulate of `cnt` values into acc[base + k]: lanes that
+// share a base add their sums once; others add their own.
+template <int CNT>
+__device__ __forceinline__ void warp_accumulate(float* acc, int base, const float (&v)[CNT], bool shared_acc,
+                                                double* gacc, int gbase) {
+  const unsigned full = 0xffffffffu;
+  const int b0 = __shfl_sync(full, base, 0);
+  const bool uniform = __all_sync(full, base == b0);
+  if (uniform) {
+    if (b0 < 0) return;
+    float s[CNT];
+#pragma unroll
+    for (int k = 0; k < CNT; ++k) {
+      float x = v[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(full, x, o);
+      s[k] = x;
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int k = 0; k < CNT; ++k) {
+        if (shared_acc)
+          atomicAdd(acc + b0 + k, s[k]);
+        else
+          atomicAdd(gacc + gbase + k, (double)s[k]);
+      }
+    }
+  } else if (base >= 0) {
+#pragma unroll
+    for (int k = 0; k < CNT; ++k) {
+      if (shared_acc)
+        atomicAdd(acc + base + k, v[k]);
+      else
+        atomicAdd(gacc + gbase + k, (double)v[k]);
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev B, BackwardCfg cfg,
+                                                            uint64_t n_local, const uint64_t* __restrict__ list,
+                                                            const float* __restrict__ T,
+                                                            const uint8_t* __restrict__ status,
+                                                            const float* __restrict__ dX,
+                                                            const float* __restrict__ dLv, double* gacc) {
+  constexpr int M = 2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* s_rec = reinterpret_cast<float*>(smem_raw);
+  float* s_aux = s_rec + S.n_obj * kRec32;
+  float* s_acc = s_aux + S.n_obj * kAux;
+  const int n_acc = S.n_obj * 9 + 3 * (S.n_tx + S.n_rx);
+  const int acc_tx = S.n_obj * 9, acc_rx = acc_tx + 3 * S.n_tx;
+  stage(s_rec, S.rec32, S.n_obj * kRec32);
+  stage(s_aux, S.aux, S.n_obj * kAux);
+  if (cfg.acc_in_smem)
+    for (int k = threadIdx.x; k < n_acc; k += blockDim.x) s_acc[k] = 0.f;
+  __syncthreads();
+  const int n_max = B.n_max;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  int tiles = 0;
+  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
+    const uint64_t j = j0 + threadIdx.x;
+    const bool have = j < n_local;
+    PathDesc d;
+    float gb[N][9];  // per slot: d/db (3), d/da1 (3), d/da2 (3)
+    float gtx[3] = {0.f, 0.f, 0.f}, grx[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) gb[i][k] = 0.f;
+    bool use = false;
+    uint8_t st = 0;
+    if (have) {
+      fetch_path(B, N, list, j, d);
+      st = d.flags;
+      if (status) st |= status[d.g];
+      use = !(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE));
+    } else {
+      d.tx = d.rx = 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) d.ids[i] = -1;
+    }
+    if (use) {
+      const uint64_t g = d.g;
+      // geometry (FP32, hi/lo differences of b) and parameters
+      float bh[N + 2][3], bl[N + 2][3], a[N][2][3];
+      bool edge[N];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        bh[0][c] = __ldg(S.tx32 + kEnd32 * d.tx + c);
+        bl[0][c] = __ldg(S.tx32 + kEnd32 * d.tx + 3 + c);
+        bh[N + 1][c] = __ldg(S.rx32 + kEnd32 * d.rx + c);
+        bl[N + 1][c] = __ldg(S.rx32 + kEnd32 * d.rx + 3 + c);
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float* r = s_rec + kRec32 * d.ids[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          bh[i + 1][c] = r[c];
+          bl[i + 1][c] = r[3 + c];
+          a[i][0][c] = r[6 + c];
+          a[i][1][c] = r[9 + c];
+        }
+        edge[i] = s_aux[kAux * d.ids[i] + 2] != 0.f;
+      }
+      const float2* Ti = reinterpret_cast<const float2*>(T) + g * (uint64_t)n_max;
+      float t[N][2];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float2 v = Ti[i];
+        t[i][0] = v.x;
+        t[i][1] = v.y;
+      }
+      float w[N][3];
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[i][c] = fmaf(a[i][1][c], t[i][1], a[i][0][c] * t[i][0]);
+      float u[N + 1][3], il[N + 1];
+#pragma unroll
+      for (int jj = 0; jj <= N; ++jj) {
+        float z[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float x = (bh[jj + 1][c] - bh[jj][c]) + (bl[jj + 1][c] - bl[jj][c]);
+          if (jj < N) x += w[jj][c];
+          if (jj > 0) x -= w[jj - 1][c];
+          z[c] = x;
+        }
+        float r = rsqrtf(fmaxf(fmaf(z[2], z[2], fmaf(z[1], z[1], z[0] * z[0])), 1e-30f));
+        il[jj] = r;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[jj][c] = z[c] * r;
+      }
+      const float dl = dLv ? dLv[g] : ((cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask) ? 1.f : 0.f);
+      float dx[N][3], dd[N][3], v[M];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          dx[i][c] = dX ? dX[(g * (uint64_t)n_max + i) * 3 + c] : 0.f;
+          dd[i][c] = u[i][c] - u[i + 1][c];
+        }
+        // v = A^T dX + dL grad_T L
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          float gk = a[i][k][0] * dd[i][0] + a[i][k][1] * dd[i][1] + a[i][k][2] * dd[i][2];
+          float ak = a[i][k][0] * dx[i][0] + a[i][k][1] * dx[i][1] + a[i][k][2] * dx[i][2];
+          v[2 * i + k] = fmaf(dl, gk, ak);
+        }
+      }
+      // u_adj = -H^{-1} v  (FP32; FP64 when ill-conditioned)
+      float lam[M];
+      BlockTri<float, N> F32;
+      bool ok = factor_hessian<float, N>(u, il, a, edge, cfg.cond_fp64, F32);
+      if (ok) {
+        float r[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) r[k] = -v[k];
+        solve_hessian<float, N>(F32, r, lam);
+      } else {
+        double ud[N + 1][3], ild[N + 1], ad[N][2][3];
+#pragma unroll
+        for (int jj = 0; jj <= N; ++jj) {
+          double z[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double* rb1 = jj < N ? S.rec64 + kRec64 * d.ids[jj] : S.rx64 + 3 * d.rx;
+            const double* rb0 = jj > 0 ? S.rec64 + kRec64 * d.ids[jj - 1] : S.tx64 + 3 * d.tx;
+            double x = rb1[c] - rb0[c];
+            if (jj < N) x += S.rec64[kRec64 * d.ids[jj] + 3 + c] * (double)t[jj][0] +
+                             S.rec64[kRec64 * d.ids[jj] + 6 + c] * (double)t[jj][1];
+            if (jj > 0) x -= S.rec64[kRec64 * d.ids[jj - 1] + 3 + c] * (double)t[jj - 1][0] +
+                             S.rec64[kRec64 * d.ids[jj - 1] + 6 + c] * (double)t[jj - 1][1];
+            z[c] = x;
+          }
+          double e = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
+          double r = e > 0.0 ? rsqrt(e) : 0.0;
+          ild[jj] = r;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ud[jj][c] = z[c] * r;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ad[i][k][c] = S.rec64[kRec64 * d.ids[i] + 3 + 3 * k + c];
+        BlockTri<double, N> F64;
+        ok = factor_hessian<double, N>(ud, ild, ad, edge, (double)cfg.cond_fp64 * 1e-6, F64);
+        double r[M], x[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) r[k] = -(double)v[k];
+        solve_hessian<double, N>(F64, r, x);
+#pragma unroll
+        for (int k = 0; k < M; ++k) lam[k] = ok ? (float)x[k] : 0.f;
+      }
+      if (ok) {
+        // q_j = M_j Dw_j
+        float q[N + 1][3];
+#pragma unroll
+        for (int jj = 0; jj <= N; ++jj) {
+          float dw[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float x = 0.f;
+            if (jj < N) x += fmaf(a[jj][1][c], lam[2 * jj + 1], a[jj][0][c] * lam[2 * jj]);
+            if (jj > 0) x -= fmaf(a[jj - 1][1][c], lam[2 * jj - 1], a[jj - 1][0][c] * lam[2 * jj - 2]);
+            dw[c] = x;
+          }
+          float ud = u[jj][0] * dw[0] + u[jj][1] * dw[1] + u[jj][2] * dw[2];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) q[jj][c] = (dw[c] - u[jj][c] * ud) * il[jj];
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float e = dx[i][c] + dl * dd[i][c] + (q[i][c] - q[i + 1][c]);
+            gb[i][c] = e;
+            gb[i][3 + c] = fmaf(e, t[i][0], dd[i][c] * lam[2 * i]);
+            gb[i][6 + c] = fmaf(e, t[i][1], dd[i][c] * lam[2 * i + 1]);
+          }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          gtx[c] = -dl * u[0][c] - q[0][c];
+          grx[c] = dl * u[N][c] + q[N][c];
+        }
+      }
+    }
+    // sums over paths
+    const bool sm = cfg.acc_in_smem != 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int id = d.ids[i];
+      warp_accumulate<9>(s_acc, id >= 0 ? 9 * id : -1, gb[i], sm, gacc, 9 * id);
+    }
+    warp_accumulate<3>(s_acc, have ? acc_tx + 3 * d.tx : -1, gtx, sm, gacc, acc_tx + 3 * d.tx);
+    warp_accumulate<3>(s_acc, have ? acc_rx + 3 * d.rx : -1, grx, sm, gacc, acc_rx + 3 * d.rx);
+    if (sm && ++tiles >= cfg.flush_tiles) {
+      tiles = 0;
+      __syncthreads();
+      for (int k = threadIdx.x; k < n_acc; k += blockDim.x) {
+        float x = s_acc[k];
+        if (x != 0.f) {
+          atomicAdd(gacc + k, (double)x);
+          s_acc[k] = 0.f;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (cfg.acc_in_smem) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_acc; k += blockDim.x) {
+      float x = s_acc[k];
+      if (x != 0.f) atomicAdd(gacc + k, (double)x);
+    }
+  }
+}
+
+// Vertex chain rule and FP64 -> FP32.
+__global__ void backward_finalize_kernel(int n_obj, int n_tx, int n_rx, const float* __restrict__ aux,
+                                         const double* __restrict__ gacc, float* g_tx, float* g_rx, float* g_vert) {
+  const int total = n_obj + n_tx + n_rx;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    if (k < n_obj) {
+      if (!g_vert) continue;
+      const double* s = gacc + 9 * k;
+      const bool edge = aux[kAux * k + 2] != 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double gbv = s[c], ga1 = s[3 + c], ga2 = edge ? 0.0 : s[6 + c];
+        g_vert[9 * k + c] = (float)(gbv - ga1 - ga2);
+        g_vert[9 * k + 3 + c] = (float)ga1;
+        g_vert[9 * k + 6 + c] = (float)ga2;
+      }
+    } else if (k < n_obj + n_tx) {
+      const int i = k - n_obj;
+      if (g_tx)
+        for (int c = 0; c < 3; ++c) g_tx[3 * i + c] = (float)gacc[9 * n_obj + 3 * i + c];
+    } else {
+      const int i = k - n_obj - n_tx;
+      if (g_rx)
+        for (int c = 0; c < 3; ++c) g_rx[3 * i + c] = (float)gacc[9 * n_obj + 3 * n_tx + 3 * i + c];
+    }
+  }
+}
+
+template <int N>
+static cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg_in,
+                                     uint64_t n_local, const uint64_t* list, const float* T, const uint8_t* status,
+                                     const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm) {
+  BackwardCfg cfg = cfg_in;
+  const size_t base = (size_t)S.n_obj * (kRec32 + kAux) * sizeof(float);
+  const size_t accb = (size_t)(S.n_obj * 9 + 3 * (S.n_tx + S.n_rx)) * sizeof(float);
+  size_t smem = base + accb;
+  if (smem > 160 * 1024) {
+    cfg.acc_in_smem = 0;
+    smem = base;
+  }
+  if (smem > 160 * 1024) return cudaErrorInvalidValue;  // scene too large for this kernel
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(backward_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<N>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t want = (n_local + kThreads - 1) / kThreads;
+  uint64_t cap = (uint64_t)n_sm * (uint64_t)per_sm;
+  unsigned grid = (unsigned)(want < cap ? want : cap);
+  if (grid == 0) return cudaSuccess;
+  backward_kernel<N><<<grid, kThreads, smem, stream>>>(S, B, cfg, n_local, list, T, status, dX, dL, gacc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,
+                            const uint64_t* list, const float* T, const uint8_t* status, const float* dX,
+                            const float* dL, double* gacc, cudaStream_t stream, int n_sm, int* err) {
+  (void)err;
+  switch (n) {
+    case 1: return launch_backward_n<1>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
+    case 2: return launch_backward_n<2>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
+    case 3: return launch_backward_n<3>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
+    case 4: return launch_backward_n<4>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
+    case 5: return launch_backward_n<5>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
+                                     float* g_rx, float* g_vertices, cudaStream_t stream) {
+  (void)types;
+  const int total = S.n_obj + S.n_tx + S.n_rx;
+  const int grid = (total + 255) / 256;
+  backward_finalize_kernel<<<grid, 256, 0, stream>>>(S.n_obj, S.n_tx, S.n_rx, S.aux, gacc, g_tx, g_rx, g_vertices);
+  return cudaGetLastError();
+}
+
+}  // namespace fpt

@@ -1,0 +1,103 @@
+// k_misc.cu -- sequence enumeration (Sec. III), order bucketing and status counts.
+#include "fpt_kernels.h"
+
+namespace fpt {
+
+static unsigned grid_for(uint64_t n, int threads, int n_sm, int per_sm) {
+  uint64_t want = (n + threads - 1) / threads;
+  uint64_t cap = (uint64_t)n_sm * per_sm;
+  return (unsigned)(want < cap ? want : cap);
+}
+
+// Write the decoded sequence of every path (bit-exact integer indexing).
+__global__ void enumerate_kernel(BatchDev B, int32_t* ids, uint8_t* order, int32_t* tx_idx, int32_t* rx_idx) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < B.n_paths; g += stride) {
+    PathDesc d;
+    decode_global(B, g, d);
+    if (ids)
+      for (int j = 0; j < B.n_max; ++j) ids[g * (uint64_t)B.n_max + j] = j < d.n ? d.ids[j] : -1;
+    if (order) order[g] = (uint8_t)d.n;
+    if (tx_idx) tx_idx[g] = d.tx;
+    if (rx_idx) rx_idx[g] = d.rx;
+  }
+}
+
+// Histogram of path orders (seeded and explicit batches solve per order).
+__global__ void order_hist_kernel(BatchDev B, unsigned long long* counts) {
+  __shared__ unsigned long long s[kMaxOrder + 1];
+  if (threadIdx.x <= kMaxOrder) s[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < B.n_paths; g += stride) {
+    PathDesc d;
+    decode_global(B, g, d);
+    atomicAdd(&s[d.n], 1ULL);
+  }
+  __syncthreads();
+  if (threadIdx.x <= kMaxOrder && s[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s[threadIdx.x]);
+}
+
+// cursors[n] starts at the first slot of order n in `lists`.
+__global__ void order_scatter_kernel(BatchDev B, unsigned long long* cursors, uint64_t* lists) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < B.n_paths; g += stride) {
+    PathDesc d;
+    decode_global(B, g, d);
+    unsigned long long slot = atomicAdd(&cursors[d.n], 1ULL);
+    lists[slot] = g;
+  }
+}
+
+__global__ void count_status_kernel(const uint8_t* __restrict__ st, uint64_t n, uint8_t mask,
+                                    unsigned long long* out) {
+  unsigned long long c = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 16;
+  for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16; base < n; base += stride) {
+    if (base + 16 <= n && ((reinterpret_cast<uintptr_t>(st + base) & 15) == 0)) {
+      uint4 v = *reinterpret_cast<const uint4*>(st + base);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) c += (((w[k] >> (8 * b)) & mask) == mask);
+    } else {
+      for (uint64_t i = base; i < n && i < base + 16; ++i) c += ((st[i] & mask) == mask);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+cudaError_t launch_enumerate(const BatchDev& B, int32_t* ids, uint8_t* order, int32_t* tx_idx, int32_t* rx_idx,
+                             cudaStream_t stream, int n_sm) {
+  unsigned grid = grid_for(B.n_paths, 256, n_sm, 8);
+  if (grid == 0) return cudaSuccess;
+  enumerate_kernel<<<grid, 256, 0, stream>>>(B, ids, order, tx_idx, rx_idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order_histogram(const BatchDev& B, unsigned long long* counts, cudaStream_t stream, int n_sm) {
+  unsigned grid = grid_for(B.n_paths, 256, n_sm, 8);
+  if (grid == 0) return cudaSuccess;
+  order_hist_kernel<<<grid, 256, 0, stream>>>(B, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order_scatter(const BatchDev& B, unsigned long long* cursors, uint64_t* lists,
+                                 cudaStream_t stream, int n_sm) {
+  unsigned grid = grid_for(B.n_paths, 256, n_sm, 8);
+  if (grid == 0) return cudaSuccess;
+  order_scatter_kernel<<<grid, 256, 0, stream>>>(B, cursors, lists);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_status(const uint8_t* status, uint64_t n, uint8_t mask, unsigned long long* out,
+                                cudaStream_t stream, int n_sm) {
+  unsigned grid = grid_for((n + 15) / 16, 256, n_sm, 8);
+  if (grid == 0) return cudaSuccess;
+  count_status_kernel<<<grid, 256, 0, stream>>>(status, n, mask, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fpt
