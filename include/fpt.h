@@ -84,7 +84,10 @@ typedef struct {
   float deg_tol;       /* a solution segment shorter than this (metres) is DEGENERATE (1e-3) */
   float cond_fp64;     /* Hessian pivot ratio below which the solve is redone in FP64 (1e-4) */
   int32_t init_mode;   /* 0: plain init, t = 1/2 (object centroid).  1: learned init (unsupported here) */
-  int32_t reserved[7]; /* must be zero */
+  int32_t polish_fp64; /* 0: polish gradient in double-float FP32 arithmetic (~2^-46, default); 1: in FP64 */
+  int32_t refill;      /* lanes of a warp that must be free before it takes new paths (8); 0: one path per
+                          lane until the whole warp is done */
+  int32_t reserved[5]; /* must be zero */
 } fpt_solve_params;
 
 typedef struct fpt_ctx fpt_ctx;
@@ -191,6 +194,14 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* b
 /* Number of paths whose status has all bits of `mask` set (device status
  * [n]; result written to *count on the host after a stream sync). */
 fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uint8_t mask, uint64_t* count);
+
+/* Tensor-core GEMM used by the warm-start network's layers (tcgen05, BF16 in,
+ * FP32 accumulation in tensor memory): C[M][N] = A[M][K] W[N][K]^T (+ bias[N]).
+ * A, W: device bf16, row-major; bias: device float [N] or NULL; C: device
+ * float [M][N].  1 <= N <= 256, M, K >= 1.  FPT_EDEVICE (via fpt_sync) if the
+ * tensor core does not complete within its bounded wait. */
+fpt_status fpt_tc_gemm_bf16(fpt_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A, const void* W,
+                            const float* bias, float* C);
 
 /* Kernel timing.  While enabled, every kernel the context launches is
  * bracketed by CUDA events on the context's stream, and fpt_profile_read()

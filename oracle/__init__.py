@@ -50,7 +50,8 @@ def build(force: bool = False) -> str:
 
 class _BfgsParams(C.Structure):
     _fields_ = [("max_iters", C.c_int), ("fp_iters", C.c_int), ("scale_h0", C.c_int), ("safeguard", C.c_int),
-                ("alpha0_first", C.c_double), ("alpha0", C.c_double), ("tol_step", C.c_double)]
+                ("alpha0_first", C.c_double), ("alpha0", C.c_double), ("tol_step", C.c_double),
+                ("stop_len", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -241,8 +242,8 @@ def seeded_paths(scene, seed: int, per_pair: int, lo: int, hi: int, g=None):
 # batch solve / backward
 # --------------------------------------------------------------------------
 def solve(scene, ids, order, tx_idx, rx_idx, solver=NEWTON, max_iters=200, fp_iters=1, alpha0_first=1.0,
-          alpha0=1.0, scale_h0=0, safeguard=1, tol_step=0.0, solved_tol=1e-5, deg_tol=DEG_TOL, n_threads=None,
-          dX=None, dL=None):
+          alpha0=1.0, scale_h0=0, safeguard=1, tol_step=0.0, stop_len=0.0, solved_tol=1e-5, deg_tol=DEG_TOL,
+          n_threads=None, dX=None, dL=None):
     """Solve every listed path; returns a dict of numpy arrays (and 'dtheta' if cotangents are given)."""
     ids = np.ascontiguousarray(ids, dtype=np.int32)
     M, n_max = ids.shape
@@ -260,7 +261,7 @@ def solve(scene, ids, order, tx_idx, rx_idx, solver=NEWTON, max_iters=200, fp_it
     B.M, B.n_max = M, n_max
     B.ids, B.order, B.tx_idx, B.rx_idx = (_p(a, C.c_int32) for a in (ids, order, tx_idx, rx_idx))
     B.solver, B.max_iters = solver, max_iters
-    B.bfgs = _BfgsParams(max_iters, fp_iters, scale_h0, safeguard, alpha0_first, alpha0, tol_step)
+    B.bfgs = _BfgsParams(max_iters, fp_iters, scale_h0, safeguard, alpha0_first, alpha0, tol_step, stop_len)
     B.solved_tol = solved_tol
     B.deg_tol = deg_tol
     B.T, B.X, B.L, B.rho, B.bdist = (_p(out[k]) for k in ("T", "X", "L", "rho", "bdist"))

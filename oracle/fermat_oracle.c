@@ -409,6 +409,7 @@ int orc_newton_solve(const orc_path* P, int max_iters, double deg_tol, double (*
 typedef struct {
   int max_iters, fp_iters, scale_h0, safeguard;
   double alpha0_first, alpha0, tol_step;
+  double stop_len; /* stop when a segment gets shorter than this (heading into a kink); 0 = never */
 } orc_bfgs_params;
 
 static void grad_flat(const orc_path* P, const orc_segments* S, double* g) {
@@ -517,6 +518,10 @@ int orc_bfgs_solve(const orc_path* P, const orc_bfgs_params* prm, double (*t)[2]
     }
     if (ws <= prm->tol_step) {
       status |= ORC_CONVERGED;
+      ++it;
+      break;
+    }
+    if (min_len(P, &S) < prm->stop_len) {
       ++it;
       break;
     }
@@ -885,7 +890,7 @@ int orc_path_solve(int n, const int32_t* types, const double* b, const double* c
   if (solver == 0) {
     st = orc_newton_solve(&P, max_iters, deg_tol, (double (*)[2])t, iters);
   } else {
-    orc_bfgs_params prm = {max_iters, fp_iters, scale_h0, safeguard, alpha0_first, alpha0, tol_step};
+    orc_bfgs_params prm = {max_iters, fp_iters, scale_h0, safeguard, alpha0_first, alpha0, tol_step, 0.0};
     st = orc_bfgs_solve(&P, &prm, (double (*)[2])t, iters);
   }
   if (rho) *rho = orc_residual(&P, (const double (*)[2])t);

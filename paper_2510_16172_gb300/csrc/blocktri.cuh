@@ -14,7 +14,10 @@
 // The solve is block LDL^T (block Thomas): D_0 = H_00,
 // C_i = H_{i-1,i}^T D_{i-1}^{-1}, D_i = H_ii - C_i H_{i-1,i}; a pivot block
 // that is not positive definite, or whose smallest eigenvalue is below
-// cond * (largest diagonal entry of H), marks the factorisation as failed.
+// cond * (largest diagonal entry of its own H_ii), marks the factorisation as
+// failed: the elimination cancelled that block down to noise.  The test is
+// per block, so objects of very different sizes or distances (a scaling, not
+// an ill-conditioning) do not trigger it.
 #pragma once
 
 namespace fpt {
@@ -93,7 +96,6 @@ __device__ __forceinline__ bool factor_hessian(const R (&u)[N + 1][3], const R (
       if (edge[i + 1]) F.Up[i][0][1] = F.Up[i][1][1] = R(0);
     }
   }
-  const R floor_ev = cond * maxdiag;
   bool ok = maxdiag > R(0);
   R D[3] = {Hd[0][0], Hd[0][1], Hd[0][2]};
 #pragma unroll
@@ -118,7 +120,8 @@ __device__ __forceinline__ bool factor_hessian(const R (&u)[N + 1][3], const R (
     R half_tr = R(0.5) * (D[0] + D[2]);
     R half_df = R(0.5) * (D[0] - D[2]);
     R lam_min = half_tr - sqrt_r<R>(half_df * half_df + D[1] * D[1]);
-    ok = ok && D[0] > R(0) && det > R(0) && lam_min > floor_ev;
+    const R own = Hd[i][0] > Hd[i][2] ? Hd[i][0] : Hd[i][2];
+    ok = ok && D[0] > R(0) && det > R(0) && lam_min > cond * own;
     R idet = R(1) / det;
     F.Dinv[i][0] = D[2] * idet;
     F.Dinv[i][1] = -D[1] * idet;

@@ -14,6 +14,7 @@
 
 #include "fpt.h"
 #include "fpt_kernels.h"
+#include "mlp.h"
 
 using namespace fpt;
 
@@ -25,6 +26,10 @@ struct fpt_ctx {
   double* d_gacc = nullptr;                // backward accumulators (FP64)
   size_t gacc_cap = 0;
   unsigned long long* d_count = nullptr;   // counters for reductions
+  unsigned long long* d_work = nullptr;    // work counter of the lane-refill solver
+  uint32_t* d_rescue = nullptr;            // paths whose FP32 Hessian pivots failed (polish scratch)
+  size_t rescue_cap = 0;
+  unsigned* d_rescue_n = nullptr;
   char msg[512] = "ok";
   // kernel timing
   bool prof = false;
@@ -70,6 +75,7 @@ struct fpt_scene {
   float* d_rec32 = nullptr;
   double* d_rec64 = nullptr;
   float* d_aux = nullptr;
+  float* d_reclo = nullptr;
   int n_tx = 0, n_rx = 0;
   float* d_tx32 = nullptr;
   float* d_rx32 = nullptr;
@@ -117,7 +123,12 @@ static SceneDev scene_dev(const fpt_scene* s) {
   d.rx32 = s->d_rx32;
   d.tx64 = s->d_tx64;
   d.rx64 = s->d_rx64;
-  for (int c = 0; c < 3; ++c) d.centre[c] = s->centre[c];
+  d.reclo = s->d_reclo;
+  for (int c = 0; c < 3; ++c) {
+    d.centre[c] = s->centre[c];
+    d.centre_hi[c] = (float)s->centre[c];
+    d.centre_lo[c] = (float)(s->centre[c] - (double)d.centre_hi[c]);
+  }
   return d;
 }
 
@@ -135,6 +146,8 @@ void fpt_default_params(fpt_solve_params* p) {
   p->deg_tol = 1e-3f;
   p->cond_fp64 = 1e-4f;
   p->init_mode = 0;
+  p->polish_fp64 = 0;
+  p->refill = 8;
 }
 
 fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
@@ -149,6 +162,8 @@ fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_work, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_rescue_n, sizeof(unsigned));
   if (e != cudaSuccess) {
     fpt_destroy(ctx);
     return FPT_ECUDA;
@@ -168,6 +183,9 @@ void fpt_destroy(fpt_ctx* ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_gacc);
   cudaFree(ctx->d_count);
+  cudaFree(ctx->d_work);
+  cudaFree(ctx->d_rescue);
+  cudaFree(ctx->d_rescue_n);
   delete ctx;
 }
 
@@ -223,7 +241,7 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
   s->n_obj = n_obj;
   s->types.assign(types, types + n_obj);
   for (int c = 0; c < 3; ++c) s->centre[c] = 0.5 * (lo[c] + hi[c]);
-  std::vector<float> rec32((size_t)n_obj * kRec32), aux((size_t)n_obj * kAux);
+  std::vector<float> rec32((size_t)n_obj * kRec32), aux((size_t)n_obj * kAux), reclo((size_t)n_obj * kRecLo);
   std::vector<double> rec64((size_t)n_obj * kRec64);
   for (int k = 0; k < n_obj; ++k) {
     const double* v = verts + 9 * k;
@@ -250,8 +268,8 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
       rec64[kRec64 * k + 3 + c] = a1[c];
       rec64[kRec64 * k + 6 + c] = a2[c];
       split(b[c], rec32[kRec32 * k + c], rec32[kRec32 * k + 3 + c]);
-      rec32[kRec32 * k + 6 + c] = (float)a1[c];
-      rec32[kRec32 * k + 9 + c] = (float)a2[c];
+      split(a1[c], rec32[kRec32 * k + 6 + c], reclo[kRecLo * k + c]);
+      split(a2[c], rec32[kRec32 * k + 9 + c], reclo[kRecLo * k + 3 + c]);
     }
     // side heights for the boundary distance: distance between the sides t1 = 0, 1 is area/|a2|
     aux[kAux * k + 0] = types[k] == FPT_QUAD ? (float)(area / n2) : (float)n1;
@@ -263,6 +281,8 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rec32, rec32.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rec64, rec64.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_aux, aux.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_reclo, reclo.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_reclo, reclo.data(), reclo.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_rec32, rec32.data(), rec32.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_rec64, rec64.data(), rec64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_aux, aux.data(), aux.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -279,6 +299,7 @@ void fpt_scene_free(fpt_scene* s) {
   cudaFree(s->d_rec32);
   cudaFree(s->d_rec64);
   cudaFree(s->d_aux);
+  cudaFree(s->d_reclo);
   cudaFree(s->d_tx32);
   cudaFree(s->d_rx32);
   cudaFree(s->d_tx64);
@@ -500,6 +521,17 @@ static fpt_status ensure_buckets(fpt_ctx* ctx, fpt_batch* b) {
   return FPT_OK;
 }
 
+// Polish scratch: one uint32 per path of the largest order slice.
+static fpt_status ensure_rescue(fpt_ctx* ctx, uint64_t n) {
+  if (n <= ctx->rescue_cap) return FPT_OK;
+  cudaFree(ctx->d_rescue);
+  ctx->d_rescue = nullptr;
+  ctx->rescue_cap = 0;
+  CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_rescue, n * sizeof(uint32_t)));
+  ctx->rescue_cap = n;
+  return FPT_OK;
+}
+
 // Paths of order n in a batch: count and list (nullptr for exhaustive batches).
 static uint64_t order_slice(const fpt_batch* b, int n, const uint64_t** list) {
   if (b->dev.mode == BATCH_EXHAUSTIVE) {
@@ -535,20 +567,24 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
   st = ensure_buckets(ctx, b);
   if (st != FPT_OK) return st;
   const SceneDev S = scene_dev(s);
-  SolveCfg sc{p.max_iters, p.fp_iters, p.fixed_iters, p.tol_step * p.tol_step, 0.01f * p.deg_tol * p.deg_tol};
-  PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, p.cond_fp64};
+  SolveCfg sc{p.max_iters, p.fp_iters, p.fixed_iters, p.tol_step * p.tol_step, 0.01f * p.deg_tol * p.deg_tol,
+              p.refill > 32 ? 32 : p.refill};
+  PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, p.cond_fp64, p.polish_fp64};
   for (int n = 1; n <= kMaxOrder; ++n) {
     const uint64_t* list;
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
     {
       ProfScope ps(ctx, FPT_K_BFGS);
-      CUDA_OR_FAIL(ctx, launch_bfgs(n, S, b->dev, sc, cnt, list, T, status, iters, ctx->stream, ctx->n_sm, ctx->d_err));
+      CUDA_OR_FAIL(ctx, launch_bfgs(n, S, b->dev, sc, cnt, list, T, status, iters, ctx->stream, ctx->n_sm, ctx->d_work));
     }
+    if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
+    st = ensure_rescue(ctx, cnt);
+    if (st != FPT_OK) return st;
     {
       ProfScope ps(ctx, FPT_K_POLISH);
       CUDA_OR_FAIL(ctx, launch_polish(n, S, b->dev, pc, cnt, list, T, X, L, status, rho, nullptr, nullptr, ctx->stream,
-                                      ctx->n_sm, ctx->d_err));
+                                      ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n));
     }
   }
   return FPT_OK;
@@ -566,14 +602,17 @@ fpt_status fpt_validity(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   fpt_solve_params p;
   fpt_default_params(&p);
   const SceneDev S = scene_dev(s);
-  PolishCfg pc{POLISH_VALIDITY, 0, p.solved_tol, p.deg_tol, p.cond_fp64};
+  PolishCfg pc{POLISH_VALIDITY, 0, p.solved_tol, p.deg_tol, p.cond_fp64, 0};
   for (int n = 1; n <= kMaxOrder; ++n) {
     const uint64_t* list;
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
+    if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
+    st = ensure_rescue(ctx, cnt);
+    if (st != FPT_OK) return st;
     ProfScope ps(ctx, FPT_K_POLISH);
     CUDA_OR_FAIL(ctx, launch_polish(n, S, b->dev, pc, cnt, list, const_cast<float*>(T), nullptr, nullptr, nullptr, rho,
-                                    mask, bdist, ctx->stream, ctx->n_sm, ctx->d_err));
+                                    mask, bdist, ctx->stream, ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n));
   }
   return FPT_OK;
 }
@@ -606,9 +645,12 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
     const uint64_t* list;
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
+    if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
+    st = ensure_rescue(ctx, cnt);
+    if (st != FPT_OK) return st;
     ProfScope ps(ctx, FPT_K_BACKWARD);
     CUDA_OR_FAIL(ctx, launch_backward(n, S, b->dev, bc_cfg, cnt, list, T, status, dX, dL, ctx->d_gacc, ctx->stream,
-                                      ctx->n_sm, ctx->d_err));
+                                      ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n));
   }
   {
     ProfScope ps(ctx, FPT_K_OTHER);
@@ -626,6 +668,32 @@ fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uin
   CUDA_OR_FAIL(ctx, cudaMemcpyAsync(&h, ctx->d_count, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
   *count = h;
+  return FPT_OK;
+}
+
+fpt_status fpt_tc_gemm_bf16(fpt_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A, const void* W,
+                            const float* bias, float* C) {
+  if (!ctx || !A || !W || !C) return fail(ctx, FPT_EINVAL, "null argument");
+  if (M < 1 || K < 1 || N < 1 || N > 256) return fail(ctx, FPT_EINVAL, "bad GEMM shape %d x %d x %d", M, N, K);
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.A = static_cast<const __nv_bfloat16*>(A);
+  g.sam = K;
+  g.sak = 1;
+  g.B = static_cast<const __nv_bfloat16*>(W);
+  g.sbn = K;
+  g.sbk = 1;
+  g.op = EPI_STORE;
+  g.bias = bias;
+  g.C = C;
+  g.scm = N;
+  g.scn = 1;
+  g.err = ctx->d_err;
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  ProfScope ps(ctx, FPT_K_OTHER);
+  CUDA_OR_FAIL(ctx, launch_gemm(g, 1, ctx->stream));
   return FPT_OK;
 }
 

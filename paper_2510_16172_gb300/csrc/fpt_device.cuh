@@ -14,6 +14,7 @@ constexpr int kMaxOrder = 5;        // longest sequence solved on the GPU
 constexpr int kRec32 = 12;          // floats per FP32 object record: b_hi[3], b_lo[3], a1[3], a2[3]
 constexpr int kRec64 = 9;           // doubles per FP64 object record: b[3], a1[3], a2[3]
 constexpr int kAux = 4;             // floats per object: side heights h1, h2 (metres), type, pad
+constexpr int kRecLo = 6;           // floats per object: low parts of a1[3], a2[3] (double-float polish)
 constexpr int kEnd32 = 6;           // floats per endpoint: hi[3], lo[3]
 
 // status bits (same values as the public header)
@@ -34,7 +35,9 @@ struct SceneDev {
   const float* rx32;     // [n_rx][6]
   const double* tx64;    // [n_tx][3]
   const double* rx64;    // [n_rx][3]
+  const float* reclo;    // [n_obj][6]
   double centre[3];
+  float centre_hi[3], centre_lo[3];
 };
 
 enum BatchMode { BATCH_EXHAUSTIVE = 0, BATCH_SEEDED = 1, BATCH_EXPLICIT = 2 };

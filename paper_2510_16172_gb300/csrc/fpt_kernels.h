@@ -16,6 +16,7 @@ struct SolveCfg {
   int fixed_iters;  // 1: run every path for max_iters steps
   float tol2;       // (world-space step tolerance)^2
   float stop2;      // a segment shorter than sqrt(stop2) stops BFGS (the path runs into a kink)
+  int refill;       // lane refill threshold (free lanes before a warp takes new paths); 0 = one path per lane per tile
 };
 
 enum PolishMode { POLISH_SOLVE = 0, POLISH_VALIDITY = 1 };
@@ -26,6 +27,7 @@ struct PolishCfg {
   float solved_tol;  // residual bound for ST_SOLVED
   float deg_tol;     // shortest segment of a regular solution
   float cond_fp64;   // pivot ratio that triggers the FP64 Hessian solve
+  int fp64;          // 1: FP64 gradients in the polish (validation); 0: double-float
 };
 
 struct BackwardCfg {
@@ -39,13 +41,18 @@ struct BackwardCfg {
 // Per-order launches (n = 1..kMaxOrder).  `list` = nullptr for exhaustive batches.
 cudaError_t launch_bfgs(int n, const SceneDev& S, const BatchDev& B, const SolveCfg& cfg, uint64_t n_local,
                         const uint64_t* list, float* T, uint8_t* status, uint8_t* iters, cudaStream_t stream,
-                        int n_sm, int* err);
+                        int n_sm, unsigned long long* work);
+// Double-float polish, then an FP64 pass over the paths whose FP32 pivots failed
+// (rescue_list: scratch of n_local entries; rescue_count: one device counter).
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                           const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
-                          uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, int* err);
+                          uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
+                          unsigned* rescue_count);
+// Adjoint + sums, then an FP64 pass over the paths whose FP32 pivots failed.
 cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,
                             const uint64_t* list, const float* T, const uint8_t* status, const float* dX,
-                            const float* dL, double* gacc, cudaStream_t stream, int n_sm, int* err);
+                            const float* dL, double* gacc, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
+                            unsigned* rescue_count);
 cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
                                      float* g_rx, float* g_vertices, cudaStream_t stream);
 

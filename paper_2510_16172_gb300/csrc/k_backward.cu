@@ -57,14 +57,85 @@ __device__ __forceinline__ void warp_accumulate(float* acc, int base, const floa
   }
 }
 
+// Per-path VJP (Sec. III-D) in precision R from the segment vectors z_j, the
+// basis vectors a and the parameters t: solve H u = -v (block LDL^T) and form
+// the per-slot gradients (d/db, d/da1, d/da2) and the TX / RX gradients.
+// Returns false (and no gradient) if the pivot test fails.
+template <typename R, int N>
+__device__ __forceinline__ bool path_vjp(const R (&z)[N + 1][3], const R (&a)[N][2][3], const R (&t)[N][2],
+                                         const bool (&edge)[N], const R (&dx)[N][3], R dl, R cond,
+                                         R (&gb)[N][9], R (&gtx)[3], R (&grx)[3]) {
+  constexpr int M = 2 * N;
+  R u[N + 1][3], il[N + 1];
+#pragma unroll
+  for (int jj = 0; jj <= N; ++jj) {
+    const R e = z[jj][0] * z[jj][0] + z[jj][1] * z[jj][1] + z[jj][2] * z[jj][2];
+    const R r = e > R(0) ? rsqrt_r<R>(e) : R(0);
+    il[jj] = r;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[jj][c] = z[jj][c] * r;
+  }
+  R dd[N][3], v[M];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dd[i][c] = u[i][c] - u[i + 1][c];
+    // v = A^T dX + dL grad_T L
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const R gk = a[i][k][0] * dd[i][0] + a[i][k][1] * dd[i][1] + a[i][k][2] * dd[i][2];
+      const R ak = a[i][k][0] * dx[i][0] + a[i][k][1] * dx[i][1] + a[i][k][2] * dx[i][2];
+      v[2 * i + k] = ak + dl * gk;
+    }
+  }
+  BlockTri<R, N> F;
+  if (!factor_hessian<R, N>(u, il, a, edge, cond, F)) return false;
+  R r[M], lam[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) r[k] = -v[k];
+  solve_hessian<R, N>(F, r, lam);
+  // q_j = M_j Dw_j with w_i = A_i u_i
+  R q[N + 1][3];
+#pragma unroll
+  for (int jj = 0; jj <= N; ++jj) {
+    R dw[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      R x = R(0);
+      if (jj < N) x += a[jj][0][c] * lam[2 * jj] + a[jj][1][c] * lam[2 * jj + 1];
+      if (jj > 0) x -= a[jj - 1][0][c] * lam[2 * jj - 2] + a[jj - 1][1][c] * lam[2 * jj - 1];
+      dw[c] = x;
+    }
+    const R ud = u[jj][0] * dw[0] + u[jj][1] * dw[1] + u[jj][2] * dw[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q[jj][c] = (dw[c] - u[jj][c] * ud) * il[jj];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R e = dx[i][c] + dl * dd[i][c] + (q[i][c] - q[i + 1][c]);
+      gb[i][c] = e;
+      gb[i][3 + c] = e * t[i][0] + dd[i][c] * lam[2 * i];
+      gb[i][6 + c] = e * t[i][1] + dd[i][c] * lam[2 * i + 1];
+    }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    gtx[c] = -dl * u[0][c] - q[0][c];
+    grx[c] = dl * u[N][c] + q[N][c];
+  }
+  return true;
+}
+
 template <int N>
 __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev B, BackwardCfg cfg,
                                                             uint64_t n_local, const uint64_t* __restrict__ list,
                                                             const float* __restrict__ T,
                                                             const uint8_t* __restrict__ status,
                                                             const float* __restrict__ dX,
-                                                            const float* __restrict__ dLv, double* gacc) {
-  constexpr int M = 2 * N;
+                                                            const float* __restrict__ dLv, double* gacc,
+                                                            uint32_t* __restrict__ rescue_list,
+                                                            unsigned* __restrict__ rescue_count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* s_rec = reinterpret_cast<float*>(smem_raw);
   float* s_aux = s_rec + S.n_obj * kRec32;
@@ -133,121 +204,31 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
         t[i][0] = v.x;
         t[i][1] = v.y;
       }
-      float w[N][3];
+      float z[N + 1][3];
 #pragma unroll
-      for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w[i][c] = fmaf(a[i][1][c], t[i][1], a[i][0][c] * t[i][0]);
-      float u[N + 1][3], il[N + 1];
-#pragma unroll
-      for (int jj = 0; jj <= N; ++jj) {
-        float z[3];
+      for (int jj = 0; jj <= N; ++jj)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           float x = (bh[jj + 1][c] - bh[jj][c]) + (bl[jj + 1][c] - bl[jj][c]);
-          if (jj < N) x += w[jj][c];
-          if (jj > 0) x -= w[jj - 1][c];
-          z[c] = x;
+          if (jj < N) x += fmaf(a[jj][1][c], t[jj][1], a[jj][0][c] * t[jj][0]);
+          if (jj > 0) x -= fmaf(a[jj - 1][1][c], t[jj - 1][1], a[jj - 1][0][c] * t[jj - 1][0]);
+          z[jj][c] = x;
         }
-        float r = rsqrtf(fmaxf(fmaf(z[2], z[2], fmaf(z[1], z[1], z[0] * z[0])), 1e-30f));
-        il[jj] = r;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) u[jj][c] = z[c] * r;
-      }
       const float dl = dLv ? dLv[g] : ((cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask) ? 1.f : 0.f);
-      float dx[N][3], dd[N][3], v[M];
+      float dx[N][3];
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
+      for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          dx[i][c] = dX ? dX[(g * (uint64_t)n_max + i) * 3 + c] : 0.f;
-          dd[i][c] = u[i][c] - u[i + 1][c];
-        }
-        // v = A^T dX + dL grad_T L
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          float gk = a[i][k][0] * dd[i][0] + a[i][k][1] * dd[i][1] + a[i][k][2] * dd[i][2];
-          float ak = a[i][k][0] * dx[i][0] + a[i][k][1] * dx[i][1] + a[i][k][2] * dx[i][2];
-          v[2 * i + k] = fmaf(dl, gk, ak);
-        }
-      }
-      // u_adj = -H^{-1} v  (FP32; FP64 when ill-conditioned)
-      float lam[M];
-      BlockTri<float, N> F32;
-      bool ok = factor_hessian<float, N>(u, il, a, edge, cfg.cond_fp64, F32);
-      if (ok) {
-        float r[M];
-#pragma unroll
-        for (int k = 0; k < M; ++k) r[k] = -v[k];
-        solve_hessian<float, N>(F32, r, lam);
-      } else {
-        double ud[N + 1][3], ild[N + 1], ad[N][2][3];
-#pragma unroll
-        for (int jj = 0; jj <= N; ++jj) {
-          double z[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const double* rb1 = jj < N ? S.rec64 + kRec64 * d.ids[jj] : S.rx64 + 3 * d.rx;
-            const double* rb0 = jj > 0 ? S.rec64 + kRec64 * d.ids[jj - 1] : S.tx64 + 3 * d.tx;
-            double x = rb1[c] - rb0[c];
-            if (jj < N) x += S.rec64[kRec64 * d.ids[jj] + 3 + c] * (double)t[jj][0] +
-                             S.rec64[kRec64 * d.ids[jj] + 6 + c] * (double)t[jj][1];
-            if (jj > 0) x -= S.rec64[kRec64 * d.ids[jj - 1] + 3 + c] * (double)t[jj - 1][0] +
-                             S.rec64[kRec64 * d.ids[jj - 1] + 6 + c] * (double)t[jj - 1][1];
-            z[c] = x;
-          }
-          double e = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
-          double r = e > 0.0 ? rsqrt(e) : 0.0;
-          ild[jj] = r;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) ud[jj][c] = z[c] * r;
-        }
+        for (int c = 0; c < 3; ++c) dx[i][c] = dX ? dX[(g * (uint64_t)n_max + i) * 3 + c] : 0.f;
+      if (!path_vjp<float, N>(z, a, t, edge, dx, dl, cfg.cond_fp64, gb, gtx, grx)) {
+        // FP32 pivots failed: the FP64 pass over the rescue list adds this path
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll
-          for (int k = 0; k < 2; ++k)
+          for (int k = 0; k < 9; ++k) gb[i][k] = 0.f;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) ad[i][k][c] = S.rec64[kRec64 * d.ids[i] + 3 + 3 * k + c];
-        BlockTri<double, N> F64;
-        ok = factor_hessian<double, N>(ud, ild, ad, edge, (double)cfg.cond_fp64 * 1e-6, F64);
-        double r[M], x[M];
-#pragma unroll
-        for (int k = 0; k < M; ++k) r[k] = -(double)v[k];
-        solve_hessian<double, N>(F64, r, x);
-#pragma unroll
-        for (int k = 0; k < M; ++k) lam[k] = ok ? (float)x[k] : 0.f;
-      }
-      if (ok) {
-        // q_j = M_j Dw_j
-        float q[N + 1][3];
-#pragma unroll
-        for (int jj = 0; jj <= N; ++jj) {
-          float dw[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float x = 0.f;
-            if (jj < N) x += fmaf(a[jj][1][c], lam[2 * jj + 1], a[jj][0][c] * lam[2 * jj]);
-            if (jj > 0) x -= fmaf(a[jj - 1][1][c], lam[2 * jj - 1], a[jj - 1][0][c] * lam[2 * jj - 2]);
-            dw[c] = x;
-          }
-          float ud = u[jj][0] * dw[0] + u[jj][1] * dw[1] + u[jj][2] * dw[2];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) q[jj][c] = (dw[c] - u[jj][c] * ud) * il[jj];
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float e = dx[i][c] + dl * dd[i][c] + (q[i][c] - q[i + 1][c]);
-            gb[i][c] = e;
-            gb[i][3 + c] = fmaf(e, t[i][0], dd[i][c] * lam[2 * i]);
-            gb[i][6 + c] = fmaf(e, t[i][1], dd[i][c] * lam[2 * i + 1]);
-          }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          gtx[c] = -dl * u[0][c] - q[0][c];
-          grx[c] = dl * u[N][c] + q[N][c];
-        }
+        for (int c = 0; c < 3; ++c) gtx[c] = grx[c] = 0.f;
+        rescue_list[atomicAdd(rescue_count, 1u)] = (uint32_t)j;
       }
     }
     // sums over paths
@@ -277,6 +258,66 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
     for (int k = threadIdx.x; k < n_acc; k += blockDim.x) {
       float x = s_acc[k];
       if (x != 0.f) atomicAdd(gacc + k, (double)x);
+    }
+  }
+}
+
+// FP64 pass over the paths whose FP32 pivots failed: FP64 records, segment
+// vectors, Hessian and VJP, summed straight into the FP64 accumulators.
+template <int N>
+__global__ void __launch_bounds__(kThreads) backward_rescue_kernel(SceneDev S, BatchDev B, BackwardCfg cfg,
+                                                                   const uint64_t* __restrict__ list,
+                                                                   const float* __restrict__ T,
+                                                                   const uint8_t* __restrict__ status,
+                                                                   const float* __restrict__ dX,
+                                                                   const float* __restrict__ dLv, double* gacc,
+                                                                   const uint32_t* __restrict__ rescue_list,
+                                                                   const unsigned* __restrict__ rescue_count) {
+  const uint64_t n = *rescue_count;
+  const int n_max = B.n_max;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
+    PathDesc d;
+    fetch_path(B, N, list, rescue_list[k], d);
+    const uint64_t g = d.g;
+    uint8_t st = d.flags;
+    if (status) st |= status[g];
+    double a[N][2][3], t[N][2], z[N + 1][3], dx[N][3];
+    bool edge[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a[i][q][c] = S.rec64[kRec64 * d.ids[i] + 3 + 3 * q + c];
+      const float2 v = reinterpret_cast<const float2*>(T)[g * (uint64_t)n_max + i];
+      t[i][0] = v.x;
+      t[i][1] = v.y;
+      edge[i] = S.aux[kAux * d.ids[i] + 2] != 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dx[i][c] = dX ? (double)dX[(g * (uint64_t)n_max + i) * 3 + c] : 0.0;
+    }
+#pragma unroll
+    for (int jj = 0; jj <= N; ++jj)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double b1 = jj < N ? S.rec64[kRec64 * d.ids[jj] + c] : S.rx64[3 * d.rx + c];
+        const double b0 = jj > 0 ? S.rec64[kRec64 * d.ids[jj - 1] + c] : S.tx64[3 * d.tx + c];
+        double x = b1 - b0;
+        if (jj < N) x += a[jj][0][c] * t[jj][0] + a[jj][1][c] * t[jj][1];
+        if (jj > 0) x -= a[jj - 1][0][c] * t[jj - 1][0] + a[jj - 1][1][c] * t[jj - 1][1];
+        z[jj][c] = x;
+      }
+    const double dl = dLv ? (double)dLv[g] : ((cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask) ? 1.0 : 0.0);
+    double gb[N][9], gtx[3], grx[3];
+    if (!path_vjp<double, N>(z, a, t, edge, dx, dl, 1e-10, gb, gtx, grx)) continue;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int q = 0; q < 9; ++q) atomicAdd(gacc + 9 * d.ids[i] + q, gb[i][q]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      atomicAdd(gacc + 9 * S.n_obj + 3 * d.tx + c, gtx[c]);
+      atomicAdd(gacc + 9 * S.n_obj + 3 * S.n_tx + 3 * d.rx + c, grx[c]);
     }
   }
 }
@@ -312,7 +353,8 @@ __global__ void backward_finalize_kernel(int n_obj, int n_tx, int n_rx, const fl
 template <int N>
 static cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg_in,
                                      uint64_t n_local, const uint64_t* list, const float* T, const uint8_t* status,
-                                     const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm) {
+                                     const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm,
+                                     uint32_t* rescue_list, unsigned* rescue_count) {
   BackwardCfg cfg = cfg_in;
   const size_t base = (size_t)S.n_obj * (kRec32 + kAux) * sizeof(float);
   const size_t accb = (size_t)(S.n_obj * 9 + 3 * (S.n_tx + S.n_rx)) * sizeof(float);
@@ -334,20 +376,34 @@ static cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const
   uint64_t cap = (uint64_t)n_sm * (uint64_t)per_sm;
   unsigned grid = (unsigned)(want < cap ? want : cap);
   if (grid == 0) return cudaSuccess;
-  backward_kernel<N><<<grid, kThreads, smem, stream>>>(S, B, cfg, n_local, list, T, status, dX, dL, gacc);
+  e = cudaMemsetAsync(rescue_count, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  backward_kernel<N><<<grid, kThreads, smem, stream>>>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, rescue_list,
+                                                        rescue_count);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const uint64_t rwant = (n_local / 16 + kThreads - 1) / kThreads;
+  const unsigned rgrid = (unsigned)(rwant < (uint64_t)n_sm * 4 ? (rwant ? rwant : 1) : (uint64_t)n_sm * 4);
+  backward_rescue_kernel<N><<<rgrid, kThreads, 0, stream>>>(S, B, cfg, list, T, status, dX, dL, gacc, rescue_list,
+                                                             rescue_count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,
                             const uint64_t* list, const float* T, const uint8_t* status, const float* dX,
-                            const float* dL, double* gacc, cudaStream_t stream, int n_sm, int* err) {
-  (void)err;
+                            const float* dL, double* gacc, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
+                            unsigned* rescue_count) {
   switch (n) {
-    case 1: return launch_backward_n<1>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
-    case 2: return launch_backward_n<2>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
-    case 3: return launch_backward_n<3>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
-    case 4: return launch_backward_n<4>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
-    case 5: return launch_backward_n<5>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm);
+#define FPT_BWD_CASE(K)                                                                                    \
+  case K:                                                                                                  \
+    return launch_backward_n<K>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm, rescue_list, \
+                                rescue_count);
+    FPT_BWD_CASE(1)
+    FPT_BWD_CASE(2)
+    FPT_BWD_CASE(3)
+    FPT_BWD_CASE(4)
+    FPT_BWD_CASE(5)
+#undef FPT_BWD_CASE
     default: return cudaErrorInvalidValue;
   }
 }

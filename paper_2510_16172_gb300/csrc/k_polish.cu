@@ -1,17 +1,22 @@
 // k_polish.cu -- stationarity polish, residual and validity, one thread per path.
 //
 // After BFGS (Sec. III-C) each path takes `steps` Newton steps on Eq. 5 whose
-// gradient is formed in FP64 (z_j from FP64 geometry, FP64 norms) and whose
-// Hessian system (block tridiagonal, blocktri.cuh) is solved in FP32, or in
-// FP64 when a pivot is ill-conditioned.  The first-order condition of Eq. 8
-// measures the result: rho = max_i |A_i delta_i| (metres), where delta solves
-// H delta = -grad_T L at the returned FP32 parameters (the factorisation from
-// the last step is reused).  The validity test (Sec. I, Sec. III: points
-// inside their objects) uses closed intervals on t.
+// gradient is formed in extended precision and whose Hessian system (block
+// tridiagonal, blocktri.cuh) is solved in FP32, or in FP64 when a pivot is
+// ill-conditioned.  The extended precision is double-float arithmetic (ff.cuh,
+// about 2^-46 relative; the default, since GB300's FP64 rate is a small
+// fraction of its FP32 rate) or FP64 (validation mode).  The parameters are
+// carried in that precision through the steps.  The first-order condition of
+// Eq. 8 measures the result: rho = max_i |A_i delta_i| (metres), where delta
+// solves H delta = -grad_T L at the final parameters (the factorisation from
+// the last step is reused); T, X and L are then rounded to FP32 for output.
+// The validity test (Sec. I, Sec. III: points inside their objects) uses
+// closed intervals on the output t.
 //
 // The same kernel evaluates rho, validity and the boundary distance at
 // caller-given parameters (POLISH_VALIDITY) without changing them.
 #include "blocktri.cuh"
+#include "ff.cuh"
 #include "fpt_kernels.h"
 
 namespace fpt {
@@ -54,52 +59,339 @@ __device__ __forceinline__ void grad64(const Geo64<N>& G, const double (&t)[N][2
   }
 }
 
+// Double-float geometry of one path: Delta b_j as pairs, basis vectors as
+// (hi, lo) floats.
 template <int N>
-__device__ __forceinline__ bool factor_any(const double (&u)[N + 1][3], const double (&len)[N + 1],
-                                           const float (&a32)[N][2][3], const Geo64<N>& G, const bool (&edge)[N],
-                                           float cond, BlockTri<float, N>& F32, BlockTri<double, N>& F64,
-                                           bool& use64) {
-  float uf[N + 1][3], ilf[N + 1];
+struct GeoFF {
+  ff db[N + 1][3];
+  float ah[N][2][3], al[N][2][3];
+};
+
+// Double-float segment data and gradient at t (pairs).  Outputs the unit
+// directions and inverse lengths rounded to float (for the Hessian), the
+// lengths, and the gradient g_i = A_i^T (u_i - u_{i+1}) in float (the
+// difference u_i - u_{i+1} is formed in double-float before rounding).
+template <int N>
+__device__ __forceinline__ void gradff(const GeoFF<N>& G, const ff (&t)[N][2], float (&uf)[N + 1][3],
+                                       float (&ilf)[N + 1], ff (&len)[N + 1], float (&g)[2 * N]) {
+  ff uo[N + 1][3];
+  ff w[N][3];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ff p1 = two_prod(G.ah[i][0][c], t[i][0].hi);
+      ff p2 = two_prod(G.ah[i][1][c], t[i][1].hi);
+      ff sm = two_sum(p1.hi, p2.hi);
+      float lo = __fadd_rn(sm.lo, __fadd_rn(p1.lo, p2.lo));
+      lo = __fmaf_rn(G.ah[i][0][c], t[i][0].lo, lo);
+      lo = __fmaf_rn(G.al[i][0][c], t[i][0].hi, lo);
+      lo = __fmaf_rn(G.ah[i][1][c], t[i][1].lo, lo);
+      lo = __fmaf_rn(G.al[i][1][c], t[i][1].hi, lo);
+      w[i][c] = two_sum(sm.hi, lo);
+    }
 #pragma unroll
   for (int j = 0; j <= N; ++j) {
-    ilf[j] = (float)(1.0 / len[j]);
+    ff z[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) uf[j][c] = (float)u[j][c];
+    for (int c = 0; c < 3; ++c) {
+      ff v = G.db[j][c];
+      if (j < N) v = ff_add(v, w[j][c]);
+      if (j > 0) v = ff_sub(v, w[j - 1][c]);
+      z[c] = v;
+    }
+    // |z|^2 in double-float
+    ff p0 = two_prod(z[0].hi, z[0].hi), p1 = two_prod(z[1].hi, z[1].hi), p2 = two_prod(z[2].hi, z[2].hi);
+    ff s1 = two_sum(p0.hi, p1.hi);
+    ff s2 = two_sum(s1.hi, p2.hi);
+    float lo = __fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(__fadd_rn(p0.lo, p1.lo), p2.lo));
+    float cross = __fmaf_rn(z[0].hi, z[0].lo, __fmaf_rn(z[1].hi, z[1].lo, __fmul_rn(z[2].hi, z[2].lo)));
+    lo = __fmaf_rn(2.f, cross, lo);
+    ff e = fast_two_sum(s2.hi, lo);
+    ff r = e.hi > 0.f ? ff_rsqrt(e) : ff{0.f, 0.f};
+    len[j] = ff_mul(e, r);
+    ilf[j] = r.hi;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uo[j][c] = ff_mul(z[c], r);
+      uf[j][c] = uo[j][c].hi;
+    }
   }
-  use64 = false;
-  if (factor_hessian<float, N>(uf, ilf, a32, edge, cond, F32)) return true;
-  use64 = true;
-  double il[N + 1];
 #pragma unroll
-  for (int j = 0; j <= N; ++j) il[j] = 1.0 / len[j];
-  return factor_hessian<double, N>(u, il, G.a, edge, (double)cond * 1e-6, F64);
+  for (int i = 0; i < N; ++i) {
+    float d[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ff dd = ff_sub(uo[i][c], uo[i + 1][c]);
+      d[c] = __fadd_rn(dd.hi, dd.lo);
+    }
+    g[2 * i] = fmaf(G.ah[i][0][2], d[2], fmaf(G.ah[i][0][1], d[1], G.ah[i][0][0] * d[0]));
+    g[2 * i + 1] = fmaf(G.ah[i][1][2], d[2], fmaf(G.ah[i][1][1], d[1], G.ah[i][1][0] * d[0]));
+  }
+}
+
+// Validity (closed intervals on the output t) and signed boundary distance.
+template <int N>
+__device__ __forceinline__ bool validity(const float (&tf)[N][2], const bool (&edge)[N], const float (&h1)[N],
+                                         const float (&h2)[N], float& bd) {
+  bool inside = true;
+  bd = INFINITY;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float t0 = tf[i][0], t1 = tf[i][1];
+    inside = inside && t0 >= 0.f && t0 <= 1.f && (edge[i] || (t1 >= 0.f && t1 <= 1.f));
+    float di = fminf(t0, 1.f - t0) * h1[i];
+    if (!edge[i]) di = fminf(di, fminf(t1, 1.f - t1) * h2[i]);
+    bd = fminf(bd, di);
+  }
+  return inside;
+}
+
+__device__ __forceinline__ uint8_t final_status(uint8_t st, bool inside, float rho, float solved_tol) {
+  if (st & ST_INVALID) inside = false;
+  if (inside) st |= ST_VALID;
+  if (rho <= solved_tol && !(st & (ST_DEGENERATE | ST_REPEAT | ST_NONFINITE | ST_INVALID))) st |= ST_SOLVED;
+  return st;
 }
 
 template <int N>
-__device__ __forceinline__ void newton_step(const BlockTri<float, N>& F32, const BlockTri<double, N>& F64, bool use64,
-                                            const double (&g)[2 * N], double (&delta)[2 * N]) {
+__device__ __forceinline__ float world_max(const float (&a)[N][2][3], const float (&delta)[2 * N]) {
+  float worst = 0.f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float w2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float w = fmaf(a[i][1][c], delta[2 * i + 1], a[i][0][c] * delta[2 * i]);
+      w2 = fmaf(w, w, w2);
+    }
+    worst = fmaxf(worst, w2);
+  }
+  float r = sqrtf(worst);
+  return isfinite(r) ? r : INFINITY;
+}
+
+// H^{-1}(-g) with the FP32 factorisation, or the FP64 one when the FP32 pivots failed.
+template <int N>
+__device__ __forceinline__ void newton_dir(const BlockTri<float, N>& F32, const BlockTri<double, N>& F64, bool use64,
+                                           const float (&g)[2 * N], float (&delta)[2 * N]) {
   if (use64) {
-    double r[2 * N];
+    double r[2 * N], x[2 * N];
+#pragma unroll
+    for (int k = 0; k < 2 * N; ++k) r[k] = -(double)g[k];
+    solve_hessian<double, N>(F64, r, x);
+#pragma unroll
+    for (int k = 0; k < 2 * N; ++k) delta[k] = (float)x[k];
+  } else {
+    float r[2 * N];
 #pragma unroll
     for (int k = 0; k < 2 * N; ++k) r[k] = -g[k];
-    solve_hessian<double, N>(F64, r, delta);
-  } else {
-    float r[2 * N], x[2 * N];
-#pragma unroll
-    for (int k = 0; k < 2 * N; ++k) r[k] = (float)(-g[k]);
-    solve_hessian<float, N>(F32, r, x);
-#pragma unroll
-    for (int k = 0; k < 2 * N; ++k) delta[k] = (double)x[k];
+    solve_hessian<float, N>(F32, r, delta);
   }
 }
 
+// ---------------------------------------------------------------------------
+// double-float polish (default)
+// ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kThreads) polish_kernel(SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local,
-                                                          const uint64_t* __restrict__ list, float* __restrict__ T,
-                                                          float* __restrict__ X, float* __restrict__ Lout,
-                                                          uint8_t* __restrict__ status, float* __restrict__ rho_out,
-                                                          uint8_t* __restrict__ mask_out,
-                                                          float* __restrict__ bdist_out, int use_smem) {
+__global__ void __launch_bounds__(kThreads) polish_ff_kernel(SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local,
+                                                             const uint64_t* __restrict__ list, float* __restrict__ T,
+                                                             float* __restrict__ X, float* __restrict__ Lout,
+                                                             uint8_t* __restrict__ status, float* __restrict__ rho_out,
+                                                             uint8_t* __restrict__ mask_out,
+                                                             float* __restrict__ bdist_out, int use_smem,
+                                                             uint32_t* __restrict__ rescue_list,
+                                                             unsigned* __restrict__ rescue_count) {
+  constexpr int M = 2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const float* rec32 = S.rec32;
+  const float* reclo = S.reclo;
+  const float* aux = S.aux;
+  if (use_smem) {
+    float* s32 = reinterpret_cast<float*>(smem_raw);
+    float* slo = s32 + S.n_obj * kRec32;
+    float* sax = slo + S.n_obj * kRecLo;
+    stage(s32, S.rec32, S.n_obj * kRec32);
+    stage(slo, S.reclo, S.n_obj * kRecLo);
+    stage(sax, S.aux, S.n_obj * kAux);
+    __syncthreads();
+    rec32 = s32;
+    reclo = slo;
+    aux = sax;
+  }
+  const int n_max = B.n_max;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_local; j += stride) {
+    PathDesc d;
+    fetch_path(B, N, list, j, d);
+    const uint64_t g = d.g;
+    uint8_t st = d.flags;
+    if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE);
+    // geometry: b as hi + lo, A as hi + lo
+    GeoFF<N> G;
+    bool edge[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const float* r = rec32 + kRec32 * d.ids[i];
+      const float* rl = reclo + kRecLo * d.ids[i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        G.ah[i][0][c] = r[6 + c];
+        G.ah[i][1][c] = r[9 + c];
+        G.al[i][0][c] = rl[c];
+        G.al[i][1][c] = rl[3 + c];
+      }
+      edge[i] = aux[kAux * d.ids[i] + 2] != 0.f;
+    }
+    {
+      float bh[N + 2][3], bl[N + 2][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        bh[0][c] = __ldg(S.tx32 + kEnd32 * d.tx + c);
+        bl[0][c] = __ldg(S.tx32 + kEnd32 * d.tx + 3 + c);
+        bh[N + 1][c] = __ldg(S.rx32 + kEnd32 * d.rx + c);
+        bl[N + 1][c] = __ldg(S.rx32 + kEnd32 * d.rx + 3 + c);
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float* r = rec32 + kRec32 * d.ids[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          bh[i + 1][c] = r[c];
+          bl[i + 1][c] = r[3 + c];
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj <= N; ++jj)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          ff sd = two_sum(bh[jj + 1][c], -bh[jj][c]);
+          G.db[jj][c] = fast_two_sum(sd.hi, __fadd_rn(sd.lo, __fsub_rn(bl[jj + 1][c], bl[jj][c])));
+        }
+    }
+    // parameters
+    const float2* Ti = reinterpret_cast<const float2*>(T) + g * (uint64_t)n_max;
+    ff t[N][2];
+    bool finite = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float2 v = Ti[i];
+      t[i][0] = ff{v.x, 0.f};
+      t[i][1] = ff{v.y, 0.f};
+      finite = finite && isfinite(v.x) && isfinite(v.y);
+    }
+    if (!finite) st |= ST_NONFINITE;
+    float rho = INFINITY;
+    ff len[N + 1];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) len[k] = ff{0.f, 0.f};
+    if (!(st & ST_INVALID) && finite) {
+      float uf[N + 1][3], ilf[N + 1], gr[M];
+      gradff<N>(G, t, uf, ilf, len, gr);
+      float lmin = len[0].hi;
+#pragma unroll
+      for (int k = 1; k <= N; ++k) lmin = fminf(lmin, len[k].hi);
+      if (!(st & ST_REPEAT) && lmin >= cfg.deg_tol) {
+        BlockTri<float, N> F32;
+        const int steps = cfg.mode == POLISH_SOLVE ? cfg.steps : 0;
+        if (factor_hessian<float, N>(uf, ilf, G.ah, edge, cfg.cond_fp64, F32)) {
+          float delta[M], r[M];
+          for (int s = 0; s < steps; ++s) {
+#pragma unroll
+            for (int k = 0; k < M; ++k) r[k] = -gr[k];
+            solve_hessian<float, N>(F32, r, delta);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              ff a0 = two_sum(t[i][0].hi, delta[2 * i]);
+              t[i][0] = fast_two_sum(a0.hi, __fadd_rn(a0.lo, t[i][0].lo));
+              if (!edge[i]) {
+                ff a1 = two_sum(t[i][1].hi, delta[2 * i + 1]);
+                t[i][1] = fast_two_sum(a1.hi, __fadd_rn(a1.lo, t[i][1].lo));
+              }
+            }
+            gradff<N>(G, t, uf, ilf, len, gr);
+          }
+#pragma unroll
+          for (int k = 0; k < M; ++k) r[k] = -gr[k];
+          solve_hessian<float, N>(F32, r, delta);
+          rho = world_max<N>(G.ah, delta);
+        } else {
+          // FP32 pivots failed: the FP64 pass over the rescue list redoes this path
+          st |= ST_FP64;
+          rescue_list[atomicAdd(rescue_count, 1u)] = (uint32_t)j;
+        }
+        lmin = len[0].hi;
+#pragma unroll
+        for (int k = 1; k <= N; ++k) lmin = fminf(lmin, len[k].hi);
+      }
+      if (!(st & ST_REPEAT) && !(lmin >= cfg.deg_tol)) st |= ST_DEGENERATE;
+    }
+    float tf[N][2], h1[N], h2[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      tf[i][0] = t[i][0].hi;
+      tf[i][1] = t[i][1].hi;
+      h1[i] = aux[kAux * d.ids[i]];
+      h2[i] = aux[kAux * d.ids[i] + 1];
+    }
+    float bd;
+    const bool inside = validity<N>(tf, edge, h1, h2, bd);
+    st = final_status(st, inside, rho, cfg.solved_tol);
+    if (cfg.mode == POLISH_SOLVE) {
+      float2* To = reinterpret_cast<float2*>(T) + g * (uint64_t)n_max;
+#pragma unroll
+      for (int i = 0; i < N; ++i) To[i] = make_float2(tf[i][0], tf[i][1]);
+      status[g] = st;
+      if (X) {
+        float* Xo = X + g * (uint64_t)n_max * 3;
+#pragma unroll
+        for (int i = 0; i < kMaxOrder; ++i)
+          if (i < n_max)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              float x = 0.f;
+              if (i < N) {
+                ff p1 = two_prod(G.ah[i][0][c], t[i][0].hi);
+                ff p2 = two_prod(G.ah[i][1][c], t[i][1].hi);
+                float lo = __fadd_rn(p1.lo, p2.lo);
+                lo = __fmaf_rn(G.ah[i][0][c], t[i][0].lo, lo);
+                lo = __fmaf_rn(G.al[i][0][c], t[i][0].hi, lo);
+                lo = __fmaf_rn(G.ah[i][1][c], t[i][1].lo, lo);
+                lo = __fmaf_rn(G.al[i][1][c], t[i][1].hi, lo);
+                ff w = ff_add(p1, ff{p2.hi, lo});
+                const float* rb = rec32 + kRec32 * d.ids[i];
+                ff xr = ff_add(ff{rb[c], rb[3 + c]}, w);
+                ff xw = ff_add(xr, ff{S.centre_hi[c], S.centre_lo[c]});
+                x = __fadd_rn(xw.hi, xw.lo);
+              }
+              Xo[3 * i + c] = x;
+            }
+      }
+      if (Lout) {
+        ff Ls{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k <= N; ++k) Ls = ff_add(Ls, len[k]);
+        Lout[g] = (!(st & ST_INVALID) && finite) ? __fadd_rn(Ls.hi, Ls.lo) : NAN;
+      }
+    }
+    if (rho_out) rho_out[g] = rho;
+    if (mask_out) mask_out[g] = (st & ST_VALID) ? 1 : 0;
+    if (bdist_out) bdist_out[g] = bd;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 polish (validation mode: polish_fp64 = 1)
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local,
+                                                            const uint64_t* __restrict__ list, float* __restrict__ T,
+                                                            float* __restrict__ X, float* __restrict__ Lout,
+                                                            uint8_t* __restrict__ status, float* __restrict__ rho_out,
+                                                            uint8_t* __restrict__ mask_out,
+                                                            float* __restrict__ bdist_out, int use_smem,
+                                                            const uint32_t* __restrict__ rescue_list,
+                                                            const unsigned* __restrict__ rescue_count) {
   constexpr int M = 2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const double* rec64 = S.rec64;
@@ -119,13 +411,16 @@ __global__ void __launch_bounds__(kThreads) polish_kernel(SceneDev S, BatchDev B
   }
   const int n_max = B.n_max;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_local; j += stride) {
+  // rescue mode: only the paths the double-float pass listed
+  const uint64_t n_iter = rescue_list ? (uint64_t)*rescue_count : n_local;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_iter; k += stride) {
+    const uint64_t j = rescue_list ? (uint64_t)rescue_list[k] : k;
     PathDesc d;
     fetch_path(B, N, list, j, d);
     const uint64_t g = d.g;
     uint8_t st = d.flags;
     if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE);
-    // geometry
+    if (rescue_list) st |= ST_FP64;
     Geo64<N> G;
     float a32[N][2][3];
     bool edge[N];
@@ -152,24 +447,21 @@ __global__ void __launch_bounds__(kThreads) polish_kernel(SceneDev S, BatchDev B
       h2[i] = ax[1];
       edge[i] = ax[2] != 0.f;
     }
-    // parameters
     const float2* Ti = reinterpret_cast<const float2*>(T) + g * (uint64_t)n_max;
-    float tf[N][2];
     double t[N][2];
+    bool finite = true;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       float2 v = Ti[i];
-      tf[i][0] = v.x;
-      tf[i][1] = v.y;
       t[i][0] = v.x;
       t[i][1] = v.y;
+      finite = finite && isfinite(v.x) && isfinite(v.y);
     }
-    double len[N + 1], u[N + 1][3], gr[M];
-    float rho = INFINITY;
-    bool finite = true;
-#pragma unroll
-    for (int i = 0; i < N; ++i) finite = finite && isfinite(tf[i][0]) && isfinite(tf[i][1]);
     if (!finite) st |= ST_NONFINITE;
+    double len[N + 1], u[N + 1][3], gr[M];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) len[k] = 0.0;
+    float rho = INFINITY;
     if (!(st & ST_INVALID) && finite) {
       grad64<N>(G, t, len, u, gr);
       double lmin = len[0];
@@ -178,38 +470,41 @@ __global__ void __launch_bounds__(kThreads) polish_kernel(SceneDev S, BatchDev B
       if (!(st & ST_REPEAT) && lmin >= (double)cfg.deg_tol) {
         BlockTri<float, N> F32;
         BlockTri<double, N> F64;
-        bool use64;
-        bool ok = factor_any<N>(u, len, a32, G, edge, cfg.cond_fp64, F32, F64, use64);
-        if (use64) st |= ST_FP64;
+        float uf[N + 1][3], ilf[N + 1];
+#pragma unroll
+        for (int jj = 0; jj <= N; ++jj) {
+          ilf[jj] = (float)(1.0 / len[jj]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) uf[jj][c] = (float)u[jj][c];
+        }
+        bool use64 = false;
+        bool ok = factor_hessian<float, N>(uf, ilf, a32, edge, cfg.cond_fp64, F32);
+        if (!ok) {
+          use64 = true;
+          double il[N + 1];
+#pragma unroll
+          for (int jj = 0; jj <= N; ++jj) il[jj] = 1.0 / len[jj];
+          ok = factor_hessian<double, N>(u, il, G.a, edge, (double)cfg.cond_fp64 * 1e-6, F64);
+          st |= ST_FP64;
+        }
         if (ok) {
-          double delta[M];
+          float gf[M], delta[M];
           const int steps = cfg.mode == POLISH_SOLVE ? cfg.steps : 0;
           for (int s = 0; s < steps; ++s) {
-            newton_step<N>(F32, F64, use64, gr, delta);
+#pragma unroll
+            for (int k = 0; k < M; ++k) gf[k] = (float)gr[k];
+            newton_dir<N>(F32, F64, use64, gf, delta);
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-              tf[i][0] = (float)(t[i][0] + delta[2 * i]);
-              tf[i][1] = edge[i] ? tf[i][1] : (float)(t[i][1] + delta[2 * i + 1]);
-              t[i][0] = tf[i][0];
-              t[i][1] = tf[i][1];
+              t[i][0] += (double)delta[2 * i];
+              if (!edge[i]) t[i][1] += (double)delta[2 * i + 1];
             }
             grad64<N>(G, t, len, u, gr);
           }
-          // residual at the returned parameters
-          newton_step<N>(F32, F64, use64, gr, delta);
-          float worst = 0.f;
 #pragma unroll
-          for (int i = 0; i < N; ++i) {
-            float w2 = 0.f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              float w = a32[i][0][c] * (float)delta[2 * i] + a32[i][1][c] * (float)delta[2 * i + 1];
-              w2 = fmaf(w, w, w2);
-            }
-            worst = fmaxf(worst, w2);
-          }
-          rho = sqrtf(worst);
-          if (!isfinite(rho)) rho = INFINITY;
+          for (int k = 0; k < M; ++k) gf[k] = (float)gr[k];
+          newton_dir<N>(F32, F64, use64, gf, delta);
+          rho = world_max<N>(a32, delta);
         }
         lmin = len[0];
 #pragma unroll
@@ -217,21 +512,15 @@ __global__ void __launch_bounds__(kThreads) polish_kernel(SceneDev S, BatchDev B
       }
       if (!(st & ST_REPEAT) && !(lmin >= (double)cfg.deg_tol)) st |= ST_DEGENERATE;
     }
-    // validity (closed intervals) and boundary distance
-    bool inside = true;
-    float bd = INFINITY;
+    float tf[N][2];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const float t0 = tf[i][0], t1 = tf[i][1];
-      inside = inside && t0 >= 0.f && t0 <= 1.f && (edge[i] || (t1 >= 0.f && t1 <= 1.f));
-      float di = fminf(t0, 1.f - t0) * h1[i];
-      if (!edge[i]) di = fminf(di, fminf(t1, 1.f - t1) * h2[i]);
-      bd = fminf(bd, di);
+      tf[i][0] = (float)t[i][0];
+      tf[i][1] = (float)t[i][1];
     }
-    if (st & ST_INVALID) inside = false;
-    if (inside) st |= ST_VALID;
-    const bool solved = rho <= cfg.solved_tol && !(st & (ST_DEGENERATE | ST_REPEAT | ST_NONFINITE | ST_INVALID));
-    if (solved) st |= ST_SOLVED;
+    float bd;
+    const bool inside = validity<N>(tf, edge, h1, h2, bd);
+    st = final_status(st, inside, rho, cfg.solved_tol);
     if (cfg.mode == POLISH_SOLVE) {
       float2* To = reinterpret_cast<float2*>(T) + g * (uint64_t)n_max;
 #pragma unroll
@@ -250,18 +539,13 @@ __global__ void __launch_bounds__(kThreads) polish_kernel(SceneDev S, BatchDev B
       }
       if (Lout) {
         double Ls = 0.0;
-        if (!(st & ST_INVALID) && finite) {
-          if (st & ST_REPEAT) grad64<N>(G, t, len, u, gr);
 #pragma unroll
-          for (int k = 0; k <= N; ++k) Ls += len[k];
-        } else {
-          Ls = NAN;
-        }
-        Lout[g] = (float)Ls;
+        for (int k = 0; k <= N; ++k) Ls += len[k];
+        Lout[g] = (!(st & ST_INVALID) && finite) ? (float)Ls : NAN;
       }
     }
     if (rho_out) rho_out[g] = rho;
-    if (mask_out) mask_out[g] = inside ? 1 : 0;
+    if (mask_out) mask_out[g] = (st & ST_VALID) ? 1 : 0;
     if (bdist_out) bdist_out[g] = bd;
   }
 }
@@ -269,37 +553,67 @@ __global__ void __launch_bounds__(kThreads) polish_kernel(SceneDev S, BatchDev B
 template <int N>
 static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                                    const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
-                                   uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm) {
-  size_t smem = (size_t)S.n_obj * (kRec64 * sizeof(double) + (kRec32 + kAux) * sizeof(float));
-  int use_smem = smem <= 160 * 1024;
-  if (!use_smem) smem = 0;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(polish_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                   uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
+                                   unsigned* rescue_count) {
+  const bool f64 = cfg.fp64 != 0;
+  const size_t smem64 = (size_t)S.n_obj * (kRec64 * sizeof(double) + (kRec32 + kAux) * sizeof(float));
+  const size_t smemff = (size_t)S.n_obj * (kRec32 + kRecLo + kAux) * sizeof(float);
+  auto grid_of = [&](const void* fn, size_t smem, uint64_t n, unsigned& grid) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
     if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t want = (n + kThreads - 1) / kThreads;
+    uint64_t cap = (uint64_t)n_sm * (uint64_t)per_sm;
+    grid = (unsigned)(want < cap ? want : cap);
+    return cudaSuccess;
+  };
+  const size_t s64 = smem64 <= 160 * 1024 ? smem64 : 0;
+  const size_t sff = smemff <= 160 * 1024 ? smemff : 0;
+  unsigned grid = 0;
+  cudaError_t e;
+  if (f64) {
+    e = grid_of((const void*)polish64_kernel<N>, s64, n_local, grid);
+    if (e != cudaSuccess || grid == 0) return e;
+    polish64_kernel<N><<<grid, kThreads, s64, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
+                                                         s64 != 0, nullptr, nullptr);
+    return cudaGetLastError();
   }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, polish_kernel<N>, kThreads, smem);
+  e = cudaMemsetAsync(rescue_count, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  uint64_t want = (n_local + kThreads - 1) / kThreads;
-  uint64_t cap = (uint64_t)n_sm * (uint64_t)per_sm;
-  unsigned grid = (unsigned)(want < cap ? want : cap);
-  if (grid == 0) return cudaSuccess;
-  polish_kernel<N><<<grid, kThreads, smem, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
-                                                      use_smem);
+  e = grid_of((const void*)polish_ff_kernel<N>, sff, n_local, grid);
+  if (e != cudaSuccess || grid == 0) return e;
+  polish_ff_kernel<N><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
+                                                        sff != 0, rescue_list, rescue_count);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // FP64 pass over the listed paths (its grid covers a few percent of the paths)
+  e = grid_of((const void*)polish64_kernel<N>, s64, (n_local + 15) / 16, grid);
+  if (e != cudaSuccess || grid == 0) return e;
+  polish64_kernel<N><<<grid, kThreads, s64, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
+                                                       s64 != 0, rescue_list, rescue_count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                           const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
-                          uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, int* err) {
-  (void)err;
+                          uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
+                          unsigned* rescue_count) {
   switch (n) {
-    case 1: return launch_polish_n<1>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm);
-    case 2: return launch_polish_n<2>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm);
-    case 3: return launch_polish_n<3>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm);
-    case 4: return launch_polish_n<4>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm);
-    case 5: return launch_polish_n<5>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm);
+#define FPT_POLISH_CASE(K)                                                                                   \
+  case K:                                                                                                    \
+    return launch_polish_n<K>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm, \
+                              rescue_list, rescue_count);
+    FPT_POLISH_CASE(1)
+    FPT_POLISH_CASE(2)
+    FPT_POLISH_CASE(3)
+    FPT_POLISH_CASE(4)
+    FPT_POLISH_CASE(5)
+#undef FPT_POLISH_CASE
     default: return cudaErrorInvalidValue;
   }
 }

@@ -41,7 +41,8 @@ class FptError(RuntimeError):
 class SolveParams(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("fp_iters", C.c_int32), ("polish", C.c_int32), ("fixed_iters", C.c_int32),
                 ("tol_step", C.c_float), ("solved_tol", C.c_float), ("deg_tol", C.c_float), ("cond_fp64", C.c_float),
-                ("init_mode", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("init_mode", C.c_int32), ("polish_fp64", C.c_int32), ("refill", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 # every symbol declared in include/fpt.h with (restype, argtypes)
@@ -67,6 +68,7 @@ _SIGS = {
     "fpt_validity": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fpt_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint8, _vp, _vp, _vp]),
     "fpt_count_status": (C.c_int, [_vp, _vp, C.c_uint64, C.c_uint8, C.POINTER(C.c_uint64)]),
+    "fpt_tc_gemm_bf16": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
     "fpt_profile_enable": (C.c_int, [_vp, C.c_int]),
     "fpt_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
 }
@@ -343,6 +345,22 @@ def profile_read(ctx: Context, reset: bool = True):
     n = (C.c_uint64 * K_COUNT)()
     _check(ctx.handle, library().fpt_profile_read(ctx.handle, ms, n, 1 if reset else 0))
     return list(ms), list(n)
+
+
+def tc_gemm_bf16(ctx: Context, A, W, bias=None, out=None):
+    """C = A W^T (+ bias) on the tensor cores; A [M,K], W [N,K] bf16 CUDA tensors."""
+    import torch
+
+    _need_cuda(A, torch.bfloat16, "A")
+    _need_cuda(W, torch.bfloat16, "W")
+    _need_cuda(bias, torch.float32, "bias")
+    M, K = A.shape
+    N = W.shape[0]
+    if W.shape[1] != K:
+        raise FptError("A and W disagree on K")
+    C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(ctx.handle, library().fpt_tc_gemm_bf16(ctx.handle, M, N, K, _ptr(A), _ptr(W), _ptr(bias), _ptr(C)))
+    return C
 
 
 def count_status(ctx: Context, status, mask: int) -> int:
