@@ -5,8 +5,8 @@ Workload (one step): the urban canyon -- 32 vertical facades (5-30 m) on a
 200 x 200 m grid plus their 128 edges, a 32-object alphabet (16 facades, 16
 edges), TX at (100, 100, 10) m and a 32 x 32 RX grid at 1.5 m; every order-3
 sequence for every RX: 32^3 * 1024 = 33,554,432 paths.  A step enumerates,
-solves (plain init, FP32 BFGS with Eq. 6 step sizes, FP64-gradient Newton
-polish, validity), and back-propagates the sum of the valid solved paths'
+solves (plain init, FP32 BFGS with Eq. 6 step sizes, a Newton polish whose
+gradient is formed in double-float arithmetic, validity), and back-propagates the sum of the valid solved paths'
 lengths to TX, RX and every vertex by implicit differentiation.  A path
 counts as solved when its stationarity residual is <= 1e-5 m.
 
@@ -35,8 +35,8 @@ if ROOT not in sys.path:
 METRIC = "path solves/s to 1e-5 m stationarity, fwd+implicit bwd; learned vs plain init"
 UNIT = "solves/s"
 WORKLOAD = ("urban canyon: 32 facades + 128 edges, 32-object alphabet (16 R + 16 D), order 3, "
-            "1 TX x 32x32 RX = 33,554,432 paths; plain init; FP32 BFGS + Eq.6 fixed point, FP64-gradient "
-            "Newton polish, validity, implicit backward of the sum of valid path lengths")
+            "1 TX x 32x32 RX = 33,554,432 paths; plain init; FP32 BFGS + Eq.6 fixed point, Newton polish with an "
+            "extended-precision gradient, validity, implicit backward of the sum of valid path lengths")
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -231,12 +231,12 @@ def run_ours(args, world, rank, local_rank):
     if world > 1:
         import torch.distributed as dist
 
-    sc = scenes.urban_canyon(0)
+    sc = scenes.urban_canyon(0, rx_grid=args.rx_grid)
     ctx = fpt.Context(local_rank)
     scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
     batch = fpt.Batch.exhaustive(ctx, scene, 3, 3, sc.alphabet)
     N = batch.n_paths
-    params = fpt.default_params()
+    params = fpt.default_params(max_iters=args.max_iters)
     out = fpt.alloc_outputs(ctx, batch, with_X=False, with_rho=False, with_iters=True)
     grads = (torch.empty((scene.n_tx, 3), device=dev), torch.empty((scene.n_rx, 3), device=dev),
              torch.empty((scene.n_obj, 3, 3), device=dev))
@@ -295,8 +295,8 @@ def run_ours(args, world, rank, local_rank):
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     per_launch = {k: (kms[k] / klaunch[k] if klaunch[k] else 0.0) for k in range(fpt.K_COUNT)}
     bfgs_flops = bfgs_flops_init(3) * run_paths + bfgs_flops_per_iter(3, params.fp_iters) * total_iters
-    names = {fpt.K_BFGS: "bfgs_kernel<3>", fpt.K_POLISH: "polish_kernel<3>", fpt.K_BACKWARD: "backward_kernel<3>",
-             fpt.K_OTHER: "backward_finalize_kernel"}
+    names = {fpt.K_BFGS: "bfgs_refill_kernel<3>", fpt.K_POLISH: "polish_ff_kernel<3> + polish64_kernel<3> (rescue)",
+             fpt.K_BACKWARD: "backward_kernel<3> + backward_rescue_kernel<3>", fpt.K_OTHER: "backward_finalize_kernel"}
     dom = max(range(fpt.K_COUNT), key=lambda k: kms[k])
     clocks = clk.summary()
     roof_bfgs = {"kernel": names[fpt.K_BFGS], "bound": "alu", "achieved": bfgs_flops / (per_launch[0] * 1e-3) / 1e12,
@@ -309,9 +309,10 @@ def run_ours(args, world, rank, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_paths": N, "init": "plain (learned init not built)",
-                       "polish": "1 Newton step, FP64 gradient", "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"replicas x{world}"},
+            "config": {"workload": WORKLOAD if args.rx_grid == 32 else WORKLOAD + f" (RX grid {args.rx_grid}^2)",
+                       "n_paths": N, "init": "plain", "max_bfgs_iters": args.max_iters, "fp_iters": 1,
+                       "polish": "1 Newton step, double-float gradient (FP64 for ill-conditioned Hessians)",
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "solved_per_step": solved, "solved_fraction": solved / N, "mean_bfgs_iters": total_iters / max(1, run_paths),
             "kernel_ms_per_step": {names[k]: kms[k] / args.steps for k in range(fpt.K_COUNT)},
             "dominant_kernel": names[dom],
@@ -353,14 +354,14 @@ def e2e(args, sc, ctx, dev, torch, fpt):
     times, solved = [], 0
     h2d = types.numel() + verts.numel() * 8 + tx.numel() * 8 + rx.numel() * 8 + alphabet.size * 4
     d2h = N * 4 + N + gv_h.numel() * 4 + gtx_h.numel() * 4 + grx_h.numel() * 4
-    for k in range(args.warmup + max(3, args.steps // 2)):
+    for k in range(args.warmup + max(3, min(10, args.steps // 2))):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         scene = fpt.Scene(ctx, types.numpy(), verts.numpy(), tx.numpy(), rx.numpy())
         batch = fpt.Batch.exhaustive(ctx, scene, 3, 3, alphabet)
         if out is None:
             out = fpt.alloc_outputs(ctx, batch, with_X=False, with_rho=False, with_iters=False)
-        fpt.solve(ctx, scene, batch, None, out)
+        fpt.solve(ctx, scene, batch, fpt.default_params(max_iters=args.max_iters), out)
         g = fpt.backward(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask)
         L_h.copy_(out["L"], non_blocking=True)
         st_h.copy_(out["status"], non_blocking=True)
@@ -387,6 +388,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--max-iters", type=int, default=32, help="BFGS step cap")
+    ap.add_argument("--rx-grid", type=int, default=32, help="RX grid side (32 = the 33.5M-path workload)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

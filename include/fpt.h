@@ -83,7 +83,7 @@ typedef struct {
   float solved_tol;    /* stationarity residual bound for FPT_ST_SOLVED, metres (1e-5) */
   float deg_tol;       /* a solution segment shorter than this (metres) is DEGENERATE (1e-3) */
   float cond_fp64;     /* Hessian pivot ratio below which the solve is redone in FP64 (1e-4) */
-  int32_t init_mode;   /* 0: plain init, t = 1/2 (object centroid).  1: learned init (unsupported here) */
+  int32_t init_mode;   /* 0: plain init, t = 1/2 (object centroid).  1: learned (fpt_set_init_mlp) */
   int32_t polish_fp64; /* 0: polish gradient in double-float FP32 arithmetic (~2^-46, default); 1: in FP64 */
   int32_t refill;      /* lanes of a warp that must be free before it takes new paths (8); 0: one path per
                           lane until the whole warp is done */
@@ -195,6 +195,60 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* b
  * [n]; result written to *count on the host after a stream sync). */
 fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uint8_t mask, uint64_t* count);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (the paper names better initial candidates as future work,
+ * Sec. V).  A network maps the geometry of a sequence to starting parameters:
+ * features (64, BF16) -> 256 -> 256 -> 256 (GELU) -> 8 outputs (t of the first
+ * four interactions), BF16 weights, FP32 accumulation on the tensor cores,
+ * activations rounded to BF16 between layers.  Features of a path of order n,
+ * with o = (TX + RX) / 2 and S the model's length scale (metres):
+ *   f[0..2] = (TX - o)/S, f[3..5] = (RX - o)/S, and for slot s < min(n, 4) at
+ *   6 + 11 s: [1, is_edge, (b - o)/S (3), a1/S (3), a2/S (3)]; all else 0.
+ * Parameters (FP32, FPT_MLP_NPARAMS floats, in this order): W1 [256][64], b1
+ * [256], W2 [256][256], b2 [256], W3 [256][256], b3 [256], W4 [16][256], b4
+ * [16] (rows / entries 8..15 of the last layer are zero).
+ * Training loss of a batch of B samples with targets t* [B][8]:
+ *   (1/B) sum_b sum_{active s} | (a1/S)(y_2s - t*_2s) + (a2/S)(y_2s+1 - t*_2s+1) |^2
+ * with a1/S, a2/S read from the sample's (BF16) features: the squared world-
+ * space error of the predicted points in units of S.
+ * ------------------------------------------------------------------------- */
+#define FPT_MLP_FEATURES 64
+#define FPT_MLP_OUT 16
+#define FPT_MLP_NPARAMS 152336
+typedef struct fpt_mlp fpt_mlp;
+
+/* New network with seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights
+ * and zero biases (splitmix64 stream of `seed`), length scale S > 0 metres. */
+fpt_status fpt_mlp_create(fpt_ctx* ctx, uint64_t seed, float length_scale, fpt_mlp** out);
+void fpt_mlp_free(fpt_mlp* mlp);
+/* Copy the FP32 parameters to / from host memory [FPT_MLP_NPARAMS]; set also
+ * resets the Adam state.  Synchronous. */
+fpt_status fpt_mlp_get_params(const fpt_mlp* mlp, float* host_params);
+fpt_status fpt_mlp_set_params(fpt_mlp* mlp, const float* host_params);
+/* Save / load parameters, Adam moments, step count and length scale to a
+ * versioned binary file (host path).  FPT_EINVAL on a bad file. */
+fpt_status fpt_mlp_save(const fpt_mlp* mlp, const char* path);
+fpt_status fpt_mlp_load(fpt_ctx* ctx, const char* path, fpt_mlp** out);
+/* Features of every path of a batch: device bf16 output [N][64]. */
+fpt_status fpt_mlp_features(fpt_ctx* ctx, const fpt_mlp* mlp, const fpt_scene* scene, const fpt_batch* batch,
+                            void* X_out);
+/* Forward pass: X device bf16 [B][64] -> Y device float [B][16]. */
+fpt_status fpt_mlp_forward(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, uint64_t B, float* Y);
+/* Loss and its gradient with respect to the parameters (device float
+ * [FPT_MLP_NPARAMS], overwritten) for X [B][64] and targets T [B][8] (device);
+ * *loss receives the loss on the host (synchronises). */
+fpt_status fpt_mlp_loss_grad(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const float* T, uint64_t B, float* loss,
+                             float* grad_out);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * loss of this batch; *loss (host, may be NULL) receives the batch loss. */
+fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const float* T, uint64_t B, float lr,
+                              float* loss);
+/* Network used by fpt_solve when init_mode = 1 (NULL detaches).  The network's
+ * prediction seeds the first min(n, 4) interactions of each path; further
+ * interactions, edges' second coordinate and non-finite predictions use the
+ * plain start t = 1/2. */
+fpt_status fpt_set_init_mlp(fpt_ctx* ctx, fpt_mlp* mlp);
+
 /* Tensor-core GEMM used by the warm-start network's layers (tcgen05, BF16 in,
  * FP32 accumulation in tensor memory): C[M][N] = A[M][K] W[N][K]^T (+ bias[N]).
  * A, W: device bf16, row-major; bias: device float [N] or NULL; C: device
@@ -207,7 +261,7 @@ fpt_status fpt_tc_gemm_bf16(fpt_ctx* ctx, int32_t M, int32_t N, int32_t K, const
  * bracketed by CUDA events on the context's stream, and fpt_profile_read()
  * returns, per kernel class, the summed device time in milliseconds and the
  * number of launches (it synchronises the stream; reset != 0 clears the sums). */
-enum { FPT_K_BFGS = 0, FPT_K_POLISH = 1, FPT_K_BACKWARD = 2, FPT_K_OTHER = 3, FPT_K_COUNT = 4 };
+enum { FPT_K_BFGS = 0, FPT_K_POLISH = 1, FPT_K_BACKWARD = 2, FPT_K_OTHER = 3, FPT_K_MLP = 4, FPT_K_COUNT = 5 };
 fpt_status fpt_profile_enable(fpt_ctx* ctx, int on);
 fpt_status fpt_profile_read(fpt_ctx* ctx, double* ms, uint64_t* launches, int reset);
 

@@ -82,6 +82,9 @@ def lib():
             L.orc_seeded_decode.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_uint64, _ip]
             L.orc_draw.restype = C.c_uint64
             L.orc_draw.argtypes = [C.c_uint64, C.c_uint64, C.c_int]
+            L.orc_decode_batch.restype = None
+            L.orc_decode_batch.argtypes = [C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, _ip,
+                                           C.c_int64, C.POINTER(C.c_uint64), C.c_int, _ip, _ip, _ip, _ip]
             L.orc_solve_batch.restype = C.c_int
             L.orc_solve_batch.argtypes = [C.POINTER(_Batch)]
             L.orc_object_record.restype = C.c_int
@@ -194,48 +197,37 @@ def exhaustive_per_pair(K: int, lo: int, hi: int) -> int:
     return int(lib().orc_exhaustive_per_pair(K, lo, hi))
 
 
+def _decode(scene, mode, seed, lo, hi, per_pair, g):
+    g = np.ascontiguousarray(g, dtype=np.uint64)
+    M = len(g)
+    ids = np.empty((M, hi), dtype=np.int32)
+    order = np.empty(M, dtype=np.int32)
+    ti = np.empty(M, dtype=np.int32)
+    ri = np.empty(M, dtype=np.int32)
+    alpha = np.ascontiguousarray(scene.alphabet, dtype=np.int32)
+    lib().orc_decode_batch(mode, int(seed), len(alpha), lo, hi, int(per_pair), len(scene.rx), _p(alpha, C.c_int32), M,
+                           g.ctypes.data_as(C.POINTER(C.c_uint64)), hi, _p(ids, C.c_int32), _p(order, C.c_int32),
+                           _p(ti, C.c_int32), _p(ri, C.c_int32))
+    return ids, order, ti, ri
+
+
 def exhaustive_paths(scene, lo: int, hi: int, g=None):
     """Decode global indices g of an exhaustive batch into (ids, order, tx_idx, rx_idx).
 
     g = ((tx * n_rx) + rx) * per_pair + r; r enumerates orders lo..hi, each in
     itertools.product order over the alphabet.
     """
-    Ka = len(scene.alphabet)
-    spp = exhaustive_per_pair(Ka, lo, hi)
-    n_pairs = len(scene.tx) * len(scene.rx)
+    spp = exhaustive_per_pair(len(scene.alphabet), lo, hi)
     if g is None:
-        g = np.arange(spp * n_pairs, dtype=np.uint64)
-    g = np.asarray(g, dtype=np.uint64)
-    ids = np.full((len(g), hi), -1, dtype=np.int32)
-    order = np.zeros(len(g), dtype=np.int32)
-    digits = np.zeros(hi, dtype=np.int32)
-    L = lib()
-    for k, gk in enumerate(g):
-        pair, r = divmod(int(gk), spp)
-        n = L.orc_exhaustive_decode(Ka, lo, hi, r, _p(digits, C.c_int32))
-        order[k] = n
-        ids[k, :n] = scene.alphabet[digits[:n]]
-    pair = (g // np.uint64(spp)).astype(np.int64)
-    return ids, order, (pair // len(scene.rx)).astype(np.int32), (pair % len(scene.rx)).astype(np.int32)
+        g = np.arange(spp * len(scene.tx) * len(scene.rx), dtype=np.uint64)
+    return _decode(scene, 0, 0, lo, hi, spp, g)
 
 
 def seeded_paths(scene, seed: int, per_pair: int, lo: int, hi: int, g=None):
     """Decode a seeded batch: per_pair sequences for each TX/RX pair, drawn by splitmix64."""
-    Ka = len(scene.alphabet)
-    n_pairs = len(scene.tx) * len(scene.rx)
     if g is None:
-        g = np.arange(per_pair * n_pairs, dtype=np.uint64)
-    g = np.asarray(g, dtype=np.uint64)
-    ids = np.full((len(g), hi), -1, dtype=np.int32)
-    order = np.zeros(len(g), dtype=np.int32)
-    digits = np.zeros(hi, dtype=np.int32)
-    L = lib()
-    for k, gk in enumerate(g):
-        n = L.orc_seeded_decode(int(seed), Ka, lo, hi, int(gk), _p(digits, C.c_int32))
-        order[k] = n
-        ids[k, :n] = scene.alphabet[digits[:n]]
-    pair = (g // np.uint64(per_pair)).astype(np.int64)
-    return ids, order, (pair // len(scene.rx)).astype(np.int32), (pair % len(scene.rx)).astype(np.int32)
+        g = np.arange(per_pair * len(scene.tx) * len(scene.rx), dtype=np.uint64)
+    return _decode(scene, 1, seed, lo, hi, per_pair, g)
 
 
 # --------------------------------------------------------------------------

@@ -694,6 +694,22 @@ int orc_seeded_decode(uint64_t seed, int K, int lo, int hi, uint64_t g, int32_t*
   return n;
 }
 
+/* decode many global indices at once (ids [M][n_max], -1 in unused slots) */
+void orc_decode_batch(int mode, uint64_t seed, int K, int lo, int hi, uint64_t per_pair, int n_rx, const int32_t* alphabet,
+                      int64_t M, const uint64_t* g, int n_max, int32_t* ids, int32_t* order, int32_t* tx_idx,
+                      int32_t* rx_idx) {
+  for (int64_t k = 0; k < M; ++k) {
+    int32_t digits[ORC_NMAX];
+    int n = mode == 0 ? orc_exhaustive_decode(K, lo, hi, g[k] % per_pair, digits)
+                      : orc_seeded_decode(seed, K, lo, hi, g[k], digits);
+    order[k] = n;
+    for (int j = 0; j < n_max; ++j) ids[k * n_max + j] = j < n ? alphabet[digits[j]] : -1;
+    uint64_t pair = g[k] / per_pair;
+    tx_idx[k] = (int32_t)(pair / (uint64_t)n_rx);
+    rx_idx[k] = (int32_t)(pair % (uint64_t)n_rx);
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Batch drivers (independent paths across threads).                         */
 /* ------------------------------------------------------------------------ */

@@ -7,6 +7,7 @@
 // solver launch is specialised to one order).
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -30,13 +31,14 @@ struct fpt_ctx {
   uint32_t* d_rescue = nullptr;            // paths whose FP32 Hessian pivots failed (polish scratch)
   size_t rescue_cap = 0;
   unsigned* d_rescue_n = nullptr;
+  fpt_mlp* init_mlp = nullptr;             // network for init_mode = 1
   char msg[512] = "ok";
   // kernel timing
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
-  double prof_ms[FPT_K_COUNT] = {0, 0, 0, 0};
-  uint64_t prof_n[FPT_K_COUNT] = {0, 0, 0, 0};
+  double prof_ms[FPT_K_COUNT] = {0, 0, 0, 0, 0};
+  uint64_t prof_n[FPT_K_COUNT] = {0, 0, 0, 0, 0};
 };
 
 // Event pair around one launch when timing is on.
@@ -110,6 +112,28 @@ static fpt_status fail(fpt_ctx* ctx, fpt_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess)                                                                         \
       return fail((ctx), FPT_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
   } while (0)
+
+struct fpt_mlp {
+  fpt_ctx* ctx = nullptr;
+  float scale = 1.f;
+  uint64_t seed = 0;
+  int64_t step = 0;
+  float* d_w = nullptr;          // FP32 master parameters
+  float* d_m = nullptr;          // Adam moments
+  float* d_v = nullptr;
+  float* d_g = nullptr;          // gradient
+  __nv_bfloat16* d_wb = nullptr;  // BF16 copy used by the tensor cores
+  float* d_loss = nullptr;
+  // activations / gradients for a batch of up to cap rows
+  uint64_t cap = 0;
+  __nv_bfloat16 *d_H1 = nullptr, *d_H2 = nullptr, *d_H3 = nullptr, *d_dZa = nullptr, *d_dZb = nullptr,
+                *d_dYb = nullptr, *d_X = nullptr;
+  float *d_Z1 = nullptr, *d_Z2 = nullptr, *d_Z3 = nullptr, *d_dZf = nullptr, *d_Y = nullptr, *d_dY = nullptr;
+};
+
+static fpt_status mlp_ensure_ws(fpt_ctx* ctx, fpt_mlp* m, uint64_t B, bool train);
+static fpt_status mlp_forward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16* X, uint64_t B, float* Y,
+                                   bool train);
 
 static SceneDev scene_dev(const fpt_scene* s) {
   SceneDev d{};
@@ -559,7 +583,8 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
   fpt_solve_params p;
   fpt_default_params(&p);
   if (prm) p = *prm;
-  if (p.init_mode != 0) return fail(ctx, FPT_EUNSUPPORTED, "learned init is not available in this build");
+  if (p.init_mode != 0 && p.init_mode != 1) return fail(ctx, FPT_EINVAL, "init_mode must be 0 or 1");
+  if (p.init_mode == 1 && !ctx->init_mlp) return fail(ctx, FPT_EINVAL, "init_mode 1 needs fpt_set_init_mlp");
   if (p.max_iters < 0 || p.fp_iters < 1 || p.polish < 0 || p.polish > 2)
     return fail(ctx, FPT_EINVAL, "bad solver parameters");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
@@ -568,17 +593,32 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
   if (st != FPT_OK) return st;
   const SceneDev S = scene_dev(s);
   SolveCfg sc{p.max_iters, p.fp_iters, p.fixed_iters, p.tol_step * p.tol_step, 0.01f * p.deg_tol * p.deg_tol,
-              p.refill > 32 ? 32 : p.refill};
+              p.refill > 32 ? 32 : p.refill, p.init_mode == 1};
   PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, p.cond_fp64, p.polish_fp64};
   for (int n = 1; n <= kMaxOrder; ++n) {
     const uint64_t* list;
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
+    if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
+    if (p.init_mode == 1) {
+      // learned start: features -> network -> T, in chunks of the network's workspace
+      fpt_mlp* m = ctx->init_mlp;
+      const uint64_t chunk = 1ull << 18;
+      st = mlp_ensure_ws(ctx, m, chunk, false);
+      if (st != FPT_OK) return st;
+      ProfScope ps(ctx, FPT_K_MLP);
+      for (uint64_t first = 0; first < cnt; first += chunk) {
+        const uint64_t c = cnt - first < chunk ? cnt - first : chunk;
+        CUDA_OR_FAIL(ctx, launch_mlp_features(S, b->dev, n, list, first, c, 1.f / m->scale, m->d_X, ctx->stream));
+        st = mlp_forward_impl(ctx, m, m->d_X, c, m->d_Y, false);
+        if (st != FPT_OK) return st;
+        CUDA_OR_FAIL(ctx, launch_mlp_start(S, b->dev, n, list, first, c, m->d_Y, T, ctx->stream));
+      }
+    }
     {
       ProfScope ps(ctx, FPT_K_BFGS);
       CUDA_OR_FAIL(ctx, launch_bfgs(n, S, b->dev, sc, cnt, list, T, status, iters, ctx->stream, ctx->n_sm, ctx->d_work));
     }
-    if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
     st = ensure_rescue(ctx, cnt);
     if (st != FPT_OK) return st;
     {
@@ -668,6 +708,372 @@ fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uin
   CUDA_OR_FAIL(ctx, cudaMemcpyAsync(&h, ctx->d_count, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
   *count = h;
+  return FPT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// learned warm start
+// ---------------------------------------------------------------------------
+static void mlp_free_ws(fpt_mlp* m) {
+  for (void* p : {(void*)m->d_H1, (void*)m->d_H2, (void*)m->d_H3, (void*)m->d_dZa, (void*)m->d_dZb, (void*)m->d_dYb,
+                  (void*)m->d_X, (void*)m->d_Z1, (void*)m->d_Z2, (void*)m->d_Z3, (void*)m->d_dZf, (void*)m->d_Y,
+                  (void*)m->d_dY})
+    cudaFree(p);
+  m->d_H1 = m->d_H2 = m->d_H3 = m->d_dZa = m->d_dZb = m->d_dYb = m->d_X = nullptr;
+  m->d_Z1 = m->d_Z2 = m->d_Z3 = m->d_dZf = m->d_Y = m->d_dY = nullptr;
+  m->cap = 0;
+}
+
+static fpt_status mlp_ensure_ws(fpt_ctx* ctx, fpt_mlp* m, uint64_t B, bool train) {
+  const uint64_t want = B < 128 ? 128 : B;
+  if (want <= m->cap && (!train || m->d_Z1)) return FPT_OK;
+  mlp_free_ws(m);
+  const size_t H = want * kMlpHidden;
+  cudaError_t e = cudaSuccess;
+  auto bf = [&](__nv_bfloat16** p, size_t n) { if (e == cudaSuccess) e = cudaMalloc(p, n * sizeof(__nv_bfloat16)); };
+  auto f32 = [&](float** p, size_t n) { if (e == cudaSuccess) e = cudaMalloc(p, n * sizeof(float)); };
+  bf(&m->d_H1, H);
+  bf(&m->d_H2, H);
+  bf(&m->d_H3, H);
+  bf(&m->d_X, want * kMlpIn);
+  f32(&m->d_Y, want * kMlpOut);
+  if (train) {
+    f32(&m->d_Z1, H);
+    f32(&m->d_Z2, H);
+    f32(&m->d_Z3, H);
+    f32(&m->d_dZf, H);
+    bf(&m->d_dZa, H);
+    bf(&m->d_dZb, H);
+    bf(&m->d_dYb, want * kMlpOut);
+    f32(&m->d_dY, want * kMlpOut);
+  }
+  if (e != cudaSuccess) {
+    mlp_free_ws(m);
+    return fail(ctx, FPT_ENOMEM, "MLP workspace for %llu rows: %s", (unsigned long long)want, cudaGetErrorString(e));
+  }
+  m->cap = want;
+  return FPT_OK;
+}
+
+static GemmArgs gemm_args(int M, int N, int K, const __nv_bfloat16* A, long long sam, long long sak,
+                          const __nv_bfloat16* Bm, long long sbn, long long sbk, int op, int* err) {
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.A = A;
+  g.sam = sam;
+  g.sak = sak;
+  g.B = Bm;
+  g.sbn = sbn;
+  g.sbk = sbk;
+  g.op = op;
+  g.err = err;
+  return g;
+}
+
+// forward pass of B rows of X; with `train`, keeps the pre-activations
+static fpt_status mlp_forward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16* X, uint64_t B, float* Y,
+                                   bool train) {
+  const int Bi = (int)B;
+  const __nv_bfloat16* W = m->d_wb;
+  const float* P = m->d_w;
+  const __nv_bfloat16* in = X;
+  __nv_bfloat16* H[3] = {m->d_H1, m->d_H2, m->d_H3};
+  float* Z[3] = {m->d_Z1, m->d_Z2, m->d_Z3};
+  const int offW[3] = {kOffW1, kOffW2, kOffW3}, offB[3] = {kOffB1, kOffB2, kOffB3};
+  for (int l = 0; l < 3; ++l) {
+    const int K = l == 0 ? kMlpIn : kMlpHidden;
+    GemmArgs g = gemm_args(Bi, kMlpHidden, K, in, K, 1, W + offW[l], K, 1, EPI_BIAS_GELU, ctx->d_err);
+    g.bias = P + offB[l];
+    g.C = train ? Z[l] : nullptr;
+    g.scm = kMlpHidden;
+    g.scn = 1;
+    g.H = H[l];
+    g.shm = kMlpHidden;
+    g.shn = 1;
+    CUDA_OR_FAIL(ctx, launch_gemm(g, 1, ctx->stream));
+    in = H[l];
+  }
+  GemmArgs g = gemm_args(Bi, kMlpOut, kMlpHidden, in, kMlpHidden, 1, W + kOffW4, kMlpHidden, 1, EPI_STORE, ctx->d_err);
+  g.bias = P + kOffB4;
+  g.C = Y;
+  g.scm = kMlpOut;
+  g.scn = 1;
+  CUDA_OR_FAIL(ctx, launch_gemm(g, 1, ctx->stream));
+  return FPT_OK;
+}
+
+// loss and gradient (into m->d_g) of a batch; loss accumulated in m->d_loss
+static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16* X, const float* T, uint64_t B) {
+  const int Bi = (int)B;
+  const int ks = Bi >= 2048 ? Bi / 1024 : 1;  // split the batch reduction of the weight gradients
+  const __nv_bfloat16* W = m->d_wb;
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(m->d_g, 0, kMlpParams * sizeof(float), ctx->stream));
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(m->d_loss, 0, sizeof(float), ctx->stream));
+  fpt_status st = mlp_forward_impl(ctx, m, X, B, m->d_Y, true);
+  if (st != FPT_OK) return st;
+  CUDA_OR_FAIL(ctx, launch_mlp_loss(X, m->d_Y, T, B, m->d_dY, m->d_dYb, m->d_loss, ctx->stream));
+  // last layer: dW4^T[in][out] = sum_b H3[b][in] dY[b][out]; db4 = sum_b dY
+  {
+    GemmArgs g = gemm_args(kMlpHidden, kMlpOut, Bi, m->d_H3, 1, kMlpHidden, m->d_dYb, 1, kMlpOut, EPI_ATOMIC, ctx->d_err);
+    g.C = m->d_g + kOffW4;
+    g.scm = 1;
+    g.scn = kMlpHidden;
+    CUDA_OR_FAIL(ctx, launch_gemm(g, ks, ctx->stream));
+    CUDA_OR_FAIL(ctx, launch_colsum(m->d_dY, B, kMlpOut, m->d_g + kOffB4, ctx->stream));
+  }
+  // dZ3 = (dY W4) * gelu'(Z3)
+  {
+    GemmArgs g = gemm_args(Bi, kMlpHidden, kMlpOut, m->d_dYb, kMlpOut, 1, W + kOffW4, 1, kMlpHidden, EPI_GELU_GRAD,
+                           ctx->d_err);
+    g.Zin = m->d_Z3;
+    g.szm = kMlpHidden;
+    g.szn = 1;
+    g.C = m->d_dZf;
+    g.scm = kMlpHidden;
+    g.scn = 1;
+    g.H = m->d_dZa;
+    g.shm = kMlpHidden;
+    g.shn = 1;
+    CUDA_OR_FAIL(ctx, launch_gemm(g, 1, ctx->stream));
+  }
+  const __nv_bfloat16* acts[3] = {X, m->d_H1, m->d_H2};  // inputs of layers 1..3
+  const float* Zs[2] = {m->d_Z1, m->d_Z2};
+  const int offW[3] = {kOffW1, kOffW2, kOffW3}, offB[3] = {kOffB1, kOffB2, kOffB3};
+  __nv_bfloat16* dZ = m->d_dZa;
+  __nv_bfloat16* dZn = m->d_dZb;
+  for (int l = 2; l >= 0; --l) {
+    const int K_in = l == 0 ? kMlpIn : kMlpHidden;
+    CUDA_OR_FAIL(ctx, launch_colsum(m->d_dZf, B, kMlpHidden, m->d_g + offB[l], ctx->stream));
+    // dW_l[out][in] = sum_b dZ[b][out] act[b][in]
+    GemmArgs gw = gemm_args(kMlpHidden, K_in, Bi, dZ, 1, kMlpHidden, acts[l], 1, K_in, EPI_ATOMIC, ctx->d_err);
+    gw.C = m->d_g + offW[l];
+    gw.scm = K_in;
+    gw.scn = 1;
+    CUDA_OR_FAIL(ctx, launch_gemm(gw, ks, ctx->stream));
+    if (l == 0) break;
+    // dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
+    GemmArgs gd = gemm_args(Bi, kMlpHidden, kMlpHidden, dZ, kMlpHidden, 1, W + offW[l], 1, kMlpHidden, EPI_GELU_GRAD,
+                            ctx->d_err);
+    gd.Zin = Zs[l - 1];
+    gd.szm = kMlpHidden;
+    gd.szn = 1;
+    gd.C = m->d_dZf;
+    gd.scm = kMlpHidden;
+    gd.scn = 1;
+    gd.H = dZn;
+    gd.shm = kMlpHidden;
+    gd.shn = 1;
+    CUDA_OR_FAIL(ctx, launch_gemm(gd, 1, ctx->stream));
+    __nv_bfloat16* tmp = dZ;
+    dZ = dZn;
+    dZn = tmp;
+  }
+  return FPT_OK;
+}
+
+// splitmix64 stream for the initial weights
+static uint64_t sm64_next(uint64_t& state) {
+  uint64_t z = (state += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+extern "C" {
+
+fpt_status fpt_mlp_create(fpt_ctx* ctx, uint64_t seed, float length_scale, fpt_mlp** out) {
+  if (!ctx || !out) return fail(ctx, FPT_EINVAL, "null argument");
+  *out = nullptr;
+  if (!(length_scale > 0.f) || !std::isfinite(length_scale)) return fail(ctx, FPT_EINVAL, "bad length scale");
+  fpt_mlp* m = new (std::nothrow) fpt_mlp();
+  if (!m) return FPT_ENOMEM;
+  m->ctx = ctx;
+  m->scale = length_scale;
+  m->seed = seed;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  for (float** p : {&m->d_w, &m->d_m, &m->d_v, &m->d_g})
+    if (e == cudaSuccess) e = cudaMalloc(p, kMlpParams * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_wb, kMlpParams * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_loss, sizeof(float));
+  if (e != cudaSuccess) {
+    fpt_mlp_free(m);
+    return fail(ctx, FPT_ENOMEM, "MLP parameters: %s", cudaGetErrorString(e));
+  }
+  std::vector<float> w(kMlpParams, 0.f);
+  uint64_t state = seed;
+  auto fill = [&](int off, int rows, int cols, int used_rows) {
+    const double bound = 1.0 / std::sqrt((double)cols);
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) {
+        const double u = (double)(sm64_next(state) >> 11) * (1.0 / 9007199254740992.0);
+        w[off + r * cols + c] = r < used_rows ? (float)((2.0 * u - 1.0) * bound) : 0.f;
+      }
+  };
+  fill(kOffW1, 256, 64, 256);
+  fill(kOffW2, 256, 256, 256);
+  fill(kOffW3, 256, 256, 256);
+  fill(kOffW4, 16, 256, 8);
+  fpt_status st = fpt_mlp_set_params(m, w.data());
+  if (st != FPT_OK) {
+    fpt_mlp_free(m);
+    return st;
+  }
+  *out = m;
+  return FPT_OK;
+}
+
+void fpt_mlp_free(fpt_mlp* m) {
+  if (!m) return;
+  if (m->ctx && m->ctx->init_mlp == m) m->ctx->init_mlp = nullptr;
+  mlp_free_ws(m);
+  for (void* p : {(void*)m->d_w, (void*)m->d_m, (void*)m->d_v, (void*)m->d_g, (void*)m->d_wb, (void*)m->d_loss})
+    cudaFree(p);
+  delete m;
+}
+
+fpt_status fpt_mlp_get_params(const fpt_mlp* m, float* host) {
+  if (!m || !host) return FPT_EINVAL;
+  fpt_ctx* ctx = m->ctx;
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_OR_FAIL(ctx, cudaMemcpy(host, m->d_w, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost));
+  return FPT_OK;
+}
+
+fpt_status fpt_mlp_set_params(fpt_mlp* m, const float* host) {
+  if (!m || !host) return FPT_EINVAL;
+  fpt_ctx* ctx = m->ctx;
+  for (int i = 0; i < kMlpParams; ++i)
+    if (!std::isfinite(host[i])) return fail(ctx, FPT_EINVAL, "non-finite parameter %d", i);
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_OR_FAIL(ctx, cudaMemcpy(m->d_w, host, kMlpParams * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(ctx, cudaMemset(m->d_m, 0, kMlpParams * sizeof(float)));
+  CUDA_OR_FAIL(ctx, cudaMemset(m->d_v, 0, kMlpParams * sizeof(float)));
+  CUDA_OR_FAIL(ctx, launch_to_bf16(m->d_w, m->d_wb, kMlpParams, ctx->stream));
+  CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  m->step = 0;
+  return FPT_OK;
+}
+
+static const char kMlpMagic[8] = {'F', 'P', 'T', 'M', 'L', 'P', '0', '1'};
+
+fpt_status fpt_mlp_save(const fpt_mlp* m, const char* path) {
+  if (!m || !path) return FPT_EINVAL;
+  fpt_ctx* ctx = m->ctx;
+  std::vector<float> buf(3 * (size_t)kMlpParams);
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_OR_FAIL(ctx, cudaMemcpy(buf.data(), m->d_w, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost));
+  CUDA_OR_FAIL(ctx, cudaMemcpy(buf.data() + kMlpParams, m->d_m, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost));
+  CUDA_OR_FAIL(ctx, cudaMemcpy(buf.data() + 2 * kMlpParams, m->d_v, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost));
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(ctx, FPT_EINVAL, "cannot write %s", path);
+  const int32_t n = kMlpParams;
+  bool ok = fwrite(kMlpMagic, 1, 8, f) == 8 && fwrite(&n, 4, 1, f) == 1 && fwrite(&m->scale, 4, 1, f) == 1 &&
+            fwrite(&m->seed, 8, 1, f) == 1 && fwrite(&m->step, 8, 1, f) == 1 &&
+            fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? FPT_OK : fail(ctx, FPT_EINVAL, "short write to %s", path);
+}
+
+fpt_status fpt_mlp_load(fpt_ctx* ctx, const char* path, fpt_mlp** out) {
+  if (!ctx || !path || !out) return fail(ctx, FPT_EINVAL, "null argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(ctx, FPT_EINVAL, "cannot read %s", path);
+  char magic[8];
+  int32_t n = 0;
+  float scale = 0.f;
+  uint64_t seed = 0;
+  int64_t step = 0;
+  std::vector<float> buf(3 * (size_t)kMlpParams);
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMlpMagic, 8) == 0 && fread(&n, 4, 1, f) == 1 &&
+            n == kMlpParams && fread(&scale, 4, 1, f) == 1 && fread(&seed, 8, 1, f) == 1 &&
+            fread(&step, 8, 1, f) == 1 && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  fclose(f);
+  if (!ok) return fail(ctx, FPT_EINVAL, "%s is not a network file of this version", path);
+  fpt_mlp* m = nullptr;
+  fpt_status st = fpt_mlp_create(ctx, seed, scale, &m);
+  if (st != FPT_OK) return st;
+  st = fpt_mlp_set_params(m, buf.data());
+  if (st == FPT_OK) {
+    cudaError_t e = cudaMemcpy(m->d_m, buf.data() + kMlpParams, kMlpParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(m->d_v, buf.data() + 2 * kMlpParams, kMlpParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = fail(ctx, FPT_ECUDA, "%s", cudaGetErrorString(e));
+  }
+  if (st != FPT_OK) {
+    fpt_mlp_free(m);
+    return st;
+  }
+  m->step = step;
+  *out = m;
+  return FPT_OK;
+}
+
+fpt_status fpt_mlp_features(fpt_ctx* ctx, const fpt_mlp* m, const fpt_scene* s, const fpt_batch* b, void* X) {
+  fpt_status st = check_scene_batch(ctx, s, b);
+  if (st != FPT_OK) return st;
+  if (!m || !X) return fail(ctx, FPT_EINVAL, "null argument");
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  ProfScope ps(ctx, FPT_K_OTHER);
+  CUDA_OR_FAIL(ctx, launch_mlp_features(scene_dev(s), b->dev, 0, nullptr, 0, b->dev.n_paths, 1.f / m->scale,
+                                        static_cast<__nv_bfloat16*>(X), ctx->stream));
+  return FPT_OK;
+}
+
+fpt_status fpt_mlp_forward(fpt_ctx* ctx, fpt_mlp* m, const void* X, uint64_t B, float* Y) {
+  if (!ctx || !m || !X || !Y) return fail(ctx, FPT_EINVAL, "null argument");
+  if (B < 1 || B > (1ull << 30)) return fail(ctx, FPT_EINVAL, "bad batch size");
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  fpt_status st = mlp_ensure_ws(ctx, m, B, false);
+  if (st != FPT_OK) return st;
+  ProfScope ps(ctx, FPT_K_OTHER);
+  return mlp_forward_impl(ctx, m, static_cast<const __nv_bfloat16*>(X), B, Y, false);
+}
+
+fpt_status fpt_mlp_loss_grad(fpt_ctx* ctx, fpt_mlp* m, const void* X, const float* T, uint64_t B, float* loss,
+                             float* grad_out) {
+  if (!ctx || !m || !X || !T) return fail(ctx, FPT_EINVAL, "null argument");
+  if (B < 1 || B > (1ull << 30)) return fail(ctx, FPT_EINVAL, "bad batch size");
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  fpt_status st = mlp_ensure_ws(ctx, m, B, true);
+  if (st != FPT_OK) return st;
+  st = mlp_backward_impl(ctx, m, static_cast<const __nv_bfloat16*>(X), T, B);
+  if (st != FPT_OK) return st;
+  if (grad_out)
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(grad_out, m->d_g, kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (loss) {
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return FPT_OK;
+}
+
+fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* m, const void* X, const float* T, uint64_t B, float lr,
+                              float* loss) {
+  if (!(lr > 0.f)) return fail(ctx, FPT_EINVAL, "learning rate must be positive");
+  fpt_status st = fpt_mlp_loss_grad(ctx, m, X, T, B, nullptr, nullptr);
+  if (st != FPT_OK) return st;
+  m->step += 1;
+  const float c1 = 1.f - std::pow(0.9f, (float)m->step), c2 = 1.f - std::pow(0.999f, (float)m->step);
+  CUDA_OR_FAIL(ctx, launch_adam(m->d_w, m->d_m, m->d_v, m->d_g, kMlpParams, lr, c1, c2, m->d_wb, ctx->stream));
+  if (loss) {
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return FPT_OK;
+}
+
+fpt_status fpt_set_init_mlp(fpt_ctx* ctx, fpt_mlp* m) {
+  if (!ctx) return FPT_EINVAL;
+  if (m && m->ctx != ctx) return fail(ctx, FPT_EINVAL, "network belongs to another context");
+  ctx->init_mlp = m;
   return FPT_OK;
 }
 

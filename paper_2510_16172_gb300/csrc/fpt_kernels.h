@@ -17,6 +17,7 @@ struct SolveCfg {
   float tol2;       // (world-space step tolerance)^2
   float stop2;      // a segment shorter than sqrt(stop2) stops BFGS (the path runs into a kink)
   int refill;       // lane refill threshold (free lanes before a warp takes new paths); 0 = one path per lane per tile
+  int init_from_T;  // 1: start from the parameters already in T (learned start); 0: t = 1/2
 };
 
 enum PolishMode { POLISH_SOLVE = 0, POLISH_VALIDITY = 1 };

@@ -175,4 +175,195 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// features, loss, bias gradients, Adam, learned start
+// ---------------------------------------------------------------------------
+
+// 64 features of one path (see include/fpt.h): origin o = (TX + RX)/2, scale S.
+__device__ __forceinline__ void path_features(const SceneDev& S, const PathDesc& d, float inv_scale,
+                                              __nv_bfloat16* f) {
+  float tx[3], rx[3], o[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    tx[c] = S.tx32[kEnd32 * d.tx + c] + S.tx32[kEnd32 * d.tx + 3 + c];
+    rx[c] = S.rx32[kEnd32 * d.rx + c] + S.rx32[kEnd32 * d.rx + 3 + c];
+    o[c] = 0.5f * (tx[c] + rx[c]);
+  }
+  float v[kMlpIn];
+#pragma unroll
+  for (int k = 0; k < kMlpIn; ++k) v[k] = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    v[c] = (tx[c] - o[c]) * inv_scale;
+    v[3 + c] = (rx[c] - o[c]) * inv_scale;
+  }
+  const bool valid = !(d.flags & ST_INVALID);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s < d.n && valid) {
+      const float* r = S.rec32 + kRec32 * d.ids[s];
+      const int base = 6 + 11 * s;
+      v[base] = 1.f;
+      v[base + 1] = S.aux[kAux * d.ids[s] + 2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[base + 2 + c] = ((r[c] + r[3 + c]) - o[c]) * inv_scale;
+        v[base + 5 + c] = r[6 + c] * inv_scale;
+        v[base + 8 + c] = r[9 + c] * inv_scale;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMlpIn; k += 8) {
+    __nv_bfloat16 e[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) e[q] = __float2bfloat16(v[k + q]);
+    *reinterpret_cast<uint4*>(f + k) = *reinterpret_cast<uint4*>(e);
+  }
+}
+
+// all paths of a batch (global index order) or one order slice (local index order)
+__global__ void mlp_features_kernel(SceneDev S, BatchDev B, int n, const uint64_t* list, uint64_t first,
+                                    uint64_t count, float inv_scale, __nv_bfloat16* X) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x) {
+    PathDesc d;
+    if (n > 0)
+      fetch_path(B, n, list, first + k, d);
+    else
+      decode_global(B, first + k, d);
+    path_features(S, d, inv_scale, X + k * kMlpIn);
+  }
+}
+
+// loss (1/B) sum_b sum_active |(a1/S) dy_2s + (a2/S) dy_2s+1|^2 and dY
+__global__ void mlp_loss_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ Y,
+                                const float* __restrict__ T, uint64_t B, float* __restrict__ dY,
+                                __nv_bfloat16* __restrict__ dYb, float* loss) {
+  float acc = 0.f;
+  const float w = 2.f / (float)B;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (uint64_t)gridDim.x * blockDim.x) {
+    float g[kMlpOut];
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) g[k] = 0.f;
+    const __nv_bfloat16* f = X + b * kMlpIn;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int base = 6 + 11 * s;
+      if (__bfloat162float(f[base]) > 0.5f) {
+        const float d0 = Y[b * kMlpOut + 2 * s] - T[b * 8 + 2 * s];
+        const float d1 = Y[b * kMlpOut + 2 * s + 1] - T[b * 8 + 2 * s + 1];
+        float e[3], a1[3], a2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          a1[c] = __bfloat162float(f[base + 5 + c]);
+          a2[c] = __bfloat162float(f[base + 8 + c]);
+          e[c] = a1[c] * d0 + a2[c] * d1;
+        }
+        acc += e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+        g[2 * s] = w * (a1[0] * e[0] + a1[1] * e[1] + a1[2] * e[2]);
+        g[2 * s + 1] = w * (a2[0] * e[0] + a2[1] * e[1] + a2[2] * e[2]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) {
+      dY[b * kMlpOut + k] = g[k];
+      dYb[b * kMlpOut + k] = __float2bfloat16(g[k]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (float)B);
+}
+
+// out[n] += sum_b A[b][n]  (bias gradients), A: [B][N] row-major
+__global__ void colsum_kernel(const float* __restrict__ A, uint64_t B, int N, float* out) {
+  const int n = threadIdx.x % N;
+  const int lanes = blockDim.x / N;
+  float acc = 0.f;
+  for (uint64_t b = (uint64_t)blockIdx.x * lanes + threadIdx.x / N; b < B; b += (uint64_t)gridDim.x * lanes)
+    acc += A[b * N + n];
+  if (threadIdx.x < lanes * N) atomicAdd(out + n, acc);
+}
+
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, int n, float lr, float c1, float c2,
+                            __nv_bfloat16* __restrict__ wb) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+    w[i] = wi;
+    wb[i] = __float2bfloat16(wi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16(src[i]);
+}
+
+// learned start: T[g] slot s < min(n, 4) from Y (edges keep t2 = 1/2; non-finite or |t| > 1e3 -> 1/2)
+__global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const uint64_t* list, uint64_t first, uint64_t count,
+                                 const float* __restrict__ Y, float* __restrict__ T) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x) {
+    PathDesc d;
+    fetch_path(B, n, list, first + k, d);
+    float2* To = reinterpret_cast<float2*>(T) + d.g * (uint64_t)B.n_max;
+    for (int s = 0; s < n; ++s) {
+      float t0 = 0.5f, t1 = 0.5f;
+      if (s < 4 && !(d.flags & ST_INVALID)) {
+        const float y0 = Y[k * kMlpOut + 2 * s], y1 = Y[k * kMlpOut + 2 * s + 1];
+        const bool edge = S.aux[kAux * d.ids[s] + 2] != 0.f;
+        if (isfinite(y0) && fabsf(y0) < 1e3f) t0 = y0;
+        if (!edge && isfinite(y1) && fabsf(y1) < 1e3f) t1 = y1;
+      }
+      To[s] = make_float2(t0, t1);
+    }
+  }
+}
+
+static unsigned grid_1d(uint64_t n, int threads, int cap) {
+  uint64_t g = (n + threads - 1) / threads;
+  return (unsigned)(g < (uint64_t)cap ? (g ? g : 1) : (uint64_t)cap);
+}
+
+cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
+                                uint64_t count, float inv_scale, __nv_bfloat16* X, cudaStream_t stream) {
+  if (!count) return cudaSuccess;
+  mlp_features_kernel<<<grid_1d(count, 128, 4096), 128, 0, stream>>>(S, B, n, list, first, count, inv_scale, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_loss(const __nv_bfloat16* X, const float* Y, const float* T, uint64_t B, float* dY,
+                            __nv_bfloat16* dYb, float* loss, cudaStream_t stream) {
+  mlp_loss_kernel<<<grid_1d(B, 256, 1024), 256, 0, stream>>>(X, Y, T, B, dY, dYb, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colsum(const float* A, uint64_t B, int N, float* out, cudaStream_t stream) {
+  const int threads = N >= 256 ? N : (256 / N) * N;
+  colsum_kernel<<<grid_1d(B, threads / N, 256), threads, 0, stream>>>(A, B, N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float c1, float c2,
+                        __nv_bfloat16* wb, cudaStream_t stream) {
+  adam_kernel<<<grid_1d(n, 256, 1024), 256, 0, stream>>>(w, m, v, g, n, lr, c1, c2, wb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int n, cudaStream_t stream) {
+  to_bf16_kernel<<<grid_1d(n, 256, 1024), 256, 0, stream>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
+                             uint64_t count, const float* Y, float* T, cudaStream_t stream) {
+  if (!count) return cudaSuccess;
+  mlp_start_kernel<<<grid_1d(count, 128, 4096), 128, 0, stream>>>(S, B, n, list, first, count, Y, T);
+  return cudaGetLastError();
+}
+
 }  // namespace fpt

@@ -128,7 +128,8 @@ struct PathState {
 // are never solved (repeats, invalid input).
 template <int N>
 __device__ __forceinline__ bool path_start(PathState<N>& P, const BatchDev& B, const SceneDev& S, const float* rec,
-                                           int n, const uint64_t* list, uint64_t j, int max_iters) {
+                                           int n, const uint64_t* list, uint64_t j, int max_iters,
+                                           const float* T_start) {
   constexpr int M = PathState<N>::M;
   PathDesc d;
   fetch_path(B, n, list, j, d);
@@ -137,8 +138,18 @@ __device__ __forceinline__ bool path_start(PathState<N>& P, const BatchDev& B, c
   P.it = 0;
   P.conv = false;
   load_geo<N>(d, rec, S, P.G);
+  if (T_start) {  // learned start written by the network pass
+    const float2* Ts = reinterpret_cast<const float2*>(T_start) + d.g * (uint64_t)B.n_max;
 #pragma unroll
-  for (int i = 0; i < N; ++i) P.t[i][0] = P.t[i][1] = 0.5f;
+    for (int i = 0; i < N; ++i) {
+      const float2 v = Ts[i];
+      P.t[i][0] = v.x;
+      P.t[i][1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) P.t[i][0] = P.t[i][1] = 0.5f;
+  }
 #pragma unroll
   for (int r = 0; r < M; ++r)
 #pragma unroll
@@ -273,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, 
     const bool have = j < n_local;
     PathState<N> P;
     bool active = false;
-    if (have) active = path_start<N>(P, B, S, rec, N, list, j, cfg.max_iters);
+    if (have) active = path_start<N>(P, B, S, rec, N, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr);
     while (__any_sync(0xffffffffu, active))
       if (active && bfgs_step<N>(P, cfg)) active = false;
     if (have) path_finish<N>(P, B.n_max, T_out, status_out, iters_out);
@@ -333,7 +344,7 @@ __global__ void __launch_bounds__(kThreads) bfgs_refill_kernel(SceneDev S, Batch
         const unsigned got_mask = __ballot_sync(full, got);
         if (got) {
           const uint64_t j = next + (uint64_t)rank;
-          if (path_start<N>(P, B, S, rec, N, list, j, cfg.max_iters)) {
+          if (path_start<N>(P, B, S, rec, N, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr)) {
             active = true;
           } else {
             path_finish<N>(P, B.n_max, T_out, status_out, iters_out);

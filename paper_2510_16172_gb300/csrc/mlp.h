@@ -5,7 +5,15 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "fpt_device.cuh"
+
 namespace fpt {
+
+constexpr int kMlpIn = 64, kMlpHidden = 256, kMlpOut = 16;
+// offsets of the parameter blocks in the flat FP32 vector
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 256 * 64, kOffW2 = kOffB1 + 256, kOffB2 = kOffW2 + 256 * 256,
+              kOffW3 = kOffB2 + 256, kOffB3 = kOffW3 + 256 * 256, kOffW4 = kOffB3 + 256, kOffB4 = kOffW4 + 16 * 256,
+              kMlpParams = kOffB4 + 16;
 
 enum EpilogueOp { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_GELU = 2, EPI_GELU_GRAD = 3 };
 
@@ -28,5 +36,15 @@ struct GemmArgs {
 };
 
 cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream);
+cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
+                                uint64_t count, float inv_scale, __nv_bfloat16* X, cudaStream_t stream);
+cudaError_t launch_mlp_loss(const __nv_bfloat16* X, const float* Y, const float* T, uint64_t B, float* dY,
+                            __nv_bfloat16* dYb, float* loss, cudaStream_t stream);
+cudaError_t launch_colsum(const float* A, uint64_t B, int N, float* out, cudaStream_t stream);
+cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float c1, float c2,
+                        __nv_bfloat16* wb, cudaStream_t stream);
+cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int n, cudaStream_t stream);
+cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
+                             uint64_t count, const float* Y, float* T, cudaStream_t stream);
 
 }  // namespace fpt

@@ -72,7 +72,7 @@ _SIGS = {
     "fpt_profile_enable": (C.c_int, [_vp, C.c_int]),
     "fpt_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
 }
-K_BFGS, K_POLISH, K_BACKWARD, K_OTHER, K_COUNT = 0, 1, 2, 3, 4
+K_BFGS, K_POLISH, K_BACKWARD, K_OTHER, K_MLP, K_COUNT = 0, 1, 2, 3, 4, 5
 
 _lock = threading.Lock()
 _lib = None
