@@ -1,0 +1,125 @@
+"""FP64 reference of the warm-start network -- TEST INFRASTRUCTURE ONLY.
+
+Plain numpy, following the network's definition (include/fpt.h): BF16 inputs
+and weights, accumulation (here FP64), bias + exact-erf GELU, activations
+rounded to BF16 between layers, and for the gradient the same rounding points
+as the definition fixes (dY and dZ enter the products as BF16, bias gradients
+use the unrounded dZ).  With round_bf16=False everything stays FP64, which the
+finite-difference pins use.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import erf
+
+N_IN, N_H, N_OUT = 64, 256, 16
+SIZES = [("W1", (256, 64)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)), ("b3", (256,)),
+         ("W4", (16, 256)), ("b4", (16,))]
+N_PARAMS = sum(int(np.prod(s)) for _, s in SIZES)
+
+
+def unpack(flat):
+    out, o = {}, 0
+    for name, shape in SIZES:
+        n = int(np.prod(shape))
+        out[name] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(shape)
+        o += n
+    return out
+
+
+def pack(d):
+    return np.concatenate([np.asarray(d[name], dtype=np.float64).ravel() for name, _ in SIZES])
+
+
+def bf16(x):
+    """Round to bfloat16 (round to nearest even on the float32 bit pattern), returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    rounded = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return rounded.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+
+
+def features(scene, ids, order, tx_idx, rx_idx, scale):
+    """The 64 features of each path (definition in include/fpt.h), FP64 before rounding."""
+    M = len(order)
+    F = np.zeros((M, N_IN))
+    for p in range(M):
+        tx, rx = scene.tx[tx_idx[p]], scene.rx[rx_idx[p]]
+        o = 0.5 * (tx + rx)
+        F[p, 0:3] = (tx - o) / scale
+        F[p, 3:6] = (rx - o) / scale
+        for s in range(min(int(order[p]), 4)):
+            k = ids[p, s]
+            v0, v1, v3 = scene.verts[k]
+            edge = scene.types[k] == 1
+            base = 6 + 11 * s
+            F[p, base] = 1.0
+            F[p, base + 1] = 1.0 if edge else 0.0
+            F[p, base + 2:base + 5] = (v0 - o) / scale
+            F[p, base + 5:base + 8] = (v1 - v0) / scale
+            F[p, base + 8:base + 11] = 0.0 if edge else (v3 - v0) / scale
+    return F
+
+
+def forward(params, X, round_bf16=True):
+    P = unpack(params)
+    r = bf16 if round_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    acts = {"X": r(X)}
+    h = acts["X"]
+    for l in (1, 2, 3):
+        z = h @ r(P[f"W{l}"]).T + P[f"b{l}"]
+        acts[f"Z{l}"] = z
+        h = r(gelu(z))
+        acts[f"H{l}"] = h
+    acts["Y"] = h @ r(P["W4"]).T + P["b4"]
+    return acts
+
+
+def loss_and_dY(X, Y, T):
+    """Loss of the definition and its gradient with respect to Y (FP64)."""
+    Xr = np.asarray(X, dtype=np.float64)
+    B = len(Y)
+    loss = 0.0
+    dY = np.zeros_like(Y)
+    for s in range(4):
+        base = 6 + 11 * s
+        act = Xr[:, base] > 0.5
+        a1, a2 = Xr[:, base + 5:base + 8], Xr[:, base + 8:base + 11]
+        d0 = Y[:, 2 * s] - T[:, 2 * s]
+        d1 = Y[:, 2 * s + 1] - T[:, 2 * s + 1]
+        e = a1 * d0[:, None] + a2 * d1[:, None]
+        loss += np.sum(act * np.sum(e * e, axis=1))
+        dY[:, 2 * s] = act * 2.0 * np.sum(a1 * e, axis=1) / B
+        dY[:, 2 * s + 1] = act * 2.0 * np.sum(a2 * e, axis=1) / B
+    return loss / B, dY
+
+
+def loss_grad(params, X, T, round_bf16=True):
+    """Loss and gradient with respect to the flat parameters."""
+    P = unpack(params)
+    r = bf16 if round_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    A = forward(params, X, round_bf16)
+    Xr = A["X"]
+    loss, dY = loss_and_dY(Xr, A["Y"], T)
+    G = {}
+    dYr = r(dY)
+    G["W4"] = dYr.T @ A["H3"]
+    G["b4"] = dY.sum(axis=0)
+    dZ = (dYr @ r(P["W4"])) * gelu_grad(A["Z3"])
+    for l in (3, 2, 1):
+        G[f"b{l}"] = dZ.sum(axis=0)
+        dZr = r(dZ)
+        inp = A[f"H{l - 1}"] if l > 1 else Xr
+        G[f"W{l}"] = dZr.T @ inp
+        if l > 1:
+            dZ = (dZr @ r(P[f"W{l}"])) * gelu_grad(A[f"Z{l - 1}"])
+    return loss, pack(G)

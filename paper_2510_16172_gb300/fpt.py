@@ -69,6 +69,17 @@ _SIGS = {
     "fpt_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint8, _vp, _vp, _vp]),
     "fpt_count_status": (C.c_int, [_vp, _vp, C.c_uint64, C.c_uint8, C.POINTER(C.c_uint64)]),
     "fpt_tc_gemm_bf16": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
+    "fpt_mlp_create": (C.c_int, [_vp, C.c_uint64, C.c_float, C.POINTER(_vp)]),
+    "fpt_mlp_free": (None, [_vp]),
+    "fpt_mlp_get_params": (C.c_int, [_vp, _vp]),
+    "fpt_mlp_set_params": (C.c_int, [_vp, _vp]),
+    "fpt_mlp_save": (C.c_int, [_vp, C.c_char_p]),
+    "fpt_mlp_load": (C.c_int, [_vp, C.c_char_p, C.POINTER(_vp)]),
+    "fpt_mlp_features": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fpt_mlp_forward": (C.c_int, [_vp, _vp, _vp, C.c_uint64, _vp]),
+    "fpt_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, C.POINTER(C.c_float), _vp]),
+    "fpt_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, C.c_float, C.POINTER(C.c_float)]),
+    "fpt_set_init_mlp": (C.c_int, [_vp, _vp]),
     "fpt_profile_enable": (C.c_int, [_vp, C.c_int]),
     "fpt_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
 }
@@ -345,6 +356,94 @@ def profile_read(ctx: Context, reset: bool = True):
     n = (C.c_uint64 * K_COUNT)()
     _check(ctx.handle, library().fpt_profile_read(ctx.handle, ms, n, 1 if reset else 0))
     return list(ms), list(n)
+
+
+MLP_FEATURES, MLP_OUT, MLP_NPARAMS = 64, 16, 152336
+
+
+class Mlp:
+    """Warm-start network (fpt_mlp_*): create (seeded) or load, features, forward, loss/grad, Adam step."""
+
+    def __init__(self, ctx: Context, seed: int = 0, length_scale: float = 10.0, handle=None):
+        self.ctx = ctx
+        if handle is None:
+            h = _vp()
+            _check(ctx.handle, library().fpt_mlp_create(ctx.handle, int(seed), float(length_scale), C.byref(h)))
+            handle = h
+        self.handle = handle
+
+    @classmethod
+    def load(cls, ctx: Context, path: str):
+        h = _vp()
+        _check(ctx.handle, library().fpt_mlp_load(ctx.handle, os.fsencode(path), C.byref(h)))
+        return cls(ctx, handle=h)
+
+    def save(self, path: str):
+        _check(self.ctx.handle, library().fpt_mlp_save(self.handle, os.fsencode(path)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(MLP_NPARAMS, dtype=np.float32)
+        _check(self.ctx.handle, library().fpt_mlp_get_params(self.handle, _ptr(out)))
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_NPARAMS:
+            raise FptError("wrong parameter count")
+        _check(self.ctx.handle, library().fpt_mlp_set_params(self.handle, _ptr(p)))
+
+    def features(self, scene: Scene, batch: Batch):
+        import torch
+
+        X = torch.empty((batch.n_paths, MLP_FEATURES), dtype=torch.bfloat16, device=f"cuda:{self.ctx.device}")
+        _check(self.ctx.handle, library().fpt_mlp_features(self.ctx.handle, self.handle, scene.handle, batch.handle,
+                                                           _ptr(X)))
+        return X
+
+    def forward(self, X):
+        import torch
+
+        _need_cuda(X, torch.bfloat16, "X")
+        Y = torch.empty((X.shape[0], MLP_OUT), dtype=torch.float32, device=X.device)
+        _check(self.ctx.handle, library().fpt_mlp_forward(self.ctx.handle, self.handle, _ptr(X), X.shape[0], _ptr(Y)))
+        return Y
+
+    def loss_grad(self, X, T):
+        import torch
+
+        _need_cuda(X, torch.bfloat16, "X")
+        _need_cuda(T, torch.float32, "T")
+        g = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=X.device)
+        loss = C.c_float(0.0)
+        _check(self.ctx.handle, library().fpt_mlp_loss_grad(self.ctx.handle, self.handle, _ptr(X), _ptr(T), X.shape[0],
+                                                             C.byref(loss), _ptr(g)))
+        return float(loss.value), g
+
+    def train_step(self, X, T, lr: float, want_loss: bool = True):
+        import torch
+
+        _need_cuda(X, torch.bfloat16, "X")
+        _need_cuda(T, torch.float32, "T")
+        loss = C.c_float(0.0)
+        _check(self.ctx.handle, library().fpt_mlp_train_step(self.ctx.handle, self.handle, _ptr(X), _ptr(T),
+                                                              X.shape[0], float(lr),
+                                                              C.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
+
+    def attach(self):
+        """Use this network for fpt_solve with init_mode = 1."""
+        _check(self.ctx.handle, library().fpt_set_init_mlp(self.ctx.handle, self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            library().fpt_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tc_gemm_bf16(ctx: Context, A, W, bias=None, out=None):

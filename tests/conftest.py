@@ -18,3 +18,8 @@ def oracle_lib():
 
     oracle.build()
     return oracle
+
+
+TESTS = os.path.dirname(os.path.abspath(__file__))
+if TESTS not in sys.path:
+    sys.path.insert(0, TESTS)

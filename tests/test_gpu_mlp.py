@@ -1,0 +1,137 @@
+"""Warm-start network on the tensor cores against the FP64 reference (GPU)."""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp_oracle as mo
+from paper_2510_16172_gb300 import fpt, scenes
+
+pytestmark = pytest.mark.gpu
+SCALE = 10.0
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2510_16172_gb300 import build
+
+    build.build()
+    oracle.build()
+    return fpt.Context(0)
+
+
+def numpy_params(seed):
+    rng = np.random.default_rng(seed)
+    P = {}
+    for name, shape in mo.SIZES:
+        if len(shape) == 2:
+            P[name] = rng.uniform(-1, 1, shape) / np.sqrt(shape[1])
+        else:
+            P[name] = 0.05 * rng.standard_normal(shape)
+    P["W4"][8:] = 0.0
+    P["b4"][8:] = 0.0
+    return mo.pack(P).astype(np.float32)
+
+
+def tiny_batch(ctx, seed, lo=1, hi=3):
+    sc = scenes.tiny_scene(seed)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    batch = fpt.Batch.exhaustive(ctx, scene, lo, hi)
+    return sc, scene, batch
+
+
+def test_features_match_definition(ctx):
+    import torch
+
+    sc, scene, batch = tiny_batch(ctx, 0)
+    net = fpt.Mlp(ctx, 1, SCALE)
+    X = net.features(scene, batch).float().cpu().numpy()
+    ids, order, ti, ri = oracle.exhaustive_paths(sc, 1, 3)
+    F = mo.bf16(mo.features(sc, ids, order, ti, ri, SCALE))
+    ulp = np.abs(F) * 2.0 ** -7 + 1e-30
+    assert np.all(np.abs(X - F) <= ulp), np.abs(X - F).max()
+    assert torch.cuda.is_available()
+
+
+def test_forward_and_gradient_match_reference(ctx):
+    import torch
+
+    sc, scene, batch = tiny_batch(ctx, 1)
+    params = numpy_params(5)
+    net = fpt.Mlp(ctx, 0, SCALE)
+    net.set_params(params)
+    X = net.features(scene, batch)
+    ids, order, ti, ri = oracle.exhaustive_paths(sc, 1, 3)
+    Xo = mo.bf16(mo.features(sc, ids, order, ti, ri, SCALE))
+    Y = net.forward(X).cpu().numpy()
+    Yo = mo.forward(params.astype(np.float64), Xo)["Y"]
+    assert np.abs(Y - Yo).max() <= 5e-3 * max(1.0, np.abs(Yo).max())
+    T = np.random.default_rng(6).uniform(-0.5, 1.5, (len(order), 8))
+    loss, g = net.loss_grad(X, torch.as_tensor(T, dtype=torch.float32, device="cuda"))
+    lo, go = mo.loss_grad(params.astype(np.float64), Xo, T)
+    assert abs(loss - lo) <= 2e-3 * abs(lo)
+    g = g.cpu().numpy()
+    assert np.abs(g - go).max() <= 3e-3 * np.abs(go).max(), (np.abs(g - go).max(), np.abs(go).max())
+    # the padded outputs stay zero
+    assert np.all(g[mo.N_PARAMS - 16 - 8 * 256 - 8:mo.N_PARAMS - 16] == 0)
+
+
+def training_set(ctx, seeds, per_pair=20000):
+    """Features and solver outputs (solved paths only) for seeded order 1-4 sequences on tiny scenes."""
+    import torch
+
+    Xs, Ts = [], []
+    net = fpt.Mlp(ctx, 0, SCALE)
+    for sd in seeds:
+        sc = scenes.tiny_scene(sd)
+        scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+        batch = fpt.Batch.seeded(ctx, scene, sd, per_pair, 1, 4)
+        out = fpt.solve(ctx, scene, batch)
+        X = net.features(scene, batch)
+        keep = (out["status"] & fpt.ST_SOLVED) > 0
+        Xs.append(X[keep])
+        Ts.append(out["T"][keep].reshape(-1, 8).contiguous())
+    return torch.cat(Xs).contiguous(), torch.cat(Ts).contiguous()
+
+
+def test_training_reduces_loss_and_checkpoint_resumes(ctx, tmp_path):
+    X, T = training_set(ctx, [11, 12, 13])
+    net = fpt.Mlp(ctx, 3, SCALE)
+    B = 4096
+    n = X.shape[0] // B * B
+    first = net.loss_grad(X[:n], T[:n])[0]
+    for step in range(200):
+        k = (step * B) % n
+        net.train_step(X[k:k + B], T[k:k + B], 2e-3, want_loss=False)
+    path = os.path.join(tmp_path, "net.bin")
+    net.save(path)
+    mid = net.loss_grad(X[:n], T[:n])[0]
+    assert mid < 0.6 * first, (first, mid)
+    other = fpt.Mlp.load(ctx, path)
+    np.testing.assert_array_equal(other.get_params(), net.get_params())
+    for step in range(200, 220):
+        k = (step * B) % n
+        la = net.train_step(X[k:k + B], T[k:k + B], 1e-3)
+        lb = other.train_step(X[k:k + B], T[k:k + B], 1e-3)
+        assert abs(la - lb) <= 1e-3 * abs(la)
+
+
+def test_learned_start_keeps_parity(ctx):
+    from test_gpu_parity import check_parity, oracle_solve, to_np
+
+    X, T = training_set(ctx, [21, 22])
+    net = fpt.Mlp(ctx, 4, SCALE)
+    B = 4096
+    n = X.shape[0] // B * B
+    for step in range(100):
+        k = (step * B) % n
+        net.train_step(X[k:k + B], T[k:k + B], 1e-3, want_loss=False)
+    net.attach()
+    for seed in (31, 32):
+        sc, scene, batch = tiny_batch(ctx, seed)
+        out = fpt.solve(ctx, scene, batch, fpt.default_params(init_mode=1))
+        ctx.sync()
+        ids, order, ti, ri = oracle.exhaustive_paths(sc, 1, 3)
+        check_parity(to_np(out), oracle_solve(sc, ids, order, ti, ri))
