@@ -191,6 +191,28 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* b
                         const uint8_t* status, const float* dX, const float* dL, uint8_t dL_status_mask,
                         float* g_tx, float* g_rx, float* g_vertices);
 
+/* fpt_backward without any device allocation, for callers that cannot
+ * allocate: for example a host application whose GPU memory is entirely
+ * reserved by another allocator (a framework's caching pool), or a latency-
+ * critical loop that forbids cudaMalloc / cudaFree because they can
+ * synchronise the device.  The paper has no counterpart; arguments, outputs
+ * and results are those of fpt_backward.
+ * Its scratch (FP64 gradient sums, the list and counter of the FP64 pass) is
+ * one fixed array inside the library, about 4.5 MB on every GPU that loads
+ * the library, held until the process exits.  Limits: 9 n_obj + 3 (n_tx +
+ * n_rx) <= 65536 and at most 2^20 paths of any one order in the batch;
+ * larger inputs return FPT_EINVAL with a message.  Seeded and explicit
+ * batches must already be bucketed by order (any earlier fpt_solve or
+ * fpt_backward on the batch does that).
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call reuses the same array and clears the sums it needs;
+ * calls that overlap on the GPU (different streams or contexts, same device)
+ * race on it and must be serialised by the caller. */
+fpt_status fpt_backward_noalloc(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* batch, const float* T,
+                                const uint8_t* status, const float* dX, const float* dL, uint8_t dL_status_mask,
+                                float* g_tx, float* g_rx, float* g_vertices);
+
 /* Number of paths whose status has all bits of `mask` set (device status
  * [n]; result written to *count on the host after a stream sync). */
 fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uint8_t mask, uint64_t* count);

@@ -699,6 +699,36 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   return FPT_OK;
 }
 
+fpt_status fpt_backward_noalloc(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* b, const float* T,
+                                const uint8_t* status, const float* dX, const float* dL, uint8_t dL_status_mask,
+                                float* g_tx, float* g_rx, float* g_vertices) {
+  fpt_status st = check_scene_batch(ctx, s, b);
+  if (st != FPT_OK) return st;
+  if (!T) return fail(ctx, FPT_EINVAL, "T is required");
+  if (!dL && dL_status_mask && !status) return fail(ctx, FPT_EINVAL, "dL_status_mask needs status");
+  const long long need = 9LL * s->n_obj + 3LL * (s->n_tx + s->n_rx);
+  if (need > kNoAllocMaxAcc)
+    return fail(ctx, FPT_EINVAL, "fpt_backward_noalloc: 9 n_obj + 3 (n_tx + n_rx) = %lld exceeds its limit %d", need,
+                kNoAllocMaxAcc);
+  if (b->dev.mode != BATCH_EXHAUSTIVE && !b->bucketed)
+    return fail(ctx, FPT_EINVAL, "fpt_backward_noalloc: seeded/explicit batch not bucketed yet (solve it first)");
+  const uint64_t* lists[kMaxOrder + 1] = {nullptr};
+  uint64_t counts[kMaxOrder + 1] = {0};
+  for (int n = 1; n <= kMaxOrder; ++n) {
+    counts[n] = order_slice(b, n, &lists[n]);
+    if (counts[n] > (uint64_t)kNoAllocMaxSlice)
+      return fail(ctx, FPT_EINVAL, "fpt_backward_noalloc: %llu paths of order %d exceed its limit %d",
+                  (unsigned long long)counts[n], n, kNoAllocMaxSlice);
+  }
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  fpt_solve_params p;
+  fpt_default_params(&p);
+  BackwardCfg cfg{p.cond_fp64, p.deg_tol, 1, 64, dL ? (uint8_t)0 : dL_status_mask};
+  CUDA_OR_FAIL(ctx, launch_backward_noalloc(ctx->device, scene_dev(s), b->dev, cfg, lists, counts, T, status, dX, dL,
+                                            g_tx, g_rx, g_vertices, ctx->stream, ctx->n_sm));
+  return FPT_OK;
+}
+
 fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uint8_t mask, uint64_t* count) {
   if (!ctx || !status || !count) return fail(ctx, FPT_EINVAL, "null argument");
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));

@@ -54,6 +54,14 @@ cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const B
                             const uint64_t* list, const float* T, const uint8_t* status, const float* dX,
                             const float* dL, double* gacc, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
                             unsigned* rescue_count);
+// Backward with its scratch in a fixed device array (no allocation): limits below.
+constexpr int kNoAllocMaxAcc = 1 << 16;      // 9 n_obj + 3 (n_tx + n_rx) FP64 accumulators
+constexpr int kNoAllocMaxSlice = 1 << 20;    // paths of one order in the batch
+constexpr int kNoAllocMaxDevices = 64;
+cudaError_t launch_backward_noalloc(int device, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
+                                    const uint64_t* const* lists, const uint64_t* counts, const float* T,
+                                    const uint8_t* status, const float* dX, const float* dL, float* g_tx, float* g_rx,
+                                    float* g_vertices, cudaStream_t stream, int n_sm);
 cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
                                      float* g_rx, float* g_vertices, cudaStream_t stream);
 

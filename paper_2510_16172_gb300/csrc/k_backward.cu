@@ -14,6 +14,8 @@
 // FP64 in global memory) and mapped to vertices by the chain rule of the
 // object records (plane: b = v0, a1 = v1 - v0, a2 = v3 - v0; edge: b = e0,
 // a1 = e1 - e0).
+#include <mutex>
+
 #include "blocktri.cuh"
 #include "fpt_kernels.h"
 
@@ -406,6 +408,59 @@ cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const B
 #undef FPT_BWD_CASE
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Fixed scratch for callers that cannot allocate device memory.
+//
+// One file-scope array holds the FP64 gradient accumulators, the counter and
+// the list of the FP64 pass.  It exists once per GPU that loads the library
+// and lives until the process exits.  Host code must not pass the symbol
+// itself to a kernel (on the host it names a host-side stand-in): its device
+// address is looked up once per device with cudaGetSymbolAddress, with that
+// device current, and cached.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocAccBytes = (size_t)kNoAllocMaxAcc * sizeof(double);
+constexpr size_t kNoAllocCountBytes = 256;
+constexpr size_t kNoAllocBytes = kNoAllocAccBytes + kNoAllocCountBytes + (size_t)kNoAllocMaxSlice * sizeof(uint32_t);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+static cudaError_t noalloc_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // the calling thread has `device` current
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[device]);
+  return cudaSuccess;
+}
+
+cudaError_t launch_backward_noalloc(int device, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
+                                    const uint64_t* const* lists, const uint64_t* counts, const float* T,
+                                    const uint8_t* status, const float* dX, const float* dL, float* g_tx, float* g_rx,
+                                    float* g_vertices, cudaStream_t stream, int n_sm) {
+  unsigned char* base = nullptr;
+  cudaError_t e = noalloc_scratch(device, &base);
+  if (e != cudaSuccess) return e;
+  double* acc = reinterpret_cast<double*>(base);
+  unsigned* count = reinterpret_cast<unsigned*>(base + kNoAllocAccBytes);
+  uint32_t* list = reinterpret_cast<uint32_t*>(base + kNoAllocAccBytes + kNoAllocCountBytes);
+  const size_t need = (size_t)(9 * S.n_obj + 3 * (S.n_tx + S.n_rx));
+  // the array keeps the previous call's sums: clear them
+  e = cudaMemsetAsync(acc, 0, need * sizeof(double), stream);
+  if (e != cudaSuccess) return e;
+  for (int n = 1; n <= kMaxOrder; ++n) {
+    if (!counts[n]) continue;
+    e = launch_backward(n, S, B, cfg, counts[n], lists[n], T, status, dX, dL, acc, stream, n_sm, list, count);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_backward_finalize(S, nullptr, acc, g_tx, g_rx, g_vertices, stream);
 }
 
 cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,

@@ -68,6 +68,7 @@ _SIGS = {
     "fpt_validity": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fpt_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint8, _vp, _vp, _vp]),
     "fpt_count_status": (C.c_int, [_vp, _vp, C.c_uint64, C.c_uint8, C.POINTER(C.c_uint64)]),
+    "fpt_backward_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint8, _vp, _vp, _vp]),
     "fpt_tc_gemm_bf16": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
     "fpt_mlp_create": (C.c_int, [_vp, C.c_uint64, C.c_float, C.POINTER(_vp)]),
     "fpt_mlp_free": (None, [_vp]),
@@ -343,6 +344,31 @@ def backward(ctx: Context, scene: Scene, batch: Batch, T, status=None, dX=None, 
     g_tx, g_rx, g_v = out
     _check(ctx.handle, library().fpt_backward(ctx.handle, scene.handle, batch.handle, _ptr(T), _ptr(status), _ptr(dX),
                                               _ptr(dL), int(dL_status_mask), _ptr(g_tx), _ptr(g_rx), _ptr(g_v)))
+    return g_tx, g_rx, g_v
+
+
+def backward_noalloc(ctx: Context, scene: Scene, batch: Batch, T, status=None, dX=None, dL=None, dL_status_mask=0,
+                     out=None):
+    """fpt_backward_noalloc: same results as backward(), scratch in the library's fixed array.
+
+    The output tensors must be supplied (out = (g_tx, g_rx, g_vertices)) by
+    callers that cannot allocate; when out is None they are created here.
+    """
+    import torch
+
+    _need_cuda(T, torch.float32, "T")
+    _need_cuda(status, torch.uint8, "status")
+    _need_cuda(dX, torch.float32, "dX")
+    _need_cuda(dL, torch.float32, "dL")
+    dev = T.device
+    if out is None:
+        out = (torch.empty((scene.n_tx, 3), dtype=torch.float32, device=dev),
+               torch.empty((scene.n_rx, 3), dtype=torch.float32, device=dev),
+               torch.empty((scene.n_obj, 3, 3), dtype=torch.float32, device=dev))
+    g_tx, g_rx, g_v = out
+    _check(ctx.handle, library().fpt_backward_noalloc(ctx.handle, scene.handle, batch.handle, _ptr(T), _ptr(status),
+                                                      _ptr(dX), _ptr(dL), int(dL_status_mask), _ptr(g_tx),
+                                                      _ptr(g_rx), _ptr(g_v)))
     return g_tx, g_rx, g_v
 
 
