@@ -82,7 +82,8 @@ typedef struct {
   float tol_step;      /* BFGS stops when max_i |A_i s_i| <= tol_step metres (1e-4) */
   float solved_tol;    /* stationarity residual bound for FPT_ST_SOLVED, metres (1e-5) */
   float deg_tol;       /* a solution segment shorter than this (metres) is DEGENERATE (1e-3) */
-  float cond_fp64;     /* Hessian pivot ratio below which the solve is redone in FP64 (1e-4) */
+  float cond_fp64;     /* Hessian pivot ratio below which the adjoint solve is redone in FP64 (1e-4); the
+                          polish, which needs less accuracy, uses 1e-2 x this value */
   int32_t init_mode;   /* 0: plain init, t = 1/2 (object centroid).  1: learned (fpt_set_init_mlp) */
   int32_t polish_fp64; /* 0: polish gradient in double-float FP32 arithmetic (~2^-46, default); 1: in FP64 */
   int32_t refill;      /* lanes of a warp that must be free before it takes new paths (8); 0: one path per
@@ -225,14 +226,18 @@ fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uin
  * activations rounded to BF16 between layers.  Features of a path of order n,
  * with o = (TX + RX) / 2 and S the model's length scale (metres):
  *   f[0..2] = (TX - o)/S, f[3..5] = (RX - o)/S, and for slot s < min(n, 4) at
- *   6 + 11 s: [1, is_edge, (b - o)/S (3), a1/S (3), a2/S (3)]; all else 0.
+ *   6 + 11 s: [1, is_edge, tau_TX (2), tau_RX (2), d_TX, d_RX, |a1|/S, w (2)]
+ *   where tau_P are the parameters of the orthogonal projection of P onto the
+ *   object's affine hull (edge: tau_2 = 0), d_P its distance to the hull / S,
+ *   and w = (d_RX tau_TX + d_TX tau_RX) / (d_TX + d_RX); all else 0.  These are
+ *   TX, RX and the object's origin and basis, expressed in the object's frame.
  * Parameters (FP32, FPT_MLP_NPARAMS floats, in this order): W1 [256][64], b1
  * [256], W2 [256][256], b2 [256], W3 [256][256], b3 [256], W4 [16][256], b4
  * [16] (rows / entries 8..15 of the last layer are zero).
- * Training loss of a batch of B samples with targets t* [B][8]:
- *   (1/B) sum_b sum_{active s} | (a1/S)(y_2s - t*_2s) + (a2/S)(y_2s+1 - t*_2s+1) |^2
- * with a1/S, a2/S read from the sample's (BF16) features: the squared world-
- * space error of the predicted points in units of S.
+ * Training loss of a batch of B samples with targets t* [B][8] and per-slot
+ * Gram matrices G [B][4][3] = (a1.a1, a1.a2, a2.a2) / S^2 (zero for unused
+ * slots):  (1/B) sum_b sum_s (y_s - t*_s)^T G_s (y_s - t*_s), the squared
+ * world-space error of the predicted points in units of S.
  * ------------------------------------------------------------------------- */
 #define FPT_MLP_FEATURES 64
 #define FPT_MLP_OUT 16
@@ -251,20 +256,22 @@ fpt_status fpt_mlp_set_params(fpt_mlp* mlp, const float* host_params);
  * versioned binary file (host path).  FPT_EINVAL on a bad file. */
 fpt_status fpt_mlp_save(const fpt_mlp* mlp, const char* path);
 fpt_status fpt_mlp_load(fpt_ctx* ctx, const char* path, fpt_mlp** out);
-/* Features of every path of a batch: device bf16 output [N][64]. */
+/* Features of every path of a batch: device bf16 output [N][64]; G_out
+ * (device float [N][4][3], may be NULL) receives the loss's Gram matrices. */
 fpt_status fpt_mlp_features(fpt_ctx* ctx, const fpt_mlp* mlp, const fpt_scene* scene, const fpt_batch* batch,
-                            void* X_out);
+                            void* X_out, float* G_out);
 /* Forward pass: X device bf16 [B][64] -> Y device float [B][16]. */
 fpt_status fpt_mlp_forward(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, uint64_t B, float* Y);
 /* Loss and its gradient with respect to the parameters (device float
- * [FPT_MLP_NPARAMS], overwritten) for X [B][64] and targets T [B][8] (device);
- * *loss receives the loss on the host (synchronises). */
-fpt_status fpt_mlp_loss_grad(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const float* T, uint64_t B, float* loss,
-                             float* grad_out);
+ * [FPT_MLP_NPARAMS], overwritten) for X [B][64], targets T [B][8] and Gram
+ * matrices G [B][4][3] (device); *loss receives the loss on the host
+ * (synchronises). */
+fpt_status fpt_mlp_loss_grad(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const float* T, const float* G, uint64_t B,
+                             float* loss, float* grad_out);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
  * loss of this batch; *loss (host, may be NULL) receives the batch loss. */
-fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const float* T, uint64_t B, float lr,
-                              float* loss);
+fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const float* T, const float* G, uint64_t B,
+                              float lr, float* loss);
 /* Network used by fpt_solve when init_mode = 1 (NULL detaches).  The network's
  * prediction seeds the first min(n, 4) interactions of each path; further
  * interactions, edges' second coordinate and non-finite predictions use the

@@ -64,7 +64,7 @@ class _Batch(C.Structure):
                 ("M", C.c_int64), ("n_max", C.c_int), ("ids", _ip), ("order", _ip), ("tx_idx", _ip), ("rx_idx", _ip),
                 ("solver", C.c_int), ("max_iters", C.c_int), ("bfgs", _BfgsParams), ("solved_tol", C.c_double),
                 ("deg_tol", C.c_double),
-                ("T", _dp), ("X", _dp), ("L", _dp), ("rho", _dp), ("bdist", _dp),
+                ("T_start", _dp), ("T", _dp), ("X", _dp), ("L", _dp), ("rho", _dp), ("bdist", _dp),
                 ("status", _ip), ("iters", _ip),
                 ("dX", _dp), ("dL", _dp), ("dtheta", _dp), ("n_threads", C.c_int)]
 
@@ -235,7 +235,7 @@ def seeded_paths(scene, seed: int, per_pair: int, lo: int, hi: int, g=None):
 # --------------------------------------------------------------------------
 def solve(scene, ids, order, tx_idx, rx_idx, solver=NEWTON, max_iters=200, fp_iters=1, alpha0_first=1.0,
           alpha0=1.0, scale_h0=0, safeguard=1, tol_step=0.0, stop_len=0.0, solved_tol=1e-5, deg_tol=DEG_TOL,
-          n_threads=None, dX=None, dL=None):
+          n_threads=None, dX=None, dL=None, T_start=None):
     """Solve every listed path; returns a dict of numpy arrays (and 'dtheta' if cotangents are given)."""
     ids = np.ascontiguousarray(ids, dtype=np.int32)
     M, n_max = ids.shape
@@ -256,6 +256,8 @@ def solve(scene, ids, order, tx_idx, rx_idx, solver=NEWTON, max_iters=200, fp_it
     B.bfgs = _BfgsParams(max_iters, fp_iters, scale_h0, safeguard, alpha0_first, alpha0, tol_step, stop_len)
     B.solved_tol = solved_tol
     B.deg_tol = deg_tol
+    Ts = None if T_start is None else np.ascontiguousarray(T_start, dtype=np.float64).reshape(M, n_max, 2)
+    B.T_start = _p(Ts)
     B.T, B.X, B.L, B.rho, B.bdist = (_p(out[k]) for k in ("T", "X", "L", "rho", "bdist"))
     B.status, B.iters = _p(out["status"], C.c_int32), _p(out["iters"], C.c_int32)
     keep = []

@@ -449,10 +449,12 @@ double orc_fixed_point_alpha(const orc_path* P, const orc_segments* S, const dou
   return alpha;
 }
 
-int orc_bfgs_solve(const orc_path* P, const orc_bfgs_params* prm, double (*t)[2], int* iters_out) {
+/* t holds the start on entry when start_given is set (a learned start), else t = 1/2 */
+int orc_bfgs_solve(const orc_path* P, const orc_bfgs_params* prm, double (*t)[2], int* iters_out, int start_given) {
   int n = P->n, m = 2 * n;
   double H[ORC_MMAX][ORC_MMAX], g[ORC_MMAX], gn[ORC_MMAX], p[ORC_MMAX], s[ORC_MMAX], y[ORC_MMAX];
-  for (int i = 0; i < n; ++i) t[i][0] = t[i][1] = 0.5;
+  if (!start_given)
+    for (int i = 0; i < n; ++i) t[i][0] = t[i][1] = 0.5;
   for (int a = 0; a < m; ++a)
     for (int c = 0; c < m; ++c) H[a][c] = (a == c) ? 1.0 : 0.0;
   orc_segments S;
@@ -734,6 +736,7 @@ typedef struct {
   double solved_tol; /* stationarity tolerance in metres */
   double deg_tol;    /* shortest segment of a non-degenerate solution (metres) */
   /* outputs (any may be NULL) */
+  const double* T_start; /* [M][n_max][2] BFGS start, or NULL for t = 1/2 */
   double* T;   /* [M][n_max][2] */
   double* X;   /* [M][n_max][3] */
   double* L;   /* [M] */
@@ -773,11 +776,16 @@ static void run_one(const orc_batch* B, int64_t p) {
   double t[ORC_NMAX][2];
   int st = build_path(B, p, &P), it = 0;
   for (int i = 0; i < ORC_NMAX; ++i) t[i][0] = t[i][1] = 0.5;
+  if (B->T_start)
+    for (int i = 0; i < P.n && i < B->n_max; ++i) {
+      t[i][0] = B->T_start[(p * B->n_max + i) * 2];
+      t[i][1] = P.type[i] == ORC_EDGE ? 0.5 : B->T_start[(p * B->n_max + i) * 2 + 1];
+    }
   if (!(st & ORC_INVALID_INPUT) && !(st & ORC_REPEAT)) {
     if (B->solver == 0)
       st |= orc_newton_solve(&P, B->max_iters, B->deg_tol, t, &it);
     else
-      st |= orc_bfgs_solve(&P, &B->bfgs, t, &it);
+      st |= orc_bfgs_solve(&P, &B->bfgs, t, &it, B->T_start != NULL);
     orc_segments S;
     segments_of(&P, (const double (*)[2])t, &S);
     if (min_len(&P, &S) < B->deg_tol) st |= ORC_DEGENERATE;
@@ -907,7 +915,7 @@ int orc_path_solve(int n, const int32_t* types, const double* b, const double* c
     st = orc_newton_solve(&P, max_iters, deg_tol, (double (*)[2])t, iters);
   } else {
     orc_bfgs_params prm = {max_iters, fp_iters, scale_h0, safeguard, alpha0_first, alpha0, tol_step, 0.0};
-    st = orc_bfgs_solve(&P, &prm, (double (*)[2])t, iters);
+    st = orc_bfgs_solve(&P, &prm, (double (*)[2])t, iters, 0);
   }
   if (rho) *rho = orc_residual(&P, (const double (*)[2])t);
   return st;

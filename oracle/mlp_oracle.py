@@ -49,9 +49,15 @@ def gelu_grad(z):
 
 
 def features(scene, ids, order, tx_idx, rx_idx, scale):
-    """The 64 features of each path (definition in include/fpt.h), FP64 before rounding."""
+    """The 64 features of each path and the per-slot Gram matrices (definition in include/fpt.h), FP64.
+
+    Per interaction: the parameters tau of the orthogonal projections of TX and
+    RX onto the object's affine hull (least squares in the object's basis), their
+    distances to it, |a1| and the distance-weighted mean of the two projections.
+    """
     M = len(order)
     F = np.zeros((M, N_IN))
+    G = np.zeros((M, 4, 3))
     for p in range(M):
         tx, rx = scene.tx[tx_idx[p]], scene.rx[rx_idx[p]]
         o = 0.5 * (tx + rx)
@@ -61,13 +67,27 @@ def features(scene, ids, order, tx_idx, rx_idx, scale):
             k = ids[p, s]
             v0, v1, v3 = scene.verts[k]
             edge = scene.types[k] == 1
+            a1 = v1 - v0
+            a2 = np.zeros(3) if edge else v3 - v0
+            A = a1[:, None] if edge else np.stack([a1, a2], axis=1)
+            tau, dist = [], []
+            for pt in (tx, rx):
+                c = np.linalg.lstsq(A, pt - v0, rcond=None)[0]
+                t2 = np.zeros(2)
+                t2[:len(c)] = c
+                tau.append(t2)
+                dist.append(np.linalg.norm(pt - v0 - A @ c) / scale)
             base = 6 + 11 * s
             F[p, base] = 1.0
             F[p, base + 1] = 1.0 if edge else 0.0
-            F[p, base + 2:base + 5] = (v0 - o) / scale
-            F[p, base + 5:base + 8] = (v1 - v0) / scale
-            F[p, base + 8:base + 11] = 0.0 if edge else (v3 - v0) / scale
-    return F
+            F[p, base + 2:base + 4] = tau[0]
+            F[p, base + 4:base + 6] = tau[1]
+            F[p, base + 6:base + 8] = dist
+            F[p, base + 8] = np.linalg.norm(a1) / scale
+            ds = dist[0] + dist[1]
+            F[p, base + 9:base + 11] = ((dist[1] * tau[0] + dist[0] * tau[1]) / ds) if ds > 0 else 0.5 * (tau[0] + tau[1])
+            G[p, s] = [a1 @ a1 / scale ** 2, a1 @ a2 / scale ** 2, a2 @ a2 / scale ** 2]
+    return F, G
 
 
 def forward(params, X, round_bf16=True):
@@ -84,42 +104,35 @@ def forward(params, X, round_bf16=True):
     return acts
 
 
-def loss_and_dY(X, Y, T):
-    """Loss of the definition and its gradient with respect to Y (FP64)."""
-    Xr = np.asarray(X, dtype=np.float64)
+def loss_and_dY(G, Y, T):
+    """Loss of the definition, (1/B) sum_b sum_s dy_s^T G_s dy_s, and its gradient with respect to Y (FP64)."""
     B = len(Y)
-    loss = 0.0
+    d = (Y[:, :8] - T).reshape(B, 4, 2)
+    m = np.stack([G[:, :, 0] * d[:, :, 0] + G[:, :, 1] * d[:, :, 1], G[:, :, 1] * d[:, :, 0] + G[:, :, 2] * d[:, :, 1]],
+                 axis=2)
+    loss = np.sum(d * m) / B
     dY = np.zeros_like(Y)
-    for s in range(4):
-        base = 6 + 11 * s
-        act = Xr[:, base] > 0.5
-        a1, a2 = Xr[:, base + 5:base + 8], Xr[:, base + 8:base + 11]
-        d0 = Y[:, 2 * s] - T[:, 2 * s]
-        d1 = Y[:, 2 * s + 1] - T[:, 2 * s + 1]
-        e = a1 * d0[:, None] + a2 * d1[:, None]
-        loss += np.sum(act * np.sum(e * e, axis=1))
-        dY[:, 2 * s] = act * 2.0 * np.sum(a1 * e, axis=1) / B
-        dY[:, 2 * s + 1] = act * 2.0 * np.sum(a2 * e, axis=1) / B
-    return loss / B, dY
+    dY[:, :8] = 2.0 * m.reshape(B, 8) / B
+    return loss, dY
 
 
-def loss_grad(params, X, T, round_bf16=True):
+def loss_grad(params, X, T, G, round_bf16=True):
     """Loss and gradient with respect to the flat parameters."""
     P = unpack(params)
     r = bf16 if round_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     A = forward(params, X, round_bf16)
     Xr = A["X"]
-    loss, dY = loss_and_dY(Xr, A["Y"], T)
-    G = {}
+    loss, dY = loss_and_dY(G, A["Y"], T)
+    grads = {}
     dYr = r(dY)
-    G["W4"] = dYr.T @ A["H3"]
-    G["b4"] = dY.sum(axis=0)
+    grads["W4"] = dYr.T @ A["H3"]
+    grads["b4"] = dY.sum(axis=0)
     dZ = (dYr @ r(P["W4"])) * gelu_grad(A["Z3"])
     for l in (3, 2, 1):
-        G[f"b{l}"] = dZ.sum(axis=0)
+        grads[f"b{l}"] = dZ.sum(axis=0)
         dZr = r(dZ)
         inp = A[f"H{l - 1}"] if l > 1 else Xr
-        G[f"W{l}"] = dZr.T @ inp
+        grads[f"W{l}"] = dZr.T @ inp
         if l > 1:
             dZ = (dZr @ r(P[f"W{l}"])) * gelu_grad(A[f"Z{l - 1}"])
-    return loss, pack(G)
+    return loss, pack(grads)

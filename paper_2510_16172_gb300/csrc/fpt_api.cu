@@ -123,6 +123,8 @@ struct fpt_mlp {
   float* d_v = nullptr;
   float* d_g = nullptr;          // gradient
   __nv_bfloat16* d_wb = nullptr;  // BF16 copy used by the tensor cores
+  __nv_bfloat16* d_wt = nullptr;  // BF16 weights pre-tiled for the fused inference kernel
+  bool wt_stale = true;
   float* d_loss = nullptr;
   // activations / gradients for a batch of up to cap rows
   uint64_t cap = 0;
@@ -594,26 +596,23 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
   const SceneDev S = scene_dev(s);
   SolveCfg sc{p.max_iters, p.fp_iters, p.fixed_iters, p.tol_step * p.tol_step, 0.01f * p.deg_tol * p.deg_tol,
               p.refill > 32 ? 32 : p.refill, p.init_mode == 1};
-  PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, p.cond_fp64, p.polish_fp64};
+  // the polish needs its Newton step only to a modest relative accuracy: 100x looser pivot test than the adjoint
+  PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, p.polish_fp64};
   for (int n = 1; n <= kMaxOrder; ++n) {
     const uint64_t* list;
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
     if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
     if (p.init_mode == 1) {
-      // learned start: features -> network -> T, in chunks of the network's workspace
+      // learned start: fused features -> network -> T on the tensor cores
       fpt_mlp* m = ctx->init_mlp;
-      const uint64_t chunk = 1ull << 18;
-      st = mlp_ensure_ws(ctx, m, chunk, false);
-      if (st != FPT_OK) return st;
-      ProfScope ps(ctx, FPT_K_MLP);
-      for (uint64_t first = 0; first < cnt; first += chunk) {
-        const uint64_t c = cnt - first < chunk ? cnt - first : chunk;
-        CUDA_OR_FAIL(ctx, launch_mlp_features(S, b->dev, n, list, first, c, 1.f / m->scale, m->d_X, ctx->stream));
-        st = mlp_forward_impl(ctx, m, m->d_X, c, m->d_Y, false);
-        if (st != FPT_OK) return st;
-        CUDA_OR_FAIL(ctx, launch_mlp_start(S, b->dev, n, list, first, c, m->d_Y, T, ctx->stream));
+      if (m->wt_stale) {
+        CUDA_OR_FAIL(ctx, launch_mlp_tile_weights(m->d_wb, m->d_wt, ctx->stream));
+        m->wt_stale = false;
       }
+      ProfScope ps(ctx, FPT_K_MLP);
+      CUDA_OR_FAIL(ctx, launch_mlp_infer(S, b->dev, n, list, cnt, 1.f / m->scale, m->d_wt, m->d_w, T, ctx->d_err,
+                                         ctx->stream, ctx->n_sm));
     }
     {
       ProfScope ps(ctx, FPT_K_BFGS);
@@ -642,7 +641,7 @@ fpt_status fpt_validity(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   fpt_solve_params p;
   fpt_default_params(&p);
   const SceneDev S = scene_dev(s);
-  PolishCfg pc{POLISH_VALIDITY, 0, p.solved_tol, p.deg_tol, p.cond_fp64, 0};
+  PolishCfg pc{POLISH_VALIDITY, 0, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, 0};
   for (int n = 1; n <= kMaxOrder; ++n) {
     const uint64_t* list;
     uint64_t cnt = order_slice(b, n, &list);
@@ -837,7 +836,8 @@ static fpt_status mlp_forward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16
 }
 
 // loss and gradient (into m->d_g) of a batch; loss accumulated in m->d_loss
-static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16* X, const float* T, uint64_t B) {
+static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16* X, const float* T, const float* G,
+                                    uint64_t B) {
   const int Bi = (int)B;
   const int ks = Bi >= 2048 ? Bi / 1024 : 1;  // split the batch reduction of the weight gradients
   const __nv_bfloat16* W = m->d_wb;
@@ -845,7 +845,7 @@ static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat1
   CUDA_OR_FAIL(ctx, cudaMemsetAsync(m->d_loss, 0, sizeof(float), ctx->stream));
   fpt_status st = mlp_forward_impl(ctx, m, X, B, m->d_Y, true);
   if (st != FPT_OK) return st;
-  CUDA_OR_FAIL(ctx, launch_mlp_loss(X, m->d_Y, T, B, m->d_dY, m->d_dYb, m->d_loss, ctx->stream));
+  CUDA_OR_FAIL(ctx, launch_mlp_loss(G, m->d_Y, T, B, m->d_dY, m->d_dYb, m->d_loss, ctx->stream));
   // last layer: dW4^T[in][out] = sum_b H3[b][in] dY[b][out]; db4 = sum_b dY
   {
     GemmArgs g = gemm_args(kMlpHidden, kMlpOut, Bi, m->d_H3, 1, kMlpHidden, m->d_dYb, 1, kMlpOut, EPI_ATOMIC, ctx->d_err);
@@ -928,6 +928,7 @@ fpt_status fpt_mlp_create(fpt_ctx* ctx, uint64_t seed, float length_scale, fpt_m
   for (float** p : {&m->d_w, &m->d_m, &m->d_v, &m->d_g})
     if (e == cudaSuccess) e = cudaMalloc(p, kMlpParams * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->d_wb, kMlpParams * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_wt, kMlpTiledBytes);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_loss, sizeof(float));
   if (e != cudaSuccess) {
     fpt_mlp_free(m);
@@ -960,7 +961,8 @@ void fpt_mlp_free(fpt_mlp* m) {
   if (!m) return;
   if (m->ctx && m->ctx->init_mlp == m) m->ctx->init_mlp = nullptr;
   mlp_free_ws(m);
-  for (void* p : {(void*)m->d_w, (void*)m->d_m, (void*)m->d_v, (void*)m->d_g, (void*)m->d_wb, (void*)m->d_loss})
+  for (void* p : {(void*)m->d_w, (void*)m->d_m, (void*)m->d_v, (void*)m->d_g, (void*)m->d_wb, (void*)m->d_wt,
+                  (void*)m->d_loss})
     cudaFree(p);
   delete m;
 }
@@ -987,6 +989,7 @@ fpt_status fpt_mlp_set_params(fpt_mlp* m, const float* host) {
   CUDA_OR_FAIL(ctx, launch_to_bf16(m->d_w, m->d_wb, kMlpParams, ctx->stream));
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
   m->step = 0;
+  m->wt_stale = true;
   return FPT_OK;
 }
 
@@ -1046,14 +1049,15 @@ fpt_status fpt_mlp_load(fpt_ctx* ctx, const char* path, fpt_mlp** out) {
   return FPT_OK;
 }
 
-fpt_status fpt_mlp_features(fpt_ctx* ctx, const fpt_mlp* m, const fpt_scene* s, const fpt_batch* b, void* X) {
+fpt_status fpt_mlp_features(fpt_ctx* ctx, const fpt_mlp* m, const fpt_scene* s, const fpt_batch* b, void* X,
+                            float* G) {
   fpt_status st = check_scene_batch(ctx, s, b);
   if (st != FPT_OK) return st;
   if (!m || !X) return fail(ctx, FPT_EINVAL, "null argument");
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   ProfScope ps(ctx, FPT_K_OTHER);
   CUDA_OR_FAIL(ctx, launch_mlp_features(scene_dev(s), b->dev, 0, nullptr, 0, b->dev.n_paths, 1.f / m->scale,
-                                        static_cast<__nv_bfloat16*>(X), ctx->stream));
+                                        static_cast<__nv_bfloat16*>(X), G, ctx->stream));
   return FPT_OK;
 }
 
@@ -1067,14 +1071,14 @@ fpt_status fpt_mlp_forward(fpt_ctx* ctx, fpt_mlp* m, const void* X, uint64_t B, 
   return mlp_forward_impl(ctx, m, static_cast<const __nv_bfloat16*>(X), B, Y, false);
 }
 
-fpt_status fpt_mlp_loss_grad(fpt_ctx* ctx, fpt_mlp* m, const void* X, const float* T, uint64_t B, float* loss,
-                             float* grad_out) {
-  if (!ctx || !m || !X || !T) return fail(ctx, FPT_EINVAL, "null argument");
+fpt_status fpt_mlp_loss_grad(fpt_ctx* ctx, fpt_mlp* m, const void* X, const float* T, const float* G, uint64_t B,
+                             float* loss, float* grad_out) {
+  if (!ctx || !m || !X || !T || !G) return fail(ctx, FPT_EINVAL, "null argument");
   if (B < 1 || B > (1ull << 30)) return fail(ctx, FPT_EINVAL, "bad batch size");
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   fpt_status st = mlp_ensure_ws(ctx, m, B, true);
   if (st != FPT_OK) return st;
-  st = mlp_backward_impl(ctx, m, static_cast<const __nv_bfloat16*>(X), T, B);
+  st = mlp_backward_impl(ctx, m, static_cast<const __nv_bfloat16*>(X), T, G, B);
   if (st != FPT_OK) return st;
   if (grad_out)
     CUDA_OR_FAIL(ctx, cudaMemcpyAsync(grad_out, m->d_g, kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1085,14 +1089,15 @@ fpt_status fpt_mlp_loss_grad(fpt_ctx* ctx, fpt_mlp* m, const void* X, const floa
   return FPT_OK;
 }
 
-fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* m, const void* X, const float* T, uint64_t B, float lr,
-                              float* loss) {
+fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* m, const void* X, const float* T, const float* G, uint64_t B,
+                              float lr, float* loss) {
   if (!(lr > 0.f)) return fail(ctx, FPT_EINVAL, "learning rate must be positive");
-  fpt_status st = fpt_mlp_loss_grad(ctx, m, X, T, B, nullptr, nullptr);
+  fpt_status st = fpt_mlp_loss_grad(ctx, m, X, T, G, B, nullptr, nullptr);
   if (st != FPT_OK) return st;
   m->step += 1;
   const float c1 = 1.f - std::pow(0.9f, (float)m->step), c2 = 1.f - std::pow(0.999f, (float)m->step);
   CUDA_OR_FAIL(ctx, launch_adam(m->d_w, m->d_m, m->d_v, m->d_g, kMlpParams, lr, c1, c2, m->d_wb, ctx->stream));
+  m->wt_stale = true;
   if (loss) {
     CUDA_OR_FAIL(ctx, cudaMemcpyAsync(loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));

@@ -179,9 +179,13 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
 // features, loss, bias gradients, Adam, learned start
 // ---------------------------------------------------------------------------
 
-// 64 features of one path (see include/fpt.h): origin o = (TX + RX)/2, scale S.
+// 64 features of one path (see include/fpt.h): origin o = (TX + RX)/2, scale S;
+// per interaction the orthogonal projections of TX and RX onto the object's
+// affine hull in its own parameters, their distances to it, the first basis
+// length, and the distance-weighted combination of the two projections.  Also
+// the per-slot Gram matrix A^T A / S^2 (g11, g12, g22) of the loss.
 __device__ __forceinline__ void path_features(const SceneDev& S, const PathDesc& d, float inv_scale,
-                                              __nv_bfloat16* f) {
+                                              __nv_bfloat16* f, float* G) {
   float tx[3], rx[3], o[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -189,9 +193,11 @@ __device__ __forceinline__ void path_features(const SceneDev& S, const PathDesc&
     rx[c] = S.rx32[kEnd32 * d.rx + c] + S.rx32[kEnd32 * d.rx + 3 + c];
     o[c] = 0.5f * (tx[c] + rx[c]);
   }
-  float v[kMlpIn];
+  float v[kMlpIn], gram[12];
 #pragma unroll
   for (int k = 0; k < kMlpIn; ++k) v[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) gram[k] = 0.f;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     v[c] = (tx[c] - o[c]) * inv_scale;
@@ -202,15 +208,61 @@ __device__ __forceinline__ void path_features(const SceneDev& S, const PathDesc&
   for (int s = 0; s < 4; ++s) {
     if (s < d.n && valid) {
       const float* r = S.rec32 + kRec32 * d.ids[s];
-      const int base = 6 + 11 * s;
-      v[base] = 1.f;
-      v[base + 1] = S.aux[kAux * d.ids[s] + 2];
+      const bool edge = S.aux[kAux * d.ids[s] + 2] != 0.f;
+      float b[3], a1[3], a2[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        v[base + 2 + c] = ((r[c] + r[3 + c]) - o[c]) * inv_scale;
-        v[base + 5 + c] = r[6 + c] * inv_scale;
-        v[base + 8 + c] = r[9 + c] * inv_scale;
+        b[c] = r[c] + r[3 + c];
+        a1[c] = r[6 + c];
+        a2[c] = r[9 + c];
       }
+      const float g11 = a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2];
+      const float g12 = a1[0] * a2[0] + a1[1] * a2[1] + a1[2] * a2[2];
+      const float g22 = a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2];
+      const float det = g11 * g22 - g12 * g12;
+      float tau[2][2], dist[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float* pt = q == 0 ? tx : rx;
+        float rr[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rr[c] = pt[c] - b[c];
+        const float c1 = a1[0] * rr[0] + a1[1] * rr[1] + a1[2] * rr[2];
+        const float c2 = a2[0] * rr[0] + a2[1] * rr[1] + a2[2] * rr[2];
+        if (edge) {
+          tau[q][0] = c1 / g11;
+          tau[q][1] = 0.f;
+        } else {
+          tau[q][0] = (g22 * c1 - g12 * c2) / det;
+          tau[q][1] = (g11 * c2 - g12 * c1) / det;
+        }
+        float e2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float e = rr[c] - tau[q][0] * a1[c] - tau[q][1] * a2[c];
+          e2 += e * e;
+        }
+        dist[q] = sqrtf(e2) * inv_scale;
+      }
+      const int base = 6 + 11 * s;
+      v[base] = 1.f;
+      v[base + 1] = edge ? 1.f : 0.f;
+      v[base + 2] = tau[0][0];
+      v[base + 3] = tau[0][1];
+      v[base + 4] = tau[1][0];
+      v[base + 5] = tau[1][1];
+      v[base + 6] = dist[0];
+      v[base + 7] = dist[1];
+      v[base + 8] = sqrtf(g11) * inv_scale;
+      const float dsum = dist[0] + dist[1];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        v[base + 9 + k] = dsum > 0.f ? (dist[1] * tau[0][k] + dist[0] * tau[1][k]) / dsum
+                                     : 0.5f * (tau[0][k] + tau[1][k]);
+      const float is2 = inv_scale * inv_scale;
+      gram[3 * s] = g11 * is2;
+      gram[3 * s + 1] = g12 * is2;
+      gram[3 * s + 2] = g22 * is2;
     }
   }
 #pragma unroll
@@ -220,23 +272,26 @@ __device__ __forceinline__ void path_features(const SceneDev& S, const PathDesc&
     for (int q = 0; q < 8; ++q) e[q] = __float2bfloat16(v[k + q]);
     *reinterpret_cast<uint4*>(f + k) = *reinterpret_cast<uint4*>(e);
   }
+  if (G)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) G[k] = gram[k];
 }
 
 // all paths of a batch (global index order) or one order slice (local index order)
 __global__ void mlp_features_kernel(SceneDev S, BatchDev B, int n, const uint64_t* list, uint64_t first,
-                                    uint64_t count, float inv_scale, __nv_bfloat16* X) {
+                                    uint64_t count, float inv_scale, __nv_bfloat16* X, float* G) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x) {
     PathDesc d;
     if (n > 0)
       fetch_path(B, n, list, first + k, d);
     else
       decode_global(B, first + k, d);
-    path_features(S, d, inv_scale, X + k * kMlpIn);
+    path_features(S, d, inv_scale, X + k * kMlpIn, G ? G + k * 12 : nullptr);
   }
 }
 
-// loss (1/B) sum_b sum_active |(a1/S) dy_2s + (a2/S) dy_2s+1|^2 and dY
-__global__ void mlp_loss_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ Y,
+// loss (1/B) sum_b sum_s dy_s^T G_s dy_s (G_s = A_s^T A_s / S^2 per slot, zero for unused slots) and dY
+__global__ void mlp_loss_kernel(const float* __restrict__ G, const float* __restrict__ Y,
                                 const float* __restrict__ T, uint64_t B, float* __restrict__ dY,
                                 __nv_bfloat16* __restrict__ dYb, float* loss) {
   float acc = 0.f;
@@ -245,24 +300,15 @@ __global__ void mlp_loss_kernel(const __nv_bfloat16* __restrict__ X, const float
     float g[kMlpOut];
 #pragma unroll
     for (int k = 0; k < kMlpOut; ++k) g[k] = 0.f;
-    const __nv_bfloat16* f = X + b * kMlpIn;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      const int base = 6 + 11 * s;
-      if (__bfloat162float(f[base]) > 0.5f) {
-        const float d0 = Y[b * kMlpOut + 2 * s] - T[b * 8 + 2 * s];
-        const float d1 = Y[b * kMlpOut + 2 * s + 1] - T[b * 8 + 2 * s + 1];
-        float e[3], a1[3], a2[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          a1[c] = __bfloat162float(f[base + 5 + c]);
-          a2[c] = __bfloat162float(f[base + 8 + c]);
-          e[c] = a1[c] * d0 + a2[c] * d1;
-        }
-        acc += e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-        g[2 * s] = w * (a1[0] * e[0] + a1[1] * e[1] + a1[2] * e[2]);
-        g[2 * s + 1] = w * (a2[0] * e[0] + a2[1] * e[1] + a2[2] * e[2]);
-      }
+      const float g11 = G[b * 12 + 3 * s], g12 = G[b * 12 + 3 * s + 1], g22 = G[b * 12 + 3 * s + 2];
+      const float d0 = Y[b * kMlpOut + 2 * s] - T[b * 8 + 2 * s];
+      const float d1 = Y[b * kMlpOut + 2 * s + 1] - T[b * 8 + 2 * s + 1];
+      const float m0 = g11 * d0 + g12 * d1, m1 = g12 * d0 + g22 * d1;
+      acc += d0 * m0 + d1 * m1;
+      g[2 * s] = w * m0;
+      g[2 * s + 1] = w * m1;
     }
 #pragma unroll
     for (int k = 0; k < kMlpOut; ++k) {
@@ -324,21 +370,244 @@ __global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const uint64_t* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused, persistent inference for the learned start (one CTA per SM).
+//
+// Per tile of 128 paths: features are computed straight into the shared
+// activation tile (K-major, K = 64), then four layers run on the tensor cores
+// with the accumulator in TMEM; each epilogue adds the bias, applies GELU and
+// writes the BF16 activations back into the same tile (K = 256) for the next
+// layer; the last one writes the starting parameters into T.  The weights
+// stream through two 32 KB shared buffers as 13 chunks per tile (64 input
+// columns each, pre-tiled in global memory so that a chunk is one contiguous
+// TMA bulk copy), prefetched one chunk ahead: thread 0 waits for the MMAs that
+// last read a buffer before refilling it.  All waits are bounded.
+// ---------------------------------------------------------------------------
+constexpr int kInferThreads = 256;
+constexpr int kChunksPerTile = 13;  // W1: 1, W2: 4, W3: 4, W4: 4 chunks of 64 input columns
+
+__host__ __device__ constexpr int chunk_layer(int q) { return q == 0 ? 0 : (q <= 4 ? 1 : (q <= 8 ? 2 : 3)); }
+__host__ __device__ constexpr int chunk_col(int q) { return q == 0 ? 0 : (q - 1) % 4; }
+__host__ __device__ constexpr uint32_t chunk_bytes(int q) { return chunk_layer(q) == 3 ? 16u * 64u * 2u : 256u * 64u * 2u; }
+__host__ __device__ constexpr uint32_t chunk_offset(int q) {
+  return q <= 8 ? (uint32_t)q * 32768u : 9u * 32768u + (uint32_t)(q - 9) * 2048u;
+}
+
+// bf16 parameter copy ([out][in] per layer) -> chunked K-major tiles
+__global__ void mlp_tile_weights_kernel(const __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt) {
+  const int n1 = 256 * 64, n2 = 256 * 256, n4 = 16 * 256;
+  const int total = n1 + 2 * n2 + n4;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int layer, r, k, K, off;
+    if (idx < n1) {
+      layer = 0; K = 64; off = kOffW1; r = idx / K; k = idx % K;
+    } else if (idx < n1 + n2) {
+      layer = 1; K = 256; off = kOffW2; r = (idx - n1) / K; k = (idx - n1) % K;
+    } else if (idx < n1 + 2 * n2) {
+      layer = 2; K = 256; off = kOffW3; r = (idx - n1 - n2) / K; k = (idx - n1 - n2) % K;
+    } else {
+      layer = 3; K = 256; off = kOffW4; r = (idx - n1 - 2 * n2) / K; k = (idx - n1 - 2 * n2) % K;
+    }
+    const int c = k / 64;
+    const int q = layer == 0 ? 0 : 1 + (layer - 1) * 4 + c;
+    const uint32_t byte = chunk_offset(q) + tc::kmajor_offset(r, k % 64, 64);
+    wt[byte / 2] = wb[off + r * K + k];
+  }
+}
+
+struct InferSmem {
+  unsigned char act[128 * 256 * 2];
+  unsigned char wbuf[2][256 * 64 * 2];
+  float bias[3 * 256 + 16];
+  uint64_t full[2], done[2], layer;
+  uint32_t tmem;
+  int fail;
+};
+
+__global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S, BatchDev B, int n,
+                                                                     const uint64_t* __restrict__ list, uint64_t count,
+                                                                     float inv_scale,
+                                                                     const __nv_bfloat16* __restrict__ wt,
+                                                                     const float* __restrict__ params, float* T,
+                                                                     int* err) {
+  extern __shared__ __align__(1024) unsigned char infer_smem[];
+  InferSmem& sm = *reinterpret_cast<InferSmem*>(infer_smem);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t n_tiles = (count + 127) / 128;
+  const uint64_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const uint64_t total_q = my_tiles * kChunksPerTile;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&sm.full[b], 1);
+      tc::mbar_init(&sm.done[b], 1);
+    }
+    tc::mbar_init(&sm.layer, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sm.fail = 0;
+  }
+  for (int i = tid; i < 256; i += blockDim.x) {
+    sm.bias[i] = params[kOffB1 + i];
+    sm.bias[256 + i] = params[kOffB2 + i];
+    sm.bias[512 + i] = params[kOffB3 + i];
+  }
+  if (tid < 16) sm.bias[768 + tid] = params[kOffB4 + tid];
+  if (warp == 0) {
+    tc::tmem_alloc(&sm.tmem, 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = sm.tmem;
+  const char* wsrc = reinterpret_cast<const char*>(wt);
+  uint32_t full_ph[2] = {0u, 0u}, done_ph[2] = {0u, 0u}, layer_ph = 0u;
+  if (tid == 0 && total_q > 0) {
+    tc::mbar_expect_tx(&sm.full[0], chunk_bytes(0));
+    tc::bulk_g2s(sm.wbuf[0], wsrc + chunk_offset(0), chunk_bytes(0), &sm.full[0]);
+  }
+  uint64_t q = 0;
+  for (uint64_t ti = 0; ti < my_tiles; ++ti) {
+    const uint64_t first = (blockIdx.x + ti * gridDim.x) * 128;
+    // features of the tile's 128 paths (K = 64 layout)
+    if (tid < 128) {
+      __nv_bfloat16 f[kMlpIn];
+      if (first + tid < count) {
+        PathDesc d;
+        fetch_path(B, n, list, first + tid, d);
+        path_features(S, d, inv_scale, f, nullptr);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) f[k] = __float2bfloat16(0.f);
+      }
+#pragma unroll
+      for (int g8 = 0; g8 < kMlpIn / 8; ++g8)
+        *reinterpret_cast<uint4*>(sm.act + tc::kmajor_offset(tid, g8 * 8, 64)) = reinterpret_cast<uint4*>(f)[g8];
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    for (int lq = 0; lq < kChunksPerTile; ++lq, ++q) {
+      const int b = (int)(q & 1);
+      const int layer = chunk_layer(lq), c = chunk_col(lq);
+      if (tid == 0) {
+        // refill the other buffer with the next chunk once the MMAs that read it (chunk q - 1) are done
+        if (q + 1 < total_q) {
+          const int nb = b ^ 1;
+          if (q >= 1) {
+            if (!tc::mbar_wait(&sm.done[nb], done_ph[nb], kWaitTries)) sm.fail = 1;
+            done_ph[nb] ^= 1u;
+          }
+          const int nq = (lq + 1) % kChunksPerTile;
+          tc::mbar_expect_tx(&sm.full[nb], chunk_bytes(nq));
+          tc::bulk_g2s(sm.wbuf[nb], wsrc + chunk_offset(nq), chunk_bytes(nq), &sm.full[nb]);
+        }
+        if (!tc::mbar_wait(&sm.full[b], full_ph[b], kWaitTries)) sm.fail = 1;
+        full_ph[b] ^= 1u;
+        tc::fence_after_sync();
+        const uint32_t K_act = layer == 0 ? 64u : 256u;
+        const uint32_t N = layer == 3 ? 16u : 256u;
+        const uint32_t a0 = tc::smem_u32(sm.act), w0 = tc::smem_u32(sm.wbuf[b]);
+        if (!sm.fail) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(c * 8 + 2 * kk) * 128u, 128u, (K_act / 8u) * 128u);
+            const uint64_t bd = tc::smem_desc(w0 + (uint32_t)(2 * kk) * 128u, 128u, 8u * 128u);
+            tc::mma_bf16(tmem, ad, bd, tc::idesc_bf16(128, N), (c > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&sm.done[b]);
+        if (layer == 0 || c == 3) tc::mma_commit(&sm.layer);
+      }
+      if (!(layer == 0 || c == 3)) continue;
+      // end of a layer: wait for its MMAs, then the epilogue
+      if (!tc::mbar_wait(&sm.layer, layer_ph, kWaitTries)) sm.fail = 1;
+      layer_ph ^= 1u;
+      tc::fence_after_sync();
+      const int rg = warp & 3;  // TMEM lane group of this warp
+      const int row = rg * 32 + lane;
+      if (layer < 3) {
+        const int c0 = (warp >> 2) * 128;
+        for (int cc = c0; cc < c0 + 128; cc += 16) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(rg * 32) << 16) + (uint32_t)cc, v);
+          __nv_bfloat16 h[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) h[k] = __float2bfloat16(gelu(v[k] + sm.bias[layer * 256 + cc + k]));
+          *reinterpret_cast<uint4*>(sm.act + tc::kmajor_offset(row, cc, 256)) = reinterpret_cast<uint4*>(h)[0];
+          *reinterpret_cast<uint4*>(sm.act + tc::kmajor_offset(row, cc + 8, 256)) = reinterpret_cast<uint4*>(h)[1];
+        }
+      } else if (warp < 4) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(rg * 32) << 16), v);
+        if (first + row < count) {
+          PathDesc d;
+          fetch_path(B, n, list, first + row, d);
+          float2* To = reinterpret_cast<float2*>(T) + d.g * (uint64_t)B.n_max;
+          for (int s = 0; s < n; ++s) {
+            float t0 = 0.5f, t1 = 0.5f;
+            if (s < 4 && !(d.flags & ST_INVALID)) {
+              const float y0 = v[2 * s] + sm.bias[768 + 2 * s], y1 = v[2 * s + 1] + sm.bias[768 + 2 * s + 1];
+              const bool edge = S.aux[kAux * d.ids[s] + 2] != 0.f;
+              if (isfinite(y0) && fabsf(y0) < 1e3f) t0 = y0;
+              if (!edge && isfinite(y1) && fabsf(y1) < 1e3f) t1 = y1;
+            }
+            To[s] = make_float2(t0, t1);
+          }
+        }
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (sm.fail) break;
+    }
+    if (sm.fail) break;
+  }
+  if (sm.fail && tid == 0) {
+    if (err) atomicCAS(err, 0, ERR_MMA_TIMEOUT);
+    tc::mbar_wait(&sm.layer, layer_ph, kWaitTries);  // let MMAs in flight finish before TMEM is freed
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+cudaError_t launch_mlp_tile_weights(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t stream) {
+  mlp_tile_weights_kernel<<<128, 256, 0, stream>>>(wb, wt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_infer(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t count,
+                             float inv_scale, const __nv_bfloat16* wt, const float* params, float* T, int* err,
+                             cudaStream_t stream, int n_sm) {
+  if (!count) return cudaSuccess;
+  static bool attr = false;
+  const int smem = (int)sizeof(InferSmem);
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const uint64_t tiles = (count + 127) / 128;
+  const unsigned grid = (unsigned)(tiles < (uint64_t)n_sm ? tiles : (uint64_t)n_sm);
+  mlp_infer_kernel<<<grid, kInferThreads, smem, stream>>>(S, B, n, list, count, inv_scale, wt, params, T, err);
+  return cudaGetLastError();
+}
+
 static unsigned grid_1d(uint64_t n, int threads, int cap) {
   uint64_t g = (n + threads - 1) / threads;
   return (unsigned)(g < (uint64_t)cap ? (g ? g : 1) : (uint64_t)cap);
 }
 
 cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
-                                uint64_t count, float inv_scale, __nv_bfloat16* X, cudaStream_t stream) {
+                                uint64_t count, float inv_scale, __nv_bfloat16* X, float* G, cudaStream_t stream) {
   if (!count) return cudaSuccess;
-  mlp_features_kernel<<<grid_1d(count, 128, 4096), 128, 0, stream>>>(S, B, n, list, first, count, inv_scale, X);
+  mlp_features_kernel<<<grid_1d(count, 128, 4096), 128, 0, stream>>>(S, B, n, list, first, count, inv_scale, X, G);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_loss(const __nv_bfloat16* X, const float* Y, const float* T, uint64_t B, float* dY,
+cudaError_t launch_mlp_loss(const float* G, const float* Y, const float* T, uint64_t B, float* dY,
                             __nv_bfloat16* dYb, float* loss, cudaStream_t stream) {
-  mlp_loss_kernel<<<grid_1d(B, 256, 1024), 256, 0, stream>>>(X, Y, T, B, dY, dYb, loss);
+  mlp_loss_kernel<<<grid_1d(B, 256, 1024), 256, 0, stream>>>(G, Y, T, B, dY, dYb, loss);
   return cudaGetLastError();
 }
 

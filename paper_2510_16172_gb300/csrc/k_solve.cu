@@ -12,7 +12,8 @@
 // Readings of points the paper leaves open: H_0 = I; every step starts the
 // fixed point at alpha = 1 and, if that yields alpha <= 0, restarts it at
 // alpha = 0 (one round from 0 is a majorise-minimise step, positive along a
-// descent direction); the update is skipped unless s^T y > 1e-6 |s| |y|.
+// descent direction); the update is skipped unless s^T y > 1e-6 |s| |y|
+// (tested as (s^T y)^2 > 1e-12 |s|^2 |y|^2 with s^T y > 0).
 #include "fpt_kernels.h"
 
 namespace fpt {
@@ -216,8 +217,8 @@ __device__ __forceinline__ bool bfgs_step(PathState<N>& P, const SolveCfg& cfg) 
     P.g[r] = gn[r];
   }
   // BFGS inverse update: H += -rho (Hy s^T + s (Hy)^T) + (rho^2 y^T H y + rho) s s^T
-  if (sy > 1e-6f * sqrtf(ss * yy)) {
-    float rho = __frcp_rn(sy);
+  if (sy > 0.f && sy * sy > 1e-12f * (ss * yy)) {
+    const float rho = __fdividef(1.f, sy);
     float Hy[M], yHy = 0.f;
 #pragma unroll
     for (int r = 0; r < M; ++r) {

@@ -76,10 +76,10 @@ _SIGS = {
     "fpt_mlp_set_params": (C.c_int, [_vp, _vp]),
     "fpt_mlp_save": (C.c_int, [_vp, C.c_char_p]),
     "fpt_mlp_load": (C.c_int, [_vp, C.c_char_p, C.POINTER(_vp)]),
-    "fpt_mlp_features": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fpt_mlp_features": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "fpt_mlp_forward": (C.c_int, [_vp, _vp, _vp, C.c_uint64, _vp]),
-    "fpt_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, C.POINTER(C.c_float), _vp]),
-    "fpt_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, C.c_float, C.POINTER(C.c_float)]),
+    "fpt_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, C.POINTER(C.c_float), _vp]),
+    "fpt_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, C.c_float, C.POINTER(C.c_float)]),
     "fpt_set_init_mlp": (C.c_int, [_vp, _vp]),
     "fpt_profile_enable": (C.c_int, [_vp, C.c_int]),
     "fpt_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
@@ -418,13 +418,16 @@ class Mlp:
             raise FptError("wrong parameter count")
         _check(self.ctx.handle, library().fpt_mlp_set_params(self.handle, _ptr(p)))
 
-    def features(self, scene: Scene, batch: Batch):
+    def features(self, scene: Scene, batch: Batch, with_gram: bool = False):
+        """Features [N, 64] (bf16), and with with_gram the loss's Gram matrices [N, 4, 3]."""
         import torch
 
-        X = torch.empty((batch.n_paths, MLP_FEATURES), dtype=torch.bfloat16, device=f"cuda:{self.ctx.device}")
+        dev = f"cuda:{self.ctx.device}"
+        X = torch.empty((batch.n_paths, MLP_FEATURES), dtype=torch.bfloat16, device=dev)
+        G = torch.empty((batch.n_paths, 4, 3), dtype=torch.float32, device=dev) if with_gram else None
         _check(self.ctx.handle, library().fpt_mlp_features(self.ctx.handle, self.handle, scene.handle, batch.handle,
-                                                           _ptr(X)))
-        return X
+                                                           _ptr(X), _ptr(G)))
+        return (X, G) if with_gram else X
 
     def forward(self, X):
         import torch
@@ -434,24 +437,26 @@ class Mlp:
         _check(self.ctx.handle, library().fpt_mlp_forward(self.ctx.handle, self.handle, _ptr(X), X.shape[0], _ptr(Y)))
         return Y
 
-    def loss_grad(self, X, T):
+    def loss_grad(self, X, T, G):
         import torch
 
         _need_cuda(X, torch.bfloat16, "X")
         _need_cuda(T, torch.float32, "T")
+        _need_cuda(G, torch.float32, "G")
         g = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=X.device)
         loss = C.c_float(0.0)
-        _check(self.ctx.handle, library().fpt_mlp_loss_grad(self.ctx.handle, self.handle, _ptr(X), _ptr(T), X.shape[0],
-                                                             C.byref(loss), _ptr(g)))
+        _check(self.ctx.handle, library().fpt_mlp_loss_grad(self.ctx.handle, self.handle, _ptr(X), _ptr(T), _ptr(G),
+                                                             X.shape[0], C.byref(loss), _ptr(g)))
         return float(loss.value), g
 
-    def train_step(self, X, T, lr: float, want_loss: bool = True):
+    def train_step(self, X, T, G, lr: float, want_loss: bool = True):
         import torch
 
         _need_cuda(X, torch.bfloat16, "X")
         _need_cuda(T, torch.float32, "T")
+        _need_cuda(G, torch.float32, "G")
         loss = C.c_float(0.0)
-        _check(self.ctx.handle, library().fpt_mlp_train_step(self.ctx.handle, self.handle, _ptr(X), _ptr(T),
+        _check(self.ctx.handle, library().fpt_mlp_train_step(self.ctx.handle, self.handle, _ptr(X), _ptr(T), _ptr(G),
                                                               X.shape[0], float(lr),
                                                               C.byref(loss) if want_loss else None))
         return float(loss.value) if want_loss else None

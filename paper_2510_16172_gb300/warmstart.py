@@ -22,27 +22,29 @@ LENGTH_SCALE = 10.0
 
 
 def make_dataset(ctx, seeds=TRAIN_SEEDS, per_pair=200_000, order_lo=1, order_hi=4, net=None):
-    """Features (bf16 [n, 64]) and solved parameters (float [n, 8]) of the solved paths of seeded batches."""
+    """Features (bf16 [n, 64]), solved parameters (float [n, 8]) and loss Gram matrices (float [n, 4, 3])
+    of the solved paths of seeded batches."""
     import torch
 
     net = net or fpt.Mlp(ctx, 0, LENGTH_SCALE)
-    Xs, Ts = [], []
+    Xs, Ts, Gs = [], [], []
     for sd in seeds:
         sc = scenes.tiny_scene(sd)
         scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
         batch = fpt.Batch.seeded(ctx, scene, sd, per_pair, order_lo, order_hi)
         out = fpt.solve(ctx, scene, batch)
-        X = net.features(scene, batch)
+        X, G = net.features(scene, batch, with_gram=True)
         keep = (out["status"] & fpt.ST_SOLVED) > 0
         T = torch.zeros((batch.n_paths, 4, 2), dtype=torch.float32, device=X.device)
         m = min(4, batch.n_max)
         T[:, :m] = out["T"][:, :m]
         Xs.append(X[keep])
         Ts.append(T[keep].reshape(-1, 8))
-    return torch.cat(Xs).contiguous(), torch.cat(Ts).contiguous()
+        Gs.append(G[keep])
+    return torch.cat(Xs).contiguous(), torch.cat(Ts).contiguous(), torch.cat(Gs).contiguous()
 
 
-def train(ctx, X, T, epochs=3, batch=8192, lr=1e-3, seed=0, log=None):
+def train(ctx, X, T, G, epochs=3, batch=8192, lr=1e-3, seed=0, log=None):
     """Adam on shuffled mini-batches; returns the network and the per-epoch mean loss."""
     import torch
 
@@ -52,11 +54,12 @@ def train(ctx, X, T, epochs=3, batch=8192, lr=1e-3, seed=0, log=None):
     history = []
     for ep in range(epochs):
         perm = torch.randperm(X.shape[0], generator=g, device=X.device)[:n]
-        Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
+        Xp, Tp, Gp = X[perm].contiguous(), T[perm].contiguous(), G[perm].contiguous()
         rate = lr * (0.5 ** ep)
         for k in range(0, n, batch):
-            net.train_step(Xp[k:k + batch], Tp[k:k + batch], rate, want_loss=False)
-        history.append(net.loss_grad(X[:min(n, 65536)], T[:min(n, 65536)])[0])
+            net.train_step(Xp[k:k + batch], Tp[k:k + batch], Gp[k:k + batch], rate, want_loss=False)
+        m = min(n, 65536)
+        history.append(net.loss_grad(X[:m], T[:m], G[:m])[0])
         if log:
             log(f"epoch {ep}: loss {history[-1]:.5f}")
     return net, history
@@ -106,9 +109,9 @@ def evaluate(ctx, net, seeds=EVAL_SEEDS, per_pair=1_000_000, order_lo=1, order_h
 
 def run(ctx, per_pair_train=200_000, per_pair_eval=1_000_000, epochs=3, log=None):
     t0 = time.perf_counter()
-    X, T = make_dataset(ctx, per_pair=per_pair_train)
+    X, T, G = make_dataset(ctx, per_pair=per_pair_train)
     t1 = time.perf_counter()
-    net, hist = train(ctx, X, T, epochs=epochs, log=log)
+    net, hist = train(ctx, X, T, G, epochs=epochs, log=log)
     t2 = time.perf_counter()
     ev = evaluate(ctx, net, per_pair=per_pair_eval)
     ev["train_samples"] = int(X.shape[0])

@@ -47,11 +47,15 @@ def test_features_match_definition(ctx):
 
     sc, scene, batch = tiny_batch(ctx, 0)
     net = fpt.Mlp(ctx, 1, SCALE)
-    X = net.features(scene, batch).float().cpu().numpy()
+    X, G = net.features(scene, batch, with_gram=True)
+    X, G = X.float().cpu().numpy(), G.cpu().numpy()
     ids, order, ti, ri = oracle.exhaustive_paths(sc, 1, 3)
-    F = mo.bf16(mo.features(sc, ids, order, ti, ri, SCALE))
-    ulp = np.abs(F) * 2.0 ** -7 + 1e-30
+    F, Go = mo.features(sc, ids, order, ti, ri, SCALE)
+    F = mo.bf16(F)
+    # FP32 projections rounded to bf16 may land one bf16 step away from the FP64 ones
+    ulp = np.abs(F) * 2.0 ** -7 + 1e-6
     assert np.all(np.abs(X - F) <= ulp), np.abs(X - F).max()
+    np.testing.assert_allclose(G, Go, rtol=1e-5, atol=1e-7)
     assert torch.cuda.is_available()
 
 
@@ -62,15 +66,16 @@ def test_forward_and_gradient_match_reference(ctx):
     params = numpy_params(5)
     net = fpt.Mlp(ctx, 0, SCALE)
     net.set_params(params)
-    X = net.features(scene, batch)
+    X, G = net.features(scene, batch, with_gram=True)
     ids, order, ti, ri = oracle.exhaustive_paths(sc, 1, 3)
-    Xo = mo.bf16(mo.features(sc, ids, order, ti, ri, SCALE))
+    Fo, Go = mo.features(sc, ids, order, ti, ri, SCALE)
+    Xo = mo.bf16(Fo)
     Y = net.forward(X).cpu().numpy()
     Yo = mo.forward(params.astype(np.float64), Xo)["Y"]
     assert np.abs(Y - Yo).max() <= 5e-3 * max(1.0, np.abs(Yo).max())
     T = np.random.default_rng(6).uniform(-0.5, 1.5, (len(order), 8))
-    loss, g = net.loss_grad(X, torch.as_tensor(T, dtype=torch.float32, device="cuda"))
-    lo, go = mo.loss_grad(params.astype(np.float64), Xo, T)
+    loss, g = net.loss_grad(X, torch.as_tensor(T, dtype=torch.float32, device="cuda"), G)
+    lo, go = mo.loss_grad(params.astype(np.float64), Xo, T, Go)
     assert abs(loss - lo) <= 2e-3 * abs(lo)
     g = g.cpu().numpy()
     assert np.abs(g - go).max() <= 3e-3 * np.abs(go).max(), (np.abs(g - go).max(), np.abs(go).max())
@@ -82,52 +87,43 @@ def training_set(ctx, seeds, per_pair=20000):
     """Features and solver outputs (solved paths only) for seeded order 1-4 sequences on tiny scenes."""
     import torch
 
-    Xs, Ts = [], []
-    net = fpt.Mlp(ctx, 0, SCALE)
-    for sd in seeds:
-        sc = scenes.tiny_scene(sd)
-        scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
-        batch = fpt.Batch.seeded(ctx, scene, sd, per_pair, 1, 4)
-        out = fpt.solve(ctx, scene, batch)
-        X = net.features(scene, batch)
-        keep = (out["status"] & fpt.ST_SOLVED) > 0
-        Xs.append(X[keep])
-        Ts.append(out["T"][keep].reshape(-1, 8).contiguous())
-    return torch.cat(Xs).contiguous(), torch.cat(Ts).contiguous()
+    from paper_2510_16172_gb300 import warmstart
+
+    return warmstart.make_dataset(ctx, seeds, per_pair)
 
 
 def test_training_reduces_loss_and_checkpoint_resumes(ctx, tmp_path):
-    X, T = training_set(ctx, [11, 12, 13])
+    X, T, G = training_set(ctx, [11, 12, 13])
     net = fpt.Mlp(ctx, 3, SCALE)
     B = 4096
     n = X.shape[0] // B * B
-    first = net.loss_grad(X[:n], T[:n])[0]
+    first = net.loss_grad(X[:n], T[:n], G[:n])[0]
     for step in range(200):
         k = (step * B) % n
-        net.train_step(X[k:k + B], T[k:k + B], 2e-3, want_loss=False)
+        net.train_step(X[k:k + B], T[k:k + B], G[k:k + B], 2e-3, want_loss=False)
     path = os.path.join(tmp_path, "net.bin")
     net.save(path)
-    mid = net.loss_grad(X[:n], T[:n])[0]
+    mid = net.loss_grad(X[:n], T[:n], G[:n])[0]
     assert mid < 0.6 * first, (first, mid)
     other = fpt.Mlp.load(ctx, path)
     np.testing.assert_array_equal(other.get_params(), net.get_params())
     for step in range(200, 220):
         k = (step * B) % n
-        la = net.train_step(X[k:k + B], T[k:k + B], 1e-3)
-        lb = other.train_step(X[k:k + B], T[k:k + B], 1e-3)
+        la = net.train_step(X[k:k + B], T[k:k + B], G[k:k + B], 1e-3)
+        lb = other.train_step(X[k:k + B], T[k:k + B], G[k:k + B], 1e-3)
         assert abs(la - lb) <= 1e-3 * abs(la)
 
 
 def test_learned_start_keeps_parity(ctx):
     from test_gpu_parity import check_parity, oracle_solve, to_np
 
-    X, T = training_set(ctx, [21, 22])
+    X, T, G = training_set(ctx, [21, 22])
     net = fpt.Mlp(ctx, 4, SCALE)
     B = 4096
     n = X.shape[0] // B * B
     for step in range(100):
         k = (step * B) % n
-        net.train_step(X[k:k + B], T[k:k + B], 1e-3, want_loss=False)
+        net.train_step(X[k:k + B], T[k:k + B], G[k:k + B], 1e-3, want_loss=False)
     net.attach()
     for seed in (31, 32):
         sc, scene, batch = tiny_batch(ctx, seed)
@@ -135,3 +131,30 @@ def test_learned_start_keeps_parity(ctx):
         ctx.sync()
         ids, order, ti, ri = oracle.exhaustive_paths(sc, 1, 3)
         check_parity(to_np(out), oracle_solve(sc, ids, order, ti, ri))
+
+
+@pytest.mark.parametrize("seed", [41, 42])
+def test_fused_inference_start_matches_reference(ctx, seed):
+    """The fused tensor-core inference writes the network's prediction as the start (checked with no BFGS steps)."""
+    params = numpy_params(seed)
+    net = fpt.Mlp(ctx, 0, SCALE)
+    net.set_params(params)
+    net.attach()
+    sc = scenes.tiny_scene(seed, n_rx=3)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    batch = fpt.Batch.seeded(ctx, scene, seed, 3000, 1, 5)  # 9000 paths: ragged last tile, orders 1-5
+    out = fpt.solve(ctx, scene, batch, fpt.default_params(init_mode=1, max_iters=0, polish=0))
+    ctx.sync()
+    T = out["T"].cpu().numpy()
+    ids, order, ti, ri = oracle.seeded_paths(sc, seed, 3000, 1, 5)
+    Fo, _ = mo.features(sc, ids, order, ti, ri, SCALE)
+    Y = mo.forward(params.astype(np.float64), mo.bf16(Fo))["Y"]
+    expect = np.full(T.shape, 0.5)
+    for p in range(len(order)):
+        for s in range(min(order[p], 4)):
+            expect[p, s, 0] = Y[p, 2 * s]
+            if sc.types[ids[p, s]] == scenes.QUAD:
+                expect[p, s, 1] = Y[p, 2 * s + 1]
+    used = np.arange(T.shape[1])[None, :] < order[:, None]
+    err = np.abs(T - expect)[used]
+    assert err.max() <= 5e-3 * max(1.0, np.abs(Y).max()), err.max()
