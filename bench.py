@@ -43,24 +43,28 @@ L2_FLUSH_BYTES = 512 << 20
 # ---------------------------------------------------------------------------
 # algorithmic work (FP32 flops, FMA = 2) of the BFGS kernel, per path
 # ---------------------------------------------------------------------------
-def bfgs_flops_per_iter(n: int, fp: int) -> int:
-    """Static op count of one BFGS step of order n with fp rounds of Eq. 6 (k_solve.cu)."""
-    m, s = 2 * n, n + 1
+def bfgs_flops_per_iter(n: int, fp: int, nq: int | None = None) -> int:
+    """Static op count of one BFGS step of order n with nq planar reflectors (2 parameters each) and n - nq
+    edges (1 parameter each), fp rounds of Eq. 6 (bfgs.cuh).  nq = n is the unified d = 2 kernel."""
+    nq = n if nq is None else nq
+    ne = n - nq
+    m, s = n + nq, n + 1
     hp = m * (m + 1) // 2
     direction = 2 * m * m + m              # p = -H g
-    world = 15 * n                         # A_i p_i and |A_i p_i|^2
+    world = 15 * nq + 9 * ne               # A_i p_i and |A_i p_i|^2
     segs = 3 * (n - 1) + 10 * s            # q_j, q_j.z_j, q_j.q_j
     fixed = fp * (9 * s + 1)               # Eq. 6 rounds
     step = 2 * m                           # s = alpha p, t += s
-    grad = 28 * n + 9 * s                  # z_j, |z_j|, u_j, g
+    grad = 28 * nq + 17 * ne + 9 * s       # z_j, |z_j|, u_j, g
     curv = 7 * m + 4                       # y, s.y, s.s, y.y, guard
     update = 1 + 2 * m * m + 2 * m + 3 + 4 * m + 4 * hp  # inverse-Hessian update
     conv = 2 + n
     return direction + world + segs + fixed + step + grad + curv + update + conv
 
 
-def bfgs_flops_init(n: int) -> int:
-    return 28 * n + 9 * (n + 1)
+def bfgs_flops_init(n: int, nq: int | None = None) -> int:
+    nq = n if nq is None else nq
+    return 28 * nq + 17 * (n - nq) + 9 * (n + 1)
 
 
 def measured_peaks():
@@ -138,7 +142,7 @@ def gpu_identifier(torch, dev) -> str:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("k_solve.cu", "k_polish.cu", "blocktri.cuh", "fpt_device.cuh"):
+    for fn in ("bfgs.cuh", "k_bfgs.cu", "k_polish.cu", "blocktri.cuh", "fpt_device.cuh"):
         with open(os.path.join(ROOT, "paper_2510_16172_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -293,13 +297,25 @@ def run_ours(args, world, rank, local_rank):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    per_launch = {k: (kms[k] / klaunch[k] if klaunch[k] else 0.0) for k in range(fpt.K_COUNT)}
-    bfgs_flops = bfgs_flops_init(3) * run_paths + bfgs_flops_per_iter(3, params.fp_iters) * total_iters
-    names = {fpt.K_BFGS: "bfgs_refill_kernel<3>", fpt.K_POLISH: "polish_ff_kernel<3> + polish64_kernel<3> (rescue)",
-             fpt.K_BACKWARD: "backward_kernel<3> + backward_rescue_kernel<3>", fpt.K_OTHER: "backward_finalize_kernel"}
+    # algorithmic flops of the pattern kernels: per path, its pattern's count per step x its steps
+    ids = fpt.enumerate(ctx, batch)[0]
+    is_quad = torch.tensor(np.asarray(sc.types) == scenes.QUAD, device=dev)
+    nq = is_quad[ids.long()].sum(dim=1)
+    del ids
+    run = (out["status"] & fpt.ST_REPEAT) == 0
+    f_step = torch.tensor([bfgs_flops_per_iter(3, params.fp_iters, q) for q in range(4)], dtype=torch.float64,
+                          device=dev)
+    f_init = torch.tensor([bfgs_flops_init(3, q) for q in range(4)], dtype=torch.float64, device=dev)
+    bfgs_flops = float(((f_init[nq] + f_step[nq] * iters.double()) * run.double()).sum().item())
+    del nq, run
+    names = {fpt.K_BFGS: "bfgs_refill_kernel<3, Q> (8 reflector/edge patterns)",
+             fpt.K_POLISH: "polish_ff_kernel<3> + polish64_kernel<3> (rescue)",
+             fpt.K_BACKWARD: "backward_kernel<3> + backward_rescue_kernel<3>", fpt.K_OTHER: "backward_finalize_kernel",
+             fpt.K_MLP: "mlp_infer_kernel (learned start)"}
     dom = max(range(fpt.K_COUNT), key=lambda k: kms[k])
     clocks = clk.summary()
-    roof_bfgs = {"kernel": names[fpt.K_BFGS], "bound": "alu", "achieved": bfgs_flops / (per_launch[0] * 1e-3) / 1e12,
+    roof_bfgs = {"kernel": names[fpt.K_BFGS], "bound": "alu",
+                 "achieved": bfgs_flops / (kms[fpt.K_BFGS] / args.steps * 1e-3) / 1e12,
                  "peak": fp32_peak, "unit": "TFLOP/s",
                  "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured peaks)",
                  "traffic": NCU_TRAFFIC.get((kernel_source_hash(), "bfgs"))}
@@ -314,7 +330,7 @@ def run_ours(args, world, rank, local_rank):
                        "polish": "1 Newton step, double-float gradient (FP64 for ill-conditioned Hessians)",
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "solved_per_step": solved, "solved_fraction": solved / N, "mean_bfgs_iters": total_iters / max(1, run_paths),
-            "kernel_ms_per_step": {names[k]: kms[k] / args.steps for k in range(fpt.K_COUNT)},
+            "kernel_ms_per_step": {names[k]: kms[k] / args.steps for k in range(fpt.K_COUNT) if klaunch[k]},
             "dominant_kernel": names[dom],
             "roofline": roof_bfgs,
             "gpu_launches": int(sum(klaunch)),

@@ -88,7 +88,11 @@ typedef struct {
   int32_t polish_fp64; /* 0: polish gradient in double-float FP32 arithmetic (~2^-46, default); 1: in FP64 */
   int32_t refill;      /* lanes of a warp that must be free before it takes new paths (8); 0: one path per
                           lane until the whole warp is done */
-  int32_t reserved[5]; /* must be zero */
+  int32_t specialize;  /* 1: BFGS runs one kernel per interaction-type pattern (reflector/edge per slot), which
+                          drops the edge's always-zero second parameter from the iteration and yields the same
+                          iterates as the unified kernel; 0: the unified kernel of Sec. III-B only (1; refill = 0
+                          implies 0) */
+  int32_t reserved[4]; /* must be zero */
 } fpt_solve_params;
 
 typedef struct fpt_ctx fpt_ctx;
@@ -135,7 +139,10 @@ fpt_status fpt_set_endpoints(fpt_scene* scene, const double* tx, int32_t n_tx, c
  * Explicit: caller-owned device arrays ids [n][n_max] (object ids),
  *   order [n], tx_idx [n], rx_idx [n].
  * FPT_EINVAL on lo < 1, hi > 5, lo > hi, empty alphabet or ids out of range
- * (host-checked arrays only). */
+ * (host-checked arrays only).  A batch records the object types of the
+ * scene it was built for; calls that pass a scene with other types return
+ * FPT_EINVAL.  Seeded and explicit batches are bucketed on the device by
+ * (order, interaction-type pattern) on their first use (synchronous). */
 fpt_status fpt_batch_exhaustive(fpt_ctx* ctx, const fpt_scene* scene, const int32_t* alphabet, int32_t n_alpha,
                                 int32_t order_lo, int32_t order_hi, fpt_batch** out);
 fpt_status fpt_batch_seeded(fpt_ctx* ctx, const fpt_scene* scene, const int32_t* alphabet, int32_t n_alpha,
@@ -286,10 +293,11 @@ fpt_status fpt_set_init_mlp(fpt_ctx* ctx, fpt_mlp* mlp);
 fpt_status fpt_tc_gemm_bf16(fpt_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A, const void* W,
                             const float* bias, float* C);
 
-/* Kernel timing.  While enabled, every kernel the context launches is
- * bracketed by CUDA events on the context's stream, and fpt_profile_read()
- * returns, per kernel class, the summed device time in milliseconds and the
- * number of launches (it synchronises the stream; reset != 0 clears the sums). */
+/* Kernel timing.  While enabled, the kernels of each class that one call
+ * launches are bracketed by CUDA events on the context's stream, and
+ * fpt_profile_read() returns, per kernel class, the summed device time in
+ * milliseconds and the number of kernels launched (it synchronises the
+ * stream; reset != 0 clears the sums). */
 enum { FPT_K_BFGS = 0, FPT_K_POLISH = 1, FPT_K_BACKWARD = 2, FPT_K_OTHER = 3, FPT_K_MLP = 4, FPT_K_COUNT = 5 };
 fpt_status fpt_profile_enable(fpt_ctx* ctx, int on);
 fpt_status fpt_profile_read(fpt_ctx* ctx, double* ms, uint64_t* launches, int reset);

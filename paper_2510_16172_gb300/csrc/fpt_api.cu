@@ -27,7 +27,11 @@ struct fpt_ctx {
   double* d_gacc = nullptr;                // backward accumulators (FP64)
   size_t gacc_cap = 0;
   unsigned long long* d_count = nullptr;   // counters for reductions
-  unsigned long long* d_work = nullptr;    // work counter of the lane-refill solver
+  unsigned long long* d_work = nullptr;    // work counters of the lane-refill solver (one per concurrent launch)
+  static constexpr int kSide = 4;          // side streams for the independent pattern launches of one order
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kSide] = {};
   uint32_t* d_rescue = nullptr;            // paths whose FP32 Hessian pivots failed (polish scratch)
   size_t rescue_cap = 0;
   unsigned* d_rescue_n = nullptr;
@@ -38,13 +42,14 @@ struct fpt_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double prof_ms[FPT_K_COUNT] = {0, 0, 0, 0, 0};
-  uint64_t prof_n[FPT_K_COUNT] = {0, 0, 0, 0, 0};
+  uint64_t prof_kernels[FPT_K_COUNT] = {0, 0, 0, 0, 0};
 };
 
-// Event pair around one launch when timing is on.
+// Event pair around the launches of one call when timing is on; counts the kernels launched in between.
 struct ProfScope {
   fpt_ctx* ctx;
   int cls;
+  uint64_t k0 = 0;
   cudaEvent_t a = nullptr, b = nullptr;
   static cudaEvent_t take(fpt_ctx* c) {
     cudaEvent_t e = nullptr;
@@ -58,12 +63,15 @@ struct ProfScope {
   }
   ProfScope(fpt_ctx* c, int k) : ctx(c), cls(k) {
     if (!ctx->prof) return;
+    k0 = tl_kernel_launches;
     a = take(ctx);
     b = take(ctx);
     if (a) cudaEventRecord(a, ctx->stream);
   }
   ~ProfScope() {
-    if (!ctx->prof || !a || !b) return;
+    if (!ctx->prof) return;
+    ctx->prof_kernels[cls] += tl_kernel_launches - k0;
+    if (!a || !b) return;
     cudaEventRecord(b, ctx->stream);
     ctx->ev_pending.push_back({cls, {a, b}});
   }
@@ -89,11 +97,13 @@ struct fpt_batch {
   fpt_ctx* ctx = nullptr;
   BatchDev dev{};
   int32_t* d_alphabet = nullptr;
-  // order buckets of seeded / explicit batches (built on first use)
+  int32_t* d_type_pos = nullptr;  // alphabet positions of the reflectors, then of the edges
+  std::vector<uint8_t> types;     // object types of the scene the batch was built for
+  // (order, pattern) buckets of seeded / explicit batches (built on first use)
   bool bucketed = false;
   uint64_t* d_lists = nullptr;
-  uint64_t count[kMaxOrder + 1] = {0};
-  uint64_t start[kMaxOrder + 1] = {0};
+  uint64_t count[kPatternKeys] = {0};
+  uint64_t start[kPatternKeys] = {0};
 };
 
 static fpt_status fail(fpt_ctx* ctx, fpt_status st, const char* fmt, ...) {
@@ -174,6 +184,7 @@ void fpt_default_params(fpt_solve_params* p) {
   p->init_mode = 0;
   p->polish_fp64 = 0;
   p->refill = 8;
+  p->specialize = 1;
 }
 
 fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
@@ -187,8 +198,13 @@ fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, 8 * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_work, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, 64 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_work, 64 * sizeof(unsigned long long));
+  for (int k = 0; k < fpt_ctx::kSide && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_rescue_n, sizeof(unsigned));
   if (e != cudaSuccess) {
     fpt_destroy(ctx);
@@ -210,6 +226,11 @@ void fpt_destroy(fpt_ctx* ctx) {
   cudaFree(ctx->d_gacc);
   cudaFree(ctx->d_count);
   cudaFree(ctx->d_work);
+  for (int k = 0; k < fpt_ctx::kSide; ++k) {
+    if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+    if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   cudaFree(ctx->d_rescue);
   cudaFree(ctx->d_rescue_n);
   delete ctx;
@@ -388,6 +409,17 @@ static fpt_status make_alphabet(fpt_ctx* ctx, const fpt_scene* s, const int32_t*
   CUDA_OR_FAIL(ctx, cudaMemcpy(b->d_alphabet, a.data(), a.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   b->dev.alphabet = b->d_alphabet;
   b->dev.n_alpha = (int)a.size();
+  // positions of the reflectors, then of the edges: the exhaustive enumeration by pattern
+  std::vector<int32_t> pos;
+  for (int pass = 0; pass < 2; ++pass)
+    for (size_t k = 0; k < a.size(); ++k)
+      if ((s->types[a[k]] == FPT_QUAD) == (pass == 0)) pos.push_back((int32_t)k);
+  b->dev.n_alpha_quad = 0;
+  for (int32_t o : a) b->dev.n_alpha_quad += s->types[o] == FPT_QUAD;
+  CUDA_OR_FAIL(ctx, cudaMalloc(&b->d_type_pos, pos.size() * sizeof(int32_t)));
+  CUDA_OR_FAIL(ctx, cudaMemcpy(b->d_type_pos, pos.data(), pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  b->dev.type_pos = b->d_type_pos;
+  b->types = s->types;
   return FPT_OK;
 }
 
@@ -496,6 +528,7 @@ fpt_status fpt_batch_explicit(fpt_ctx* ctx, const fpt_scene* s, const int32_t* i
   d.order = order_dev;
   d.tx_idx = tx_idx_dev;
   d.rx_idx = rx_idx_dev;
+  b->types = s->types;
   *out = b;
   return FPT_OK;
 }
@@ -510,6 +543,7 @@ fpt_status fpt_batch_size(const fpt_batch* b, uint64_t* n_paths, int32_t* n_max)
 void fpt_batch_free(fpt_batch* b) {
   if (!b) return;
   cudaFree(b->d_alphabet);
+  cudaFree(b->d_type_pos);
   cudaFree(b->d_lists);
   delete b;
 }
@@ -522,26 +556,26 @@ fpt_status fpt_enumerate(fpt_ctx* ctx, const fpt_batch* b, int32_t* ids, uint8_t
   return FPT_OK;
 }
 
-// Bucket a seeded/explicit batch by order (once per batch; synchronous).
-static fpt_status ensure_buckets(fpt_ctx* ctx, fpt_batch* b) {
+// Bucket a seeded/explicit batch by (order, pattern) (once per batch; synchronous).
+static fpt_status ensure_buckets(fpt_ctx* ctx, fpt_batch* b, const SceneDev& S) {
   if (b->dev.mode == BATCH_EXHAUSTIVE || b->bucketed) return FPT_OK;
-  unsigned long long h[kMaxOrder + 1] = {0};
-  CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_count, 0, 8 * sizeof(unsigned long long), ctx->stream));
-  CUDA_OR_FAIL(ctx, launch_order_histogram(b->dev, ctx->d_count, ctx->stream, ctx->n_sm));
+  unsigned long long h[kPatternKeys] = {0};
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_count, 0, sizeof(h), ctx->stream));
+  CUDA_OR_FAIL(ctx, launch_pattern_histogram(S, b->dev, ctx->d_count, ctx->stream, ctx->n_sm));
   CUDA_OR_FAIL(ctx, cudaMemcpyAsync(h, ctx->d_count, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
   uint64_t acc = 0;
-  unsigned long long cur[kMaxOrder + 1];
-  for (int n = 0; n <= kMaxOrder; ++n) {
-    b->start[n] = acc;
-    b->count[n] = h[n];
-    cur[n] = acc;
-    acc += h[n];
+  unsigned long long cur[kPatternKeys];
+  for (int k = 0; k < kPatternKeys; ++k) {
+    b->start[k] = acc;
+    b->count[k] = h[k];
+    cur[k] = acc;
+    acc += h[k];
   }
-  if (acc != b->dev.n_paths) return fail(ctx, FPT_EDEVICE, "order histogram mismatch");
+  if (acc != b->dev.n_paths) return fail(ctx, FPT_EDEVICE, "pattern histogram mismatch");
   CUDA_OR_FAIL(ctx, cudaMalloc(&b->d_lists, (acc ? acc : 1) * sizeof(uint64_t)));
   CUDA_OR_FAIL(ctx, cudaMemcpyAsync(ctx->d_count, cur, sizeof(cur), cudaMemcpyHostToDevice, ctx->stream));
-  CUDA_OR_FAIL(ctx, launch_order_scatter(b->dev, ctx->d_count, b->d_lists, ctx->stream, ctx->n_sm));
+  CUDA_OR_FAIL(ctx, launch_pattern_scatter(S, b->dev, ctx->d_count, b->d_lists, ctx->stream, ctx->n_sm));
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
   b->bucketed = true;
   return FPT_OK;
@@ -565,8 +599,25 @@ static uint64_t order_slice(const fpt_batch* b, int n, const uint64_t** list) {
     if (n < b->dev.lo || n > b->dev.hi) return 0;
     return b->dev.kpow[n] * (uint64_t)b->dev.n_tx * (uint64_t)b->dev.n_rx;
   }
-  *list = b->d_lists + b->start[n];
-  return b->count[n];
+  // the buckets of order n are contiguous: keys pattern_key(n, 0) .. pattern_key(n, 2^n - 1)
+  *list = b->d_lists + b->start[pattern_key(n, 0)];
+  uint64_t c = 0;
+  for (unsigned q = 0; q < (1u << n); ++q) c += b->count[pattern_key(n, q)];
+  return c;
+}
+
+// Paths of order n and interaction-type pattern q: count and list (nullptr for exhaustive batches).
+static uint64_t pattern_slice(const fpt_batch* b, int n, unsigned q, const uint64_t** list) {
+  if (b->dev.mode == BATCH_EXHAUSTIVE) {
+    *list = nullptr;
+    if (n < b->dev.lo || n > b->dev.hi) return 0;
+    uint64_t c = (uint64_t)b->dev.n_tx * (uint64_t)b->dev.n_rx;
+    for (int i = 0; i < n; ++i)
+      c *= (uint64_t)(((q >> i) & 1u) ? b->dev.n_alpha_quad : b->dev.n_alpha - b->dev.n_alpha_quad);
+    return c;
+  }
+  *list = b->d_lists + b->start[pattern_key(n, q)];
+  return b->count[pattern_key(n, q)];
 }
 
 static fpt_status check_scene_batch(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* b) {
@@ -574,6 +625,7 @@ static fpt_status check_scene_batch(fpt_ctx* ctx, const fpt_scene* s, const fpt_
   if (b->dev.n_tx != s->n_tx || b->dev.n_rx != s->n_rx)
     return fail(ctx, FPT_EINVAL, "batch was built for other endpoints");
   if (b->dev.mode == BATCH_EXPLICIT && b->dev.n_alpha != s->n_obj) return fail(ctx, FPT_EINVAL, "batch/scene mismatch");
+  if (b->types != s->types) return fail(ctx, FPT_EINVAL, "batch was built for a scene with other object types");
   return FPT_OK;
 }
 
@@ -587,15 +639,15 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
   if (prm) p = *prm;
   if (p.init_mode != 0 && p.init_mode != 1) return fail(ctx, FPT_EINVAL, "init_mode must be 0 or 1");
   if (p.init_mode == 1 && !ctx->init_mlp) return fail(ctx, FPT_EINVAL, "init_mode 1 needs fpt_set_init_mlp");
-  if (p.max_iters < 0 || p.fp_iters < 1 || p.polish < 0 || p.polish > 2)
+  if (p.max_iters < 0 || p.fp_iters < 1 || p.polish < 0 || p.polish > 2 || p.specialize < 0 || p.specialize > 1)
     return fail(ctx, FPT_EINVAL, "bad solver parameters");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
-  st = ensure_buckets(ctx, b);
+  st = ensure_buckets(ctx, b, scene_dev(s));
   if (st != FPT_OK) return st;
   const SceneDev S = scene_dev(s);
   SolveCfg sc{p.max_iters, p.fp_iters, p.fixed_iters, p.tol_step * p.tol_step, 0.01f * p.deg_tol * p.deg_tol,
-              p.refill > 32 ? 32 : p.refill, p.init_mode == 1};
+              p.refill > 32 ? 32 : p.refill, p.init_mode == 1, kMaxChunk};
   // the polish needs its Newton step only to a modest relative accuracy: 100x looser pivot test than the adjoint
   PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, p.polish_fp64};
   for (int n = 1; n <= kMaxOrder; ++n) {
@@ -616,7 +668,29 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
     }
     {
       ProfScope ps(ctx, FPT_K_BFGS);
-      CUDA_OR_FAIL(ctx, launch_bfgs(n, S, b->dev, sc, cnt, list, T, status, iters, ctx->stream, ctx->n_sm, ctx->d_work));
+      if (p.specialize && sc.refill > 0) {
+        // the pattern launches of one order are independent: spread them over the side streams so that
+        // each launch's tail overlaps the next one; each concurrent launch has its own work counter
+        CUDA_OR_FAIL(ctx, cudaEventRecord(ctx->fork_ev, ctx->stream));
+        for (int k = 0; k < fpt_ctx::kSide; ++k) CUDA_OR_FAIL(ctx, cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0));
+        int used = 0;
+        for (unsigned q = 0; q < (1u << n); ++q) {
+          const uint64_t* qlist;
+          const uint64_t qcnt = pattern_slice(b, n, q, &qlist);
+          if (!qcnt) continue;
+          cudaStream_t sq = ctx->side[used % fpt_ctx::kSide];
+          ++used;
+          CUDA_OR_FAIL(ctx, launch_bfgs(n, (int)q, S, b->dev, sc, qcnt, qlist, T, status, iters, sq, ctx->n_sm,
+                                        ctx->d_work + q));
+        }
+        for (int k = 0; k < fpt_ctx::kSide && k < used; ++k) {
+          CUDA_OR_FAIL(ctx, cudaEventRecord(ctx->join_ev[k], ctx->side[k]));
+          CUDA_OR_FAIL(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join_ev[k], 0));
+        }
+      } else {
+        CUDA_OR_FAIL(ctx, launch_bfgs(n, -1, S, b->dev, sc, cnt, list, T, status, iters, ctx->stream, ctx->n_sm,
+                                      ctx->d_work));
+      }
     }
     st = ensure_rescue(ctx, cnt);
     if (st != FPT_OK) return st;
@@ -636,7 +710,7 @@ fpt_status fpt_validity(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   if (!T) return fail(ctx, FPT_EINVAL, "T is required");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
-  st = ensure_buckets(ctx, b);
+  st = ensure_buckets(ctx, b, scene_dev(s));
   if (st != FPT_OK) return st;
   fpt_solve_params p;
   fpt_default_params(&p);
@@ -664,7 +738,7 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   if (!T) return fail(ctx, FPT_EINVAL, "T is required");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
-  st = ensure_buckets(ctx, b);
+  st = ensure_buckets(ctx, b, scene_dev(s));
   if (st != FPT_OK) return st;
   const size_t need = (size_t)(9 * s->n_obj + 3 * (s->n_tx + s->n_rx));
   if (need > ctx->gacc_cap) {
@@ -1150,20 +1224,17 @@ fpt_status fpt_profile_read(fpt_ctx* ctx, double* ms, uint64_t* launches, int re
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
   for (auto& p : ctx->ev_pending) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess) {
-      ctx->prof_ms[p.first] += t;
-      ctx->prof_n[p.first] += 1;
-    }
+    if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess) ctx->prof_ms[p.first] += t;
     ctx->ev_pool.push_back(p.second.first);
     ctx->ev_pool.push_back(p.second.second);
   }
   ctx->ev_pending.clear();
   for (int k = 0; k < FPT_K_COUNT; ++k) {
     if (ms) ms[k] = ctx->prof_ms[k];
-    if (launches) launches[k] = ctx->prof_n[k];
+    if (launches) launches[k] = ctx->prof_kernels[k];
     if (reset) {
       ctx->prof_ms[k] = 0;
-      ctx->prof_n[k] = 0;
+      ctx->prof_kernels[k] = 0;
     }
   }
   return FPT_OK;

@@ -57,7 +57,16 @@ struct BatchDev {
   const uint8_t* order;     // explicit [n]
   const int32_t* tx_idx;    // explicit [n]
   const int32_t* rx_idx;    // explicit [n]
+  const int32_t* type_pos;  // exhaustive: alphabet positions of the reflectors, then of the edges (ascending)
+  int n_alpha_quad;         // exhaustive: reflectors in the alphabet
 };
+
+// Interaction-type pattern of a sequence of order n: bit i set = slot i is a
+// planar reflector, clear = an edge.  Seeded and explicit batches are bucketed
+// by (order, pattern); key(n, Q) = 2^n - 2 + Q orders the buckets by order
+// first, so the buckets of one order form one contiguous range.
+constexpr int kPatternKeys = (2 << kMaxOrder) - 2;  // 62 for orders 1..5
+__host__ __device__ constexpr int pattern_key(int n, unsigned q) { return (1 << n) - 2 + (int)q; }
 
 // One candidate sequence, decoded.
 struct PathDesc {
@@ -174,6 +183,55 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
     }
   }
   finish_desc(B, digits, d);
+}
+
+// Seeded / explicit batch, sequence g taken from a bucket of order N: the same
+// decoding as decode_global with the order known at compile time, so that the
+// descriptor stays in registers.
+template <int N>
+__device__ __forceinline__ void decode_listed(const BatchDev& B, uint64_t g, PathDesc& d) {
+  d.g = g;
+  d.n = N;
+  d.flags = 0;
+  if (B.mode == BATCH_EXPLICIT) {
+    const int n = B.order[g];
+    d.tx = B.tx_idx[g];
+    d.rx = B.rx_idx[g];
+    if (n < 1 || n > B.n_max || n > kMaxOrder || d.tx < 0 || d.tx >= B.n_tx || d.rx < 0 || d.rx >= B.n_rx) {
+      d.flags = ST_INVALID;
+#pragma unroll
+      for (int j = 0; j < kMaxOrder; ++j) d.ids[j] = 0;
+      if (d.tx < 0 || d.tx >= B.n_tx) d.tx = 0;
+      if (d.rx < 0 || d.rx >= B.n_rx) d.rx = 0;
+      return;
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const int o = B.ids[g * (uint64_t)B.n_max + j];
+      d.ids[j] = o;
+      if (o < 0 || o >= B.n_alpha) {
+        d.flags |= ST_INVALID;
+        d.ids[j] = 0;
+      }
+      if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
+    }
+    return;
+  }
+  const uint64_t pair = g / B.per_pair;
+  d.tx = (int)(pair / (uint64_t)B.n_rx);
+  d.rx = (int)(pair - (uint64_t)d.tx * (uint64_t)B.n_rx);
+  const uint64_t K = (uint64_t)B.n_alpha;
+  int digits[N];
+  digits[0] = (int)(seeded_draw(B.seed, g, 1) % K);
+#pragma unroll
+  for (int j = 1; j < N; ++j)
+    digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + seeded_draw(B.seed, g, j + 1) % (K - 1)) % K);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const int o = B.alphabet[digits[j]];
+    d.ids[j] = o;
+    if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
+  }
 }
 
 // Path source for one per-order launch: exhaustive batches need no list; other

@@ -10,6 +10,13 @@ namespace fpt {
 
 constexpr int kThreads = 128;  // threads per CTA for all path kernels
 
+// Kernels launched by the calling thread; the API's profiler reads the
+// difference around each call.
+extern thread_local uint64_t tl_kernel_launches;
+inline void count_launch() { ++tl_kernel_launches; }
+
+constexpr int kMaxChunk = 256;  // most paths a warp of the refill kernel claims at a time
+
 struct SolveCfg {
   int max_iters;    // BFGS step cap
   int fp_iters;     // Eq. 6 rounds per step
@@ -18,6 +25,7 @@ struct SolveCfg {
   float stop2;      // a segment shorter than sqrt(stop2) stops BFGS (the path runs into a kink)
   int refill;       // lane refill threshold (free lanes before a warp takes new paths); 0 = one path per lane per tile
   int init_from_T;  // 1: start from the parameters already in T (learned start); 0: t = 1/2
+  int chunk;        // paths a warp claims at a time (refill kernel; set per launch)
 };
 
 enum PolishMode { POLISH_SOLVE = 0, POLISH_VALIDITY = 1 };
@@ -40,7 +48,10 @@ struct BackwardCfg {
 };
 
 // Per-order launches (n = 1..kMaxOrder).  `list` = nullptr for exhaustive batches.
-cudaError_t launch_bfgs(int n, const SceneDev& S, const BatchDev& B, const SolveCfg& cfg, uint64_t n_local,
+// BFGS: pattern < 0 runs the unified kernel over every sequence of order n;
+// pattern = Q in [0, 2^n) runs the kernel of that interaction-type pattern
+// over a slice holding only sequences of pattern Q.
+cudaError_t launch_bfgs(int n, int pattern, const SceneDev& S, const BatchDev& B, const SolveCfg& cfg, uint64_t n_local,
                         const uint64_t* list, float* T, uint8_t* status, uint8_t* iters, cudaStream_t stream,
                         int n_sm, unsigned long long* work);
 // Double-float polish, then an FP64 pass over the paths whose FP32 pivots failed
@@ -68,9 +79,11 @@ cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, co
 // Batch utilities.
 cudaError_t launch_enumerate(const BatchDev& B, int32_t* ids, uint8_t* order, int32_t* tx_idx, int32_t* rx_idx,
                              cudaStream_t stream, int n_sm);
-cudaError_t launch_order_histogram(const BatchDev& B, unsigned long long* counts, cudaStream_t stream, int n_sm);
-cudaError_t launch_order_scatter(const BatchDev& B, unsigned long long* cursors, uint64_t* lists,
-                                 cudaStream_t stream, int n_sm);
+// Bucketing of seeded / explicit batches by pattern_key(order, pattern): counts[kPatternKeys].
+cudaError_t launch_pattern_histogram(const SceneDev& S, const BatchDev& B, unsigned long long* counts,
+                                     cudaStream_t stream, int n_sm);
+cudaError_t launch_pattern_scatter(const SceneDev& S, const BatchDev& B, unsigned long long* cursors, uint64_t* lists,
+                                   cudaStream_t stream, int n_sm);
 cudaError_t launch_count_status(const uint8_t* status, uint64_t n, uint8_t mask, unsigned long long* out,
                                 cudaStream_t stream, int n_sm);
 

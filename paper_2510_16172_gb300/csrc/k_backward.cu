@@ -382,12 +382,14 @@ static cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const
   if (e != cudaSuccess) return e;
   backward_kernel<N><<<grid, kThreads, smem, stream>>>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, rescue_list,
                                                         rescue_count);
+  count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const uint64_t rwant = (n_local / 16 + kThreads - 1) / kThreads;
   const unsigned rgrid = (unsigned)(rwant < (uint64_t)n_sm * 4 ? (rwant ? rwant : 1) : (uint64_t)n_sm * 4);
   backward_rescue_kernel<N><<<rgrid, kThreads, 0, stream>>>(S, B, cfg, list, T, status, dX, dL, gacc, rescue_list,
                                                              rescue_count);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -469,6 +471,7 @@ cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, co
   const int total = S.n_obj + S.n_tx + S.n_rx;
   const int grid = (total + 255) / 256;
   backward_finalize_kernel<<<grid, 256, 0, stream>>>(S.n_obj, S.n_tx, S.n_rx, S.aux, gacc, g_tx, g_rx, g_vertices);
+  count_launch();
   return cudaGetLastError();
 }
 

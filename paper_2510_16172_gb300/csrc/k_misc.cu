@@ -1,7 +1,9 @@
-// k_misc.cu -- sequence enumeration (Sec. III), order bucketing and status counts.
+// k_misc.cu -- sequence enumeration (Sec. III), bucketing by order and pattern, status counts.
 #include "fpt_kernels.h"
 
 namespace fpt {
+
+thread_local uint64_t tl_kernel_launches = 0;
 
 static unsigned grid_for(uint64_t n, int threads, int n_sm, int per_sm) {
   uint64_t want = (n + threads - 1) / threads;
@@ -23,28 +25,37 @@ __global__ void enumerate_kernel(BatchDev B, int32_t* ids, uint8_t* order, int32
   }
 }
 
-// Histogram of path orders (seeded and explicit batches solve per order).
-__global__ void order_hist_kernel(BatchDev B, unsigned long long* counts) {
-  __shared__ unsigned long long s[kMaxOrder + 1];
-  if (threadIdx.x <= kMaxOrder) s[threadIdx.x] = 0;
-  __syncthreads();
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < B.n_paths; g += stride) {
-    PathDesc d;
-    decode_global(B, g, d);
-    atomicAdd(&s[d.n], 1ULL);
-  }
-  __syncthreads();
-  if (threadIdx.x <= kMaxOrder && s[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s[threadIdx.x]);
+// Pattern of a decoded sequence from the scene's object types.
+__device__ __forceinline__ int path_key(const SceneDev& S, const PathDesc& d) {
+  unsigned q = 0;
+  for (int i = 0; i < d.n; ++i)
+    if (S.aux[kAux * d.ids[i] + 2] == 0.f) q |= 1u << i;
+  return pattern_key(d.n, q);
 }
 
-// cursors[n] starts at the first slot of order n in `lists`.
-__global__ void order_scatter_kernel(BatchDev B, unsigned long long* cursors, uint64_t* lists) {
+// Histogram of (order, pattern) keys (seeded and explicit batches are solved per bucket).
+__global__ void pattern_hist_kernel(SceneDev S, BatchDev B, unsigned long long* counts) {
+  __shared__ unsigned long long s[kPatternKeys];
+  for (int k = threadIdx.x; k < kPatternKeys; k += blockDim.x) s[k] = 0;
+  __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < B.n_paths; g += stride) {
     PathDesc d;
     decode_global(B, g, d);
-    unsigned long long slot = atomicAdd(&cursors[d.n], 1ULL);
+    atomicAdd(&s[path_key(S, d)], 1ULL);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kPatternKeys; k += blockDim.x)
+    if (s[k]) atomicAdd(&counts[k], s[k]);
+}
+
+// cursors[key] starts at the first slot of that bucket in `lists`.
+__global__ void pattern_scatter_kernel(SceneDev S, BatchDev B, unsigned long long* cursors, uint64_t* lists) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < B.n_paths; g += stride) {
+    PathDesc d;
+    decode_global(B, g, d);
+    unsigned long long slot = atomicAdd(&cursors[path_key(S, d)], 1ULL);
     lists[slot] = g;
   }
 }
@@ -74,21 +85,25 @@ cudaError_t launch_enumerate(const BatchDev& B, int32_t* ids, uint8_t* order, in
   unsigned grid = grid_for(B.n_paths, 256, n_sm, 8);
   if (grid == 0) return cudaSuccess;
   enumerate_kernel<<<grid, 256, 0, stream>>>(B, ids, order, tx_idx, rx_idx);
+  count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_order_histogram(const BatchDev& B, unsigned long long* counts, cudaStream_t stream, int n_sm) {
+cudaError_t launch_pattern_histogram(const SceneDev& S, const BatchDev& B, unsigned long long* counts,
+                                     cudaStream_t stream, int n_sm) {
   unsigned grid = grid_for(B.n_paths, 256, n_sm, 8);
   if (grid == 0) return cudaSuccess;
-  order_hist_kernel<<<grid, 256, 0, stream>>>(B, counts);
+  pattern_hist_kernel<<<grid, 256, 0, stream>>>(S, B, counts);
+  count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_order_scatter(const BatchDev& B, unsigned long long* cursors, uint64_t* lists,
-                                 cudaStream_t stream, int n_sm) {
+cudaError_t launch_pattern_scatter(const SceneDev& S, const BatchDev& B, unsigned long long* cursors, uint64_t* lists,
+                                   cudaStream_t stream, int n_sm) {
   unsigned grid = grid_for(B.n_paths, 256, n_sm, 8);
   if (grid == 0) return cudaSuccess;
-  order_scatter_kernel<<<grid, 256, 0, stream>>>(B, cursors, lists);
+  pattern_scatter_kernel<<<grid, 256, 0, stream>>>(S, B, cursors, lists);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -97,6 +112,7 @@ cudaError_t launch_count_status(const uint8_t* status, uint64_t n, uint8_t mask,
   unsigned grid = grid_for((n + 15) / 16, 256, n_sm, 8);
   if (grid == 0) return cudaSuccess;
   count_status_kernel<<<grid, 256, 0, stream>>>(status, n, mask, out);
+  count_launch();
   return cudaGetLastError();
 }
 

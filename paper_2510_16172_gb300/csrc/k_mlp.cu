@@ -172,6 +172,7 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
   }
   dim3 grid((g.M + 127) / 128, k_split);
   gemm_kernel<<<grid, 128, kGemmSmem, stream>>>(g);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -573,6 +574,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S,
 
 cudaError_t launch_mlp_tile_weights(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t stream) {
   mlp_tile_weights_kernel<<<128, 256, 0, stream>>>(wb, wt);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -590,6 +592,7 @@ cudaError_t launch_mlp_infer(const SceneDev& S, const BatchDev& B, int n, const 
   const uint64_t tiles = (count + 127) / 128;
   const unsigned grid = (unsigned)(tiles < (uint64_t)n_sm ? tiles : (uint64_t)n_sm);
   mlp_infer_kernel<<<grid, kInferThreads, smem, stream>>>(S, B, n, list, count, inv_scale, wt, params, T, err);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -602,29 +605,34 @@ cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, con
                                 uint64_t count, float inv_scale, __nv_bfloat16* X, float* G, cudaStream_t stream) {
   if (!count) return cudaSuccess;
   mlp_features_kernel<<<grid_1d(count, 128, 4096), 128, 0, stream>>>(S, B, n, list, first, count, inv_scale, X, G);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_loss(const float* G, const float* Y, const float* T, uint64_t B, float* dY,
                             __nv_bfloat16* dYb, float* loss, cudaStream_t stream) {
   mlp_loss_kernel<<<grid_1d(B, 256, 1024), 256, 0, stream>>>(G, Y, T, B, dY, dYb, loss);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_colsum(const float* A, uint64_t B, int N, float* out, cudaStream_t stream) {
   const int threads = N >= 256 ? N : (256 / N) * N;
   colsum_kernel<<<grid_1d(B, threads / N, 256), threads, 0, stream>>>(A, B, N, out);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float c1, float c2,
                         __nv_bfloat16* wb, cudaStream_t stream) {
   adam_kernel<<<grid_1d(n, 256, 1024), 256, 0, stream>>>(w, m, v, g, n, lr, c1, c2, wb);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int n, cudaStream_t stream) {
   to_bf16_kernel<<<grid_1d(n, 256, 1024), 256, 0, stream>>>(src, dst, n);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -632,6 +640,7 @@ cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const 
                              uint64_t count, const float* Y, float* T, cudaStream_t stream) {
   if (!count) return cudaSuccess;
   mlp_start_kernel<<<grid_1d(count, 128, 4096), 128, 0, stream>>>(S, B, n, list, first, count, Y, T);
+  count_launch();
   return cudaGetLastError();
 }
 

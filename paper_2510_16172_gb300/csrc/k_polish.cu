@@ -581,6 +581,7 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
     if (e != cudaSuccess || grid == 0) return e;
     polish64_kernel<N><<<grid, kThreads, s64, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
                                                          s64 != 0, nullptr, nullptr);
+    count_launch();
     return cudaGetLastError();
   }
   e = cudaMemsetAsync(rescue_count, 0, sizeof(unsigned), stream);
@@ -589,6 +590,7 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
   if (e != cudaSuccess || grid == 0) return e;
   polish_ff_kernel<N><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
                                                         sff != 0, rescue_list, rescue_count);
+  count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // FP64 pass over the listed paths (its grid covers a few percent of the paths)
@@ -596,6 +598,7 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
   if (e != cudaSuccess || grid == 0) return e;
   polish64_kernel<N><<<grid, kThreads, s64, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
                                                        s64 != 0, rescue_list, rescue_count);
+  count_launch();
   return cudaGetLastError();
 }
 

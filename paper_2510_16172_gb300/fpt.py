@@ -42,7 +42,7 @@ class SolveParams(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("fp_iters", C.c_int32), ("polish", C.c_int32), ("fixed_iters", C.c_int32),
                 ("tol_step", C.c_float), ("solved_tol", C.c_float), ("deg_tol", C.c_float), ("cond_fp64", C.c_float),
                 ("init_mode", C.c_int32), ("polish_fp64", C.c_int32), ("refill", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("specialize", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 # every symbol declared in include/fpt.h with (restype, argtypes)

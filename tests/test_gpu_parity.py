@@ -179,6 +179,51 @@ def test_lane_refill_is_bit_identical(ctx):
         assert np.array_equal(a[k], b[k], equal_nan=True) and np.array_equal(a[k], c[k], equal_nan=True), k
 
 
+def _bits(ctx, scene, batch, **kw):
+    out = to_np(fpt.solve(ctx, scene, batch, fpt.default_params(**kw)))
+    ctx.sync()
+    return out
+
+
+@pytest.mark.parametrize("case", ["canyon", "city", "tiny_quads_only", "tiny_edges_only"])
+def test_pattern_kernels_match_unified_kernel(ctx, case):
+    """The interaction-type pattern kernels drop the edges' always-zero second parameter; iterates,
+    iteration counts, lengths and flags are bit-identical to the unified d = 2 kernel."""
+    if case == "canyon":
+        sc = scenes.urban_canyon(0, rx_grid=4)
+        scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+        batch = fpt.Batch.exhaustive(ctx, scene, 3, 3, sc.alphabet)
+    elif case == "city":
+        sc = scenes.city(2, n_rx=3)
+        scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+        batch = fpt.Batch.seeded(ctx, scene, 9, 6000, 1, 5)
+    else:
+        quads = case == "tiny_quads_only"
+        sc = scenes.tiny_scene(3, n_quads=6 if quads else 0, n_edges=0 if quads else 6, n_rx=2)
+        scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+        batch = fpt.Batch.exhaustive(ctx, scene, 1, 3, sc.alphabet)
+    a = _bits(ctx, scene, batch, specialize=0)
+    b = _bits(ctx, scene, batch, specialize=1)
+    for k in ("T", "status", "iters", "L", "X", "rho"):
+        if a.get(k) is not None:
+            assert np.array_equal(a[k], b[k], equal_nan=True), k
+
+
+def test_batch_refuses_scene_with_other_types(ctx):
+    sc = scenes.tiny_scene(1)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    batch = fpt.Batch.exhaustive(ctx, scene, 1, 2)
+    types = sc.types.copy()
+    k = int(np.argmax(types == scenes.QUAD))
+    types[k] = scenes.EDGE
+    verts = sc.verts.copy()
+    verts[k, 2] = 0.0
+    other = fpt.Scene(ctx, types, verts, sc.tx, sc.rx)
+    with pytest.raises(fpt.FptError):
+        fpt.solve(ctx, other, batch)
+    ctx.sync()
+
+
 @pytest.mark.parametrize("seed", [0, 5])
 def test_fp64_polish_parity(ctx, seed):
     """The FP64 polish (validation mode) meets the same bars as the double-float default."""
