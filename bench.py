@@ -346,8 +346,35 @@ def run_ours(args, world, rank, local_rank):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{m} seeded uniformly sampled paths of the workload, FP64 damped Newton "
                                           f"+ implicit VJP, {dt:.1f} s on {threads} threads"}
+    if rank == 0 and world == 1 and not args.no_learned:
+        line["learned_vs_plain"] = learned_vs_plain(ctx, fpt)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def learned_vs_plain(ctx, fpt):
+    """The learned start against the plain one (same solver, same unseen scenes).
+
+    The network (64-256-256-256-8, GELU, BF16 weights, FP32 accumulation) is
+    trained here by the library's tensor-core kernels on the solver's own
+    solutions of seeded order-1..4 sequences on 50 random 10 m scenes (8 quads
+    and 4 edges each), then both starts solve seeded order-1..4 sequences on 10
+    unseen scenes; each side is timed with CUDA events over solve + implicit
+    backward.
+    """
+    from paper_2510_16172_gb300 import warmstart
+
+    t0 = time.perf_counter()
+    net, ev = warmstart.run(ctx, per_pair_train=200_000, per_pair_eval=200_000, epochs=6)
+    net.close()
+    res = {"workload": "train: 50 seeded 10 m scenes (8 quads + 4 edges) x 200,000 seeded order-1..4 sequences, "
+                       "solved paths as targets, 6 epochs of Adam; eval: 10 unseen scenes x 200,000 sequences",
+           "train_samples": ev["train_samples"], "train_loss_per_epoch": ev["train_loss_per_epoch"],
+           "train_s": ev["train_s"], "plain": ev["plain"], "learned": ev["learned"],
+           "learned_over_plain_solves_per_s": ev["learned"]["solves_per_s"] / ev["plain"]["solves_per_s"],
+           "learned_over_plain_iterations": ev["learned"]["mean_bfgs_iters"] / ev["plain"]["mean_bfgs_iters"],
+           "wall_s": time.perf_counter() - t0}
+    return res
 
 
 def e2e(args, sc, ctx, dev, torch, fpt):
@@ -406,6 +433,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--max-iters", type=int, default=32, help="BFGS step cap")
     ap.add_argument("--rx-grid", type=int, default=32, help="RX grid side (32 = the 33.5M-path workload)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain start comparison")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

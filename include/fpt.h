@@ -90,8 +90,9 @@ typedef struct {
                           lane until the whole warp is done */
   int32_t specialize;  /* 1: BFGS runs one kernel per interaction-type pattern (reflector/edge per slot), which
                           drops the edge's always-zero second parameter from the iteration and yields the same
-                          iterates as the unified kernel; 0: the unified kernel of Sec. III-B only (1; refill = 0
-                          implies 0) */
+                          iterates as the unified kernel, for every order whose non-empty pattern buckets all
+                          hold at least 2048 paths per SM; 2: for every order; 0: the unified kernel of
+                          Sec. III-B only (1; refill = 0 implies 0) */
   int32_t reserved[4]; /* must be zero */
 } fpt_solve_params;
 

@@ -67,50 +67,52 @@ __host__ __device__ constexpr int hidx(int r, int c) {
   return r <= c ? r * M - r * (r - 1) / 2 + (c - r) : c * M - c * (c - 1) / 2 + (r - c);
 }
 
+// Lookup tables of a launch, in shared memory where they fit.
+struct Tables {
+  const float* rec;         // FP32 object records [n_obj][kRec32]
+  const float* tx;          // endpoints [n][kEnd32]
+  const float* rx;
+  const int32_t* alphabet;  // [n_alpha] (nullptr for explicit batches)
+  const int32_t* type_pos;  // [n_alpha] (exhaustive batches)
+};
+
 // Exhaustive batch, sequences of order N and pattern Q only: local index j
 // over n_pairs * prod_i |alphabet part of slot i| paths.  The alphabet's
-// reflectors and edges are listed (ascending positions) in B.type_pos.  The
+// reflectors and edges are listed (ascending positions) in type_pos.  The
 // decoded sequence and its global index g are those of the full enumeration.
+// One order of a batch holds at most 2^32 paths (checked by the host), so the
+// local index arithmetic is 32-bit.
 template <int N, unsigned Q>
-__device__ __forceinline__ void decode_exhaustive_pattern(const BatchDev& B, uint64_t j, PathDesc& d) {
+__device__ __forceinline__ void decode_exhaustive_pattern(const BatchDev& B, const Tables& tb, uint64_t j,
+                                                          PathDesc& d) {
   const uint32_t nq = (uint32_t)B.n_alpha_quad, ne = (uint32_t)(B.n_alpha - B.n_alpha_quad);
-  uint64_t cnt = 1;
+  uint32_t cnt = 1;
 #pragma unroll
   for (int i = 0; i < N; ++i) cnt *= Pat<N, Q>::quad(i) ? nq : ne;
-  const uint64_t pair = j / cnt;
-  uint64_t r = j - pair * cnt;
+  const uint32_t j32 = (uint32_t)j;
+  const uint32_t pair = j32 / cnt;
+  uint32_t r = j32 - pair * cnt;
   d.n = N;
-  d.tx = (int)(pair / (uint64_t)B.n_rx);
-  d.rx = (int)(pair - (uint64_t)d.tx * (uint64_t)B.n_rx);
+  d.tx = (int)(pair / (uint32_t)B.n_rx);
+  d.rx = (int)(pair - (uint32_t)d.tx * (uint32_t)B.n_rx);
   int pos[N];
-  if (cnt <= 0xFFFFFFFFull) {
-    uint32_t r32 = (uint32_t)r;
 #pragma unroll
-    for (int i = N - 1; i >= 0; --i) {
-      const uint32_t base = Pat<N, Q>::quad(i) ? nq : ne;
-      const uint32_t q = r32 / base;
-      pos[i] = B.type_pos[(Pat<N, Q>::quad(i) ? 0u : nq) + (r32 - q * base)];
-      r32 = q;
-    }
-  } else {
-#pragma unroll
-    for (int i = N - 1; i >= 0; --i) {
-      const uint64_t base = Pat<N, Q>::quad(i) ? nq : ne;
-      const uint64_t q = r / base;
-      pos[i] = B.type_pos[(Pat<N, Q>::quad(i) ? 0u : nq) + (uint32_t)(r - q * base)];
-      r = q;
-    }
+  for (int i = N - 1; i >= 0; --i) {
+    const uint32_t base = Pat<N, Q>::quad(i) ? nq : ne;
+    const uint32_t q = r / base;
+    pos[i] = tb.type_pos[(Pat<N, Q>::quad(i) ? 0u : nq) + (r - q * base)];
+    r = q;
   }
   uint64_t rg = 0;
   d.flags = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     rg = rg * (uint64_t)B.n_alpha + (uint64_t)pos[i];
-    const int o = B.alphabet[pos[i]];
+    const int o = tb.alphabet[pos[i]];
     d.ids[i] = o;
     if (i > 0 && d.ids[i - 1] == o) d.flags |= ST_REPEAT;
   }
-  d.g = pair * B.per_pair + B.offset[N] + rg;
+  d.g = (uint64_t)pair * B.per_pair + B.offset[N] + rg;
 }
 
 // Where a kernel's paths come from; each source is its own instantiation so
@@ -122,30 +124,31 @@ enum BfgsSource {
 };
 
 template <int N, unsigned Q, int kSrc>
-__device__ __forceinline__ void fetch_path_q(const BatchDev& B, const uint64_t* list, uint64_t j, PathDesc& d) {
+__device__ __forceinline__ void fetch_path_q(const BatchDev& B, const Tables& tb, const uint64_t* list, uint64_t j,
+                                             PathDesc& d) {
   if constexpr (kSrc == SRC_LIST)
-    decode_listed<N>(B, list[j], d);
+    decode_listed<N>(B, tb.alphabet, list[j], d);
   else if constexpr (kSrc == SRC_PATTERN)
-    decode_exhaustive_pattern<N, Q>(B, j, d);
+    decode_exhaustive_pattern<N, Q>(B, tb, j, d);
   else
     decode_exhaustive_order(B, N, j, d);
 }
 
 template <int N, unsigned Q>
-__device__ __forceinline__ void load_geo(const PathDesc& d, const float* rec, const SceneDev& S, Geo<N>& G) {
+__device__ __forceinline__ void load_geo(const PathDesc& d, const Tables& tb, Geo<N>& G) {
   float bh[N + 2][3], bl[N + 2][3];
-  const float* tx = S.tx32 + kEnd32 * d.tx;
-  const float* rx = S.rx32 + kEnd32 * d.rx;
+  const float* tx = tb.tx + kEnd32 * d.tx;
+  const float* rx = tb.rx + kEnd32 * d.rx;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    bh[0][c] = __ldg(tx + c);
-    bl[0][c] = __ldg(tx + 3 + c);
-    bh[N + 1][c] = __ldg(rx + c);
-    bl[N + 1][c] = __ldg(rx + 3 + c);
+    bh[0][c] = tx[c];
+    bl[0][c] = tx[3 + c];
+    bh[N + 1][c] = rx[c];
+    bl[N + 1][c] = rx[3 + c];
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const float* r = rec + kRec32 * d.ids[i];
+    const float* r = tb.rec + kRec32 * d.ids[i];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       bh[i + 1][c] = r[c];
@@ -231,16 +234,16 @@ struct PathState {
 // or at the given start, with H = I, and evaluate the first gradient.
 // Returns false for paths that are never solved (repeats, invalid input).
 template <int N, unsigned Q, int kSrc>
-__device__ __forceinline__ bool path_start(PathState<N, Q>& P, const BatchDev& B, const SceneDev& S, const float* rec,
+__device__ __forceinline__ bool path_start(PathState<N, Q>& P, const BatchDev& B, const Tables& tb,
                                            const uint64_t* list, uint64_t j, int max_iters, const float* T_start) {
   constexpr int M = PathState<N, Q>::M;
   PathDesc d;
-  fetch_path_q<N, Q, kSrc>(B, list, j, d);
+  fetch_path_q<N, Q, kSrc>(B, tb, list, j, d);
   P.gidx = d.g;
   P.st = d.flags;
   P.it = 0;
   P.conv = false;
-  load_geo<N, Q>(d, rec, S, P.G);
+  load_geo<N, Q>(d, tb, P.G);
   if (T_start) {  // learned start written by the network pass
     const float2* Ts = reinterpret_cast<const float2*>(T_start) + d.g * (uint64_t)B.n_max;
 #pragma unroll
@@ -375,6 +378,53 @@ __device__ __forceinline__ void path_finish(const PathState<N, Q>& P, int n_max,
   if (iters_out) iters_out[P.gidx] = (uint8_t)(P.it > 255 ? 255 : P.it);
 }
 
+// Shared-memory staging of a launch's tables: bit 0 of `use_smem` stages the
+// object records, bit 1 also the endpoints and the alphabet tables (the host
+// sizes the dynamic shared memory to match, smem_tables_bytes).
+__device__ __forceinline__ Tables stage_tables(const SceneDev& S, const BatchDev& B, int use_smem, float* smem) {
+  Tables tb{S.rec32, S.tx32, S.rx32, B.alphabet, B.type_pos};
+  if (use_smem & 1) {
+    stage(smem, S.rec32, S.n_obj * kRec32);
+    tb.rec = smem;
+    smem += S.n_obj * kRec32;
+  }
+  if (use_smem & 2) {
+    stage(smem, S.tx32, S.n_tx * kEnd32);
+    tb.tx = smem;
+    smem += S.n_tx * kEnd32;
+    stage(smem, S.rx32, S.n_rx * kEnd32);
+    tb.rx = smem;
+    smem += S.n_rx * kEnd32;
+    int32_t* si = reinterpret_cast<int32_t*>(smem);
+    if (B.alphabet) {
+      stage(si, B.alphabet, B.n_alpha);
+      tb.alphabet = si;
+      si += B.n_alpha;
+    }
+    if (B.type_pos) {
+      stage(si, B.type_pos, B.n_alpha);
+      tb.type_pos = si;
+    }
+  }
+  __syncthreads();
+  return tb;
+}
+
+// Bytes of shared memory for stage_tables and the matching use_smem flags
+// (records up to 96 KB; endpoints and alphabet tables too if the total stays
+// within 64 KB, so that several CTAs still fit on an SM).
+inline size_t smem_tables_bytes(const SceneDev& S, const BatchDev& B, int* use_smem) {
+  const size_t rec = (size_t)S.n_obj * kRec32 * sizeof(float);
+  const size_t ends = (size_t)(S.n_tx + S.n_rx) * kEnd32 * sizeof(float) +
+                      (size_t)((B.alphabet ? 1 : 0) + (B.type_pos ? 1 : 0)) * B.n_alpha * sizeof(int32_t);
+  *use_smem = 0;
+  if (rec > 96 * 1024) return 0;
+  *use_smem = 1;
+  if (rec + ends > 64 * 1024) return rec;
+  *use_smem = 3;
+  return rec + ends;
+}
+
 // One path per thread per tile; a warp leaves its BFGS loop when all 32 lanes are done.
 template <int N>
 __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, SolveCfg cfg, uint64_t n_local,
@@ -382,13 +432,8 @@ __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, 
                                                         uint8_t* __restrict__ status_out,
                                                         uint8_t* __restrict__ iters_out, int use_smem) {
   constexpr unsigned Q = kAllQuads<N>;
-  extern __shared__ float s_rec[];
-  const float* rec = S.rec32;
-  if (use_smem) {
-    stage(s_rec, S.rec32, S.n_obj * kRec32);
-    __syncthreads();
-    rec = s_rec;
-  }
+  extern __shared__ __align__(16) float s_tab[];
+  const Tables tb = stage_tables(S, B, use_smem, s_tab);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
     const uint64_t j = j0 + threadIdx.x;
@@ -396,10 +441,8 @@ __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, 
     PathState<N, Q> P;
     bool active = false;
     if (have)
-      active = list ? path_start<N, Q, SRC_LIST>(P, B, S, rec, list, j, cfg.max_iters,
-                                                 cfg.init_from_T ? T_out : nullptr)
-                    : path_start<N, Q, SRC_ORDER>(P, B, S, rec, list, j, cfg.max_iters,
-                                                  cfg.init_from_T ? T_out : nullptr);
+      active = list ? path_start<N, Q, SRC_LIST>(P, B, tb, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr)
+                    : path_start<N, Q, SRC_ORDER>(P, B, tb, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr);
     while (__any_sync(0xffffffffu, active))
       if (active && bfgs_step<N, Q>(P, cfg)) active = false;
     if (have) path_finish<N, Q>(P, B.n_max, T_out, status_out, iters_out);
@@ -426,13 +469,8 @@ __global__ void __launch_bounds__(kThreads, FPT_BFGS_MIN_CTAS) bfgs_refill_kerne
                                                                uint8_t* __restrict__ status_out,
                                                                uint8_t* __restrict__ iters_out, int use_smem,
                                                                unsigned long long* __restrict__ work) {
-  extern __shared__ float s_rec[];
-  const float* rec = S.rec32;
-  if (use_smem) {
-    stage(s_rec, S.rec32, S.n_obj * kRec32);
-    __syncthreads();
-    rec = s_rec;
-  }
+  extern __shared__ __align__(16) float s_tab[];
+  const Tables tb = stage_tables(S, B, use_smem, s_tab);
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -465,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, FPT_BFGS_MIN_CTAS) bfgs_refill_kerne
         const unsigned got_mask = __ballot_sync(full, got);
         if (got) {
           const uint64_t j = next + (uint64_t)rank;
-          if (path_start<N, Q, kSrc>(P, B, S, rec, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr)) {
+          if (path_start<N, Q, kSrc>(P, B, tb, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr)) {
             active = true;
           } else {
             path_finish<N, Q>(P, B.n_max, T_out, status_out, iters_out);
@@ -505,9 +543,8 @@ struct BfgsLaunch {
 
 template <int N, unsigned Q, int kSrc>
 cudaError_t launch_bfgs_nq(const BfgsLaunch& a) {
-  size_t smem = (size_t)a.S.n_obj * kRec32 * sizeof(float);
-  int use_smem = smem <= 96 * 1024;
-  if (!use_smem) smem = 0;
+  int use_smem = 0;
+  const size_t smem = smem_tables_bytes(a.S, a.B, &use_smem);
   constexpr bool kPat = kSrc == SRC_PATTERN || Q != kAllQuads<N>;
   const bool refill = kPat || (a.cfg.refill > 0 && a.work != nullptr);
   const void* fn;

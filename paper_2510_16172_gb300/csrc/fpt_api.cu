@@ -639,7 +639,7 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
   if (prm) p = *prm;
   if (p.init_mode != 0 && p.init_mode != 1) return fail(ctx, FPT_EINVAL, "init_mode must be 0 or 1");
   if (p.init_mode == 1 && !ctx->init_mlp) return fail(ctx, FPT_EINVAL, "init_mode 1 needs fpt_set_init_mlp");
-  if (p.max_iters < 0 || p.fp_iters < 1 || p.polish < 0 || p.polish > 2 || p.specialize < 0 || p.specialize > 1)
+  if (p.max_iters < 0 || p.fp_iters < 1 || p.polish < 0 || p.polish > 2 || p.specialize < 0 || p.specialize > 2)
     return fail(ctx, FPT_EINVAL, "bad solver parameters");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
@@ -668,7 +668,16 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
     }
     {
       ProfScope ps(ctx, FPT_K_BFGS);
-      if (p.specialize && sc.refill > 0) {
+      // pattern kernels pay off when every pattern bucket fills the GPU several times over; an order
+      // split into many small buckets runs the unified kernel instead
+      bool by_pattern = p.specialize && sc.refill > 0;
+      const uint64_t min_bucket = (uint64_t)ctx->n_sm * 4 * 128 * 4;
+      for (unsigned q = 0; by_pattern && q < (1u << n); ++q) {
+        const uint64_t* qlist;
+        const uint64_t qcnt = pattern_slice(b, n, q, &qlist);
+        if (qcnt && qcnt < min_bucket && p.specialize == 1) by_pattern = false;
+      }
+      if (by_pattern) {
         // the pattern launches of one order are independent: spread them over the side streams so that
         // each launch's tail overlaps the next one; each concurrent launch has its own work counter
         CUDA_OR_FAIL(ctx, cudaEventRecord(ctx->fork_ev, ctx->stream));

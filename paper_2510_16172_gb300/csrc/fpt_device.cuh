@@ -101,8 +101,15 @@ __device__ __forceinline__ void finish_desc(const BatchDev& B, const int* digits
 // Exhaustive batch, order n known: local index j over n_pairs * K^n paths.
 __device__ __forceinline__ void decode_exhaustive_order(const BatchDev& B, int n, uint64_t j, PathDesc& d) {
   uint64_t kn = B.kpow[n];
-  uint64_t pair = j / kn;
-  uint64_t r = j - pair * kn;
+  uint64_t pair, r;
+  if (j <= 0xFFFFFFFFull && kn <= 0xFFFFFFFFull) {  // one order holds at most 2^32 paths: the usual case
+    const uint32_t p32 = (uint32_t)j / (uint32_t)kn;
+    pair = p32;
+    r = (uint32_t)j - p32 * (uint32_t)kn;
+  } else {
+    pair = j / kn;
+    r = j - pair * kn;
+  }
   d.g = pair * B.per_pair + B.offset[n] + r;
   d.n = n;
   d.tx = (int)(pair / (uint64_t)B.n_rx);
@@ -189,7 +196,7 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
 // decoding as decode_global with the order known at compile time, so that the
 // descriptor stays in registers.
 template <int N>
-__device__ __forceinline__ void decode_listed(const BatchDev& B, uint64_t g, PathDesc& d) {
+__device__ __forceinline__ void decode_listed(const BatchDev& B, const int32_t* alphabet, uint64_t g, PathDesc& d) {
   d.g = g;
   d.n = N;
   d.flags = 0;
@@ -228,7 +235,7 @@ __device__ __forceinline__ void decode_listed(const BatchDev& B, uint64_t g, Pat
     digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + seeded_draw(B.seed, g, j + 1) % (K - 1)) % K);
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    const int o = B.alphabet[digits[j]];
+    const int o = alphabet[digits[j]];
     d.ids[j] = o;
     if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
   }
