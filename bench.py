@@ -7,8 +7,9 @@ edges), TX at (100, 100, 10) m and a 32 x 32 RX grid at 1.5 m; every order-3
 sequence for every RX: 32^3 * 1024 = 33,554,432 paths.  A step enumerates,
 solves (plain init, FP32 BFGS with Eq. 6 step sizes, a Newton polish whose
 gradient is formed in double-float arithmetic, validity), and back-propagates the sum of the valid solved paths'
-lengths to TX, RX and every vertex by implicit differentiation.  A path
-counts as solved when its stationarity residual is <= 1e-5 m.
+lengths to TX, RX and every vertex by implicit differentiation -- one
+fpt_solve_grad call.  A path counts as solved when its stationarity residual
+is <= 1e-5 m.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -36,7 +37,8 @@ METRIC = "path solves/s to 1e-5 m stationarity, fwd+implicit bwd; learned vs pla
 UNIT = "solves/s"
 WORKLOAD = ("urban canyon: 32 facades + 128 edges, 32-object alphabet (16 R + 16 D), order 3, "
             "1 TX x 32x32 RX = 33,554,432 paths; plain init; FP32 BFGS + Eq.6 fixed point, Newton polish with an "
-            "extended-precision gradient, validity, implicit backward of the sum of valid path lengths")
+            "extended-precision gradient, validity, implicit backward of the sum of valid path lengths "
+            "(one fpt_solve_grad call)")
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -249,8 +251,7 @@ def run_ours(args, world, rank, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        fpt.solve(ctx, scene, batch, params, out)
-        fpt.backward(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask, out=grads)
+        fpt.solve_grad(ctx, scene, batch, params, dL_status_mask=mask, out=out, grads=grads)
 
     for _ in range(args.warmup):
         step()
@@ -404,8 +405,8 @@ def e2e(args, sc, ctx, dev, torch, fpt):
         batch = fpt.Batch.exhaustive(ctx, scene, 3, 3, alphabet)
         if out is None:
             out = fpt.alloc_outputs(ctx, batch, with_X=False, with_rho=False, with_iters=False)
-        fpt.solve(ctx, scene, batch, fpt.default_params(max_iters=args.max_iters), out)
-        g = fpt.backward(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask)
+        _, g = fpt.solve_grad(ctx, scene, batch, fpt.default_params(max_iters=args.max_iters), dL_status_mask=mask,
+                              out=out)
         L_h.copy_(out["L"], non_blocking=True)
         st_h.copy_(out["status"], non_blocking=True)
         gtx_h.copy_(g[0], non_blocking=True)

@@ -93,7 +93,11 @@ typedef struct {
                           iterates as the unified kernel, for every order whose non-empty pattern buckets all
                           hold at least 2048 paths per SM; 2: for every order; 0: the unified kernel of
                           Sec. III-B only (1; refill = 0 implies 0) */
-  int32_t reserved[4]; /* must be zero */
+  int32_t fuse_adjoint; /* fpt_solve_grad only.  1: each path's adjoint is formed inside the polish kernel;
+                           0: the adjoint kernels of fpt_backward run after the solve (0; measured faster on
+                           GB300 at order 3, where the fused kernel's larger code and register footprint lower
+                           its issue rate more than the shared decoding saves) */
+  int32_t reserved[3]; /* must be zero */
 } fpt_solve_params;
 
 typedef struct fpt_ctx fpt_ctx;
@@ -200,6 +204,23 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* b
                         const uint8_t* status, const float* dX, const float* dL, uint8_t dL_status_mask,
                         float* g_tx, float* g_rx, float* g_vertices);
 
+/* Solve and backward in one call, for cotangents known when the solve starts
+ * (Sec. III-C then Sec. III-D): the outputs of fpt_solve and the gradients of
+ * fpt_backward(T_out, status_out, dX, dL, dL_status_mask).  The adjoint of
+ * each path is formed either by the adjoint kernels of fpt_backward after
+ * the solve (params->fuse_adjoint = 0, the default) or inside the polish
+ * kernel from the state it already holds (fuse_adjoint = 1: geometry,
+ * segment directions, lengths and Hessian factorisation at the returned
+ * point); paths whose FP32 pivots fail the adjoint's test (or whose polish
+ * ran in FP64) get an FP64 adjoint pass.  Gradients agree with fpt_backward
+ * to FP32 rounding.  Requires polish >= 1 and polish_fp64 = 0 (FPT_EINVAL /
+ * FPT_EUNSUPPORTED otherwise); status_out is required.  dX [N][n_max][3], dL [N] device or NULL; the
+ * gradient outputs are overwritten as in fpt_backward. */
+fpt_status fpt_solve_grad(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* batch, const fpt_solve_params* params,
+                          const float* dX, const float* dL, uint8_t dL_status_mask, float* T_out, float* X_out,
+                          float* L_out, uint8_t* status_out, uint8_t* iters_out, float* rho_out, float* g_tx,
+                          float* g_rx, float* g_vertices);
+
 /* fpt_backward without any device allocation, for callers that cannot
  * allocate: for example a host application whose GPU memory is entirely
  * reserved by another allocator (a framework's caching pool), or a latency-
@@ -211,8 +232,8 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* b
  * the library, held until the process exits.  Limits: 9 n_obj + 3 (n_tx +
  * n_rx) <= 65536 and at most 2^20 paths of any one order in the batch;
  * larger inputs return FPT_EINVAL with a message.  Seeded and explicit
- * batches must already be bucketed by order (any earlier fpt_solve or
- * fpt_backward on the batch does that).
+ * batches must already be bucketed (any earlier fpt_solve or fpt_backward
+ * on the batch does that).
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it; make that first call before any stream
  * capture.  Every call reuses the same array and clears the sums it needs;

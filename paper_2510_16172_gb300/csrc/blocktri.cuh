@@ -44,10 +44,13 @@ template <>
 __device__ __forceinline__ double sqrt_r<double>(double x) { return sqrt(x); }
 
 // u [N+1][3] unit segment directions, il [N+1] inverse lengths, a [N][2][3],
-// edge[N] flags.  Returns false if a pivot fails the test.
+// edge[N] flags.  Returns false if a pivot fails the test with `cond`; if
+// strict_ok is given, it also receives the outcome of the test with
+// cond_strict (one factorisation serving two accuracy needs).
 template <typename R, int N>
 __device__ __forceinline__ bool factor_hessian(const R (&u)[N + 1][3], const R (&il)[N + 1], const R (&a)[N][2][3],
-                                               const bool (&edge)[N], R cond, BlockTri<R, N>& F) {
+                                               const bool (&edge)[N], R cond, BlockTri<R, N>& F,
+                                               R cond_strict = R(0), bool* strict_ok = nullptr) {
   // M_j packed (xx, xy, xz, yy, yz, zz)
   R Mj[N + 1][6];
 #pragma unroll
@@ -122,6 +125,7 @@ __device__ __forceinline__ bool factor_hessian(const R (&u)[N + 1][3], const R (
     R lam_min = half_tr - sqrt_r<R>(half_df * half_df + D[1] * D[1]);
     const R own = Hd[i][0] > Hd[i][2] ? Hd[i][0] : Hd[i][2];
     ok = ok && D[0] > R(0) && det > R(0) && lam_min > cond * own;
+    if (strict_ok) *strict_ok = *strict_ok && lam_min > cond_strict * own;
     R idet = R(1) / det;
     F.Dinv[i][0] = D[2] * idet;
     F.Dinv[i][1] = -D[1] * idet;

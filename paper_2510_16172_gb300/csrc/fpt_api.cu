@@ -32,7 +32,7 @@ struct fpt_ctx {
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kSide] = {};
-  uint32_t* d_rescue = nullptr;            // paths whose FP32 Hessian pivots failed (polish scratch)
+  uint32_t* d_rescue = nullptr;            // paths for the FP64 passes: polish list, then adjoint list
   size_t rescue_cap = 0;
   unsigned* d_rescue_n = nullptr;
   fpt_mlp* init_mlp = nullptr;             // network for init_mode = 1
@@ -205,7 +205,7 @@ fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_rescue_n, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_rescue_n, 2 * sizeof(unsigned));
   if (e != cudaSuccess) {
     fpt_destroy(ctx);
     return FPT_ECUDA;
@@ -587,7 +587,7 @@ static fpt_status ensure_rescue(fpt_ctx* ctx, uint64_t n) {
   cudaFree(ctx->d_rescue);
   ctx->d_rescue = nullptr;
   ctx->rescue_cap = 0;
-  CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_rescue, n * sizeof(uint32_t)));
+  CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_rescue, 2 * n * sizeof(uint32_t)));
   ctx->rescue_cap = n;
   return FPT_OK;
 }
@@ -629,8 +629,10 @@ static fpt_status check_scene_batch(fpt_ctx* ctx, const fpt_scene* s, const fpt_
   return FPT_OK;
 }
 
-fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, const fpt_solve_params* prm, float* T,
-                     float* X, float* L, uint8_t* status, uint8_t* iters, float* rho) {
+// Solve (and, with grad, the fused backward) of every order of the batch.
+static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, const fpt_solve_params* prm,
+                             float* T, float* X, float* L, uint8_t* status, uint8_t* iters, float* rho,
+                             const GradCfg* grad) {
   fpt_status st = check_scene_batch(ctx, s, bc);
   if (st != FPT_OK) return st;
   if (!T || !status) return fail(ctx, FPT_EINVAL, "T_out and status_out are required");
@@ -705,10 +707,71 @@ fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, cons
     if (st != FPT_OK) return st;
     {
       ProfScope ps(ctx, FPT_K_POLISH);
+      GradCfg gc{};
+      if (grad) {
+        gc = *grad;
+        gc.rescue_list = ctx->d_rescue + cnt;
+        gc.rescue_count = ctx->d_rescue_n + 1;
+      }
       CUDA_OR_FAIL(ctx, launch_polish(n, S, b->dev, pc, cnt, list, T, X, L, status, rho, nullptr, nullptr, ctx->stream,
-                                      ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n));
+                                      ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n, grad ? &gc : nullptr));
     }
   }
+  return FPT_OK;
+}
+
+fpt_status fpt_solve(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, const fpt_solve_params* prm, float* T,
+                     float* X, float* L, uint8_t* status, uint8_t* iters, float* rho) {
+  return solve_impl(ctx, s, bc, prm, T, X, L, status, iters, rho, nullptr);
+}
+
+// Context-owned FP64 gradient accumulators, sized for the scene and cleared.
+static fpt_status ensure_gacc(fpt_ctx* ctx, const fpt_scene* s) {
+  const size_t need = (size_t)(9 * s->n_obj + 3 * (s->n_tx + s->n_rx));
+  if (need > ctx->gacc_cap) {
+    cudaFree(ctx->d_gacc);
+    ctx->d_gacc = nullptr;
+    ctx->gacc_cap = 0;
+    CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_gacc, need * sizeof(double)));
+    ctx->gacc_cap = need;
+  }
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_gacc, 0, need * sizeof(double), ctx->stream));
+  return FPT_OK;
+}
+
+fpt_status fpt_solve_grad(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, const fpt_solve_params* prm,
+                          const float* dX, const float* dL, uint8_t dL_status_mask, float* T, float* X, float* L,
+                          uint8_t* status, uint8_t* iters, float* rho, float* g_tx, float* g_rx,
+                          float* g_vertices) {
+  fpt_status st = check_scene_batch(ctx, s, bc);
+  if (st != FPT_OK) return st;
+  if (prm && prm->polish_fp64) return fail(ctx, FPT_EUNSUPPORTED, "fpt_solve_grad runs the double-float polish");
+  if (prm && prm->polish < 1) return fail(ctx, FPT_EINVAL, "fpt_solve_grad needs polish >= 1");
+  if (!status) return fail(ctx, FPT_EINVAL, "status_out is required");
+  if (!(prm && prm->fuse_adjoint)) {
+    // the adjoint kernels after the solve, with the cotangents given here
+    st = fpt_solve(ctx, s, bc, prm, T, X, L, status, iters, rho);
+    if (st != FPT_OK) return st;
+    return fpt_backward(ctx, s, bc, T, status, dX, dL, dL_status_mask, g_tx, g_rx, g_vertices);
+  }
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  st = ensure_gacc(ctx, s);
+  if (st != FPT_OK) return st;
+  fpt_solve_params p;
+  fpt_default_params(&p);
+  GradCfg gc{};
+  gc.dX = dX;
+  gc.dL = dL;
+  gc.dl_mask = dL ? (uint8_t)0 : dL_status_mask;
+  gc.cond_adj = p.cond_fp64;
+  gc.deg_tol = prm ? prm->deg_tol : p.deg_tol;
+  gc.gacc = ctx->d_gacc;
+  gc.flush_tiles = 64;
+  st = solve_impl(ctx, s, bc, prm, T, X, L, status, iters, rho, &gc);
+  if (st != FPT_OK) return st;
+  const SceneDev S = scene_dev(s);
+  ProfScope ps(ctx, FPT_K_OTHER);
+  CUDA_OR_FAIL(ctx, launch_backward_finalize(S, nullptr, ctx->d_gacc, g_tx, g_rx, g_vertices, ctx->stream));
   return FPT_OK;
 }
 
@@ -749,15 +812,8 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   st = ensure_buckets(ctx, b, scene_dev(s));
   if (st != FPT_OK) return st;
-  const size_t need = (size_t)(9 * s->n_obj + 3 * (s->n_tx + s->n_rx));
-  if (need > ctx->gacc_cap) {
-    cudaFree(ctx->d_gacc);
-    ctx->d_gacc = nullptr;
-    ctx->gacc_cap = 0;
-    CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_gacc, need * sizeof(double)));
-    ctx->gacc_cap = need;
-  }
-  CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_gacc, 0, need * sizeof(double), ctx->stream));
+  st = ensure_gacc(ctx, s);
+  if (st != FPT_OK) return st;
   const SceneDev S = scene_dev(s);
   fpt_solve_params p;
   fpt_default_params(&p);

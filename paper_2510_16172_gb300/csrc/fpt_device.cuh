@@ -251,6 +251,16 @@ __device__ __forceinline__ void fetch_path(const BatchDev& B, int n, const uint6
     decode_global(B, list[j], d);
 }
 
+// Path source of a kernel compiled for order N: the bucket list, else the
+// exhaustive enumeration of order N (both keep the descriptor in registers).
+template <int N>
+__device__ __forceinline__ void fetch_path_n(const BatchDev& B, const uint64_t* list, uint64_t j, PathDesc& d) {
+  if (list != nullptr)
+    decode_listed<N>(B, B.alphabet, list[j], d);
+  else
+    decode_exhaustive_order(B, N, j, d);
+}
+
 // Stage `count` elements of T from global to shared memory (whole CTA).
 template <typename T>
 __device__ __forceinline__ void stage(T* dst, const T* src, int count) {

@@ -54,12 +54,28 @@ struct BackwardCfg {
 cudaError_t launch_bfgs(int n, int pattern, const SceneDev& S, const BatchDev& B, const SolveCfg& cfg, uint64_t n_local,
                         const uint64_t* list, float* T, uint8_t* status, uint8_t* iters, cudaStream_t stream,
                         int n_sm, unsigned long long* work);
+// The implicit backward fused into the polish (fpt_solve_grad): cotangents
+// known at solve time, sums into FP64 accumulators.
+struct GradCfg {
+  const float* dX;          // [N][n_max][3] or nullptr
+  const float* dL;          // [N] or nullptr
+  uint8_t dl_mask;          // with no dL array: dL = 1 where (status & dl_mask) == dl_mask (0 = no length term)
+  float cond_adj;           // pivot test of the adjoint solve
+  float deg_tol;
+  double* gacc;             // 9 n_obj + 3 (n_tx + n_rx) FP64 accumulators
+  uint32_t* rescue_list;    // paths whose adjoint runs in the FP64 pass (n_local entries)
+  unsigned* rescue_count;
+  int flush_tiles;          // flush the shared accumulators every this many CTA tiles
+};
+
 // Double-float polish, then an FP64 pass over the paths whose FP32 pivots failed
 // (rescue_list: scratch of n_local entries; rescue_count: one device counter).
+// With grad != nullptr the same kernel also forms each path's VJP from its
+// polished state and sums it, and an FP64 adjoint pass follows.
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                           const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                           uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
-                          unsigned* rescue_count);
+                          unsigned* rescue_count, const GradCfg* grad = nullptr);
 // Adjoint + sums, then an FP64 pass over the paths whose FP32 pivots failed.
 cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,
                             const uint64_t* list, const float* T, const uint8_t* status, const float* dX,
@@ -73,6 +89,11 @@ cudaError_t launch_backward_noalloc(int device, const SceneDev& S, const BatchDe
                                     const uint64_t* const* lists, const uint64_t* counts, const float* T,
                                     const uint8_t* status, const float* dX, const float* dL, float* g_tx, float* g_rx,
                                     float* g_vertices, cudaStream_t stream, int n_sm);
+// FP64 adjoint over a rescue list (paths of one order slice).
+cudaError_t launch_backward_rescue(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
+                                   uint64_t n_local, const uint64_t* list, const float* T, const uint8_t* status,
+                                   const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm,
+                                   const uint32_t* rescue_list, const unsigned* rescue_count);
 cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
                                      float* g_rx, float* g_vertices, cudaStream_t stream);
 

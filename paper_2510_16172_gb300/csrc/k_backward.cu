@@ -16,118 +16,10 @@
 // a1 = e1 - e0).
 #include <mutex>
 
-#include "blocktri.cuh"
 #include "fpt_kernels.h"
+#include "vjp.cuh"
 
 namespace fpt {
-
-// Warp-aggregated accumulate of `cnt` values into acc[base + k]: lanes that
-// share a base add their sums once; others add their own.
-template <int CNT>
-__device__ __forceinline__ void warp_accumulate(float* acc, int base, const float (&v)[CNT], bool shared_acc,
-                                                double* gacc, int gbase) {
-  const unsigned full = 0xffffffffu;
-  const int b0 = __shfl_sync(full, base, 0);
-  const bool uniform = __all_sync(full, base == b0);
-  if (uniform) {
-    if (b0 < 0) return;
-    float s[CNT];
-#pragma unroll
-    for (int k = 0; k < CNT; ++k) {
-      float x = v[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(full, x, o);
-      s[k] = x;
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-      for (int k = 0; k < CNT; ++k) {
-        if (shared_acc)
-          atomicAdd(acc + b0 + k, s[k]);
-        else
-          atomicAdd(gacc + gbase + k, (double)s[k]);
-      }
-    }
-  } else if (base >= 0) {
-#pragma unroll
-    for (int k = 0; k < CNT; ++k) {
-      if (shared_acc)
-        atomicAdd(acc + base + k, v[k]);
-      else
-        atomicAdd(gacc + gbase + k, (double)v[k]);
-    }
-  }
-}
-
-// Per-path VJP (Sec. III-D) in precision R from the segment vectors z_j, the
-// basis vectors a and the parameters t: solve H u = -v (block LDL^T) and form
-// the per-slot gradients (d/db, d/da1, d/da2) and the TX / RX gradients.
-// Returns false (and no gradient) if the pivot test fails.
-template <typename R, int N>
-__device__ __forceinline__ bool path_vjp(const R (&z)[N + 1][3], const R (&a)[N][2][3], const R (&t)[N][2],
-                                         const bool (&edge)[N], const R (&dx)[N][3], R dl, R cond,
-                                         R (&gb)[N][9], R (&gtx)[3], R (&grx)[3]) {
-  constexpr int M = 2 * N;
-  R u[N + 1][3], il[N + 1];
-#pragma unroll
-  for (int jj = 0; jj <= N; ++jj) {
-    const R e = z[jj][0] * z[jj][0] + z[jj][1] * z[jj][1] + z[jj][2] * z[jj][2];
-    const R r = e > R(0) ? rsqrt_r<R>(e) : R(0);
-    il[jj] = r;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) u[jj][c] = z[jj][c] * r;
-  }
-  R dd[N][3], v[M];
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) dd[i][c] = u[i][c] - u[i + 1][c];
-    // v = A^T dX + dL grad_T L
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const R gk = a[i][k][0] * dd[i][0] + a[i][k][1] * dd[i][1] + a[i][k][2] * dd[i][2];
-      const R ak = a[i][k][0] * dx[i][0] + a[i][k][1] * dx[i][1] + a[i][k][2] * dx[i][2];
-      v[2 * i + k] = ak + dl * gk;
-    }
-  }
-  BlockTri<R, N> F;
-  if (!factor_hessian<R, N>(u, il, a, edge, cond, F)) return false;
-  R r[M], lam[M];
-#pragma unroll
-  for (int k = 0; k < M; ++k) r[k] = -v[k];
-  solve_hessian<R, N>(F, r, lam);
-  // q_j = M_j Dw_j with w_i = A_i u_i
-  R q[N + 1][3];
-#pragma unroll
-  for (int jj = 0; jj <= N; ++jj) {
-    R dw[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      R x = R(0);
-      if (jj < N) x += a[jj][0][c] * lam[2 * jj] + a[jj][1][c] * lam[2 * jj + 1];
-      if (jj > 0) x -= a[jj - 1][0][c] * lam[2 * jj - 2] + a[jj - 1][1][c] * lam[2 * jj - 1];
-      dw[c] = x;
-    }
-    const R ud = u[jj][0] * dw[0] + u[jj][1] * dw[1] + u[jj][2] * dw[2];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) q[jj][c] = (dw[c] - u[jj][c] * ud) * il[jj];
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const R e = dx[i][c] + dl * dd[i][c] + (q[i][c] - q[i + 1][c]);
-      gb[i][c] = e;
-      gb[i][3 + c] = e * t[i][0] + dd[i][c] * lam[2 * i];
-      gb[i][6 + c] = e * t[i][1] + dd[i][c] * lam[2 * i + 1];
-    }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    gtx[c] = -dl * u[0][c] - q[0][c];
-    grx[c] = dl * u[N][c] + q[N][c];
-  }
-  return true;
-}
 
 template <int N>
 __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev B, BackwardCfg cfg,
@@ -165,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
     bool use = false;
     uint8_t st = 0;
     if (have) {
-      fetch_path(B, N, list, j, d);
+      fetch_path_n<N>(B, list, j, d);
       st = d.flags;
       if (status) st |= status[d.g];
       use = !(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE));
@@ -279,10 +171,12 @@ __global__ void __launch_bounds__(kThreads) backward_rescue_kernel(SceneDev S, B
   const int n_max = B.n_max;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
     PathDesc d;
-    fetch_path(B, N, list, rescue_list[k], d);
+    fetch_path_n<N>(B, list, rescue_list[k], d);
     const uint64_t g = d.g;
     uint8_t st = d.flags;
     if (status) st |= status[g];
+    // the fused polish also lists paths whose polish went to the FP64 pass: their final status decides
+    if (st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE)) continue;
     double a[N][2][3], t[N][2], z[N + 1][3], dx[N][3];
     bool edge[N];
 #pragma unroll
@@ -352,6 +246,40 @@ __global__ void backward_finalize_kernel(int n_obj, int n_tx, int n_rx, const fl
   }
 }
 
+// FP64 adjoint over the listed paths (a few percent of a slice of n_local paths).
+template <int N>
+static cudaError_t launch_backward_rescue_n(const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
+                                            uint64_t n_local, const uint64_t* list, const float* T,
+                                            const uint8_t* status, const float* dX, const float* dL, double* gacc,
+                                            cudaStream_t stream, int n_sm, const uint32_t* rescue_list,
+                                            const unsigned* rescue_count) {
+  const uint64_t rwant = (n_local / 16 + kThreads - 1) / kThreads;
+  const unsigned rgrid = (unsigned)(rwant < (uint64_t)n_sm * 4 ? (rwant ? rwant : 1) : (uint64_t)n_sm * 4);
+  backward_rescue_kernel<N><<<rgrid, kThreads, 0, stream>>>(S, B, cfg, list, T, status, dX, dL, gacc, rescue_list,
+                                                             rescue_count);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_rescue(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
+                                   uint64_t n_local, const uint64_t* list, const float* T, const uint8_t* status,
+                                   const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm,
+                                   const uint32_t* rescue_list, const unsigned* rescue_count) {
+  switch (n) {
+    case 1: return launch_backward_rescue_n<1>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm,
+                                               rescue_list, rescue_count);
+    case 2: return launch_backward_rescue_n<2>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm,
+                                               rescue_list, rescue_count);
+    case 3: return launch_backward_rescue_n<3>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm,
+                                               rescue_list, rescue_count);
+    case 4: return launch_backward_rescue_n<4>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm,
+                                               rescue_list, rescue_count);
+    case 5: return launch_backward_rescue_n<5>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm,
+                                               rescue_list, rescue_count);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int N>
 static cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg_in,
                                      uint64_t n_local, const uint64_t* list, const float* T, const uint8_t* status,
@@ -385,12 +313,8 @@ static cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const uint64_t rwant = (n_local / 16 + kThreads - 1) / kThreads;
-  const unsigned rgrid = (unsigned)(rwant < (uint64_t)n_sm * 4 ? (rwant ? rwant : 1) : (uint64_t)n_sm * 4);
-  backward_rescue_kernel<N><<<rgrid, kThreads, 0, stream>>>(S, B, cfg, list, T, status, dX, dL, gacc, rescue_list,
-                                                             rescue_count);
-  count_launch();
-  return cudaGetLastError();
+  return launch_backward_rescue_n<N>(S, B, cfg, n_local, list, T, status, dX, dL, gacc, stream, n_sm, rescue_list,
+                                     rescue_count);
 }
 
 cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,

@@ -8,16 +8,16 @@
 // fraction of its FP32 rate) or FP64 (validation mode).  The parameters are
 // carried in that precision through the steps.  The first-order condition of
 // Eq. 8 measures the result: rho = max_i |A_i delta_i| (metres), where delta
-// solves H delta = -grad_T L at the final parameters (the factorisation from
-// the last step is reused); T, X and L are then rounded to FP32 for output.
+// solves H delta = -grad_T L at the final parameters (H factorised there);
+// T, X and L are then rounded to FP32 for output.
 // The validity test (Sec. I, Sec. III: points inside their objects) uses
 // closed intervals on the output t.
 //
 // The same kernel evaluates rho, validity and the boundary distance at
 // caller-given parameters (POLISH_VALIDITY) without changing them.
-#include "blocktri.cuh"
 #include "ff.cuh"
 #include "fpt_kernels.h"
+#include "vjp.cuh"
 
 namespace fpt {
 
@@ -73,7 +73,8 @@ struct GeoFF {
 // difference u_i - u_{i+1} is formed in double-float before rounding).
 template <int N>
 __device__ __forceinline__ void gradff(const GeoFF<N>& G, const ff (&t)[N][2], float (&uf)[N + 1][3],
-                                       float (&ilf)[N + 1], ff (&len)[N + 1], float (&g)[2 * N]) {
+                                       float (&ilf)[N + 1], ff (&len)[N + 1], float (&g)[2 * N],
+                                       float (&dd)[N][3]) {
   ff uo[N + 1][3];
   ff w[N][3];
 #pragma unroll
@@ -119,11 +120,11 @@ __device__ __forceinline__ void gradff(const GeoFF<N>& G, const ff (&t)[N][2], f
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    float d[3];
+    float (&d)[3] = dd[i];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      ff dd = ff_sub(uo[i][c], uo[i + 1][c]);
-      d[c] = __fadd_rn(dd.hi, dd.lo);
+      ff dc = ff_sub(uo[i][c], uo[i + 1][c]);
+      d[c] = __fadd_rn(dc.hi, dc.lo);
     }
     g[2 * i] = fmaf(G.ah[i][0][2], d[2], fmaf(G.ah[i][0][1], d[1], G.ah[i][0][0] * d[0]));
     g[2 * i + 1] = fmaf(G.ah[i][1][2], d[2], fmaf(G.ah[i][1][1], d[1], G.ah[i][1][0] * d[0]));
@@ -193,190 +194,285 @@ __device__ __forceinline__ void newton_dir(const BlockTri<float, N>& F32, const 
 // ---------------------------------------------------------------------------
 // double-float polish (default)
 // ---------------------------------------------------------------------------
+// Register budget of the double-float polish: up to order 3 the kernel fits in
+// 168 registers without spilling, which allows 3 CTAs per SM instead of 2.
 template <int N>
-__global__ void __launch_bounds__(kThreads) polish_ff_kernel(SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local,
-                                                             const uint64_t* __restrict__ list, float* __restrict__ T,
-                                                             float* __restrict__ X, float* __restrict__ Lout,
-                                                             uint8_t* __restrict__ status, float* __restrict__ rho_out,
-                                                             uint8_t* __restrict__ mask_out,
-                                                             float* __restrict__ bdist_out, int use_smem,
-                                                             uint32_t* __restrict__ rescue_list,
-                                                             unsigned* __restrict__ rescue_count) {
+constexpr int kPolishMinBlocks = N <= 3 ? 3 : 1;
+
+// use_smem bits of the polish kernels: records staged, gradient sums in shared memory.
+constexpr int kSmemRecords = 1;
+constexpr int kSmemAcc = 2;
+
+// kGrad: the implicit backward fused in (fpt_solve_grad).  The polished path's
+// geometry, unit directions, inverse lengths, u_i - u_{i+1} and the Hessian
+// factorisation at the returned point are still in registers, so the VJP
+// costs one block-tridiagonal solve and the sums.  The adjoint's stricter
+// pivot test is taken on the same factorisation; paths that fail it -- or
+// whose polish went to the FP64 pass -- are listed for the FP64 adjoint pass.
+template <int N, bool kGrad>
+__global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kernel(
+    SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local, const uint64_t* __restrict__ list,
+    float* __restrict__ T, float* __restrict__ X, float* __restrict__ Lout, uint8_t* __restrict__ status,
+    float* __restrict__ rho_out, uint8_t* __restrict__ mask_out, float* __restrict__ bdist_out, int use_smem,
+    uint32_t* __restrict__ rescue_list, unsigned* __restrict__ rescue_count, GradCfg gc) {
   constexpr int M = 2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const float* rec32 = S.rec32;
   const float* reclo = S.reclo;
   const float* aux = S.aux;
-  if (use_smem) {
+  float* s_acc = nullptr;
+  if (use_smem & kSmemRecords) {
     float* s32 = reinterpret_cast<float*>(smem_raw);
     float* slo = s32 + S.n_obj * kRec32;
     float* sax = slo + S.n_obj * kRecLo;
     stage(s32, S.rec32, S.n_obj * kRec32);
     stage(slo, S.reclo, S.n_obj * kRecLo);
     stage(sax, S.aux, S.n_obj * kAux);
-    __syncthreads();
     rec32 = s32;
     reclo = slo;
     aux = sax;
+    s_acc = sax + S.n_obj * kAux;
   }
+  const int n_acc = S.n_obj * 9 + 3 * (S.n_tx + S.n_rx);
+  const int acc_tx = S.n_obj * 9, acc_rx = acc_tx + 3 * S.n_tx;
+  const bool sm_acc = kGrad && (use_smem & kSmemAcc);
+  if (sm_acc)
+    for (int k = threadIdx.x; k < n_acc; k += blockDim.x) s_acc[k] = 0.f;
+  __syncthreads();
   const int n_max = B.n_max;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_local; j += stride) {
-    PathDesc d;
-    fetch_path(B, N, list, j, d);
-    const uint64_t g = d.g;
-    uint8_t st = d.flags;
-    if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE);
-    // geometry: b as hi + lo, A as hi + lo
-    GeoFF<N> G;
-    bool edge[N];
+  int tiles = 0;
+  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
+    const uint64_t j = j0 + threadIdx.x;
+    const bool have = j < n_local;
+    // per-path gradient terms (kGrad), summed over the warp below
+    float gb[N][9], gtx[3], grx[3];
+    int acc_id[N], acc_t = -1, acc_r = -1;
+    if constexpr (kGrad) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const float* r = rec32 + kRec32 * d.ids[i];
-      const float* rl = reclo + kRecLo * d.ids[i];
+      for (int i = 0; i < N; ++i) {
+        acc_id[i] = -1;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        G.ah[i][0][c] = r[6 + c];
-        G.ah[i][1][c] = r[9 + c];
-        G.al[i][0][c] = rl[c];
-        G.al[i][1][c] = rl[3 + c];
+        for (int k = 0; k < 9; ++k) gb[i][k] = 0.f;
       }
-      edge[i] = aux[kAux * d.ids[i] + 2] != 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gtx[c] = grx[c] = 0.f;
     }
-    {
-      float bh[N + 2][3], bl[N + 2][3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        bh[0][c] = __ldg(S.tx32 + kEnd32 * d.tx + c);
-        bl[0][c] = __ldg(S.tx32 + kEnd32 * d.tx + 3 + c);
-        bh[N + 1][c] = __ldg(S.rx32 + kEnd32 * d.rx + c);
-        bl[N + 1][c] = __ldg(S.rx32 + kEnd32 * d.rx + 3 + c);
-      }
+    if (have) {
+      PathDesc d;
+      fetch_path_n<N>(B, list, j, d);
+      const uint64_t g = d.g;
+      uint8_t st = d.flags;
+      if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE);
+      // geometry: b as hi + lo, A as hi + lo
+      GeoFF<N> G;
+      bool edge[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const float* r = rec32 + kRec32 * d.ids[i];
+        const float* rl = reclo + kRecLo * d.ids[i];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          bh[i + 1][c] = r[c];
-          bl[i + 1][c] = r[3 + c];
+          G.ah[i][0][c] = r[6 + c];
+          G.ah[i][1][c] = r[9 + c];
+          G.al[i][0][c] = rl[c];
+          G.al[i][1][c] = rl[3 + c];
         }
+        edge[i] = aux[kAux * d.ids[i] + 2] != 0.f;
       }
-#pragma unroll
-      for (int jj = 0; jj <= N; ++jj)
+      {
+        float bh[N + 2][3], bl[N + 2][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          ff sd = two_sum(bh[jj + 1][c], -bh[jj][c]);
-          G.db[jj][c] = fast_two_sum(sd.hi, __fadd_rn(sd.lo, __fsub_rn(bl[jj + 1][c], bl[jj][c])));
+          bh[0][c] = __ldg(S.tx32 + kEnd32 * d.tx + c);
+          bl[0][c] = __ldg(S.tx32 + kEnd32 * d.tx + 3 + c);
+          bh[N + 1][c] = __ldg(S.rx32 + kEnd32 * d.rx + c);
+          bl[N + 1][c] = __ldg(S.rx32 + kEnd32 * d.rx + 3 + c);
         }
-    }
-    // parameters
-    const float2* Ti = reinterpret_cast<const float2*>(T) + g * (uint64_t)n_max;
-    ff t[N][2];
-    bool finite = true;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float2 v = Ti[i];
-      t[i][0] = ff{v.x, 0.f};
-      t[i][1] = ff{v.y, 0.f};
-      finite = finite && isfinite(v.x) && isfinite(v.y);
-    }
-    if (!finite) st |= ST_NONFINITE;
-    float rho = INFINITY;
-    ff len[N + 1];
+        for (int i = 0; i < N; ++i) {
+          const float* r = rec32 + kRec32 * d.ids[i];
 #pragma unroll
-    for (int k = 0; k <= N; ++k) len[k] = ff{0.f, 0.f};
-    if (!(st & ST_INVALID) && finite) {
-      float uf[N + 1][3], ilf[N + 1], gr[M];
-      gradff<N>(G, t, uf, ilf, len, gr);
-      float lmin = len[0].hi;
-#pragma unroll
-      for (int k = 1; k <= N; ++k) lmin = fminf(lmin, len[k].hi);
-      if (!(st & ST_REPEAT) && lmin >= cfg.deg_tol) {
-        BlockTri<float, N> F32;
-        const int steps = cfg.mode == POLISH_SOLVE ? cfg.steps : 0;
-        if (factor_hessian<float, N>(uf, ilf, G.ah, edge, cfg.cond_fp64, F32)) {
-          float delta[M], r[M];
-          for (int s = 0; s < steps; ++s) {
-#pragma unroll
-            for (int k = 0; k < M; ++k) r[k] = -gr[k];
-            solve_hessian<float, N>(F32, r, delta);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              ff a0 = two_sum(t[i][0].hi, delta[2 * i]);
-              t[i][0] = fast_two_sum(a0.hi, __fadd_rn(a0.lo, t[i][0].lo));
-              if (!edge[i]) {
-                ff a1 = two_sum(t[i][1].hi, delta[2 * i + 1]);
-                t[i][1] = fast_two_sum(a1.hi, __fadd_rn(a1.lo, t[i][1].lo));
-              }
-            }
-            gradff<N>(G, t, uf, ilf, len, gr);
+          for (int c = 0; c < 3; ++c) {
+            bh[i + 1][c] = r[c];
+            bl[i + 1][c] = r[3 + c];
           }
+        }
+#pragma unroll
+        for (int jj = 0; jj <= N; ++jj)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            ff sd = two_sum(bh[jj + 1][c], -bh[jj][c]);
+            G.db[jj][c] = fast_two_sum(sd.hi, __fadd_rn(sd.lo, __fsub_rn(bl[jj + 1][c], bl[jj][c])));
+          }
+      }
+      // parameters
+      const float2* Ti = reinterpret_cast<const float2*>(T) + g * (uint64_t)n_max;
+      ff t[N][2];
+      bool finite = true;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float2 v = Ti[i];
+        t[i][0] = ff{v.x, 0.f};
+        t[i][1] = ff{v.y, 0.f};
+        finite = finite && isfinite(v.x) && isfinite(v.y);
+      }
+      if (!finite) st |= ST_NONFINITE;
+      float rho = INFINITY;
+      ff len[N + 1];
+#pragma unroll
+      for (int k = 0; k <= N; ++k) len[k] = ff{0.f, 0.f};
+      // state the fused backward reuses
+      float uf[N + 1][3], ilf[N + 1], dd[N][3];
+      BlockTri<float, N> F32;
+      bool fact_ok = false, adj_ok = false, listed64 = false;
+      if (!(st & ST_INVALID) && finite) {
+        // Newton steps, then the residual: one gradient, factorisation and solve per pass (one code copy each)
+        const int steps = cfg.mode == POLISH_SOLVE ? cfg.steps : 0;
+        for (int s = 0;; ++s) {
+          float gr[M];
+          gradff<N>(G, t, uf, ilf, len, gr, dd);
+          float lmin = len[0].hi;
+#pragma unroll
+          for (int k = 1; k <= N; ++k) lmin = fminf(lmin, len[k].hi);
+          if ((st & ST_REPEAT) || !(lmin >= cfg.deg_tol)) {
+            if (!(st & ST_REPEAT)) st |= ST_DEGENERATE;  // a kink: no Newton system
+            break;
+          }
+          bool strict = true;
+          fact_ok = factor_hessian<float, N>(uf, ilf, G.ah, edge, cfg.cond_fp64, F32, kGrad ? gc.cond_adj : 0.f,
+                                             &strict);
+          if (!fact_ok) {
+            // FP32 pivots failed: the FP64 pass over the rescue list redoes this path
+            st |= ST_FP64;
+            rescue_list[atomicAdd(rescue_count, 1u)] = (uint32_t)j;
+            listed64 = true;
+            break;
+          }
+          float delta[M], r[M];
 #pragma unroll
           for (int k = 0; k < M; ++k) r[k] = -gr[k];
           solve_hessian<float, N>(F32, r, delta);
-          rho = world_max<N>(G.ah, delta);
-        } else {
-          // FP32 pivots failed: the FP64 pass over the rescue list redoes this path
-          st |= ST_FP64;
-          rescue_list[atomicAdd(rescue_count, 1u)] = (uint32_t)j;
-        }
-        lmin = len[0].hi;
+          if (s >= steps) {
+            // at the returned point: the residual, and for the adjoint its own pivot test
+            rho = world_max<N>(G.ah, delta);
+            adj_ok = strict;
+            break;
+          }
 #pragma unroll
-        for (int k = 1; k <= N; ++k) lmin = fminf(lmin, len[k].hi);
-      }
-      if (!(st & ST_REPEAT) && !(lmin >= cfg.deg_tol)) st |= ST_DEGENERATE;
-    }
-    float tf[N][2], h1[N], h2[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      tf[i][0] = t[i][0].hi;
-      tf[i][1] = t[i][1].hi;
-      h1[i] = aux[kAux * d.ids[i]];
-      h2[i] = aux[kAux * d.ids[i] + 1];
-    }
-    float bd;
-    const bool inside = validity<N>(tf, edge, h1, h2, bd);
-    st = final_status(st, inside, rho, cfg.solved_tol);
-    if (cfg.mode == POLISH_SOLVE) {
-      float2* To = reinterpret_cast<float2*>(T) + g * (uint64_t)n_max;
-#pragma unroll
-      for (int i = 0; i < N; ++i) To[i] = make_float2(tf[i][0], tf[i][1]);
-      status[g] = st;
-      if (X) {
-        float* Xo = X + g * (uint64_t)n_max * 3;
-#pragma unroll
-        for (int i = 0; i < kMaxOrder; ++i)
-          if (i < n_max)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              float x = 0.f;
-              if (i < N) {
-                ff p1 = two_prod(G.ah[i][0][c], t[i][0].hi);
-                ff p2 = two_prod(G.ah[i][1][c], t[i][1].hi);
-                float lo = __fadd_rn(p1.lo, p2.lo);
-                lo = __fmaf_rn(G.ah[i][0][c], t[i][0].lo, lo);
-                lo = __fmaf_rn(G.al[i][0][c], t[i][0].hi, lo);
-                lo = __fmaf_rn(G.ah[i][1][c], t[i][1].lo, lo);
-                lo = __fmaf_rn(G.al[i][1][c], t[i][1].hi, lo);
-                ff w = ff_add(p1, ff{p2.hi, lo});
-                const float* rb = rec32 + kRec32 * d.ids[i];
-                ff xr = ff_add(ff{rb[c], rb[3 + c]}, w);
-                ff xw = ff_add(xr, ff{S.centre_hi[c], S.centre_lo[c]});
-                x = __fadd_rn(xw.hi, xw.lo);
-              }
-              Xo[3 * i + c] = x;
+          for (int i = 0; i < N; ++i) {
+            ff a0 = two_sum(t[i][0].hi, delta[2 * i]);
+            t[i][0] = fast_two_sum(a0.hi, __fadd_rn(a0.lo, t[i][0].lo));
+            if (!edge[i]) {
+              ff a1 = two_sum(t[i][1].hi, delta[2 * i + 1]);
+              t[i][1] = fast_two_sum(a1.hi, __fadd_rn(a1.lo, t[i][1].lo));
             }
+          }
+        }
       }
-      if (Lout) {
-        ff Ls{0.f, 0.f};
+      float tf[N][2], h1[N], h2[N];
 #pragma unroll
-        for (int k = 0; k <= N; ++k) Ls = ff_add(Ls, len[k]);
-        Lout[g] = (!(st & ST_INVALID) && finite) ? __fadd_rn(Ls.hi, Ls.lo) : NAN;
+      for (int i = 0; i < N; ++i) {
+        tf[i][0] = t[i][0].hi;
+        tf[i][1] = t[i][1].hi;
+        h1[i] = aux[kAux * d.ids[i]];
+        h2[i] = aux[kAux * d.ids[i] + 1];
+      }
+      float bd;
+      const bool inside = validity<N>(tf, edge, h1, h2, bd);
+      st = final_status(st, inside, rho, cfg.solved_tol);
+      if constexpr (kGrad) {
+        if (listed64) {
+          // the FP64 polish decides this path's status; the FP64 adjoint pass reads it
+          gc.rescue_list[atomicAdd(gc.rescue_count, 1u)] = (uint32_t)j;
+        } else if (!(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE))) {
+          if (fact_ok && adj_ok) {
+            const float dl = gc.dL ? gc.dL[g] : ((gc.dl_mask && (st & gc.dl_mask) == gc.dl_mask) ? 1.f : 0.f);
+            float dx[N][3];
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) dx[i][c] = gc.dX ? gc.dX[(g * (uint64_t)n_max + i) * 3 + c] : 0.f;
+            vjp_solved<float, N>(uf, ilf, dd, G.ah, tf, F32, dx, dl, gb, gtx, grx);
+#pragma unroll
+            for (int i = 0; i < N; ++i) acc_id[i] = d.ids[i];
+            acc_t = d.tx;
+            acc_r = d.rx;
+          } else {
+            gc.rescue_list[atomicAdd(gc.rescue_count, 1u)] = (uint32_t)j;
+          }
+        }
+      }
+      if (cfg.mode == POLISH_SOLVE) {
+        float2* To = reinterpret_cast<float2*>(T) + g * (uint64_t)n_max;
+#pragma unroll
+        for (int i = 0; i < N; ++i) To[i] = make_float2(tf[i][0], tf[i][1]);
+        status[g] = st;
+        if (X) {
+          float* Xo = X + g * (uint64_t)n_max * 3;
+#pragma unroll
+          for (int i = 0; i < kMaxOrder; ++i)
+            if (i < n_max)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                float x = 0.f;
+                if (i < N) {
+                  ff p1 = two_prod(G.ah[i][0][c], t[i][0].hi);
+                  ff p2 = two_prod(G.ah[i][1][c], t[i][1].hi);
+                  float lo = __fadd_rn(p1.lo, p2.lo);
+                  lo = __fmaf_rn(G.ah[i][0][c], t[i][0].lo, lo);
+                  lo = __fmaf_rn(G.al[i][0][c], t[i][0].hi, lo);
+                  lo = __fmaf_rn(G.ah[i][1][c], t[i][1].lo, lo);
+                  lo = __fmaf_rn(G.al[i][1][c], t[i][1].hi, lo);
+                  ff w = ff_add(p1, ff{p2.hi, lo});
+                  const float* rb = rec32 + kRec32 * d.ids[i];
+                  ff xr = ff_add(ff{rb[c], rb[3 + c]}, w);
+                  ff xw = ff_add(xr, ff{S.centre_hi[c], S.centre_lo[c]});
+                  x = __fadd_rn(xw.hi, xw.lo);
+                }
+                Xo[3 * i + c] = x;
+              }
+        }
+        if (Lout) {
+          ff Ls{0.f, 0.f};
+#pragma unroll
+          for (int k = 0; k <= N; ++k) Ls = ff_add(Ls, len[k]);
+          Lout[g] = (!(st & ST_INVALID) && finite) ? __fadd_rn(Ls.hi, Ls.lo) : NAN;
+        }
+      }
+      if (rho_out) rho_out[g] = rho;
+      if (mask_out) mask_out[g] = (st & ST_VALID) ? 1 : 0;
+      if (bdist_out) bdist_out[g] = bd;
+    }
+    if constexpr (kGrad) {
+      // sums over paths (all lanes of the warp take part)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int id = acc_id[i];
+        warp_accumulate<9>(s_acc, id >= 0 ? 9 * id : -1, gb[i], sm_acc, gc.gacc, 9 * id);
+      }
+      warp_accumulate<3>(s_acc, acc_t >= 0 ? acc_tx + 3 * acc_t : -1, gtx, sm_acc, gc.gacc, acc_tx + 3 * acc_t);
+      warp_accumulate<3>(s_acc, acc_r >= 0 ? acc_rx + 3 * acc_r : -1, grx, sm_acc, gc.gacc, acc_rx + 3 * acc_r);
+      if (sm_acc && ++tiles >= gc.flush_tiles) {
+        tiles = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < n_acc; k += blockDim.x) {
+          const float x = s_acc[k];
+          if (x != 0.f) {
+            atomicAdd(gc.gacc + k, (double)x);
+            s_acc[k] = 0.f;
+          }
+        }
+        __syncthreads();
       }
     }
-    if (rho_out) rho_out[g] = rho;
-    if (mask_out) mask_out[g] = (st & ST_VALID) ? 1 : 0;
-    if (bdist_out) bdist_out[g] = bd;
+  }
+  if (sm_acc) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_acc; k += blockDim.x) {
+      const float x = s_acc[k];
+      if (x != 0.f) atomicAdd(gc.gacc + k, (double)x);
+    }
   }
 }
 
@@ -416,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_iter; k += stride) {
     const uint64_t j = rescue_list ? (uint64_t)rescue_list[k] : k;
     PathDesc d;
-    fetch_path(B, N, list, j, d);
+    fetch_path_n<N>(B, list, j, d);
     const uint64_t g = d.g;
     uint8_t st = d.flags;
     if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE);
@@ -463,11 +559,17 @@ __global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev
     for (int k = 0; k <= N; ++k) len[k] = 0.0;
     float rho = INFINITY;
     if (!(st & ST_INVALID) && finite) {
-      grad64<N>(G, t, len, u, gr);
-      double lmin = len[0];
+      // Newton steps, then the residual, each with the Hessian factorised at the current point
+      const int steps = cfg.mode == POLISH_SOLVE ? cfg.steps : 0;
+      for (int s = 0;; ++s) {
+        grad64<N>(G, t, len, u, gr);
+        double lmin = len[0];
 #pragma unroll
-      for (int k = 1; k <= N; ++k) lmin = fmin(lmin, len[k]);
-      if (!(st & ST_REPEAT) && lmin >= (double)cfg.deg_tol) {
+        for (int k = 1; k <= N; ++k) lmin = fmin(lmin, len[k]);
+        if ((st & ST_REPEAT) || !(lmin >= (double)cfg.deg_tol)) {
+          if (!(st & ST_REPEAT)) st |= ST_DEGENERATE;  // a kink: no Newton system
+          break;
+        }
         BlockTri<float, N> F32;
         BlockTri<double, N> F64;
         float uf[N + 1][3], ilf[N + 1];
@@ -487,30 +589,21 @@ __global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev
           ok = factor_hessian<double, N>(u, il, G.a, edge, (double)cfg.cond_fp64 * 1e-6, F64);
           st |= ST_FP64;
         }
-        if (ok) {
-          float gf[M], delta[M];
-          const int steps = cfg.mode == POLISH_SOLVE ? cfg.steps : 0;
-          for (int s = 0; s < steps; ++s) {
+        if (!ok) break;
+        float gf[M], delta[M];
 #pragma unroll
-            for (int k = 0; k < M; ++k) gf[k] = (float)gr[k];
-            newton_dir<N>(F32, F64, use64, gf, delta);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              t[i][0] += (double)delta[2 * i];
-              if (!edge[i]) t[i][1] += (double)delta[2 * i + 1];
-            }
-            grad64<N>(G, t, len, u, gr);
-          }
-#pragma unroll
-          for (int k = 0; k < M; ++k) gf[k] = (float)gr[k];
-          newton_dir<N>(F32, F64, use64, gf, delta);
+        for (int k = 0; k < M; ++k) gf[k] = (float)gr[k];
+        newton_dir<N>(F32, F64, use64, gf, delta);
+        if (s >= steps) {
           rho = world_max<N>(a32, delta);
+          break;
         }
-        lmin = len[0];
 #pragma unroll
-        for (int k = 1; k <= N; ++k) lmin = fmin(lmin, len[k]);
+        for (int i = 0; i < N; ++i) {
+          t[i][0] += (double)delta[2 * i];
+          if (!edge[i]) t[i][1] += (double)delta[2 * i + 1];
+        }
       }
-      if (!(st & ST_REPEAT) && !(lmin >= (double)cfg.deg_tol)) st |= ST_DEGENERATE;
     }
     float tf[N][2];
 #pragma unroll
@@ -554,7 +647,7 @@ template <int N>
 static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                                    const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                                    uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
-                                   unsigned* rescue_count) {
+                                   unsigned* rescue_count, const GradCfg* grad) {
   const bool f64 = cfg.fp64 != 0;
   const size_t smem64 = (size_t)S.n_obj * (kRec64 * sizeof(double) + (kRec32 + kAux) * sizeof(float));
   const size_t smemff = (size_t)S.n_obj * (kRec32 + kRecLo + kAux) * sizeof(float);
@@ -573,10 +666,9 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
     return cudaSuccess;
   };
   const size_t s64 = smem64 <= 160 * 1024 ? smem64 : 0;
-  const size_t sff = smemff <= 160 * 1024 ? smemff : 0;
   unsigned grid = 0;
   cudaError_t e;
-  if (f64) {
+  if (f64 && !grad) {
     e = grid_of((const void*)polish64_kernel<N>, s64, n_local, grid);
     if (e != cudaSuccess || grid == 0) return e;
     polish64_kernel<N><<<grid, kThreads, s64, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
@@ -584,12 +676,38 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
     count_launch();
     return cudaGetLastError();
   }
+  if (f64) return cudaErrorInvalidValue;  // the fused backward runs with the double-float polish only
+  // shared memory: records, and with the fused backward its per-CTA sums
+  int use_smem = 0;
+  size_t sff = 0;
+  if (smemff <= 160 * 1024) {
+    use_smem = kSmemRecords;
+    sff = smemff;
+    if (grad) {
+      const size_t acc = (size_t)(9 * S.n_obj + 3 * (S.n_tx + S.n_rx)) * sizeof(float);
+      if (sff + acc <= 160 * 1024) {
+        use_smem |= kSmemAcc;
+        sff += acc;
+      }
+    }
+  }
   e = cudaMemsetAsync(rescue_count, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
-  e = grid_of((const void*)polish_ff_kernel<N>, sff, n_local, grid);
-  if (e != cudaSuccess || grid == 0) return e;
-  polish_ff_kernel<N><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
-                                                        sff != 0, rescue_list, rescue_count);
+  GradCfg gc{};
+  if (grad) {
+    gc = *grad;
+    e = cudaMemsetAsync(gc.rescue_count, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    e = grid_of((const void*)polish_ff_kernel<N, true>, sff, n_local, grid);
+    if (e != cudaSuccess || grid == 0) return e;
+    polish_ff_kernel<N, true><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask,
+                                                               bdist, use_smem, rescue_list, rescue_count, gc);
+  } else {
+    e = grid_of((const void*)polish_ff_kernel<N, false>, sff, n_local, grid);
+    if (e != cudaSuccess || grid == 0) return e;
+    polish_ff_kernel<N, false><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask,
+                                                                bdist, use_smem, rescue_list, rescue_count, gc);
+  }
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -599,18 +717,23 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
   polish64_kernel<N><<<grid, kThreads, s64, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist,
                                                        s64 != 0, rescue_list, rescue_count);
   count_launch();
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !grad) return e;
+  // FP64 adjoint for the paths the fused kernel listed (final T and status are in place)
+  const BackwardCfg bc{gc.cond_adj, gc.deg_tol, 0, 0, gc.dL ? (uint8_t)0 : gc.dl_mask};
+  return launch_backward_rescue(N, S, B, bc, n_local, list, T, status, gc.dX, gc.dL, gc.gacc, stream, n_sm,
+                                gc.rescue_list, gc.rescue_count);
 }
 
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                           const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                           uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
-                          unsigned* rescue_count) {
+                          unsigned* rescue_count, const GradCfg* grad) {
   switch (n) {
 #define FPT_POLISH_CASE(K)                                                                                   \
   case K:                                                                                                    \
     return launch_polish_n<K>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm, \
-                              rescue_list, rescue_count);
+                              rescue_list, rescue_count, grad);
     FPT_POLISH_CASE(1)
     FPT_POLISH_CASE(2)
     FPT_POLISH_CASE(3)

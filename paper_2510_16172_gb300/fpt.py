@@ -42,7 +42,7 @@ class SolveParams(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("fp_iters", C.c_int32), ("polish", C.c_int32), ("fixed_iters", C.c_int32),
                 ("tol_step", C.c_float), ("solved_tol", C.c_float), ("deg_tol", C.c_float), ("cond_fp64", C.c_float),
                 ("init_mode", C.c_int32), ("polish_fp64", C.c_int32), ("refill", C.c_int32),
-                ("specialize", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("specialize", C.c_int32), ("fuse_adjoint", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 # every symbol declared in include/fpt.h with (restype, argtypes)
@@ -67,6 +67,8 @@ _SIGS = {
     "fpt_solve": (C.c_int, [_vp, _vp, _vp, C.POINTER(SolveParams), _vp, _vp, _vp, _vp, _vp, _vp]),
     "fpt_validity": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fpt_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint8, _vp, _vp, _vp]),
+    "fpt_solve_grad": (C.c_int, [_vp, _vp, _vp, C.POINTER(SolveParams), _vp, _vp, C.c_uint8, _vp, _vp, _vp, _vp, _vp,
+                                 _vp, _vp, _vp, _vp]),
     "fpt_count_status": (C.c_int, [_vp, _vp, C.c_uint64, C.c_uint8, C.POINTER(C.c_uint64)]),
     "fpt_backward_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint8, _vp, _vp, _vp]),
     "fpt_tc_gemm_bf16": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
@@ -311,6 +313,34 @@ def solve(ctx: Context, scene: Scene, batch: Batch, params: SolveParams | None =
                                            _ptr(out.get("X")), _ptr(out.get("L")), _ptr(out["status"]),
                                            _ptr(out.get("iters")), _ptr(out.get("rho"))))
     return out
+
+
+def solve_grad(ctx: Context, scene: Scene, batch: Batch, params: SolveParams | None = None, dX=None, dL=None,
+               dL_status_mask=0, out=None, grads=None):
+    """fpt_solve_grad: the outputs of solve() and the gradients of backward() in one pass.
+
+    Returns (out dict, (g_tx, g_rx, g_vertices)).
+    """
+    import torch
+
+    out = out if out is not None else alloc_outputs(ctx, batch)
+    for k, dt in (("T", torch.float32), ("X", torch.float32), ("L", torch.float32), ("status", torch.uint8),
+                  ("iters", torch.uint8), ("rho", torch.float32)):
+        _need_cuda(out.get(k), dt, k)
+    _need_cuda(dX, torch.float32, "dX")
+    _need_cuda(dL, torch.float32, "dL")
+    dev = out["T"].device
+    if grads is None:
+        grads = (torch.empty((scene.n_tx, 3), dtype=torch.float32, device=dev),
+                 torch.empty((scene.n_rx, 3), dtype=torch.float32, device=dev),
+                 torch.empty((scene.n_obj, 3, 3), dtype=torch.float32, device=dev))
+    g_tx, g_rx, g_v = grads
+    p = params if params is not None else default_params()
+    _check(ctx.handle, library().fpt_solve_grad(ctx.handle, scene.handle, batch.handle, C.byref(p), _ptr(dX),
+                                                _ptr(dL), int(dL_status_mask), _ptr(out["T"]), _ptr(out.get("X")),
+                                                _ptr(out.get("L")), _ptr(out["status"]), _ptr(out.get("iters")),
+                                                _ptr(out.get("rho")), _ptr(g_tx), _ptr(g_rx), _ptr(g_v)))
+    return out, grads
 
 
 def validity(ctx: Context, scene: Scene, batch: Batch, T):

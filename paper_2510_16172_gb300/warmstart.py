@@ -88,8 +88,7 @@ def evaluate(ctx, net, seeds=EVAL_SEEDS, per_pair=1_000_000, order_lo=1, order_h
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for _ in range(repeats):
-                fpt.solve(ctx, scene, batch, p, out)
-                fpt.backward(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=m)
+                fpt.solve_grad(ctx, scene, batch, p, dL_status_mask=m, out=out)
             b.record(stream)
             torch.cuda.synchronize()
             tot_ms += a.elapsed_time(b) / repeats
