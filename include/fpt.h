@@ -67,7 +67,8 @@ enum {
   FPT_ST_CONVERGED = 2,     /* BFGS stopped on its world-space step tolerance */
   FPT_ST_SOLVED = 4,        /* stationarity residual <= solved_tol and not DEGENERATE/REPEAT/NONFINITE */
   FPT_ST_FP64 = 8,          /* the Hessian solve was redone in FP64 (ill-conditioned) */
-  FPT_ST_DEGENERATE = 16,   /* a segment shorter than deg_tol at the solution (kink of L) */
+  FPT_ST_DEGENERATE = 16,   /* a kink of L: a segment shorter than deg_tol at the solution, or BFGS ran a
+                               segment below kink_stop before converging */
   FPT_ST_REPEAT = 32,       /* the same object twice in a row: not solved */
   FPT_ST_NONFINITE = 64,    /* NaN/Inf met */
   FPT_ST_INVALID_INPUT = 128 /* object id, order or TX/RX index out of range */
@@ -97,7 +98,11 @@ typedef struct {
                            0: the adjoint kernels of fpt_backward run after the solve (0; measured faster on
                            GB300 at order 3, where the fused kernel's larger code and register footprint lower
                            its issue rate more than the shared decoding saves) */
-  int32_t reserved[3]; /* must be zero */
+  float kink_stop;      /* BFGS stops a path, and flags it DEGENERATE, when one of its segments is shorter than
+                           this (metres) after 4 or more steps without convergence: it is running into a kink,
+                           where L is not smooth (0 = 0.1 deg_tol).  Larger values save BFGS steps on
+                           kinked paths but also stop some regular paths whose iterates pass close to a kink */
+  int32_t reserved[2]; /* must be zero */
 } fpt_solve_params;
 
 typedef struct fpt_ctx fpt_ctx;

@@ -364,7 +364,11 @@ __device__ __forceinline__ bool bfgs_step(PathState<N, Q>& P, const SolveCfg& cf
   for (int jj = 1; jj <= N; ++jj) emin = fminf(emin, P.e[jj]);
   const bool bad = !isfinite(sy) || !isfinite(alpha);
   if (bad) P.st |= ST_NONFINITE;
-  return P.it >= cfg.max_iters || bad || emin < cfg.stop2 || (P.conv && !cfg.fixed_iters);
+  // a segment collapsing before convergence, past the first steps (a start may put two points close
+  // together): the path runs into a kink of L, not a smooth minimiser
+  const bool kink = emin < cfg.stop2 && !P.conv && P.it >= kKinkMinIters;
+  if (kink) P.st |= ST_DEGENERATE;
+  return P.it >= cfg.max_iters || bad || kink || (P.conv && !cfg.fixed_iters);
 }
 
 template <int N, unsigned Q>

@@ -19,6 +19,13 @@
 
 using namespace fpt;
 
+// Streams over which the BFGS pattern launches of one order are spread (a
+// build-time tuning constant: more streams overlap the launches' tails, but
+// co-resident kernels share each SM's instruction cache).
+#ifndef FPT_SIDE_STREAMS
+#define FPT_SIDE_STREAMS 4
+#endif
+
 struct fpt_ctx {
   int device = 0;
   int n_sm = 0;
@@ -28,7 +35,7 @@ struct fpt_ctx {
   size_t gacc_cap = 0;
   unsigned long long* d_count = nullptr;   // counters for reductions
   unsigned long long* d_work = nullptr;    // work counters of the lane-refill solver (one per concurrent launch)
-  static constexpr int kSide = 4;          // side streams for the independent pattern launches of one order
+  static constexpr int kSide = FPT_SIDE_STREAMS;  // streams for the independent pattern launches of one order
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kSide] = {};
@@ -104,7 +111,13 @@ struct fpt_batch {
   uint64_t* d_lists = nullptr;
   uint64_t count[kPatternKeys] = {0};
   uint64_t start[kPatternKeys] = {0};
+  // per order: the buckets too small for a pattern launch sit together at the end of the order's range
+  uint64_t small_start[kMaxOrder + 1] = {0};
+  uint64_t small_count[kMaxOrder + 1] = {0};
 };
+
+// Smallest bucket worth its own pattern launch: about four paths per resident lane.
+static uint64_t min_pattern_bucket(const fpt_ctx* ctx) { return (uint64_t)ctx->n_sm * 4 * 128 * 4; }
 
 static fpt_status fail(fpt_ctx* ctx, fpt_status st, const char* fmt, ...) {
   if (ctx) {
@@ -564,13 +577,24 @@ static fpt_status ensure_buckets(fpt_ctx* ctx, fpt_batch* b, const SceneDev& S) 
   CUDA_OR_FAIL(ctx, launch_pattern_histogram(S, b->dev, ctx->d_count, ctx->stream, ctx->n_sm));
   CUDA_OR_FAIL(ctx, cudaMemcpyAsync(h, ctx->d_count, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  // layout: orders in sequence; inside an order, the buckets large enough for a pattern launch, then the
+  // small ones together (the unified kernel takes them in one launch)
+  const uint64_t min_bucket = min_pattern_bucket(ctx);
   uint64_t acc = 0;
   unsigned long long cur[kPatternKeys];
-  for (int k = 0; k < kPatternKeys; ++k) {
-    b->start[k] = acc;
-    b->count[k] = h[k];
-    cur[k] = acc;
-    acc += h[k];
+  for (int n = 1; n <= kMaxOrder; ++n) {
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) b->small_start[n] = acc;
+      for (unsigned q = 0; q < (1u << n); ++q) {
+        const int k = pattern_key(n, q);
+        if ((h[k] >= min_bucket) != (pass == 0)) continue;
+        b->start[k] = acc;
+        b->count[k] = h[k];
+        cur[k] = acc;
+        acc += h[k];
+      }
+      if (pass == 1) b->small_count[n] = acc - b->small_start[n];
+    }
   }
   if (acc != b->dev.n_paths) return fail(ctx, FPT_EDEVICE, "pattern histogram mismatch");
   CUDA_OR_FAIL(ctx, cudaMalloc(&b->d_lists, (acc ? acc : 1) * sizeof(uint64_t)));
@@ -599,10 +623,14 @@ static uint64_t order_slice(const fpt_batch* b, int n, const uint64_t** list) {
     if (n < b->dev.lo || n > b->dev.hi) return 0;
     return b->dev.kpow[n] * (uint64_t)b->dev.n_tx * (uint64_t)b->dev.n_rx;
   }
-  // the buckets of order n are contiguous: keys pattern_key(n, 0) .. pattern_key(n, 2^n - 1)
-  *list = b->d_lists + b->start[pattern_key(n, 0)];
-  uint64_t c = 0;
-  for (unsigned q = 0; q < (1u << n); ++q) c += b->count[pattern_key(n, q)];
+  // the buckets of order n are contiguous; the order's range starts at its first bucket in the layout
+  uint64_t first = b->small_start[n], c = 0;
+  for (unsigned q = 0; q < (1u << n); ++q) {
+    const int k = pattern_key(n, q);
+    c += b->count[k];
+    if (b->count[k] && b->start[k] < first) first = b->start[k];
+  }
+  *list = b->d_lists + first;
   return c;
 }
 
@@ -641,14 +669,16 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
   if (prm) p = *prm;
   if (p.init_mode != 0 && p.init_mode != 1) return fail(ctx, FPT_EINVAL, "init_mode must be 0 or 1");
   if (p.init_mode == 1 && !ctx->init_mlp) return fail(ctx, FPT_EINVAL, "init_mode 1 needs fpt_set_init_mlp");
-  if (p.max_iters < 0 || p.fp_iters < 1 || p.polish < 0 || p.polish > 2 || p.specialize < 0 || p.specialize > 2)
+  if (p.max_iters < 0 || p.fp_iters < 1 || p.polish < 0 || p.polish > 2 || p.specialize < 0 || p.specialize > 2 ||
+      !(p.kink_stop >= 0.f))
     return fail(ctx, FPT_EINVAL, "bad solver parameters");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   st = ensure_buckets(ctx, b, scene_dev(s));
   if (st != FPT_OK) return st;
   const SceneDev S = scene_dev(s);
-  SolveCfg sc{p.max_iters, p.fp_iters, p.fixed_iters, p.tol_step * p.tol_step, 0.01f * p.deg_tol * p.deg_tol,
+  const float kink = p.kink_stop > 0.f ? p.kink_stop : 0.1f * p.deg_tol;
+  SolveCfg sc{p.max_iters, p.fp_iters, p.fixed_iters, p.tol_step * p.tol_step, kink * kink,
               p.refill > 32 ? 32 : p.refill, p.init_mode == 1, kMaxChunk};
   // the polish needs its Newton step only to a modest relative accuracy: 100x looser pivot test than the adjoint
   PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, p.polish_fp64};
@@ -670,14 +700,16 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
     }
     {
       ProfScope ps(ctx, FPT_K_BFGS);
-      // pattern kernels pay off when every pattern bucket fills the GPU several times over; an order
-      // split into many small buckets runs the unified kernel instead
+      // pattern kernels pay off for buckets that fill the GPU several times over.  Seeded and explicit
+      // batches keep an order's small buckets together, and the unified kernel takes them in one launch;
+      // an exhaustive order with a small pattern runs the unified kernel throughout.
+      const bool listed = b->dev.mode != BATCH_EXHAUSTIVE;
+      const bool force = p.specialize == 2;
       bool by_pattern = p.specialize && sc.refill > 0;
-      const uint64_t min_bucket = (uint64_t)ctx->n_sm * 4 * 128 * 4;
-      for (unsigned q = 0; by_pattern && q < (1u << n); ++q) {
+      for (unsigned q = 0; by_pattern && !listed && !force && q < (1u << n); ++q) {
         const uint64_t* qlist;
         const uint64_t qcnt = pattern_slice(b, n, q, &qlist);
-        if (qcnt && qcnt < min_bucket && p.specialize == 1) by_pattern = false;
+        if (qcnt && qcnt < min_pattern_bucket(ctx)) by_pattern = false;
       }
       if (by_pattern) {
         // the pattern launches of one order are independent: spread them over the side streams so that
@@ -688,11 +720,17 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
         for (unsigned q = 0; q < (1u << n); ++q) {
           const uint64_t* qlist;
           const uint64_t qcnt = pattern_slice(b, n, q, &qlist);
-          if (!qcnt) continue;
+          if (!qcnt || (listed && !force && qcnt < min_pattern_bucket(ctx))) continue;
           cudaStream_t sq = ctx->side[used % fpt_ctx::kSide];
           ++used;
           CUDA_OR_FAIL(ctx, launch_bfgs(n, (int)q, S, b->dev, sc, qcnt, qlist, T, status, iters, sq, ctx->n_sm,
                                         ctx->d_work + q));
+        }
+        if (listed && !force && b->small_count[n]) {
+          cudaStream_t sq = ctx->side[used % fpt_ctx::kSide];
+          ++used;
+          CUDA_OR_FAIL(ctx, launch_bfgs(n, -1, S, b->dev, sc, b->small_count[n], b->d_lists + b->small_start[n], T,
+                                        status, iters, sq, ctx->n_sm, ctx->d_work + 32));
         }
         for (int k = 0; k < fpt_ctx::kSide && k < used; ++k) {
           CUDA_OR_FAIL(ctx, cudaEventRecord(ctx->join_ev[k], ctx->side[k]));

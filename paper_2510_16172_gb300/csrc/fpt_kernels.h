@@ -16,13 +16,14 @@ extern thread_local uint64_t tl_kernel_launches;
 inline void count_launch() { ++tl_kernel_launches; }
 
 constexpr int kMaxChunk = 256;  // most paths a warp of the refill kernel claims at a time
+constexpr int kKinkMinIters = 4;  // BFGS steps before the kink stop applies
 
 struct SolveCfg {
   int max_iters;    // BFGS step cap
   int fp_iters;     // Eq. 6 rounds per step
   int fixed_iters;  // 1: run every path for max_iters steps
   float tol2;       // (world-space step tolerance)^2
-  float stop2;      // a segment shorter than sqrt(stop2) stops BFGS (the path runs into a kink)
+  float stop2;      // a segment shorter than sqrt(stop2) before convergence stops BFGS: DEGENERATE (a kink)
   int refill;       // lane refill threshold (free lanes before a warp takes new paths); 0 = one path per lane per tile
   int init_from_T;  // 1: start from the parameters already in T (learned start); 0: t = 1/2
   int chunk;        // paths a warp claims at a time (refill kernel; set per launch)

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
       fetch_path_n<N>(B, list, j, d);
       const uint64_t g = d.g;
       uint8_t st = d.flags;
-      if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE);
+      if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE | ST_DEGENERATE);
       // geometry: b as hi + lo, A as hi + lo
       GeoFF<N> G;
       bool edge[N];
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
           float lmin = len[0].hi;
 #pragma unroll
           for (int k = 1; k <= N; ++k) lmin = fminf(lmin, len[k].hi);
-          if ((st & ST_REPEAT) || !(lmin >= cfg.deg_tol)) {
+          if ((st & (ST_REPEAT | ST_DEGENERATE)) || !(lmin >= cfg.deg_tol)) {
             if (!(st & ST_REPEAT)) st |= ST_DEGENERATE;  // a kink: no Newton system
             break;
           }
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev
     fetch_path_n<N>(B, list, j, d);
     const uint64_t g = d.g;
     uint8_t st = d.flags;
-    if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE);
+    if (cfg.mode == POLISH_SOLVE) st |= status[g] & (ST_CONVERGED | ST_NONFINITE | ST_DEGENERATE);
     if (rescue_list) st |= ST_FP64;
     Geo64<N> G;
     float a32[N][2][3];
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev
         double lmin = len[0];
 #pragma unroll
         for (int k = 1; k <= N; ++k) lmin = fmin(lmin, len[k]);
-        if ((st & ST_REPEAT) || !(lmin >= (double)cfg.deg_tol)) {
+        if ((st & (ST_REPEAT | ST_DEGENERATE)) || !(lmin >= (double)cfg.deg_tol)) {
           if (!(st & ST_REPEAT)) st |= ST_DEGENERATE;  // a kink: no Newton system
           break;
         }

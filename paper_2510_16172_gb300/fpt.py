@@ -42,7 +42,8 @@ class SolveParams(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("fp_iters", C.c_int32), ("polish", C.c_int32), ("fixed_iters", C.c_int32),
                 ("tol_step", C.c_float), ("solved_tol", C.c_float), ("deg_tol", C.c_float), ("cond_fp64", C.c_float),
                 ("init_mode", C.c_int32), ("polish_fp64", C.c_int32), ("refill", C.c_int32),
-                ("specialize", C.c_int32), ("fuse_adjoint", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("specialize", C.c_int32), ("fuse_adjoint", C.c_int32),
+                ("kink_stop", C.c_float), ("reserved", C.c_int32 * 2)]
 
 
 # every symbol declared in include/fpt.h with (restype, argtypes)

@@ -90,8 +90,24 @@ def test_solve_grad_equals_solve_then_backward(ctx, case, fuse):
         scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
         batch = fpt.Batch.seeded(ctx, scene, 11, 20000, 1, 5)
     a = fpt.solve(ctx, scene, batch)
-    dX = torch.as_tensor(scenes.cotangents(5, batch.n_paths, batch.n_max)[0], dtype=torch.float32,
-                         device=a["T"].device) * 0.1
+    # point cotangents on paths whose segments are all >= 1 cm: near a kink the adjoint amplifies rounding
+    # differences by 1/|z|, which would let a few paths dominate the comparison of the sums
+    dev = a["T"].device
+    Xa = a["X"].double()
+    _, order, txi, rxi = fpt.enumerate(ctx, batch)
+    ends_tx = torch.as_tensor(sc.tx, device=dev)[txi.long()]
+    ends_rx = torch.as_tensor(sc.rx, device=dev)[rxi.long()]
+    order = order.long()
+    pts = torch.cat([ends_tx[:, None], Xa, ends_rx[:, None]], dim=1)
+    idx = torch.arange(batch.n_max + 2, device=dev)[None, :]
+    inner = ((idx >= 1) & (idx <= order[:, None]))[:, :, None]
+    pts = torch.where(inner, pts, ends_rx[:, None].expand_as(pts))
+    pts[:, 0] = ends_tx
+    seg = (pts[:, 1:] - pts[:, :-1]).norm(dim=2)
+    last = torch.arange(batch.n_max + 1, device=dev)[None, :] <= order[:, None]
+    far = torch.where(last, seg, torch.full_like(seg, 1e9)).min(dim=1).values >= 0.01
+    dX = torch.as_tensor(scenes.cotangents(5, batch.n_paths, batch.n_max)[0], dtype=torch.float32, device=dev)
+    dX = (dX * 0.1 * far[:, None, None]).contiguous()
     ref = fpt.backward(ctx, scene, batch, a["T"], a["status"], dX, None, dL_status_mask=MASK)
     b, got = fpt.solve_grad(ctx, scene, batch, fpt.default_params(fuse_adjoint=fuse), dX=dX, dL_status_mask=MASK)
     ctx.sync()
