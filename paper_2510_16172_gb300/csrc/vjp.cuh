@@ -15,7 +15,7 @@ namespace fpt {
 // shared accumulators, into gacc[gbase + k]).  Lanes with base < 0 add
 // nothing.  If every adding lane has the same base the warp sums its values
 // and one lane adds them (the common case: neighbouring paths share objects);
-// otherwise each adding lane adds its own.
+// otherwise each adding lane adds its own.  CNT <= 32.
 template <int CNT>
 __device__ __forceinline__ void warp_accumulate(float* acc, int base, const float (&v)[CNT], bool shared_acc,
                                                 double* gacc, int gbase) {
@@ -26,22 +26,23 @@ __device__ __forceinline__ void warp_accumulate(float* acc, int base, const floa
   const int b0 = __shfl_sync(full, base, leader);
   const bool uniform = __all_sync(full, base < 0 || base == b0);
   if (uniform) {
-    float s[CNT];
+    // butterfly sums leave every lane with all CNT totals; lane k adds total k, so the CNT
+    // additions are one warp instruction instead of CNT single-lane ones
+    const int lane = (int)(threadIdx.x & 31);
+    const int g0 = __shfl_sync(full, gbase, leader);
+    float mine = 0.f;
 #pragma unroll
     for (int k = 0; k < CNT; ++k) {
       float x = base >= 0 ? v[k] : 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(full, x, o);
-      s[k] = x;
+      if (lane == k) mine = x;
     }
-    if ((int)(threadIdx.x & 31) == leader) {
-#pragma unroll
-      for (int k = 0; k < CNT; ++k) {
-        if (shared_acc)
-          atomicAdd(acc + b0 + k, s[k]);
-        else
-          atomicAdd(gacc + gbase + k, (double)s[k]);
-      }
+    if (lane < CNT) {
+      if (shared_acc)
+        atomicAdd(acc + b0 + lane, mine);
+      else
+        atomicAdd(gacc + g0 + lane, (double)mine);
     }
   } else if (base >= 0) {
 #pragma unroll
