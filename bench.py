@@ -11,7 +11,11 @@ lengths to TX, RX and every vertex by implicit differentiation -- one
 fpt_solve_grad call.  A path counts as solved when its stationarity residual
 is <= 1e-5 m.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload canyon|city]
+
+--workload city times the ragged large batch instead: 100,000,000 seeded
+sequences of order 1-5 on a 256-object city with the learned start (and the
+plain start alongside), one fpt_solve_grad call per step.
 
 Under torchrun (N > 1) every rank solves its own copy of the workload (weak
 scaling, no data-path collective); rank 0 prints one JSON line.
@@ -160,8 +164,11 @@ NCU_TRAFFIC = {
 # ---------------------------------------------------------------------------
 # the oracle (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rate(sc, n_paths, seed, target_s=None, max_paths=None):
-    """Oracle fwd+bwd on a seeded uniform sample of the workload: (solved/s, sample size, seconds, threads)."""
+def oracle_rate(sc, n_paths, seed, target_s=None, max_paths=None, decode=None):
+    """Oracle fwd+bwd on a seeded uniform sample of the workload: (solved/s, sample size, seconds, threads).
+
+    decode(g) -> (ids, order, tx_idx, rx_idx) of global path indices g (default: the canyon's order-3
+    exhaustive enumeration)."""
     import numpy as np
 
     import oracle
@@ -169,10 +176,11 @@ def oracle_rate(sc, n_paths, seed, target_s=None, max_paths=None):
     oracle.build()
     rng = np.random.default_rng(seed)
     threads = os.cpu_count() or 1
+    decode = decode or (lambda g: oracle.exhaustive_paths(sc, 3, 3, g))
 
     def run(m):
         g = np.sort(rng.choice(n_paths, m, replace=False))
-        ids, order, ti, ri = oracle.exhaustive_paths(sc, 3, 3, g)
+        ids, order, ti, ri = decode(g)
         t0 = time.perf_counter()
         out = oracle.solve(sc, ids, order, ti, ri, dL=np.ones(m), n_threads=threads)
         dt = time.perf_counter() - t0
@@ -381,6 +389,119 @@ def learned_vs_plain(ctx, fpt):
     return res
 
 
+CITY_WORKLOAD = ("ragged city: 256 objects (154 facades 5-30 m, 102 of their edges, 500 x 500 x 60 m), 1 TX x 16 RX, "
+                 "100,000,000 seeded sequences of order 1-5; learned start (the network trained here on the solver's "
+                 "solutions of 50 random 10 m scenes), FP32 BFGS + Eq.6 fixed point, double-float Newton polish, "
+                 "validity, implicit backward of the sum of valid path lengths (one fpt_solve_grad call)")
+
+
+def run_city(args, world, rank, local_rank):
+    """The ragged large batch: seeded orders 1-5 on a city, learned start; the plain start alongside."""
+    import numpy as np
+    import torch
+
+    from paper_2510_16172_gb300 import build, fpt, scenes, warmstart
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ctx = fpt.Context(local_rank)
+    t0 = time.perf_counter()
+    X, T, G = warmstart.make_dataset(ctx)
+    net, hist = warmstart.train(ctx, X, T, G, epochs=6)
+    del X, T, G
+    train_s = time.perf_counter() - t0
+    net.attach()
+    sc = scenes.city(0, n_rx=16)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    per_pair = args.city_paths // (len(sc.tx) * len(sc.rx))
+    batch = fpt.Batch.seeded(ctx, scene, 5, per_pair, 1, 5)
+    N = batch.n_paths
+    out = fpt.alloc_outputs(ctx, batch, with_X=False, with_rho=False, with_iters=True)
+    grads = (torch.empty((scene.n_tx, 3), device=dev), torch.empty((scene.n_rx, 3), device=dev),
+             torch.empty((scene.n_obj, 3, 3), device=dev))
+    mask = fpt.ST_VALID | fpt.ST_SOLVED
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for init in (1, 0):
+        params = fpt.default_params(max_iters=args.max_iters, init_mode=init)
+        for _ in range(args.warmup):
+            fpt.solve_grad(ctx, scene, batch, params, dL_status_mask=mask, out=out, grads=grads)
+        ctx.sync()
+        fpt.profile_enable(ctx, True)
+        fpt.profile_read(ctx, reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with ClockSampler(gpu_identifier(torch, dev)) as clk:
+            torch.cuda.synchronize(dev)
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                fpt.solve_grad(ctx, scene, batch, params, dL_status_mask=mask, out=out, grads=grads)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize(dev)
+        ctx.sync()
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        kms, klaunch = fpt.profile_read(ctx, reset=True)
+        fpt.profile_enable(ctx, False)
+        solved = fpt.count_status(ctx, out["status"], fpt.ST_SOLVED)
+        run = (out["status"] & fpt.ST_REPEAT) == 0
+        iters = out["iters"].to(torch.int64)
+        res[init] = {"value": solved * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                     "solved_per_step": solved, "mean_bfgs_iters": float(iters[run].double().mean()),
+                     "kernel_ms": kms, "launches": int(sum(klaunch)), "clocks": clk.summary()}
+        if init == 1:
+            # algorithmic BFGS flops of this step: per path, its (order, reflector count)'s count per step
+            ids, order, _, _ = fpt.enumerate(ctx, batch)
+            is_quad = torch.tensor(np.asarray(sc.types) == scenes.QUAD, device=dev)
+            flops = 0.0
+            for n in range(1, 6):
+                sel = order == n
+                nq = (is_quad[ids[sel][:, :n].long()]).sum(dim=1)
+                f_step = torch.tensor([bfgs_flops_per_iter(n, params.fp_iters, q) for q in range(n + 1)],
+                                      dtype=torch.float64, device=dev)
+                f_init = torch.tensor([bfgs_flops_init(n, q) for q in range(n + 1)], dtype=torch.float64,
+                                      device=dev)
+                r = run[sel].double()
+                flops += float(((f_init[nq] + f_step[nq] * iters[sel].double()) * r).sum().item())
+            del ids, order
+            res[init]["bfgs_flops"] = flops
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    L = res[1]
+    bfgs_ms = L["kernel_ms"][fpt.K_BFGS] / args.steps
+    roof = {"kernel": "bfgs_refill_kernel<n, Q> (orders 1-5, reflector/edge patterns)", "bound": "alu",
+            "achieved": L["bfgs_flops"] / (bfgs_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+            "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz", "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    names = {fpt.K_BFGS: "bfgs", fpt.K_POLISH: "polish", fpt.K_BACKWARD: "backward", fpt.K_OTHER: "finalize",
+             fpt.K_MLP: "mlp_infer_kernel (learned start)"}
+    line = {"metric": METRIC, "value": L["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": L["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": CITY_WORKLOAD, "n_paths": N, "init": "learned", "max_bfgs_iters": args.max_iters,
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+            "solved_per_step": L["solved_per_step"], "mean_bfgs_iters": L["mean_bfgs_iters"],
+            "kernel_ms_per_step": {names[k]: L["kernel_ms"][k] / args.steps for k in range(fpt.K_COUNT)},
+            "roofline": roof, "gpu_launches": L["launches"], "clocks": L["clocks"],
+            "plain_start": {"value": res[0]["value"], "ms_per_step": res[0]["ms_per_step"],
+                            "solved_per_step": res[0]["solved_per_step"],
+                            "mean_bfgs_iters": res[0]["mean_bfgs_iters"]},
+            "network": {"train_s": train_s, "train_loss_per_epoch": hist}}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
+        rate, m, dt, threads = oracle_rate(sc, N, 1, target_s=args.cpu_seconds,
+                                           decode=lambda g: oracle.seeded_paths(sc, 5, per_pair, 1, 5, g))
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{m} uniformly sampled paths of the batch, FP64 damped Newton + implicit "
+                                          f"VJP, {dt:.1f} s on {threads} threads"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def e2e(args, sc, ctx, dev, torch, fpt):
     """Same metric through the public API: host scene/endpoints in, host lengths/status/gradients out."""
     import numpy as np
@@ -438,6 +559,9 @@ def main():
     ap.add_argument("--max-iters", type=int, default=32, help="BFGS step cap")
     ap.add_argument("--rx-grid", type=int, default=32, help="RX grid side (32 = the 33.5M-path workload)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain start comparison")
+    ap.add_argument("--workload", choices=["canyon", "city"], default="canyon",
+                    help="canyon: the 33.5M-path urban canyon (default); city: the 100M-path ragged city batch")
+    ap.add_argument("--city-paths", type=int, default=100_000_000)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -451,7 +575,10 @@ def main():
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, world, rank, local_rank)
+    if args.workload == "city":
+        run_city(args, world, rank, local_rank)
+    else:
+        run_ours(args, world, rank, local_rank)
     if world > 1:
         import torch.distributed as dist
 
