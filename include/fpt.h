@@ -102,7 +102,9 @@ typedef struct {
                            this (metres) after 4 or more steps without convergence: it is running into a kink,
                            where L is not smooth (0 = 0.1 deg_tol).  Larger values save BFGS steps on
                            kinked paths but also stop some regular paths whose iterates pass close to a kink */
-  int32_t reserved[2]; /* must be zero */
+  int32_t polish_all;   /* 0: a path whose residual at the BFGS point already meets solved_tol is returned as is,
+                           the others take the `polish` Newton steps (0); 1: every path takes them */
+  int32_t reserved[1]; /* must be zero */
 } fpt_solve_params;
 
 typedef struct fpt_ctx fpt_ctx;
@@ -169,11 +171,12 @@ fpt_status fpt_enumerate(fpt_ctx* ctx, const fpt_batch* batch, int32_t* ids_out,
                          int32_t* tx_idx_out, int32_t* rx_idx_out);
 
 /* Solve every path of the batch (Sec. III-C): plain init t = 1/2, BFGS with
- * Eq. 6 step sizes in FP32, then `polish` Newton steps whose gradient is
- * formed in FP64 and whose block-tridiagonal Hessian system is solved in
- * FP32 (FP64 when ill-conditioned), then the validity test and the
- * stationarity residual rho = max_i |A_i delta_i| of the Newton step at the
- * returned T.  Device outputs (caller-owned; any but status_out may be NULL):
+ * Eq. 6 step sizes in FP32, then up to `polish` Newton steps whose gradient
+ * is formed in extended precision and whose block-tridiagonal Hessian system
+ * is solved in FP32 (FP64 when ill-conditioned), then the validity test and
+ * the stationarity residual rho = max_i |A_i delta_i| of the Newton step at
+ * the returned T (paths already within solved_tol at the BFGS point skip the
+ * steps unless polish_all = 1).  Device outputs (caller-owned; any but status_out may be NULL):
  *   T_out [N][n_max][2] float   parameters t_i (edges: t_i2 stays 1/2)
  *   X_out [N][n_max][3] float   world points x_i
  *   L_out [N] float             path length

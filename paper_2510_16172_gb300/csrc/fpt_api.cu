@@ -39,7 +39,7 @@ struct fpt_ctx {
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kSide] = {};
-  uint32_t* d_rescue = nullptr;            // paths for the FP64 passes: polish list, then adjoint list
+  uint32_t* d_rescue = nullptr;            // path lists: FP64 polish, FP64 adjoint, second polish pass
   size_t rescue_cap = 0;
   unsigned* d_rescue_n = nullptr;
   fpt_mlp* init_mlp = nullptr;             // network for init_mode = 1
@@ -218,7 +218,7 @@ fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_rescue_n, 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_rescue_n, 3 * sizeof(unsigned));
   if (e != cudaSuccess) {
     fpt_destroy(ctx);
     return FPT_ECUDA;
@@ -611,7 +611,7 @@ static fpt_status ensure_rescue(fpt_ctx* ctx, uint64_t n) {
   cudaFree(ctx->d_rescue);
   ctx->d_rescue = nullptr;
   ctx->rescue_cap = 0;
-  CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_rescue, 2 * n * sizeof(uint32_t)));
+  CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_rescue, 3 * n * sizeof(uint32_t)));
   ctx->rescue_cap = n;
   return FPT_OK;
 }
@@ -751,8 +751,10 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
         gc.rescue_list = ctx->d_rescue + cnt;
         gc.rescue_count = ctx->d_rescue_n + 1;
       }
+      uint32_t* step_list = p.polish_all ? nullptr : ctx->d_rescue + 2 * cnt;
       CUDA_OR_FAIL(ctx, launch_polish(n, S, b->dev, pc, cnt, list, T, X, L, status, rho, nullptr, nullptr, ctx->stream,
-                                      ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n, grad ? &gc : nullptr));
+                                      ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n, grad ? &gc : nullptr, step_list,
+                                      ctx->d_rescue_n + 2));
     }
   }
   return FPT_OK;

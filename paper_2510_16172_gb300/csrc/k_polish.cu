@@ -214,7 +214,9 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
     SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local, const uint64_t* __restrict__ list,
     float* __restrict__ T, float* __restrict__ X, float* __restrict__ Lout, uint8_t* __restrict__ status,
     float* __restrict__ rho_out, uint8_t* __restrict__ mask_out, float* __restrict__ bdist_out, int use_smem,
-    uint32_t* __restrict__ rescue_list, unsigned* __restrict__ rescue_count, GradCfg gc) {
+    uint32_t* __restrict__ rescue_list, unsigned* __restrict__ rescue_count, GradCfg gc,
+    const uint32_t* __restrict__ in_list, const unsigned* __restrict__ in_count, uint32_t* __restrict__ step_list,
+    unsigned* __restrict__ step_count) {
   constexpr int M = 2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const float* rec32 = S.rec32;
@@ -241,10 +243,13 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
   __syncthreads();
   const int n_max = B.n_max;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // second pass: only the paths the first pass listed for a Newton step
+  const uint64_t n_iter = in_list ? (uint64_t)*in_count : n_local;
   int tiles = 0;
-  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
-    const uint64_t j = j0 + threadIdx.x;
-    const bool have = j < n_local;
+  for (uint64_t k0 = (uint64_t)blockIdx.x * blockDim.x; k0 < n_iter; k0 += stride) {
+    const uint64_t k = k0 + threadIdx.x;
+    const bool have = k < n_iter;
+    const uint64_t j = have ? (in_list ? (uint64_t)in_list[k] : k) : 0;
     // per-path gradient terms (kGrad), summed over the warp below
     float gb[N][9], gtx[3], grx[3];
     int acc_id[N], acc_t = -1, acc_r = -1;
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
       // state the fused backward reuses
       float uf[N + 1][3], ilf[N + 1], dd[N][3];
       BlockTri<float, N> F32;
-      bool fact_ok = false, adj_ok = false, listed64 = false;
+      bool fact_ok = false, adj_ok = false, listed64 = false, pending = false;
       if (!(st & ST_INVALID) && finite) {
         // Newton steps, then the residual: one gradient, factorisation and solve per pass (one code copy each)
         const int steps = cfg.mode == POLISH_SOLVE ? cfg.steps : 0;
@@ -353,10 +358,18 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
 #pragma unroll
           for (int k = 0; k < M; ++k) r[k] = -gr[k];
           solve_hessian<float, N>(F32, r, delta);
-          if (s >= steps) {
-            // at the returned point: the residual, and for the adjoint its own pivot test
-            rho = world_max<N>(G.ah, delta);
-            adj_ok = strict;
+          if (s >= steps || (step_list && s == 0)) {
+            // at the returned point: the residual, and for the adjoint its own pivot test.  The first
+            // pass returns the solver's point when it already meets the bound; otherwise it lists the
+            // path, and the second pass takes the Newton steps from the start.
+            const float r0 = world_max<N>(G.ah, delta);
+            if (s >= steps || r0 <= cfg.solved_tol) {
+              rho = r0;
+              adj_ok = strict;
+            } else {
+              step_list[atomicAdd(step_count, 1u)] = (uint32_t)j;
+              pending = true;
+            }
             break;
           }
 #pragma unroll
@@ -382,7 +395,9 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
       const bool inside = validity<N>(tf, edge, h1, h2, bd);
       st = final_status(st, inside, rho, cfg.solved_tol);
       if constexpr (kGrad) {
-        if (listed64) {
+        if (pending) {
+          // the second pass forms this path's adjoint
+        } else if (listed64) {
           // the FP64 polish decides this path's status; the FP64 adjoint pass reads it
           gc.rescue_list[atomicAdd(gc.rescue_count, 1u)] = (uint32_t)j;
         } else if (!(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE))) {
@@ -403,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
           }
         }
       }
-      if (cfg.mode == POLISH_SOLVE) {
+      if (cfg.mode == POLISH_SOLVE && !pending) {
         float2* To = reinterpret_cast<float2*>(T) + g * (uint64_t)n_max;
 #pragma unroll
         for (int i = 0; i < N; ++i) To[i] = make_float2(tf[i][0], tf[i][1]);
@@ -440,9 +455,11 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
           Lout[g] = (!(st & ST_INVALID) && finite) ? __fadd_rn(Ls.hi, Ls.lo) : NAN;
         }
       }
-      if (rho_out) rho_out[g] = rho;
-      if (mask_out) mask_out[g] = (st & ST_VALID) ? 1 : 0;
-      if (bdist_out) bdist_out[g] = bd;
+      if (!pending) {
+        if (rho_out) rho_out[g] = rho;
+        if (mask_out) mask_out[g] = (st & ST_VALID) ? 1 : 0;
+        if (bdist_out) bdist_out[g] = bd;
+      }
     }
     if constexpr (kGrad) {
       // sums over paths (all lanes of the warp take part)
@@ -647,7 +664,8 @@ template <int N>
 static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                                    const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                                    uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
-                                   unsigned* rescue_count, const GradCfg* grad) {
+                                   unsigned* rescue_count, const GradCfg* grad, uint32_t* step_list,
+                                   unsigned* step_count) {
   const bool f64 = cfg.fp64 != 0;
   const size_t smem64 = (size_t)S.n_obj * (kRec64 * sizeof(double) + (kRec32 + kAux) * sizeof(float));
   const size_t smemff = (size_t)S.n_obj * (kRec32 + kRecLo + kAux) * sizeof(float);
@@ -698,19 +716,37 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
     gc = *grad;
     e = cudaMemsetAsync(gc.rescue_count, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
-    e = grid_of((const void*)polish_ff_kernel<N, true>, sff, n_local, grid);
-    if (e != cudaSuccess || grid == 0) return e;
-    polish_ff_kernel<N, true><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask,
-                                                               bdist, use_smem, rescue_list, rescue_count, gc);
-  } else {
-    e = grid_of((const void*)polish_ff_kernel<N, false>, sff, n_local, grid);
-    if (e != cudaSuccess || grid == 0) return e;
-    polish_ff_kernel<N, false><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho, mask,
-                                                                bdist, use_smem, rescue_list, rescue_count, gc);
   }
-  count_launch();
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  // adaptive polish: the first pass lists the paths that still need their Newton steps, the second
+  // pass (a grid for a quarter of the slice; it strides over the list) takes them
+  const bool two_pass = step_list != nullptr && cfg.mode == POLISH_SOLVE && cfg.steps > 0;
+  if (two_pass) {
+    e = cudaMemsetAsync(step_count, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+  }
+  for (int pass = 0; pass < (two_pass ? 2 : 1); ++pass) {
+    const uint32_t* in_l = pass == 1 ? step_list : nullptr;
+    const unsigned* in_c = pass == 1 ? step_count : nullptr;
+    uint32_t* out_l = two_pass && pass == 0 ? step_list : nullptr;
+    unsigned* out_c = two_pass && pass == 0 ? step_count : nullptr;
+    const uint64_t n_grid = pass == 1 ? (n_local + 3) / 4 : n_local;
+    if (grad) {
+      e = grid_of((const void*)polish_ff_kernel<N, true>, sff, n_grid, grid);
+      if (e != cudaSuccess || grid == 0) return e;
+      polish_ff_kernel<N, true><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho,
+                                                                 mask, bdist, use_smem, rescue_list, rescue_count, gc,
+                                                                 in_l, in_c, out_l, out_c);
+    } else {
+      e = grid_of((const void*)polish_ff_kernel<N, false>, sff, n_grid, grid);
+      if (e != cudaSuccess || grid == 0) return e;
+      polish_ff_kernel<N, false><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho,
+                                                                  mask, bdist, use_smem, rescue_list, rescue_count,
+                                                                  gc, in_l, in_c, out_l, out_c);
+    }
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   // FP64 pass over the listed paths (its grid covers a few percent of the paths)
   e = grid_of((const void*)polish64_kernel<N>, s64, (n_local + 15) / 16, grid);
   if (e != cudaSuccess || grid == 0) return e;
@@ -728,12 +764,12 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                           const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                           uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
-                          unsigned* rescue_count, const GradCfg* grad) {
+                          unsigned* rescue_count, const GradCfg* grad, uint32_t* step_list, unsigned* step_count) {
   switch (n) {
 #define FPT_POLISH_CASE(K)                                                                                   \
   case K:                                                                                                    \
     return launch_polish_n<K>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm, \
-                              rescue_list, rescue_count, grad);
+                              rescue_list, rescue_count, grad, step_list, step_count);
     FPT_POLISH_CASE(1)
     FPT_POLISH_CASE(2)
     FPT_POLISH_CASE(3)
