@@ -40,6 +40,7 @@ struct fpt_ctx {
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kSide] = {};
   uint32_t* d_rescue = nullptr;            // path lists: FP64 polish, FP64 adjoint, second polish pass
+  float* d_step = nullptr;                 // first Newton steps of the second polish pass's paths
   size_t rescue_cap = 0;
   unsigned* d_rescue_n = nullptr;
   fpt_mlp* init_mlp = nullptr;             // network for init_mode = 1
@@ -245,6 +246,7 @@ void fpt_destroy(fpt_ctx* ctx) {
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   cudaFree(ctx->d_rescue);
+  cudaFree(ctx->d_step);
   cudaFree(ctx->d_rescue_n);
   delete ctx;
 }
@@ -612,6 +614,9 @@ static fpt_status ensure_rescue(fpt_ctx* ctx, uint64_t n) {
   ctx->d_rescue = nullptr;
   ctx->rescue_cap = 0;
   CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_rescue, 3 * n * sizeof(uint32_t)));
+  cudaFree(ctx->d_step);
+  ctx->d_step = nullptr;
+  CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_step, (size_t)2 * kMaxOrder * n * sizeof(float)));
   ctx->rescue_cap = n;
   return FPT_OK;
 }
@@ -754,7 +759,7 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
       uint32_t* step_list = p.polish_all ? nullptr : ctx->d_rescue + 2 * cnt;
       CUDA_OR_FAIL(ctx, launch_polish(n, S, b->dev, pc, cnt, list, T, X, L, status, rho, nullptr, nullptr, ctx->stream,
                                       ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n, grad ? &gc : nullptr, step_list,
-                                      ctx->d_rescue_n + 2));
+                                      ctx->d_rescue_n + 2, ctx->d_step));
     }
   }
   return FPT_OK;

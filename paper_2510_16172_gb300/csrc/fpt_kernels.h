@@ -73,14 +73,15 @@ struct GradCfg {
 // (rescue_list: scratch of n_local entries; rescue_count: one device counter).
 // With grad != nullptr the same kernel also forms each path's VJP from its
 // polished state and sums it, and an FP64 adjoint pass follows.  With a
-// step_list (n_local entries) the polish is adaptive: paths whose residual
-// already meets solved_tol at the solver's point keep it, the others are
-// listed and take their Newton steps in a second pass.
+// step_list (n_local entries) and step_delta (n_local x 2n floats) the
+// polish is adaptive: paths whose residual already meets solved_tol at the
+// solver's point keep it, the others are listed with their first Newton step
+// and finish in a second pass.
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                           const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                           uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
                           unsigned* rescue_count, const GradCfg* grad = nullptr, uint32_t* step_list = nullptr,
-                          unsigned* step_count = nullptr);
+                          unsigned* step_count = nullptr, float* step_delta = nullptr);
 // Adjoint + sums, then an FP64 pass over the paths whose FP32 pivots failed.
 cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,
                             const uint64_t* list, const float* T, const uint8_t* status, const float* dX,

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
     float* __restrict__ rho_out, uint8_t* __restrict__ mask_out, float* __restrict__ bdist_out, int use_smem,
     uint32_t* __restrict__ rescue_list, unsigned* __restrict__ rescue_count, GradCfg gc,
     const uint32_t* __restrict__ in_list, const unsigned* __restrict__ in_count, uint32_t* __restrict__ step_list,
-    unsigned* __restrict__ step_count) {
+    unsigned* __restrict__ step_count, float* __restrict__ step_delta) {
   constexpr int M = 2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const float* rec32 = S.rec32;
@@ -334,7 +334,25 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
       if (!(st & ST_INVALID) && finite) {
         // Newton steps, then the residual: one gradient, factorisation and solve per pass (one code copy each)
         const int steps = cfg.mode == POLISH_SOLVE ? cfg.steps : 0;
-        for (int s = 0;; ++s) {
+        // the second pass starts with the Newton step the first pass computed (same arithmetic as one pass)
+        float delta[M];
+        bool stepped = in_list != nullptr;
+        if (stepped) {
+#pragma unroll
+          for (int q = 0; q < M; ++q) delta[q] = step_delta[k * M + q];
+        }
+        for (int s = stepped ? 1 : 0;; ++s) {
+          if (stepped) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              ff a0 = two_sum(t[i][0].hi, delta[2 * i]);
+              t[i][0] = fast_two_sum(a0.hi, __fadd_rn(a0.lo, t[i][0].lo));
+              if (!edge[i]) {
+                ff a1 = two_sum(t[i][1].hi, delta[2 * i + 1]);
+                t[i][1] = fast_two_sum(a1.hi, __fadd_rn(a1.lo, t[i][1].lo));
+              }
+            }
+          }
           float gr[M];
           gradff<N>(G, t, uf, ilf, len, gr, dd);
           float lmin = len[0].hi;
@@ -354,33 +372,28 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
             listed64 = true;
             break;
           }
-          float delta[M], r[M];
+          float r[M];
 #pragma unroll
-          for (int k = 0; k < M; ++k) r[k] = -gr[k];
+          for (int q = 0; q < M; ++q) r[q] = -gr[q];
           solve_hessian<float, N>(F32, r, delta);
           if (s >= steps || (step_list && s == 0)) {
             // at the returned point: the residual, and for the adjoint its own pivot test.  The first
             // pass returns the solver's point when it already meets the bound; otherwise it lists the
-            // path, and the second pass takes the Newton steps from the start.
+            // path with its Newton step, and the second pass continues from there.
             const float r0 = world_max<N>(G.ah, delta);
             if (s >= steps || r0 <= cfg.solved_tol) {
               rho = r0;
               adj_ok = strict;
             } else {
-              step_list[atomicAdd(step_count, 1u)] = (uint32_t)j;
+              const unsigned slot = atomicAdd(step_count, 1u);
+              step_list[slot] = (uint32_t)j;
+#pragma unroll
+              for (int q = 0; q < M; ++q) step_delta[(uint64_t)slot * M + q] = delta[q];
               pending = true;
             }
             break;
           }
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            ff a0 = two_sum(t[i][0].hi, delta[2 * i]);
-            t[i][0] = fast_two_sum(a0.hi, __fadd_rn(a0.lo, t[i][0].lo));
-            if (!edge[i]) {
-              ff a1 = two_sum(t[i][1].hi, delta[2 * i + 1]);
-              t[i][1] = fast_two_sum(a1.hi, __fadd_rn(a1.lo, t[i][1].lo));
-            }
-          }
+          stepped = true;
         }
       }
       float tf[N][2], h1[N], h2[N];
@@ -665,7 +678,7 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
                                    const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                                    uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
                                    unsigned* rescue_count, const GradCfg* grad, uint32_t* step_list,
-                                   unsigned* step_count) {
+                                   unsigned* step_count, float* step_delta) {
   const bool f64 = cfg.fp64 != 0;
   const size_t smem64 = (size_t)S.n_obj * (kRec64 * sizeof(double) + (kRec32 + kAux) * sizeof(float));
   const size_t smemff = (size_t)S.n_obj * (kRec32 + kRecLo + kAux) * sizeof(float);
@@ -719,7 +732,7 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
   }
   // adaptive polish: the first pass lists the paths that still need their Newton steps, the second
   // pass (a grid for a quarter of the slice; it strides over the list) takes them
-  const bool two_pass = step_list != nullptr && cfg.mode == POLISH_SOLVE && cfg.steps > 0;
+  const bool two_pass = step_list != nullptr && step_delta != nullptr && cfg.mode == POLISH_SOLVE && cfg.steps > 0;
   if (two_pass) {
     e = cudaMemsetAsync(step_count, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
@@ -735,13 +748,13 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
       if (e != cudaSuccess || grid == 0) return e;
       polish_ff_kernel<N, true><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho,
                                                                  mask, bdist, use_smem, rescue_list, rescue_count, gc,
-                                                                 in_l, in_c, out_l, out_c);
+                                                                 in_l, in_c, out_l, out_c, step_delta);
     } else {
       e = grid_of((const void*)polish_ff_kernel<N, false>, sff, n_grid, grid);
       if (e != cudaSuccess || grid == 0) return e;
       polish_ff_kernel<N, false><<<grid, kThreads, sff, stream>>>(S, B, cfg, n_local, list, T, X, L, status, rho,
                                                                   mask, bdist, use_smem, rescue_list, rescue_count,
-                                                                  gc, in_l, in_c, out_l, out_c);
+                                                                  gc, in_l, in_c, out_l, out_c, step_delta);
     }
     count_launch();
     e = cudaGetLastError();
@@ -764,12 +777,13 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
                           const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                           uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
-                          unsigned* rescue_count, const GradCfg* grad, uint32_t* step_list, unsigned* step_count) {
+                          unsigned* rescue_count, const GradCfg* grad, uint32_t* step_list, unsigned* step_count,
+                          float* step_delta) {
   switch (n) {
 #define FPT_POLISH_CASE(K)                                                                                   \
   case K:                                                                                                    \
     return launch_polish_n<K>(S, B, cfg, n_local, list, T, X, L, status, rho, mask, bdist, stream, n_sm, \
-                              rescue_list, rescue_count, grad, step_list, step_count);
+                              rescue_list, rescue_count, grad, step_list, step_count, step_delta);
     FPT_POLISH_CASE(1)
     FPT_POLISH_CASE(2)
     FPT_POLISH_CASE(3)
