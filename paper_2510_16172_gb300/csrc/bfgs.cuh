@@ -120,14 +120,14 @@ __device__ __forceinline__ void decode_exhaustive_pattern(const BatchDev& B, con
 enum BfgsSource {
   SRC_ORDER = 0,    // exhaustive batch: every sequence of order N, decoded from the local index
   SRC_PATTERN = 1,  // exhaustive batch: the sequences of pattern Q only
-  SRC_LIST = 2,     // seeded / explicit batch: a bucket list of global indices
+  SRC_LIST = 2,     // seeded / explicit batch: a bucket of decoded path records
 };
 
 template <int N, unsigned Q, int kSrc>
-__device__ __forceinline__ void fetch_path_q(const BatchDev& B, const Tables& tb, const uint64_t* list, uint64_t j,
+__device__ __forceinline__ void fetch_path_q(const BatchDev& B, const Tables& tb, const PathRec* list, uint64_t j,
                                              PathDesc& d) {
   if constexpr (kSrc == SRC_LIST)
-    decode_listed<N>(B, tb.alphabet, list[j], d);
+    load_rec(list, j, d);
   else if constexpr (kSrc == SRC_PATTERN)
     decode_exhaustive_pattern<N, Q>(B, tb, j, d);
   else
@@ -235,7 +235,7 @@ struct PathState {
 // Returns false for paths that are never solved (repeats, invalid input).
 template <int N, unsigned Q, int kSrc>
 __device__ __forceinline__ bool path_start(PathState<N, Q>& P, const BatchDev& B, const Tables& tb,
-                                           const uint64_t* list, uint64_t j, int max_iters, const float* T_start) {
+                                           const PathRec* list, uint64_t j, int max_iters, const float* T_start) {
   constexpr int M = PathState<N, Q>::M;
   PathDesc d;
   fetch_path_q<N, Q, kSrc>(B, tb, list, j, d);
@@ -432,7 +432,7 @@ inline size_t smem_tables_bytes(const SceneDev& S, const BatchDev& B, int* use_s
 // One path per thread per tile; a warp leaves its BFGS loop when all 32 lanes are done.
 template <int N>
 __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, SolveCfg cfg, uint64_t n_local,
-                                                        const uint64_t* __restrict__ list, float* __restrict__ T_out,
+                                                        const PathRec* __restrict__ list, float* __restrict__ T_out,
                                                         uint8_t* __restrict__ status_out,
                                                         uint8_t* __restrict__ iters_out, int use_smem) {
   constexpr unsigned Q = kAllQuads<N>;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, 
 
 template <int N, unsigned Q, int kSrc>
 __global__ void __launch_bounds__(kThreads, FPT_BFGS_MIN_CTAS) bfgs_refill_kernel(SceneDev S, BatchDev B, SolveCfg cfg, uint64_t n_local,
-                                                               const uint64_t* __restrict__ list,
+                                                               const PathRec* __restrict__ list,
                                                                float* __restrict__ T_out,
                                                                uint8_t* __restrict__ status_out,
                                                                uint8_t* __restrict__ iters_out, int use_smem,
@@ -536,7 +536,7 @@ struct BfgsLaunch {
   BatchDev B;
   SolveCfg cfg;
   uint64_t n_local;
-  const uint64_t* list;  // nullptr: exhaustive batch, decoded from the local index
+  const PathRec* list;  // nullptr: exhaustive batch, decoded from the local index
   float* T;
   uint8_t* status;
   uint8_t* iters;

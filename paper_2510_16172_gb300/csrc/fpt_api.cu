@@ -109,7 +109,7 @@ struct fpt_batch {
   std::vector<uint8_t> types;     // object types of the scene the batch was built for
   // (order, pattern) buckets of seeded / explicit batches (built on first use)
   bool bucketed = false;
-  uint64_t* d_lists = nullptr;
+  PathRec* d_lists = nullptr;
   uint64_t count[kPatternKeys] = {0};
   uint64_t start[kPatternKeys] = {0};
   // per order: the buckets too small for a pattern launch sit together at the end of the order's range
@@ -599,7 +599,7 @@ static fpt_status ensure_buckets(fpt_ctx* ctx, fpt_batch* b, const SceneDev& S) 
     }
   }
   if (acc != b->dev.n_paths) return fail(ctx, FPT_EDEVICE, "pattern histogram mismatch");
-  CUDA_OR_FAIL(ctx, cudaMalloc(&b->d_lists, (acc ? acc : 1) * sizeof(uint64_t)));
+  CUDA_OR_FAIL(ctx, cudaMalloc(&b->d_lists, (acc ? acc : 1) * sizeof(PathRec)));
   CUDA_OR_FAIL(ctx, cudaMemcpyAsync(ctx->d_count, cur, sizeof(cur), cudaMemcpyHostToDevice, ctx->stream));
   CUDA_OR_FAIL(ctx, launch_pattern_scatter(S, b->dev, ctx->d_count, b->d_lists, ctx->stream, ctx->n_sm));
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
@@ -622,7 +622,7 @@ static fpt_status ensure_rescue(fpt_ctx* ctx, uint64_t n) {
 }
 
 // Paths of order n in a batch: count and list (nullptr for exhaustive batches).
-static uint64_t order_slice(const fpt_batch* b, int n, const uint64_t** list) {
+static uint64_t order_slice(const fpt_batch* b, int n, const PathRec** list) {
   if (b->dev.mode == BATCH_EXHAUSTIVE) {
     *list = nullptr;
     if (n < b->dev.lo || n > b->dev.hi) return 0;
@@ -640,7 +640,7 @@ static uint64_t order_slice(const fpt_batch* b, int n, const uint64_t** list) {
 }
 
 // Paths of order n and interaction-type pattern q: count and list (nullptr for exhaustive batches).
-static uint64_t pattern_slice(const fpt_batch* b, int n, unsigned q, const uint64_t** list) {
+static uint64_t pattern_slice(const fpt_batch* b, int n, unsigned q, const PathRec** list) {
   if (b->dev.mode == BATCH_EXHAUSTIVE) {
     *list = nullptr;
     if (n < b->dev.lo || n > b->dev.hi) return 0;
@@ -688,7 +688,7 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
   // the polish needs its Newton step only to a modest relative accuracy: 100x looser pivot test than the adjoint
   PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, p.polish_fp64};
   for (int n = 1; n <= kMaxOrder; ++n) {
-    const uint64_t* list;
+    const PathRec* list;
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
     if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
@@ -712,7 +712,7 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
       const bool force = p.specialize == 2;
       bool by_pattern = p.specialize && sc.refill > 0;
       for (unsigned q = 0; by_pattern && !listed && !force && q < (1u << n); ++q) {
-        const uint64_t* qlist;
+        const PathRec* qlist;
         const uint64_t qcnt = pattern_slice(b, n, q, &qlist);
         if (qcnt && qcnt < min_pattern_bucket(ctx)) by_pattern = false;
       }
@@ -723,7 +723,7 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
         for (int k = 0; k < fpt_ctx::kSide; ++k) CUDA_OR_FAIL(ctx, cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0));
         int used = 0;
         for (unsigned q = 0; q < (1u << n); ++q) {
-          const uint64_t* qlist;
+          const PathRec* qlist;
           const uint64_t qcnt = pattern_slice(b, n, q, &qlist);
           if (!qcnt || (listed && !force && qcnt < min_pattern_bucket(ctx))) continue;
           cudaStream_t sq = ctx->side[used % fpt_ctx::kSide];
@@ -834,7 +834,7 @@ fpt_status fpt_validity(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   const SceneDev S = scene_dev(s);
   PolishCfg pc{POLISH_VALIDITY, 0, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, 0};
   for (int n = 1; n <= kMaxOrder; ++n) {
-    const uint64_t* list;
+    const PathRec* list;
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
     if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
@@ -865,7 +865,7 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   if (!dL && dL_status_mask && !status) return fail(ctx, FPT_EINVAL, "dL_status_mask needs status");
   BackwardCfg bc_cfg{p.cond_fp64, p.deg_tol, 1, 64, dL ? (uint8_t)0 : dL_status_mask};
   for (int n = 1; n <= kMaxOrder; ++n) {
-    const uint64_t* list;
+    const PathRec* list;
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
     if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
@@ -895,7 +895,7 @@ fpt_status fpt_backward_noalloc(fpt_ctx* ctx, const fpt_scene* s, const fpt_batc
                 kNoAllocMaxAcc);
   if (b->dev.mode != BATCH_EXHAUSTIVE && !b->bucketed)
     return fail(ctx, FPT_EINVAL, "fpt_backward_noalloc: seeded/explicit batch not bucketed yet (solve it first)");
-  const uint64_t* lists[kMaxOrder + 1] = {nullptr};
+  const PathRec* lists[kMaxOrder + 1] = {nullptr};
   uint64_t counts[kMaxOrder + 1] = {0};
   for (int n = 1; n <= kMaxOrder; ++n) {
     counts[n] = order_slice(b, n, &lists[n]);

@@ -77,6 +77,39 @@ struct PathDesc {
   uint8_t flags;  // ST_REPEAT / ST_INVALID
 };
 
+// A path of a seeded or explicit batch, decoded once when the batch is bucketed
+// (32 bytes, two 16-byte loads): words 0-1 g, 2 tx, 3 rx, 4-5 ids[0..3] as
+// 16-bit pairs, 6 ids[4] | n << 16 | flags << 24, 7 unused.  Object ids fit in
+// 16 bits (a scene holds at most 65535 objects).
+struct __align__(16) PathRec {
+  uint32_t w[8];
+};
+
+__device__ __forceinline__ void load_rec(const PathRec* list, uint64_t j, PathDesc& d) {
+  const uint4* p = reinterpret_cast<const uint4*>(list + j);
+  const uint4 a = __ldg(p), b = __ldg(p + 1);
+  d.g = (uint64_t)a.x | ((uint64_t)a.y << 32);
+  d.tx = (int)a.z;
+  d.rx = (int)a.w;
+  d.ids[0] = (int)(b.x & 0xFFFFu);
+  d.ids[1] = (int)(b.x >> 16);
+  d.ids[2] = (int)(b.y & 0xFFFFu);
+  d.ids[3] = (int)(b.y >> 16);
+  d.ids[4] = (int)(b.z & 0xFFFFu);
+  d.n = (int)((b.z >> 16) & 0xFFu);
+  d.flags = (uint8_t)(b.z >> 24);
+}
+
+__device__ __forceinline__ void store_rec(PathRec* list, uint64_t slot, const PathDesc& d) {
+  uint32_t id[kMaxOrder];
+#pragma unroll
+  for (int i = 0; i < kMaxOrder; ++i) id[i] = i < d.n ? (uint32_t)d.ids[i] & 0xFFFFu : 0u;
+  uint4* p = reinterpret_cast<uint4*>(list + slot);
+  p[0] = make_uint4((uint32_t)d.g, (uint32_t)(d.g >> 32), (uint32_t)d.tx, (uint32_t)d.rx);
+  p[1] = make_uint4(id[0] | (id[1] << 16), id[2] | (id[3] << 16),
+                    id[4] | ((uint32_t)d.n << 16) | ((uint32_t)d.flags << 24), 0u);
+}
+
 // splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014).
 __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -192,71 +225,22 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
   finish_desc(B, digits, d);
 }
 
-// Seeded / explicit batch, sequence g taken from a bucket of order N: the same
-// decoding as decode_global with the order known at compile time, so that the
-// descriptor stays in registers.
-template <int N>
-__device__ __forceinline__ void decode_listed(const BatchDev& B, const int32_t* alphabet, uint64_t g, PathDesc& d) {
-  d.g = g;
-  d.n = N;
-  d.flags = 0;
-  if (B.mode == BATCH_EXPLICIT) {
-    const int n = B.order[g];
-    d.tx = B.tx_idx[g];
-    d.rx = B.rx_idx[g];
-    if (n < 1 || n > B.n_max || n > kMaxOrder || d.tx < 0 || d.tx >= B.n_tx || d.rx < 0 || d.rx >= B.n_rx) {
-      d.flags = ST_INVALID;
-#pragma unroll
-      for (int j = 0; j < kMaxOrder; ++j) d.ids[j] = 0;
-      if (d.tx < 0 || d.tx >= B.n_tx) d.tx = 0;
-      if (d.rx < 0 || d.rx >= B.n_rx) d.rx = 0;
-      return;
-    }
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const int o = B.ids[g * (uint64_t)B.n_max + j];
-      d.ids[j] = o;
-      if (o < 0 || o >= B.n_alpha) {
-        d.flags |= ST_INVALID;
-        d.ids[j] = 0;
-      }
-      if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
-    }
-    return;
-  }
-  const uint64_t pair = g / B.per_pair;
-  d.tx = (int)(pair / (uint64_t)B.n_rx);
-  d.rx = (int)(pair - (uint64_t)d.tx * (uint64_t)B.n_rx);
-  const uint64_t K = (uint64_t)B.n_alpha;
-  int digits[N];
-  digits[0] = (int)(seeded_draw(B.seed, g, 1) % K);
-#pragma unroll
-  for (int j = 1; j < N; ++j)
-    digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + seeded_draw(B.seed, g, j + 1) % (K - 1)) % K);
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    const int o = alphabet[digits[j]];
-    d.ids[j] = o;
-    if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
-  }
-}
-
 // Path source for one per-order launch: exhaustive batches need no list; other
-// batches pass the list of global indices that have this order.
-__device__ __forceinline__ void fetch_path(const BatchDev& B, int n, const uint64_t* list, uint64_t j,
+// batches pass their bucket of decoded path records.
+__device__ __forceinline__ void fetch_path(const BatchDev& B, int n, const PathRec* list, uint64_t j,
                                            PathDesc& d) {
   if (list == nullptr)
     decode_exhaustive_order(B, n, j, d);
   else
-    decode_global(B, list[j], d);
+    load_rec(list, j, d);
 }
 
-// Path source of a kernel compiled for order N: the bucket list, else the
+// Path source of a kernel compiled for order N: the bucket of records, else the
 // exhaustive enumeration of order N (both keep the descriptor in registers).
 template <int N>
-__device__ __forceinline__ void fetch_path_n(const BatchDev& B, const uint64_t* list, uint64_t j, PathDesc& d) {
+__device__ __forceinline__ void fetch_path_n(const BatchDev& B, const PathRec* list, uint64_t j, PathDesc& d) {
   if (list != nullptr)
-    decode_listed<N>(B, B.alphabet, list[j], d);
+    load_rec(list, j, d);
   else
     decode_exhaustive_order(B, N, j, d);
 }

@@ -53,7 +53,7 @@ struct BackwardCfg {
 // pattern = Q in [0, 2^n) runs the kernel of that interaction-type pattern
 // over a slice holding only sequences of pattern Q.
 cudaError_t launch_bfgs(int n, int pattern, const SceneDev& S, const BatchDev& B, const SolveCfg& cfg, uint64_t n_local,
-                        const uint64_t* list, float* T, uint8_t* status, uint8_t* iters, cudaStream_t stream,
+                        const PathRec* list, float* T, uint8_t* status, uint8_t* iters, cudaStream_t stream,
                         int n_sm, unsigned long long* work);
 // The implicit backward fused into the polish (fpt_solve_grad): cotangents
 // known at solve time, sums into FP64 accumulators.
@@ -78,13 +78,13 @@ struct GradCfg {
 // solver's point keep it, the others are listed with their first Newton step
 // and finish in a second pass.
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
-                          const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
+                          const PathRec* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                           uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
                           unsigned* rescue_count, const GradCfg* grad = nullptr, uint32_t* step_list = nullptr,
                           unsigned* step_count = nullptr, float* step_delta = nullptr);
 // Adjoint + sums, then an FP64 pass over the paths whose FP32 pivots failed.
 cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,
-                            const uint64_t* list, const float* T, const uint8_t* status, const float* dX,
+                            const PathRec* list, const float* T, const uint8_t* status, const float* dX,
                             const float* dL, double* gacc, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
                             unsigned* rescue_count);
 // Backward with its scratch in a fixed device array (no allocation): limits below.
@@ -92,12 +92,12 @@ constexpr int kNoAllocMaxAcc = 1 << 16;      // 9 n_obj + 3 (n_tx + n_rx) FP64 a
 constexpr int kNoAllocMaxSlice = 1 << 20;    // paths of one order in the batch
 constexpr int kNoAllocMaxDevices = 64;
 cudaError_t launch_backward_noalloc(int device, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
-                                    const uint64_t* const* lists, const uint64_t* counts, const float* T,
+                                    const PathRec* const* lists, const uint64_t* counts, const float* T,
                                     const uint8_t* status, const float* dX, const float* dL, float* g_tx, float* g_rx,
                                     float* g_vertices, cudaStream_t stream, int n_sm);
 // FP64 adjoint over a rescue list (paths of one order slice).
 cudaError_t launch_backward_rescue(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
-                                   uint64_t n_local, const uint64_t* list, const float* T, const uint8_t* status,
+                                   uint64_t n_local, const PathRec* list, const float* T, const uint8_t* status,
                                    const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm,
                                    const uint32_t* rescue_list, const unsigned* rescue_count);
 cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
@@ -109,7 +109,7 @@ cudaError_t launch_enumerate(const BatchDev& B, int32_t* ids, uint8_t* order, in
 // Bucketing of seeded / explicit batches by pattern_key(order, pattern): counts[kPatternKeys].
 cudaError_t launch_pattern_histogram(const SceneDev& S, const BatchDev& B, unsigned long long* counts,
                                      cudaStream_t stream, int n_sm);
-cudaError_t launch_pattern_scatter(const SceneDev& S, const BatchDev& B, unsigned long long* cursors, uint64_t* lists,
+cudaError_t launch_pattern_scatter(const SceneDev& S, const BatchDev& B, unsigned long long* cursors, PathRec* lists,
                                    cudaStream_t stream, int n_sm);
 cudaError_t launch_count_status(const uint8_t* status, uint64_t n, uint8_t mask, unsigned long long* out,
                                 cudaStream_t stream, int n_sm);

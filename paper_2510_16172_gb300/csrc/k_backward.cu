@@ -23,7 +23,7 @@ namespace fpt {
 
 template <int N>
 __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev B, BackwardCfg cfg,
-                                                            uint64_t n_local, const uint64_t* __restrict__ list,
+                                                            uint64_t n_local, const PathRec* __restrict__ list,
                                                             const float* __restrict__ T,
                                                             const uint8_t* __restrict__ status,
                                                             const float* __restrict__ dX,
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
 // vectors, Hessian and VJP, summed straight into the FP64 accumulators.
 template <int N>
 __global__ void __launch_bounds__(kThreads) backward_rescue_kernel(SceneDev S, BatchDev B, BackwardCfg cfg,
-                                                                   const uint64_t* __restrict__ list,
+                                                                   const PathRec* __restrict__ list,
                                                                    const float* __restrict__ T,
                                                                    const uint8_t* __restrict__ status,
                                                                    const float* __restrict__ dX,
@@ -249,7 +249,7 @@ __global__ void backward_finalize_kernel(int n_obj, int n_tx, int n_rx, const fl
 // FP64 adjoint over the listed paths (a few percent of a slice of n_local paths).
 template <int N>
 static cudaError_t launch_backward_rescue_n(const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
-                                            uint64_t n_local, const uint64_t* list, const float* T,
+                                            uint64_t n_local, const PathRec* list, const float* T,
                                             const uint8_t* status, const float* dX, const float* dL, double* gacc,
                                             cudaStream_t stream, int n_sm, const uint32_t* rescue_list,
                                             const unsigned* rescue_count) {
@@ -262,7 +262,7 @@ static cudaError_t launch_backward_rescue_n(const SceneDev& S, const BatchDev& B
 }
 
 cudaError_t launch_backward_rescue(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
-                                   uint64_t n_local, const uint64_t* list, const float* T, const uint8_t* status,
+                                   uint64_t n_local, const PathRec* list, const float* T, const uint8_t* status,
                                    const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm,
                                    const uint32_t* rescue_list, const unsigned* rescue_count) {
   switch (n) {
@@ -282,7 +282,7 @@ cudaError_t launch_backward_rescue(int n, const SceneDev& S, const BatchDev& B, 
 
 template <int N>
 static cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg_in,
-                                     uint64_t n_local, const uint64_t* list, const float* T, const uint8_t* status,
+                                     uint64_t n_local, const PathRec* list, const float* T, const uint8_t* status,
                                      const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm,
                                      uint32_t* rescue_list, unsigned* rescue_count) {
   BackwardCfg cfg = cfg_in;
@@ -318,7 +318,7 @@ static cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const
 }
 
 cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg, uint64_t n_local,
-                            const uint64_t* list, const float* T, const uint8_t* status, const float* dX,
+                            const PathRec* list, const float* T, const uint8_t* status, const float* dX,
                             const float* dL, double* gacc, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
                             unsigned* rescue_count) {
   switch (n) {
@@ -368,7 +368,7 @@ static cudaError_t noalloc_scratch(int device, unsigned char** out) {
 }
 
 cudaError_t launch_backward_noalloc(int device, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
-                                    const uint64_t* const* lists, const uint64_t* counts, const float* T,
+                                    const PathRec* const* lists, const uint64_t* counts, const float* T,
                                     const uint8_t* status, const float* dX, const float* dL, float* g_tx, float* g_rx,
                                     float* g_vertices, cudaStream_t stream, int n_sm) {
   unsigned char* base = nullptr;

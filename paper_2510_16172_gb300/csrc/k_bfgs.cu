@@ -16,7 +16,7 @@ static cudaError_t launch_unified(const BfgsLaunch& a) {
 }
 
 cudaError_t launch_bfgs(int n, int pattern, const SceneDev& S, const BatchDev& B, const SolveCfg& cfg,
-                        uint64_t n_local, const uint64_t* list, float* T, uint8_t* status, uint8_t* iters,
+                        uint64_t n_local, const PathRec* list, float* T, uint8_t* status, uint8_t* iters,
                         cudaStream_t stream, int n_sm, unsigned long long* work) {
   const BfgsLaunch a{S, B, cfg, n_local, list, T, status, iters, stream, n_sm, work};
   if (pattern < 0) {

@@ -49,14 +49,15 @@ __global__ void pattern_hist_kernel(SceneDev S, BatchDev B, unsigned long long* 
     if (s[k]) atomicAdd(&counts[k], s[k]);
 }
 
-// cursors[key] starts at the first slot of that bucket in `lists`.
-__global__ void pattern_scatter_kernel(SceneDev S, BatchDev B, unsigned long long* cursors, uint64_t* lists) {
+// cursors[key] starts at the first slot of that bucket in `lists`; each slot
+// receives the decoded path.
+__global__ void pattern_scatter_kernel(SceneDev S, BatchDev B, unsigned long long* cursors, PathRec* lists) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < B.n_paths; g += stride) {
     PathDesc d;
     decode_global(B, g, d);
     unsigned long long slot = atomicAdd(&cursors[path_key(S, d)], 1ULL);
-    lists[slot] = g;
+    store_rec(lists, slot, d);
   }
 }
 
@@ -98,7 +99,7 @@ cudaError_t launch_pattern_histogram(const SceneDev& S, const BatchDev& B, unsig
   return cudaGetLastError();
 }
 
-cudaError_t launch_pattern_scatter(const SceneDev& S, const BatchDev& B, unsigned long long* cursors, uint64_t* lists,
+cudaError_t launch_pattern_scatter(const SceneDev& S, const BatchDev& B, unsigned long long* cursors, PathRec* lists,
                                    cudaStream_t stream, int n_sm) {
   unsigned grid = grid_for(B.n_paths, 256, n_sm, 8);
   if (grid == 0) return cudaSuccess;

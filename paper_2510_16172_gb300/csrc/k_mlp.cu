@@ -279,7 +279,7 @@ __device__ __forceinline__ void path_features(const SceneDev& S, const PathDesc&
 }
 
 // all paths of a batch (global index order) or one order slice (local index order)
-__global__ void mlp_features_kernel(SceneDev S, BatchDev B, int n, const uint64_t* list, uint64_t first,
+__global__ void mlp_features_kernel(SceneDev S, BatchDev B, int n, const PathRec* list, uint64_t first,
                                     uint64_t count, float inv_scale, __nv_bfloat16* X, float* G) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x) {
     PathDesc d;
@@ -352,7 +352,7 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __r
 }
 
 // learned start: T[g] slot s < min(n, 4) from Y (edges keep t2 = 1/2; non-finite or |t| > 1e3 -> 1/2)
-__global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const uint64_t* list, uint64_t first, uint64_t count,
+__global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const PathRec* list, uint64_t first, uint64_t count,
                                  const float* __restrict__ Y, float* __restrict__ T) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x) {
     PathDesc d;
@@ -426,7 +426,7 @@ struct InferSmem {
 };
 
 __global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S, BatchDev B, int n,
-                                                                     const uint64_t* __restrict__ list, uint64_t count,
+                                                                     const PathRec* __restrict__ list, uint64_t count,
                                                                      float inv_scale,
                                                                      const __nv_bfloat16* __restrict__ wt,
                                                                      const float* __restrict__ params, float* T,
@@ -578,7 +578,7 @@ cudaError_t launch_mlp_tile_weights(const __nv_bfloat16* wb, __nv_bfloat16* wt, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_infer(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t count,
+cudaError_t launch_mlp_infer(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t count,
                              float inv_scale, const __nv_bfloat16* wt, const float* params, float* T, int* err,
                              cudaStream_t stream, int n_sm) {
   if (!count) return cudaSuccess;
@@ -601,7 +601,7 @@ static unsigned grid_1d(uint64_t n, int threads, int cap) {
   return (unsigned)(g < (uint64_t)cap ? (g ? g : 1) : (uint64_t)cap);
 }
 
-cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
+cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t first,
                                 uint64_t count, float inv_scale, __nv_bfloat16* X, float* G, cudaStream_t stream) {
   if (!count) return cudaSuccess;
   mlp_features_kernel<<<grid_1d(count, 128, 4096), 128, 0, stream>>>(S, B, n, list, first, count, inv_scale, X, G);
@@ -636,7 +636,7 @@ cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int n, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
+cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t first,
                              uint64_t count, const float* Y, float* T, cudaStream_t stream) {
   if (!count) return cudaSuccess;
   mlp_start_kernel<<<grid_1d(count, 128, 4096), 128, 0, stream>>>(S, B, n, list, first, count, Y, T);

@@ -211,7 +211,7 @@ constexpr int kSmemAcc = 2;
 // whose polish went to the FP64 pass -- are listed for the FP64 adjoint pass.
 template <int N, bool kGrad>
 __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kernel(
-    SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local, const uint64_t* __restrict__ list,
+    SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local, const PathRec* __restrict__ list,
     float* __restrict__ T, float* __restrict__ X, float* __restrict__ Lout, uint8_t* __restrict__ status,
     float* __restrict__ rho_out, uint8_t* __restrict__ mask_out, float* __restrict__ bdist_out, int use_smem,
     uint32_t* __restrict__ rescue_list, unsigned* __restrict__ rescue_count, GradCfg gc,
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local,
-                                                            const uint64_t* __restrict__ list, float* __restrict__ T,
+                                                            const PathRec* __restrict__ list, float* __restrict__ T,
                                                             float* __restrict__ X, float* __restrict__ Lout,
                                                             uint8_t* __restrict__ status, float* __restrict__ rho_out,
                                                             uint8_t* __restrict__ mask_out,
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev
 
 template <int N>
 static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
-                                   const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
+                                   const PathRec* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                                    uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
                                    unsigned* rescue_count, const GradCfg* grad, uint32_t* step_list,
                                    unsigned* step_count, float* step_delta) {
@@ -775,7 +775,7 @@ static cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const P
 }
 
 cudaError_t launch_polish(int n, const SceneDev& S, const BatchDev& B, const PolishCfg& cfg, uint64_t n_local,
-                          const uint64_t* list, float* T, float* X, float* L, uint8_t* status, float* rho,
+                          const PathRec* list, float* T, float* X, float* L, uint8_t* status, float* rho,
                           uint8_t* mask, float* bdist, cudaStream_t stream, int n_sm, uint32_t* rescue_list,
                           unsigned* rescue_count, const GradCfg* grad, uint32_t* step_list, unsigned* step_count,
                           float* step_delta) {

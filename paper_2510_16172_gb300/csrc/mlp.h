@@ -36,7 +36,7 @@ struct GemmArgs {
 };
 
 cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream);
-cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
+cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t first,
                                 uint64_t count, float inv_scale, __nv_bfloat16* X, float* G, cudaStream_t stream);
 cudaError_t launch_mlp_loss(const float* G, const float* Y, const float* T, uint64_t B, float* dY,
                             __nv_bfloat16* dYb, float* loss, cudaStream_t stream);
@@ -46,10 +46,10 @@ cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, flo
 cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int n, cudaStream_t stream);
 constexpr size_t kMlpTiledBytes = 9 * 32768 + 4 * 2048;  // weights pre-tiled for the fused inference
 cudaError_t launch_mlp_tile_weights(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t stream);
-cudaError_t launch_mlp_infer(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t count,
+cudaError_t launch_mlp_infer(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t count,
                              float inv_scale, const __nv_bfloat16* wt, const float* params, float* T, int* err,
                              cudaStream_t stream, int n_sm);
-cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const uint64_t* list, uint64_t first,
+cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t first,
                              uint64_t count, const float* Y, float* T, cudaStream_t stream);
 
 }  // namespace fpt
