@@ -104,7 +104,10 @@ typedef struct {
                            kinked paths but also stop some regular paths whose iterates pass close to a kink */
   int32_t polish_all;   /* 0: a path whose residual at the BFGS point already meets solved_tol is returned as is,
                            the others take the `polish` Newton steps (0); 1: every path takes them */
-  int32_t reserved[1]; /* must be zero */
+  float polish_radius;  /* adaptive polish: Newton steps are taken only from a point whose residual is at most
+                           this (metres; farther points are not near a stationary path and stay unsolved;
+                           0.1; 0 = no limit) */
+  int32_t reserved[4]; /* must be zero */
 } fpt_solve_params;
 
 typedef struct fpt_ctx fpt_ctx;

@@ -199,6 +199,7 @@ void fpt_default_params(fpt_solve_params* p) {
   p->polish_fp64 = 0;
   p->refill = 8;
   p->specialize = 1;
+  p->polish_radius = 0.1f;
 }
 
 fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
@@ -675,7 +676,7 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
   if (p.init_mode != 0 && p.init_mode != 1) return fail(ctx, FPT_EINVAL, "init_mode must be 0 or 1");
   if (p.init_mode == 1 && !ctx->init_mlp) return fail(ctx, FPT_EINVAL, "init_mode 1 needs fpt_set_init_mlp");
   if (p.max_iters < 0 || p.fp_iters < 1 || p.polish < 0 || p.polish > 2 || p.specialize < 0 || p.specialize > 2 ||
-      !(p.kink_stop >= 0.f))
+      !(p.kink_stop >= 0.f) || !(p.polish_radius >= 0.f))
     return fail(ctx, FPT_EINVAL, "bad solver parameters");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
@@ -686,7 +687,8 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
   SolveCfg sc{p.max_iters, p.fp_iters, p.fixed_iters, p.tol_step * p.tol_step, kink * kink,
               p.refill > 32 ? 32 : p.refill, p.init_mode == 1, kMaxChunk};
   // the polish needs its Newton step only to a modest relative accuracy: 100x looser pivot test than the adjoint
-  PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, p.polish_fp64};
+  PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, p.polish_fp64,
+               p.polish_radius};
   for (int n = 1; n <= kMaxOrder; ++n) {
     const PathRec* list;
     uint64_t cnt = order_slice(b, n, &list);

@@ -38,6 +38,7 @@ struct PolishCfg {
   float deg_tol;     // shortest segment of a regular solution
   float cond_fp64;   // pivot ratio that triggers the FP64 Hessian solve
   int fp64;          // 1: FP64 gradients in the polish (validation); 0: double-float
+  float radius;      // adaptive polish: largest first residual from which the Newton steps are taken (0 = any)
 };
 
 struct BackwardCfg {

@@ -56,11 +56,17 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
       for (int k = 0; k < 9; ++k) gb[i][k] = 0.f;
     bool use = false;
     uint8_t st = 0;
+    float dl = 0.f;
     if (have) {
       fetch_path_n<N>(B, list, j, d);
       st = d.flags;
       if (status) st |= status[d.g];
       use = !(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE));
+      // a path with no cotangent contributes exactly zero: skip it
+      if (use) {
+        dl = dLv ? dLv[d.g] : ((cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask) ? 1.f : 0.f);
+        use = dX != nullptr || dl != 0.f;
+      }
     } else {
       d.tx = d.rx = 0;
 #pragma unroll
@@ -108,7 +114,6 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
           if (jj > 0) x -= fmaf(a[jj - 1][1][c], t[jj - 1][1], a[jj - 1][0][c] * t[jj - 1][0]);
           z[jj][c] = x;
         }
-      const float dl = dLv ? dLv[g] : ((cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask) ? 1.f : 0.f);
       float dx[N][3];
 #pragma unroll
       for (int i = 0; i < N; ++i)
@@ -204,6 +209,7 @@ __global__ void __launch_bounds__(kThreads) backward_rescue_kernel(SceneDev S, B
         z[jj][c] = x;
       }
     const double dl = dLv ? (double)dLv[g] : ((cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask) ? 1.0 : 0.0);
+    if (!dX && dl == 0.0) continue;  // no cotangent: the path contributes exactly zero
     double gb[N][9], gtx[3], grx[3];
     if (!path_vjp<double, N>(z, a, t, edge, dx, dl, 1e-10, gb, gtx, grx)) continue;
 #pragma unroll

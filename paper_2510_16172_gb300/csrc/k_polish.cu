@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
             // pass returns the solver's point when it already meets the bound; otherwise it lists the
             // path with its Newton step, and the second pass continues from there.
             const float r0 = world_max<N>(G.ah, delta);
-            if (s >= steps || r0 <= cfg.solved_tol) {
+            if (s >= steps || r0 <= cfg.solved_tol || (cfg.radius > 0.f && r0 > cfg.radius)) {
               rho = r0;
               adj_ok = strict;
             } else {
@@ -413,7 +413,10 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
         } else if (listed64) {
           // the FP64 polish decides this path's status; the FP64 adjoint pass reads it
           gc.rescue_list[atomicAdd(gc.rescue_count, 1u)] = (uint32_t)j;
-        } else if (!(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE))) {
+        } else if (!(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE)) &&
+                   (gc.dX != nullptr ||
+                    (gc.dL ? gc.dL[g] != 0.f : (gc.dl_mask && (st & gc.dl_mask) == gc.dl_mask)))) {
+          // (a path with no cotangent contributes exactly zero and is skipped)
           if (fact_ok && adj_ok) {
             const float dl = gc.dL ? gc.dL[g] : ((gc.dl_mask && (st & gc.dl_mask) == gc.dl_mask) ? 1.f : 0.f);
             float dx[N][3];

@@ -43,7 +43,8 @@ class SolveParams(C.Structure):
                 ("tol_step", C.c_float), ("solved_tol", C.c_float), ("deg_tol", C.c_float), ("cond_fp64", C.c_float),
                 ("init_mode", C.c_int32), ("polish_fp64", C.c_int32), ("refill", C.c_int32),
                 ("specialize", C.c_int32), ("fuse_adjoint", C.c_int32),
-                ("kink_stop", C.c_float), ("polish_all", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("kink_stop", C.c_float), ("polish_all", C.c_int32), ("polish_radius", C.c_float),
+                ("reserved", C.c_int32 * 4)]
 
 
 # every symbol declared in include/fpt.h with (restype, argtypes)
