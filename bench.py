@@ -502,6 +502,78 @@ def run_city(args, world, rank, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_fig2(args, world, rank, local_rank):
+    """Sec. IV-A, Fig. 2 (our solver's side): mean point error against solver time.
+
+    For diffraction-only (d = 1), reflection-only (d = 2) and mixed sequences of order n = 1..5 on
+    random 10 m scenes (12 objects of one kind, or 8 planes + 4 edges), 1000 seeded paths per case are
+    solved with exactly k BFGS steps (no polish) for k = 1..100, with one ('ours') or 64 ('ours-64')
+    Eq. 6 rounds per step; diffractions also in the unified d = 2 form.  The error is the mean distance
+    of the interaction points from the polished solution (stationarity residual <= 1e-5 m) over the
+    paths that reach it; the time is the BFGS kernels' device time (CUDA events), for the 1000 paths
+    and per path at 1,000,000 paths.
+    """
+    import numpy as np
+    import torch
+
+    from paper_2510_16172_gb300 import build, fpt, scenes
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ctx = fpt.Context(local_rank)
+    kinds = {"d1": dict(n_quads=0, n_edges=12), "d2": dict(n_quads=12, n_edges=0),
+             "mixed": dict(n_quads=8, n_edges=4)}
+    ks = [1, 2, 3, 5, 8, 12, 20, 32, 50, 100]
+    curves = []
+    for kind, kw in kinds.items():
+        sc = scenes.tiny_scene(3, **kw)
+        scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+        for n in range(1, 6):
+            small = fpt.Batch.seeded(ctx, scene, 100 + n, 1000, n, n)
+            big = fpt.Batch.seeded(ctx, scene, 200 + n, 1_000_000, n, n)
+            ref = fpt.solve(ctx, scene, small, fpt.default_params(max_iters=100, polish=2))
+            ok = (ref["status"] & fpt.ST_SOLVED) > 0
+            Xr = ref["X"][ok].double()
+            variants = [("ours", 1, 2), ("ours-64", 64, 2)]
+            if kind == "d1":
+                variants += [("ours d=2", 1, 0), ("ours-64 d=2", 64, 0)]
+            for name, fp, spec in variants:
+                pts = []
+                for k in ks:
+                    p = fpt.default_params(max_iters=k, fixed_iters=1, fp_iters=fp, polish=0, specialize=spec)
+                    row = {"k": k}
+                    for label, batch in (("small", small), ("big", big)):
+                        out = fpt.alloc_outputs(ctx, batch, with_X=label == "small")
+                        fpt.solve(ctx, scene, batch, p, out)  # warm-up
+                        ctx.sync()
+                        fpt.profile_enable(ctx, True)
+                        fpt.profile_read(ctx, reset=True)
+                        reps = 5 if label == "small" else 2
+                        for _ in range(reps):
+                            fpt.solve(ctx, scene, batch, p, out)
+                        kms, _ = fpt.profile_read(ctx, reset=True)
+                        fpt.profile_enable(ctx, False)
+                        if label == "small":
+                            row["ms_1000_paths"] = kms[fpt.K_BFGS] / reps
+                            err = (out["X"][ok].double() - Xr).norm(dim=2)[:, :n].mean(dim=1)
+                            fin = torch.isfinite(err)
+                            row["mean_err_m"] = float(err[fin].mean())
+                            row["nonfinite_paths"] = int((~fin).sum())
+                        else:
+                            row["ns_per_path_at_1M"] = kms[fpt.K_BFGS] / reps * 1e6 / batch.n_paths
+                        del out
+                    pts.append(row)
+                curves.append({"kind": kind, "n": n, "solver": name, "paths_with_reference": int(ok.sum()),
+                               "points": pts})
+    line = {"metric": "mean interaction-point error vs BFGS time (Fig. 2, our solver)", "unit": "m",
+            "config": {"workload": "1000 seeded paths per (kind, n) on a random 10 m scene; k = 1..100 fixed BFGS "
+                                   "steps, no polish; reference = polished solution (residual <= 1e-5 m)"},
+            "curves": curves}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def e2e(args, sc, ctx, dev, torch, fpt):
     """Same metric through the public API: host scene/endpoints in, host lengths/status/gradients out."""
     import numpy as np
@@ -559,8 +631,9 @@ def main():
     ap.add_argument("--max-iters", type=int, default=32, help="BFGS step cap")
     ap.add_argument("--rx-grid", type=int, default=32, help="RX grid side (32 = the 33.5M-path workload)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain start comparison")
-    ap.add_argument("--workload", choices=["canyon", "city"], default="canyon",
-                    help="canyon: the 33.5M-path urban canyon (default); city: the 100M-path ragged city batch")
+    ap.add_argument("--workload", choices=["canyon", "city", "fig2"], default="canyon",
+                    help="canyon: the 33.5M-path urban canyon (default); city: the 100M-path ragged city batch; "
+                         "fig2: point error against solver time by iteration budget")
     ap.add_argument("--city-paths", type=int, default=100_000_000)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -577,6 +650,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "city":
         run_city(args, world, rank, local_rank)
+    elif args.workload == "fig2":
+        run_fig2(args, world, rank, local_rank)
     else:
         run_ours(args, world, rank, local_rank)
     if world > 1:

@@ -427,6 +427,9 @@ static void apply_cols(const orc_path* P, const double* p, int i, double* out) {
 }
 
 /* Eq. 6: fixed-point update of the step size along direction p.             */
+/* Steps are capped at this many quasi-Newton steps (keeps rounds at a vanishing direction finite). */
+#define ORC_ALPHA_MAX 1e3
+
 double orc_fixed_point_alpha(const orc_path* P, const orc_segments* S, const double* p, double alpha, int fp_iters) {
   int n = P->n;
   double q[ORC_NMAX + 1][3], Ap[ORC_NMAX + 2][3];
@@ -445,6 +448,7 @@ double orc_fixed_point_alpha(const orc_path* P, const orc_segments* S, const dou
     }
     if (!(den > 1e-300)) return 0.0;
     alpha = -num / den;
+    if (alpha > ORC_ALPHA_MAX) alpha = ORC_ALPHA_MAX; /* step cap (same reading as the GPU solver) */
   }
   return alpha;
 }

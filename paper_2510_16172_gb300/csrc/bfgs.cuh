@@ -199,7 +199,10 @@ __device__ __forceinline__ void grad_eval(const Geo<N>& G, const float (&t)[N][2
 }
 
 // Eq. 6: alpha <- -sum_j (q_j.z_j)/|z_j + alpha q_j| / sum_j (q_j.q_j)/|z_j + alpha q_j|,
-// with |z_j + alpha q_j|^2 = e_j + alpha (2 qa_j + alpha qc_j).
+// with |z_j + alpha q_j|^2 = e_j + alpha (2 qa_j + alpha qc_j).  Steps are capped at
+// kAlphaMax times the quasi-Newton step, which keeps many rounds at a vanishing
+// direction (a converged path run for a fixed step count) finite.
+constexpr float kAlphaMax = 1e3f;
 template <int N>
 __device__ __forceinline__ float fixed_point(const float (&e)[N + 1], const float (&qa)[N + 1],
                                              const float (&qc)[N + 1], float alpha, int rounds) {
@@ -212,7 +215,7 @@ __device__ __forceinline__ float fixed_point(const float (&e)[N + 1], const floa
       num = fmaf(qa[j], r, num);
       den = fmaf(qc[j], r, den);
     }
-    alpha = den > 1e-30f ? -__fdividef(num, den) : 0.f;
+    alpha = den > 1e-30f ? fminf(-__fdividef(num, den), kAlphaMax) : 0.f;
   }
   return alpha;
 }

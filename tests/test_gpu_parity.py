@@ -414,3 +414,30 @@ def test_bad_arguments_are_errors_not_faults(ctx):
     with pytest.raises(fpt.FptError):
         fpt.Scene(ctx, sc.types, flat)
     ctx.sync()
+
+
+def test_fixed_point_rounds_reach_the_oracle_in_fewer_steps(ctx):
+    """Sec. IV-A: more Eq. 6 rounds per step converge in fewer steps (fixed step counts, no polish), and the
+    reduced d = 1 kernels for diffractions give exactly the unified d = 2 iterates."""
+    sc = scenes.tiny_scene(3, n_quads=0, n_edges=12)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    batch = fpt.Batch.seeded(ctx, scene, 103, 1000, 3, 3)
+    ids, order, ti, ri = oracle.seeded_paths(sc, 103, 1000, 3, 3)
+    ref = oracle_solve(sc, ids, order, ti, ri)
+    keep = regular(ref["status"])
+    assert keep.sum() > 500
+
+    def err(k, fp, spec):
+        out = to_np(fpt.solve(ctx, scene, batch, fpt.default_params(max_iters=k, fixed_iters=1, fp_iters=fp,
+                                                                     polish=0, specialize=spec)))
+        ctx.sync()
+        e = np.linalg.norm(out["X"][keep] - ref["X"][keep], axis=2).mean(axis=1)
+        return e[np.isfinite(e)].mean(), out
+
+    e1, o1 = err(8, 1, 2)
+    e64, _ = err(8, 64, 2)
+    assert e64 < 0.5 * e1, (e1, e64)
+    _, o_unified = err(8, 1, 0)
+    assert np.array_equal(o1["T"], o_unified["T"])
+    e_late, _ = err(32, 1, 2)
+    assert e_late < 1e-5
