@@ -574,6 +574,71 @@ def run_fig2(args, world, rank, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_fig3(args, world, rank, local_rank):
+    """Sec. IV-B, Fig. 3: time of the gradient of the path lengths, implicit vs through the iterations.
+
+    On a random 10 m scene (8 planes + 4 edges), seeded sequences of order n = 1..5: the gradient of
+    sum L with respect to TX, RX and every vertex after k = 16 or 128 solver steps with 1 or 64 Eq. 6
+    rounds per step (d = 2).  'implicit' = fpt_solve_grad (k fixed steps, the Newton polish, the
+    implicit backward of Sec. III-D); 'ad' = fpt_backward_unrolled (the same k steps taped, then
+    reverse mode through every step).  Device time by CUDA events on the launching stream, for 1000
+    paths (the paper's batch) and per path at 1,000,000 paths.
+    """
+    import torch
+
+    from paper_2510_16172_gb300 import build, fpt, scenes
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ctx = fpt.Context(local_rank)
+    sc = scenes.tiny_scene(3, n_quads=8, n_edges=4)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    rows = []
+    for n in range(1, 6):
+        for label, per_pair in (("1000", 1000), ("1M", 1_000_000)):
+            batch = fpt.Batch.seeded(ctx, scene, 300 + n, per_pair, n, n)
+            N = batch.n_paths
+            ones = torch.ones(N, dtype=torch.float32, device=dev)
+            out = fpt.alloc_outputs(ctx, batch)
+            for k in (16, 128):
+                for fp in (1, 64):
+                    p = fpt.default_params(max_iters=k, fixed_iters=1, fp_iters=fp)
+                    reps = 10 if label == "1000" else 2
+                    t_imp = timed(lambda: fpt.solve_grad(ctx, scene, batch, p, dL=ones, out=out), reps)
+                    t_ad = timed(lambda: fpt.backward_unrolled(ctx, scene, batch, k, fp, dL=ones), reps)
+                    row = {"n": n, "paths": N, "k": k, "fp_iters": fp, "implicit_ms": t_imp, "ad_ms": t_ad,
+                           "ad_over_implicit": t_ad / t_imp}
+                    if label == "1000":
+                        # how far the gradient through the k FP32 steps is from the implicit one
+                        _, (_, _, gi) = fpt.solve_grad(ctx, scene, batch, p, dL=ones, out=out)
+                        _, _, ga, _, _ = fpt.backward_unrolled(ctx, scene, batch, k, fp, dL=ones)
+                        row["ad_vs_implicit_rel_diff"] = float((ga - gi).norm() / gi.norm())
+                    rows.append(row)
+                    if rank == 0:
+                        print(json.dumps(row), file=sys.stderr, flush=True)
+            del out, ones
+    line = {"metric": "gradient time of sum L, implicit vs AD through the iterations (Fig. 3)", "unit": "ms",
+            "config": {"workload": "seeded order-n sequences on a random 10 m scene (8 planes + 4 edges), "
+                                   "1000 paths and 1,000,000 paths per n; k fixed solver steps, fp Eq. 6 rounds"},
+            "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def e2e(args, sc, ctx, dev, torch, fpt):
     """Same metric through the public API: host scene/endpoints in, host lengths/status/gradients out."""
     import numpy as np
@@ -631,9 +696,10 @@ def main():
     ap.add_argument("--max-iters", type=int, default=32, help="BFGS step cap")
     ap.add_argument("--rx-grid", type=int, default=32, help="RX grid side (32 = the 33.5M-path workload)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain start comparison")
-    ap.add_argument("--workload", choices=["canyon", "city", "fig2"], default="canyon",
+    ap.add_argument("--workload", choices=["canyon", "city", "fig2", "fig3"], default="canyon",
                     help="canyon: the 33.5M-path urban canyon (default); city: the 100M-path ragged city batch; "
-                         "fig2: point error against solver time by iteration budget")
+                         "fig2: point error against solver time by iteration budget; fig3: gradient time, implicit vs AD "
+                         "through the iterations")
     ap.add_argument("--city-paths", type=int, default=100_000_000)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -652,6 +718,8 @@ def main():
         run_city(args, world, rank, local_rank)
     elif args.workload == "fig2":
         run_fig2(args, world, rank, local_rank)
+    elif args.workload == "fig3":
+        run_fig3(args, world, rank, local_rank)
     else:
         run_ours(args, world, rank, local_rank)
     if world > 1:

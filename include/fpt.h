@@ -232,6 +232,30 @@ fpt_status fpt_solve_grad(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch*
                           float* L_out, uint8_t* status_out, uint8_t* iters_out, float* rho_out, float* g_tx,
                           float* g_rx, float* g_vertices);
 
+/* Gradient by automatic differentiation through the solver's iterations, the
+ * alternative the implicit backward is compared with (Sec. IV-B, Fig. 3).
+ * Every path of the batch runs exactly `steps` steps of the unified solver of
+ * Sec. III-C (d = 2 unknowns per interaction, an edge's second basis vector
+ * zero) from t = 1/2: H_0 = I, p = -H g, `fp_iters` rounds of the Eq. 6 fixed
+ * point from alpha = 1 (redone from alpha = 0 when they give alpha <= 0; alpha
+ * at most 1e3 times the quasi-Newton step), t += alpha p, and the BFGS inverse
+ * update unless s.y <= 0 or (s.y)^2 <= 1e-12 |s|^2 |y|^2.  No convergence test,
+ * polish or validity test runs.  The gradient of
+ *   sum over paths of dX . X + dL L   (X, L at the last iterate)
+ * with respect to TX, RX and the object vertices is then formed in reverse
+ * mode through all steps (the line-search rounds and the inverse-Hessian
+ * updates included), one path per GPU thread, with each step's iterate and
+ * inverse Hessian kept on a context-owned device tape of steps (2n + 2n(2n+1)/2)
+ * floats per resident thread (at most 16 GiB; fewer resident threads when it is
+ * short).  steps in [0, 4096], fp_iters in [1, 64] (FPT_EINVAL otherwise).
+ * dX [N][n_max][3], dL [N] device or NULL (zero).  T_out [N][n_max][2] (the last
+ * iterate) and status_out [N] (REPEAT / INVALID as in fpt_solve, NONFINITE when
+ * the path's gradient is not finite: it is then left out of the sums) are
+ * optional.  Gradient outputs as in fpt_backward. */
+fpt_status fpt_backward_unrolled(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* batch, int32_t steps,
+                                 int32_t fp_iters, const float* dX, const float* dL, float* T_out, uint8_t* status_out,
+                                 float* g_tx, float* g_rx, float* g_vertices);
+
 /* fpt_backward without any device allocation, for callers that cannot
  * allocate: for example a host application whose GPU memory is entirely
  * reserved by another allocator (a framework's caching pool), or a latency-

@@ -33,6 +33,8 @@ struct fpt_ctx {
   int* d_err = nullptr;                    // device error word
   double* d_gacc = nullptr;                // backward accumulators (FP64)
   size_t gacc_cap = 0;
+  float* d_tape = nullptr;                 // per-step state of fpt_backward_unrolled
+  size_t tape_cap = 0;                     // floats
   unsigned long long* d_count = nullptr;   // counters for reductions
   unsigned long long* d_work = nullptr;    // work counters of the lane-refill solver (one per concurrent launch)
   static constexpr int kSide = FPT_SIDE_STREAMS;  // streams for the independent pattern launches of one order
@@ -249,6 +251,7 @@ void fpt_destroy(fpt_ctx* ctx) {
   cudaFree(ctx->d_rescue);
   cudaFree(ctx->d_step);
   cudaFree(ctx->d_rescue_n);
+  cudaFree(ctx->d_tape);
   delete ctx;
 }
 
@@ -876,6 +879,50 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
     ProfScope ps(ctx, FPT_K_BACKWARD);
     CUDA_OR_FAIL(ctx, launch_backward(n, S, b->dev, bc_cfg, cnt, list, T, status, dX, dL, ctx->d_gacc, ctx->stream,
                                       ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n));
+  }
+  {
+    ProfScope ps(ctx, FPT_K_OTHER);
+    CUDA_OR_FAIL(ctx, launch_backward_finalize(S, nullptr, ctx->d_gacc, g_tx, g_rx, g_vertices, ctx->stream));
+  }
+  return FPT_OK;
+}
+
+fpt_status fpt_backward_unrolled(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, int32_t steps,
+                                 int32_t fp_iters, const float* dX, const float* dL, float* T_out, uint8_t* status_out,
+                                 float* g_tx, float* g_rx, float* g_vertices) {
+  fpt_status st = check_scene_batch(ctx, s, bc);
+  if (st != FPT_OK) return st;
+  if (steps < 0 || steps > kUnrolledMaxSteps)
+    return fail(ctx, FPT_EINVAL, "steps must be in [0, %d]", kUnrolledMaxSteps);
+  if (fp_iters < 1 || fp_iters > kUnrolledMaxRounds) return fail(ctx, FPT_EINVAL, "fp_iters must be in [1, %d]",
+                                                                 kUnrolledMaxRounds);
+  fpt_batch* b = const_cast<fpt_batch*>(bc);
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  st = ensure_buckets(ctx, b, scene_dev(s));
+  if (st != FPT_OK) return st;
+  st = ensure_gacc(ctx, s);
+  if (st != FPT_OK) return st;
+  const SceneDev S = scene_dev(s);
+  for (int n = 1; n <= kMaxOrder; ++n) {
+    const PathRec* list;
+    const uint64_t cnt = order_slice(b, n, &list);
+    if (!cnt) continue;
+    // tape for every resident thread (at most 8 CTAs of kThreads per SM), within kUnrolledMaxTape bytes
+    uint64_t threads = ((cnt + kThreads - 1) / kThreads) * kThreads;
+    const uint64_t resident = (uint64_t)ctx->n_sm * 8 * kThreads;
+    if (threads > resident) threads = resident;
+    size_t need = unrolled_tape_floats(n, steps, threads);
+    if (need * sizeof(float) > kUnrolledMaxTape) need = kUnrolledMaxTape / sizeof(float);
+    if (need > ctx->tape_cap) {
+      cudaFree(ctx->d_tape);
+      ctx->d_tape = nullptr;
+      ctx->tape_cap = 0;
+      CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_tape, need * sizeof(float)));
+      ctx->tape_cap = need;
+    }
+    ProfScope ps(ctx, FPT_K_BACKWARD);
+    CUDA_OR_FAIL(ctx, launch_unrolled(n, S, b->dev, steps, fp_iters, cnt, list, dX, dL, ctx->d_gacc, ctx->d_tape,
+                                      ctx->tape_cap, T_out, status_out, ctx->stream, ctx->n_sm));
   }
   {
     ProfScope ps(ctx, FPT_K_OTHER);

@@ -101,6 +101,16 @@ cudaError_t launch_backward_rescue(int n, const SceneDev& S, const BatchDev& B, 
                                    uint64_t n_local, const PathRec* list, const float* T, const uint8_t* status,
                                    const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm,
                                    const uint32_t* rescue_list, const unsigned* rescue_count);
+// Gradient by reverse-mode differentiation through `steps` unified solver steps
+// (Sec. IV-B's comparison): one path per thread, its per-step state on a tape
+// of at most tape_floats floats (fewer resident threads when it is short).
+constexpr int kUnrolledMaxRounds = 64;
+constexpr int kUnrolledMaxSteps = 4096;
+constexpr size_t kUnrolledMaxTape = size_t(16) << 30;  // bytes
+size_t unrolled_tape_floats(int n, int steps, uint64_t threads);
+cudaError_t launch_unrolled(int n, const SceneDev& S, const BatchDev& B, int steps, int rounds, uint64_t n_local,
+                            const PathRec* list, const float* dX, const float* dL, double* gacc, float* tape,
+                            size_t tape_floats, float* T_out, uint8_t* status, cudaStream_t stream, int n_sm);
 cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
                                      float* g_rx, float* g_vertices, cudaStream_t stream);
 

@@ -73,6 +73,7 @@ _SIGS = {
                                  _vp, _vp, _vp, _vp]),
     "fpt_count_status": (C.c_int, [_vp, _vp, C.c_uint64, C.c_uint8, C.POINTER(C.c_uint64)]),
     "fpt_backward_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint8, _vp, _vp, _vp]),
+    "fpt_backward_unrolled": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fpt_tc_gemm_bf16": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
     "fpt_mlp_create": (C.c_int, [_vp, C.c_uint64, C.c_float, C.POINTER(_vp)]),
     "fpt_mlp_free": (None, [_vp]),
@@ -402,6 +403,32 @@ def backward_noalloc(ctx: Context, scene: Scene, batch: Batch, T, status=None, d
                                                       _ptr(dX), _ptr(dL), int(dL_status_mask), _ptr(g_tx),
                                                       _ptr(g_rx), _ptr(g_v)))
     return g_tx, g_rx, g_v
+
+
+def backward_unrolled(ctx: Context, scene: Scene, batch: Batch, steps: int, fp_iters: int = 1, dX=None, dL=None,
+                      want_T: bool = False, out=None):
+    """fpt_backward_unrolled: gradient through `steps` solver steps by reverse mode.
+
+    Returns (g_tx, g_rx, g_vertices, T, status); T [N, n_max, 2] (the last
+    iterate) only with want_T, status [N] always.
+    """
+    import torch
+
+    _need_cuda(dX, torch.float32, "dX")
+    _need_cuda(dL, torch.float32, "dL")
+    dev = f"cuda:{ctx.device}"
+    if out is None:
+        out = (torch.empty((scene.n_tx, 3), dtype=torch.float32, device=dev),
+               torch.empty((scene.n_rx, 3), dtype=torch.float32, device=dev),
+               torch.empty((scene.n_obj, 3, 3), dtype=torch.float32, device=dev))
+    g_tx, g_rx, g_v = out
+    N = batch.n_paths
+    T = torch.zeros((N, batch.n_max, 2), dtype=torch.float32, device=dev) if want_T else None
+    status = torch.zeros(N, dtype=torch.uint8, device=dev)
+    _check(ctx.handle, library().fpt_backward_unrolled(ctx.handle, scene.handle, batch.handle, int(steps),
+                                                       int(fp_iters), _ptr(dX), _ptr(dL), _ptr(T), _ptr(status),
+                                                       _ptr(g_tx), _ptr(g_rx), _ptr(g_v)))
+    return g_tx, g_rx, g_v, T, status
 
 
 def profile_enable(ctx: Context, on: bool = True):
