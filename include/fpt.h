@@ -153,7 +153,7 @@ fpt_status fpt_set_endpoints(fpt_scene* scene, const double* tx, int32_t n_tx, c
  *   seed + 0x9E3779B97F4A7C15 * (8 g + s + 1).
  * Explicit: caller-owned device arrays ids [n][n_max] (object ids),
  *   order [n], tx_idx [n], rx_idx [n].
- * FPT_EINVAL on lo < 1, hi > 5, lo > hi, empty alphabet or ids out of range
+ * FPT_EINVAL on lo < 1, hi > 10, lo > hi, empty alphabet or ids out of range
  * (host-checked arrays only).  A batch records the object types of the
  * scene it was built for; calls that pass a scene with other types return
  * FPT_EINVAL.  Seeded and explicit batches are bucketed on the device by
@@ -174,7 +174,10 @@ fpt_status fpt_enumerate(fpt_ctx* ctx, const fpt_batch* batch, int32_t* ids_out,
                          int32_t* tx_idx_out, int32_t* rx_idx_out);
 
 /* Solve every path of the batch (Sec. III-C): plain init t = 1/2, BFGS with
- * Eq. 6 step sizes in FP32, then up to `polish` Newton steps whose gradient
+ * Eq. 6 step sizes in FP32 (sequences of order 6-10, whose dense inverse-
+ * Hessian estimate would not fit a thread's registers: Newton steps on the
+ * exact block-tridiagonal Hessian with the same Eq. 6 step sizes and stop
+ * rules; `specialize` applies to orders 1-5), then up to `polish` Newton steps whose gradient
  * is formed in extended precision and whose block-tridiagonal Hessian system
  * is solved in FP32 (FP64 when ill-conditioned), then the validity test and
  * the stationarity residual rho = max_i |A_i delta_i| of the Newton step at

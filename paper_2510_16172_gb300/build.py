@@ -53,7 +53,10 @@ def _units() -> list[tuple[str, str, list[str]]]:
     units = []
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         base = os.path.basename(src)[:-3]
-        if base == "k_bfgs_pat":
+        if base == "k_high":
+            for n in range(6, 11):
+                units.append((src, os.path.join(OUT, f"{base}_o{n}.o"), [f"-DFPT_HIGH_ORDER={n}"]))
+        elif base == "k_bfgs_pat":
             for n, q0, qn in _pattern_ranges():
                 units.append((src, os.path.join(OUT, f"{base}_o{n}_q{q0}.o"),
                               [f"-DFPT_BFGS_ORDER={n}", f"-DFPT_BFGS_Q0={q0}u", f"-DFPT_BFGS_QN={qn}u"]))

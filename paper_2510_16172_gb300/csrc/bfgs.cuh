@@ -45,8 +45,9 @@ struct Pat {
   static constexpr __host__ __device__ bool quad(int i) { return ((Q >> i) & 1u) != 0u; }
   static constexpr __host__ __device__ int dim(int i) { return quad(i) ? 2 : 1; }
   static constexpr __host__ __device__ int off(int i) {
-    return i + (i > 0 && quad(0)) + (i > 1 && quad(1)) + (i > 2 && quad(2)) + (i > 3 && quad(3)) +
-           (i > 4 && quad(4));
+    int o = 0;
+    for (int k = 0; k < i; ++k) o += dim(k);
+    return o;
   }
   static constexpr int M = off(N);
   static constexpr int HP = M * (M + 1) / 2;
@@ -379,8 +380,10 @@ __device__ __forceinline__ void path_finish(const PathState<N, Q>& P, int n_max,
                                             uint8_t* __restrict__ status_out, uint8_t* __restrict__ iters_out) {
   float2* To = reinterpret_cast<float2*>(T_out) + P.gidx * (uint64_t)n_max;
 #pragma unroll
-  for (int i = 0; i < kMaxOrder; ++i)
+  for (int i = 0; i < kMaxBfgsOrder; ++i)
     if (i < n_max) To[i] = i < N ? make_float2(P.t[i][0], P.t[i][1]) : make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int i = kMaxBfgsOrder; i < n_max; ++i) To[i] = make_float2(0.f, 0.f);  // batches with longer sequences
   status_out[P.gidx] = P.st | (P.conv ? ST_CONVERGED : 0);
   if (iters_out) iters_out[P.gidx] = (uint8_t)(P.it > 255 ? 255 : P.it);
 }

@@ -44,6 +44,7 @@ struct fpt_ctx {
   uint32_t* d_rescue = nullptr;            // path lists: FP64 polish, FP64 adjoint, second polish pass
   float* d_step = nullptr;                 // first Newton steps of the second polish pass's paths
   size_t rescue_cap = 0;
+  size_t step_cap = 0;                     // floats of d_step
   unsigned* d_rescue_n = nullptr;
   fpt_mlp* init_mlp = nullptr;             // network for init_mode = 1
   char msg[512] = "ok";
@@ -215,7 +216,8 @@ fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, 64 * sizeof(unsigned long long));
+  static_assert(kPatternKeys <= 128, "pattern counters");
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_count, 128 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_work, 64 * sizeof(unsigned long long));
   for (int k = 0; k < fpt_ctx::kSide && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking);
@@ -591,7 +593,7 @@ static fpt_status ensure_buckets(fpt_ctx* ctx, fpt_batch* b, const SceneDev& S) 
   for (int n = 1; n <= kMaxOrder; ++n) {
     for (int pass = 0; pass < 2; ++pass) {
       if (pass == 1) b->small_start[n] = acc;
-      for (unsigned q = 0; q < (1u << n); ++q) {
+      for (unsigned q = 0; q < (unsigned)n_patterns(n); ++q) {
         const int k = pattern_key(n, q);
         if ((h[k] >= min_bucket) != (pass == 0)) continue;
         b->start[k] = acc;
@@ -611,17 +613,24 @@ static fpt_status ensure_buckets(fpt_ctx* ctx, fpt_batch* b, const SceneDev& S) 
   return FPT_OK;
 }
 
-// Polish scratch: one uint32 per path of the largest order slice.
-static fpt_status ensure_rescue(fpt_ctx* ctx, uint64_t n) {
-  if (n <= ctx->rescue_cap) return FPT_OK;
-  cudaFree(ctx->d_rescue);
-  ctx->d_rescue = nullptr;
-  ctx->rescue_cap = 0;
-  CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_rescue, 3 * n * sizeof(uint32_t)));
-  cudaFree(ctx->d_step);
-  ctx->d_step = nullptr;
-  CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_step, (size_t)2 * kMaxOrder * n * sizeof(float)));
-  ctx->rescue_cap = n;
+// Polish scratch for an order slice of n paths of order `order`: three uint32
+// lists of n entries and the first Newton steps (2 order floats per path).
+static fpt_status ensure_rescue(fpt_ctx* ctx, uint64_t n, int order) {
+  if (n > ctx->rescue_cap) {
+    cudaFree(ctx->d_rescue);
+    ctx->d_rescue = nullptr;
+    ctx->rescue_cap = 0;
+    CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_rescue, 3 * n * sizeof(uint32_t)));
+    ctx->rescue_cap = n;
+  }
+  const size_t step = (size_t)2 * order * n;
+  if (step > ctx->step_cap) {
+    cudaFree(ctx->d_step);
+    ctx->d_step = nullptr;
+    ctx->step_cap = 0;
+    CUDA_OR_FAIL(ctx, cudaMalloc(&ctx->d_step, step * sizeof(float)));
+    ctx->step_cap = step;
+  }
   return FPT_OK;
 }
 
@@ -634,7 +643,7 @@ static uint64_t order_slice(const fpt_batch* b, int n, const PathRec** list) {
   }
   // the buckets of order n are contiguous; the order's range starts at its first bucket in the layout
   uint64_t first = b->small_start[n], c = 0;
-  for (unsigned q = 0; q < (1u << n); ++q) {
+  for (unsigned q = 0; q < (unsigned)n_patterns(n); ++q) {
     const int k = pattern_key(n, q);
     c += b->count[k];
     if (b->count[k] && b->start[k] < first) first = b->start[k];
@@ -715,7 +724,7 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
       // an exhaustive order with a small pattern runs the unified kernel throughout.
       const bool listed = b->dev.mode != BATCH_EXHAUSTIVE;
       const bool force = p.specialize == 2;
-      bool by_pattern = p.specialize && sc.refill > 0;
+      bool by_pattern = p.specialize && sc.refill > 0 && n <= kMaxBfgsOrder;
       for (unsigned q = 0; by_pattern && !listed && !force && q < (1u << n); ++q) {
         const PathRec* qlist;
         const uint64_t qcnt = pattern_slice(b, n, q, &qlist);
@@ -751,7 +760,7 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
                                       ctx->d_work));
       }
     }
-    st = ensure_rescue(ctx, cnt);
+    st = ensure_rescue(ctx, cnt, n);
     if (st != FPT_OK) return st;
     {
       ProfScope ps(ctx, FPT_K_POLISH);
@@ -843,7 +852,7 @@ fpt_status fpt_validity(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
     if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
-    st = ensure_rescue(ctx, cnt);
+    st = ensure_rescue(ctx, cnt, n);
     if (st != FPT_OK) return st;
     ProfScope ps(ctx, FPT_K_POLISH);
     CUDA_OR_FAIL(ctx, launch_polish(n, S, b->dev, pc, cnt, list, const_cast<float*>(T), nullptr, nullptr, nullptr, rho,
@@ -874,7 +883,7 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
     uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
     if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
-    st = ensure_rescue(ctx, cnt);
+    st = ensure_rescue(ctx, cnt, n);
     if (st != FPT_OK) return st;
     ProfScope ps(ctx, FPT_K_BACKWARD);
     CUDA_OR_FAIL(ctx, launch_backward(n, S, b->dev, bc_cfg, cnt, list, T, status, dX, dL, ctx->d_gacc, ctx->stream,
@@ -903,7 +912,12 @@ fpt_status fpt_backward_unrolled(fpt_ctx* ctx, const fpt_scene* s, const fpt_bat
   st = ensure_gacc(ctx, s);
   if (st != FPT_OK) return st;
   const SceneDev S = scene_dev(s);
-  for (int n = 1; n <= kMaxOrder; ++n) {
+  for (int n = kMaxBfgsOrder + 1; n <= kMaxOrder; ++n) {
+    const PathRec* list;
+    if (order_slice(b, n, &list))
+      return fail(ctx, FPT_EUNSUPPORTED, "fpt_backward_unrolled runs the BFGS solver: orders up to %d", kMaxBfgsOrder);
+  }
+  for (int n = 1; n <= kMaxBfgsOrder; ++n) {
     const PathRec* list;
     const uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;

@@ -10,7 +10,8 @@
 
 namespace fpt {
 
-constexpr int kMaxOrder = 5;        // longest sequence solved on the GPU
+constexpr int kMaxOrder = 10;       // longest sequence solved on the GPU
+constexpr int kMaxBfgsOrder = 5;    // longest sequence solved by the register-resident BFGS kernels
 constexpr int kRec32 = 12;          // floats per FP32 object record: b_hi[3], b_lo[3], a1[3], a2[3]
 constexpr int kRec64 = 9;           // doubles per FP64 object record: b[3], a1[3], a2[3]
 constexpr int kAux = 4;             // floats per object: side heights h1, h2 (metres), type, pad
@@ -63,10 +64,14 @@ struct BatchDev {
 
 // Interaction-type pattern of a sequence of order n: bit i set = slot i is a
 // planar reflector, clear = an edge.  Seeded and explicit batches are bucketed
-// by (order, pattern); key(n, Q) = 2^n - 2 + Q orders the buckets by order
-// first, so the buckets of one order form one contiguous range.
-constexpr int kPatternKeys = (2 << kMaxOrder) - 2;  // 62 for orders 1..5
-__host__ __device__ constexpr int pattern_key(int n, unsigned q) { return (1 << n) - 2 + (int)q; }
+// by (order, pattern) up to the BFGS orders, key(n, Q) = 2^n - 2 + Q, and by
+// order alone above them (one bucket, Q = 0); keys follow the orders, so the
+// buckets of one order form one contiguous range.
+constexpr int kPatternKeys = (2 << kMaxBfgsOrder) - 2 + (kMaxOrder - kMaxBfgsOrder);  // 62 + 5
+__host__ __device__ constexpr int n_patterns(int n) { return n <= kMaxBfgsOrder ? 1 << n : 1; }
+__host__ __device__ constexpr int pattern_key(int n, unsigned q) {
+  return n <= kMaxBfgsOrder ? (1 << n) - 2 + (int)q : (2 << kMaxBfgsOrder) - 2 + (n - kMaxBfgsOrder - 1);
+}
 
 // One candidate sequence, decoded.
 struct PathDesc {
@@ -80,7 +85,9 @@ struct PathDesc {
 // A path of a seeded or explicit batch, decoded once when the batch is bucketed
 // (32 bytes, two 16-byte loads): words 0-1 g, 2 tx, 3 rx, 4-5 ids[0..3] as
 // 16-bit pairs, 6 ids[4] | n << 16 | flags << 24, 7 unused.  Object ids fit in
-// 16 bits (a scene holds at most 65535 objects).
+// 16 bits (a scene holds at most 65535 objects).  Records of sequences longer
+// than kMaxBfgsOrder keep g, tx, rx, n and flags; their kernels decode the
+// ids from g again (decode_global).
 struct __align__(16) PathRec {
   uint32_t w[8];
 };
@@ -101,9 +108,9 @@ __device__ __forceinline__ void load_rec(const PathRec* list, uint64_t j, PathDe
 }
 
 __device__ __forceinline__ void store_rec(PathRec* list, uint64_t slot, const PathDesc& d) {
-  uint32_t id[kMaxOrder];
+  uint32_t id[kMaxBfgsOrder];
 #pragma unroll
-  for (int i = 0; i < kMaxOrder; ++i) id[i] = i < d.n ? (uint32_t)d.ids[i] & 0xFFFFu : 0u;
+  for (int i = 0; i < kMaxBfgsOrder; ++i) id[i] = i < d.n && d.n <= kMaxBfgsOrder ? (uint32_t)d.ids[i] & 0xFFFFu : 0u;
   uint4* p = reinterpret_cast<uint4*>(list + slot);
   p[0] = make_uint4((uint32_t)d.g, (uint32_t)(d.g >> 32), (uint32_t)d.tx, (uint32_t)d.rx);
   p[1] = make_uint4(id[0] | (id[1] << 16), id[2] | (id[3] << 16),
@@ -229,20 +236,24 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
 // batches pass their bucket of decoded path records.
 __device__ __forceinline__ void fetch_path(const BatchDev& B, int n, const PathRec* list, uint64_t j,
                                            PathDesc& d) {
-  if (list == nullptr)
+  if (list == nullptr) {
     decode_exhaustive_order(B, n, j, d);
-  else
+  } else {
     load_rec(list, j, d);
+    if (n > kMaxBfgsOrder) decode_global(B, d.g, d);
+  }
 }
 
 // Path source of a kernel compiled for order N: the bucket of records, else the
 // exhaustive enumeration of order N (both keep the descriptor in registers).
 template <int N>
 __device__ __forceinline__ void fetch_path_n(const BatchDev& B, const PathRec* list, uint64_t j, PathDesc& d) {
-  if (list != nullptr)
+  if (list != nullptr) {
     load_rec(list, j, d);
-  else
+    if constexpr (N > kMaxBfgsOrder) decode_global(B, d.g, d);
+  } else {
     decode_exhaustive_order(B, N, j, d);
+  }
 }
 
 // Stage `count` elements of T from global to shared memory (whole CTA).

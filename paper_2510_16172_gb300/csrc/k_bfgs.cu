@@ -1,9 +1,17 @@
-// k_bfgs.cu -- BFGS launch dispatch and the unified kernels of every order.
-// The interaction-type pattern kernels are instantiated in k_bfgs_pat.cu,
-// compiled once per entry of FPT_BFGS_RANGES.
+// k_bfgs.cu -- solver launch dispatch and the unified BFGS kernels of every BFGS
+// order.  The interaction-type pattern kernels are instantiated in
+// k_bfgs_pat.cu, compiled once per entry of FPT_BFGS_RANGES; the Newton
+// kernels of the longer sequences in k_high.cu, once per order.
 #include "bfgs.cuh"
+#include "newton.cuh"
 
 namespace fpt {
+
+extern template struct NewtonOrder<6>;
+extern template struct NewtonOrder<7>;
+extern template struct NewtonOrder<8>;
+extern template struct NewtonOrder<9>;
+extern template struct NewtonOrder<10>;
 
 #define FPT_BFGS_EXTERN(n, q0, qn) extern template cudaError_t launch_bfgs_range<n, q0, qn>(unsigned, const BfgsLaunch&);
 FPT_BFGS_RANGES(FPT_BFGS_EXTERN)
@@ -19,6 +27,14 @@ cudaError_t launch_bfgs(int n, int pattern, const SceneDev& S, const BatchDev& B
                         uint64_t n_local, const PathRec* list, float* T, uint8_t* status, uint8_t* iters,
                         cudaStream_t stream, int n_sm, unsigned long long* work) {
   const BfgsLaunch a{S, B, cfg, n_local, list, T, status, iters, stream, n_sm, work};
+  switch (n) {  // longer sequences: the Newton solver (newton.cuh), one kernel per order
+    case 6: return NewtonOrder<6>::launch(a);
+    case 7: return NewtonOrder<7>::launch(a);
+    case 8: return NewtonOrder<8>::launch(a);
+    case 9: return NewtonOrder<9>::launch(a);
+    case 10: return NewtonOrder<10>::launch(a);
+    default: break;
+  }
   if (pattern < 0) {
     switch (n) {
       case 1: return launch_unified<1>(a);

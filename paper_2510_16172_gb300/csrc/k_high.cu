@@ -1,0 +1,20 @@
+// k_high.cu -- the per-order kernels of one sequence order above the BFGS
+// orders: Newton solver, polish and backward of order FPT_HIGH_ORDER.  The
+// build compiles this file once per order 6..10, in parallel.
+#include "backward.cuh"
+#include "newton.cuh"
+#include "polish.cuh"
+
+#if !defined(FPT_HIGH_ORDER)
+#error "k_high.cu is compiled once per order: define FPT_HIGH_ORDER"
+#endif
+
+namespace fpt {
+
+static_assert(FPT_HIGH_ORDER > kMaxBfgsOrder && FPT_HIGH_ORDER <= kMaxOrder, "order outside the Newton orders");
+
+template struct NewtonOrder<FPT_HIGH_ORDER>;
+template struct PolishOrder<FPT_HIGH_ORDER>;
+template struct BackwardOrder<FPT_HIGH_ORDER>;
+
+}  // namespace fpt

@@ -579,3 +579,66 @@ def test_seeded_sampler_properties(oracle_lib):
         assert np.all(seq[1:] != seq[:-1])
     again = oracle_lib.seeded_paths(sc, 1234, 50, 1, 5)
     assert np.array_equal(again[0], ids[:50])
+
+
+# ---------------------------------------------------------------------------
+# sequences of order 6-10 (the orders of the paper's Fig. 3 above 5)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [6, 8, 10])
+def test_hall_of_mirrors_image_method(oracle_lib, n):
+    """Two facing mirrors (planes z = 0 and z = h, tilted bases), n alternating reflections: the image
+    method unfolds the path into the straight line from TX to the n-fold mirrored RX."""
+    rng = np.random.default_rng(100 + n)
+    for _ in range(5):
+        h = rng.uniform(2.0, 4.0)
+        lo = np.array([[-1.0, -2.0, 0.0], [3.0, -1.0, 0.0], [-2.0, 4.0, 0.0]])  # v0, v1, v3 in z = 0
+        hi = lo + np.array([0.0, 0.0, h])
+        tx = np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.2, 0.8) * h])
+        rx = np.array([rng.uniform(2, 6), rng.uniform(-3, 3), rng.uniform(0.2, 0.8) * h])
+        first = int(rng.integers(0, 2))  # 0: start at the floor
+        seq = [(first + i) % 2 for i in range(n)]
+        objs = [(scenes.QUAD, lo if s == 0 else hi) for s in seq]
+        path = make_path(oracle_lib, objs, tx, rx)
+        X, t, st, rho = solve_points(oracle_lib, path)
+        # mirror RX through the planes in reverse order: the last reflection is applied first
+        img = rx.copy()
+        for s in reversed(seq):
+            b, nrm = plane_of(lo if s == 0 else hi)
+            img = mirror(img, b, nrm)
+        L = np.linalg.norm(img - tx)
+        pts = np.vstack([tx, X, rx])
+        assert abs(np.linalg.norm(np.diff(pts, axis=0), axis=1).sum() - L) < 1e-9 * L
+        # each point is where the unfolded line crosses its plane, mapped back
+        p, img_k = tx, img
+        for i, s in enumerate(seq):
+            b, nrm = plane_of(lo if s == 0 else hi)
+            x, _ = cross_plane(p, img_k, b, nrm)
+            assert np.linalg.norm(x - X[i]) < 1e-8
+            # reflect the remaining image back across this plane and continue from x
+            img_k = mirror(img_k, b, nrm)
+            p = x
+
+
+def test_stationarity_law_at_orders_6_to_10(oracle_lib):
+    """Reflection and Keller's laws at every point of the regular order-6..10 solutions of tiny scenes."""
+    for seed in range(3):
+        sc = scenes.tiny_scene(seed)
+        ids, order, ti, ri = oracle_lib.seeded_paths(sc, 31 + seed, 1500, 6, 10)
+        out = oracle_lib.solve(sc, ids, order, ti, ri)
+        ok = usable(oracle_lib, out["status"])
+        assert ok.sum() > 50 and set(order[ok]) >= {6, 7, 8}
+        for p in np.nonzero(ok)[0]:
+            n = order[p]
+            pts = np.vstack([sc.tx[ti[p]], out["X"][p, :n], sc.rx[ri[p]]])
+            z = np.diff(pts, axis=0)
+            u = z / np.linalg.norm(z, axis=1, keepdims=True)
+            for i in range(n):
+                d = u[i] - u[i + 1]
+                o = ids[p, i]
+                v = sc.verts[o]
+                if sc.types[o] == scenes.QUAD:
+                    _, nrm = plane_of(v)
+                    assert np.linalg.norm(d - np.dot(d, nrm) * nrm) < 1e-9
+                else:
+                    e = (v[1] - v[0]) / np.linalg.norm(v[1] - v[0])
+                    assert abs(np.dot(d, e)) < 1e-9
