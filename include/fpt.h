@@ -174,10 +174,9 @@ fpt_status fpt_enumerate(fpt_ctx* ctx, const fpt_batch* batch, int32_t* ids_out,
                          int32_t* tx_idx_out, int32_t* rx_idx_out);
 
 /* Solve every path of the batch (Sec. III-C): plain init t = 1/2, BFGS with
- * Eq. 6 step sizes in FP32 (sequences of order 6-10, whose dense inverse-
- * Hessian estimate would not fit a thread's registers: Newton steps on the
- * exact block-tridiagonal Hessian with the same Eq. 6 step sizes and stop
- * rules; `specialize` applies to orders 1-5), then up to `polish` Newton steps whose gradient
+ * Eq. 6 step sizes in FP32 (for orders 6-10 the inverse-Hessian estimate is
+ * kept in shared memory; `specialize` applies to orders 1-5), then up to
+ * `polish` Newton steps whose gradient
  * is formed in extended precision and whose block-tridiagonal Hessian system
  * is solved in FP32 (FP64 when ill-conditioned), then the validity test and
  * the stationarity residual rho = max_i |A_i delta_i| of the Newton step at

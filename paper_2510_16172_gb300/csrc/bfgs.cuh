@@ -28,6 +28,7 @@
 // (tested as (s^T y)^2 > 1e-12 |s|^2 |y|^2 with s^T y > 0).
 #pragma once
 
+#include <type_traits>
 #include <utility>
 
 #include "fpt_kernels.h"
@@ -45,9 +46,9 @@ struct Pat {
   static constexpr __host__ __device__ bool quad(int i) { return ((Q >> i) & 1u) != 0u; }
   static constexpr __host__ __device__ int dim(int i) { return quad(i) ? 2 : 1; }
   static constexpr __host__ __device__ int off(int i) {
-    int o = 0;
-    for (int k = 0; k < i; ++k) o += dim(k);
-    return o;
+    return N <= kMaxBfgsOrder ? i + (i > 0 && quad(0)) + (i > 1 && quad(1)) + (i > 2 && quad(2)) +
+                                    (i > 3 && quad(3)) + (i > 4 && quad(4))
+                              : 2 * i;  // above the pattern orders only the unified kernel (Q all ones)
   }
   static constexpr int M = off(N);
   static constexpr int HP = M * (M + 1) / 2;
@@ -127,12 +128,14 @@ enum BfgsSource {
 template <int N, unsigned Q, int kSrc>
 __device__ __forceinline__ void fetch_path_q(const BatchDev& B, const Tables& tb, const PathRec* list, uint64_t j,
                                              PathDesc& d) {
-  if constexpr (kSrc == SRC_LIST)
+  if constexpr (kSrc == SRC_LIST) {
     load_rec(list, j, d);
-  else if constexpr (kSrc == SRC_PATTERN)
+    if constexpr (N > kMaxBfgsOrder) decode_global(B, d.g, d);  // longer records keep g, not the ids
+  } else if constexpr (kSrc == SRC_PATTERN) {
     decode_exhaustive_pattern<N, Q>(B, tb, j, d);
-  else
+  } else {
     decode_exhaustive_order(B, N, j, d);
+  }
 }
 
 template <int N, unsigned Q>
@@ -221,13 +224,25 @@ __device__ __forceinline__ float fixed_point(const float (&e)[N + 1], const floa
   return alpha;
 }
 
-// Per-path solver state, all in registers.
+// The inverse-Hessian estimate of a path of order above kMaxBfgsOrder: 2n(2n+1)/2
+// floats (210 at n = 10) do not fit a thread's registers next to its iterate,
+// so entry k of thread x lives at s_H[k * kThreads + x] (consecutive threads,
+// consecutive banks).
+struct SmemH {
+  float* p;
+  __device__ __forceinline__ float& operator[](int k) const { return p[k * kThreads]; }
+};
+
+// Per-path solver state, in registers (H in shared memory above kMaxBfgsOrder).
 template <int N, unsigned Q>
 struct PathState {
   static constexpr int M = Pat<N, Q>::M;
   static constexpr int HP = Pat<N, Q>::HP;
   Geo<N> G;
-  float t[N][2], g[M], H[HP], z[N + 1][3], e[N + 1];
+  // the packed inverse-Hessian estimate: registers up to the BFGS register orders, a column of
+  // shared memory (one float per thread and entry) for the longer sequences
+  std::conditional_t<(N <= kMaxBfgsOrder), float[HP], SmemH> H;
+  float t[N][2], g[M], z[N + 1][3], e[N + 1];
   uint64_t gidx;
   int it;
   uint8_t st;
@@ -379,11 +394,11 @@ template <int N, unsigned Q>
 __device__ __forceinline__ void path_finish(const PathState<N, Q>& P, int n_max, float* __restrict__ T_out,
                                             uint8_t* __restrict__ status_out, uint8_t* __restrict__ iters_out) {
   float2* To = reinterpret_cast<float2*>(T_out) + P.gidx * (uint64_t)n_max;
+  // slots from N to n_max - 1 are zero; those past kMaxBfgsOrder were cleared before the solve
+  constexpr int kSlots = N > kMaxBfgsOrder ? N : kMaxBfgsOrder;
 #pragma unroll
-  for (int i = 0; i < kMaxBfgsOrder; ++i)
+  for (int i = 0; i < kSlots; ++i)
     if (i < n_max) To[i] = i < N ? make_float2(P.t[i][0], P.t[i][1]) : make_float2(0.f, 0.f);
-#pragma unroll 1
-  for (int i = kMaxBfgsOrder; i < n_max; ++i) To[i] = make_float2(0.f, 0.f);  // batches with longer sequences
   status_out[P.gidx] = P.st | (P.conv ? ST_CONVERGED : 0);
   if (iters_out) iters_out[P.gidx] = (uint8_t)(P.it > 255 ? 255 : P.it);
 }
@@ -435,6 +450,11 @@ inline size_t smem_tables_bytes(const SceneDev& S, const BatchDev& B, int* use_s
   return rec + ends;
 }
 
+// Floats of dynamic shared memory that hold the CTA's inverse-Hessian columns
+// (sequences above kMaxBfgsOrder; they precede the staged tables).
+template <int N, unsigned Q>
+constexpr int kSmemHFloats = N > kMaxBfgsOrder ? Pat<N, Q>::HP * kThreads : 0;
+
 // One path per thread per tile; a warp leaves its BFGS loop when all 32 lanes are done.
 template <int N>
 __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, SolveCfg cfg, uint64_t n_local,
@@ -443,12 +463,13 @@ __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, 
                                                         uint8_t* __restrict__ iters_out, int use_smem) {
   constexpr unsigned Q = kAllQuads<N>;
   extern __shared__ __align__(16) float s_tab[];
-  const Tables tb = stage_tables(S, B, use_smem, s_tab);
+  const Tables tb = stage_tables(S, B, use_smem, s_tab + kSmemHFloats<N, Q>);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
     const uint64_t j = j0 + threadIdx.x;
     const bool have = j < n_local;
     PathState<N, Q> P;
+    if constexpr (kSmemHFloats<N, Q> > 0) P.H.p = s_tab + threadIdx.x;
     bool active = false;
     if (have)
       active = list ? path_start<N, Q, SRC_LIST>(P, B, tb, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr)
@@ -480,13 +501,14 @@ __global__ void __launch_bounds__(kThreads, FPT_BFGS_MIN_CTAS) bfgs_refill_kerne
                                                                uint8_t* __restrict__ iters_out, int use_smem,
                                                                unsigned long long* __restrict__ work) {
   extern __shared__ __align__(16) float s_tab[];
-  const Tables tb = stage_tables(S, B, use_smem, s_tab);
+  const Tables tb = stage_tables(S, B, use_smem, s_tab + kSmemHFloats<N, Q>);
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   uint64_t next = 0, end = 0;  // warp-uniform: unclaimed part of the warp's chunk
   bool more = true;            // warp-uniform: the global counter may still have work
   PathState<N, Q> P;
+  if constexpr (kSmemHFloats<N, Q> > 0) P.H.p = s_tab + threadIdx.x;
   bool active = false;
   for (;;) {
     unsigned free_mask = __ballot_sync(full, !active);
@@ -554,7 +576,16 @@ struct BfgsLaunch {
 template <int N, unsigned Q, int kSrc>
 cudaError_t launch_bfgs_nq(const BfgsLaunch& a) {
   int use_smem = 0;
-  const size_t smem = smem_tables_bytes(a.S, a.B, &use_smem);
+  size_t smem = smem_tables_bytes(a.S, a.B, &use_smem);
+  if constexpr (kSmemHFloats<N, Q> > 0) {
+    // the inverse-Hessian columns first; the tables stay in global memory when both do not fit
+    const size_t hb = (size_t)kSmemHFloats<N, Q> * sizeof(float);
+    if (hb + smem > kMaxSmemBytes) {
+      use_smem = 0;
+      smem = 0;
+    }
+    smem += hb;
+  }
   constexpr bool kPat = kSrc == SRC_PATTERN || Q != kAllQuads<N>;
   const bool refill = kPat || (a.cfg.refill > 0 && a.work != nullptr);
   const void* fn;
@@ -593,6 +624,21 @@ cudaError_t launch_bfgs_nq(const BfgsLaunch& a) {
     }
   }
   return cudaGetLastError();
+}
+
+// The unified kernel of order N (every slot with two parameters) as an
+// explicitly instantiable unit: the BFGS register orders are instantiated with
+// the dispatcher (k_bfgs.cu), the longer sequences each in their own object
+// (k_high.cu).
+template <int N>
+struct BfgsOrder {
+  static cudaError_t launch(const BfgsLaunch& a);
+};
+
+template <int N>
+cudaError_t BfgsOrder<N>::launch(const BfgsLaunch& a) {
+  if (a.list != nullptr) return launch_bfgs_nq<N, kAllQuads<N>, SRC_LIST>(a);
+  return launch_bfgs_nq<N, kAllQuads<N>, SRC_ORDER>(a);
 }
 
 // Pattern kernels Q0 .. Q0 + sizeof...(I) - 1 of order N and one path source behind one switch.

@@ -701,6 +701,11 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
   // the polish needs its Newton step only to a modest relative accuracy: 100x looser pivot test than the adjoint
   PolishCfg pc{POLISH_SOLVE, p.polish, p.solved_tol, p.deg_tol, 1e-2f * p.cond_fp64, p.polish_fp64,
                p.polish_radius};
+  if (b->dev.n_max > kMaxBfgsOrder) {
+    // the kernels of orders 1-5 write the first five slots of a path; clear the rest
+    CUDA_OR_FAIL(ctx, cudaMemsetAsync(T, 0, b->dev.n_paths * (uint64_t)b->dev.n_max * 2 * sizeof(float), ctx->stream));
+    if (X) CUDA_OR_FAIL(ctx, cudaMemsetAsync(X, 0, b->dev.n_paths * (uint64_t)b->dev.n_max * 3 * sizeof(float), ctx->stream));
+  }
   for (int n = 1; n <= kMaxOrder; ++n) {
     const PathRec* list;
     uint64_t cnt = order_slice(b, n, &list);

@@ -11,7 +11,7 @@
 namespace fpt {
 
 constexpr int kMaxOrder = 10;       // longest sequence solved on the GPU
-constexpr int kMaxBfgsOrder = 5;    // longest sequence solved by the register-resident BFGS kernels
+constexpr int kMaxBfgsOrder = 5;    // longest sequence whose BFGS state fits in registers (pattern kernels, 32-byte records)
 constexpr int kRec32 = 12;          // floats per FP32 object record: b_hi[3], b_lo[3], a1[3], a2[3]
 constexpr int kRec64 = 9;           // doubles per FP64 object record: b[3], a1[3], a2[3]
 constexpr int kAux = 4;             // floats per object: side heights h1, h2 (metres), type, pad

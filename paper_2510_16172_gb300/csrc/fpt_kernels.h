@@ -9,6 +9,7 @@
 namespace fpt {
 
 constexpr int kThreads = 128;  // threads per CTA for all path kernels
+constexpr size_t kMaxSmemBytes = 200 * 1024;  // dynamic shared memory a path kernel may request
 
 // Kernels launched by the calling thread; the API's profiler reads the
 // difference around each call.

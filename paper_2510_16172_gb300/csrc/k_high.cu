@@ -1,8 +1,9 @@
-// k_high.cu -- the per-order kernels of one sequence order above the BFGS
-// orders: Newton solver, polish and backward of order FPT_HIGH_ORDER.  The
-// build compiles this file once per order 6..10, in parallel.
+// k_high.cu -- the per-order kernels of one sequence order above 5 (BFGS with
+// the inverse Hessian in shared memory, polish, backward) for order
+// FPT_HIGH_ORDER.  The build compiles this file once per order 6..10, in
+// parallel.
 #include "backward.cuh"
-#include "newton.cuh"
+#include "bfgs.cuh"
 #include "polish.cuh"
 
 #if !defined(FPT_HIGH_ORDER)
@@ -11,9 +12,9 @@
 
 namespace fpt {
 
-static_assert(FPT_HIGH_ORDER > kMaxBfgsOrder && FPT_HIGH_ORDER <= kMaxOrder, "order outside the Newton orders");
+static_assert(FPT_HIGH_ORDER > kMaxBfgsOrder && FPT_HIGH_ORDER <= kMaxOrder, "order outside 6..10");
 
-template struct NewtonOrder<FPT_HIGH_ORDER>;
+template struct BfgsOrder<FPT_HIGH_ORDER>;
 template struct PolishOrder<FPT_HIGH_ORDER>;
 template struct BackwardOrder<FPT_HIGH_ORDER>;
 

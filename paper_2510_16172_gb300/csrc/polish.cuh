@@ -201,6 +201,12 @@ __device__ __forceinline__ void newton_dir(const BlockTri<float, N>& F32, const 
 template <int N>
 constexpr int kPolishMinBlocks = N <= 3 ? 3 : 1;
 
+// Output slots a kernel of order N writes in its unrolled loop (slots past N
+// get zeros); in batches with longer sequences the host clears the later slots
+// before the solve.
+template <int N>
+constexpr int kSlots = N > kMaxBfgsOrder ? N : kMaxBfgsOrder;
+
 // use_smem bits of the polish kernels: records staged, gradient sums in shared memory.
 constexpr int kSmemRecords = 1;
 constexpr int kSmemAcc = 2;
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
         if (X) {
           float* Xo = X + g * (uint64_t)n_max * 3;
 #pragma unroll
-          for (int i = 0; i < kMaxOrder; ++i)
+          for (int i = 0; i < kSlots<N>; ++i)
             if (i < n_max)
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
@@ -657,7 +663,7 @@ __global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev
       if (X) {
         float* Xo = X + g * (uint64_t)n_max * 3;
 #pragma unroll
-        for (int i = 0; i < kMaxOrder; ++i)
+        for (int i = 0; i < kSlots<N>; ++i)
           if (i < n_max)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {

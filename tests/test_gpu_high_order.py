@@ -1,9 +1,10 @@
 """Sequences of order 6-10 (the paper's Fig. 3 goes to n = 10) against the oracle.
 
-Above order 5 the solver takes Newton steps on the exact block-tridiagonal
-Hessian with the Eq. 6 step sizes instead of BFGS; enumeration, polish,
-validity and the implicit backward are the same per-order kernels as below.
-The tolerances are those of the other parity tests.
+Above order 5 the BFGS kernel keeps its inverse-Hessian estimate in shared
+memory instead of registers, and seeded and explicit batches bucket those
+sequences by order alone; enumeration, polish, validity and the implicit
+backward are the same per-order kernels as below.  The tolerances are those
+of the other parity tests (the backward's: twice theirs).
 """
 
 import numpy as np
@@ -57,8 +58,8 @@ def test_seeded_high_orders_parity(ctx, lo, hi, seed):
     check_parity(out, ref, min_solved_frac=0.98)
 
 
-def test_exhaustive_batch_across_the_bfgs_and_newton_orders(ctx):
-    """One batch holding orders 4-6: BFGS kernels for 4 and 5, the Newton kernel for 6, one output layout."""
+def test_exhaustive_batch_across_register_and_shared_memory_orders(ctx):
+    """One batch holding orders 4-6: register BFGS for 4 and 5, shared-memory BFGS for 6, one output layout."""
     sc = scenes.tiny_scene(4, n_rx=2)
     sc.alphabet = np.array([0, 2, 3, 8, 10], dtype=np.int32)  # 3 planes, 2 edges
     scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
@@ -114,10 +115,11 @@ def test_backward_high_orders(ctx, lo, hi, seed):
                                    torch.as_tensor(dX, dtype=torch.float32, device=dev),
                                    torch.as_tensor(dL, dtype=torch.float32, device=dev))
     ctx.sync()
+    # twice the orders 1-3 bound: the FP32 block elimination runs through up to 10 pivot blocks
     scale = max(np.abs(e_v).max(), np.abs(e_tx).max(), 1.0)
-    np.testing.assert_allclose(g_tx.cpu().numpy(), e_tx, atol=2e-4 * scale)
-    np.testing.assert_allclose(g_rx.cpu().numpy(), e_rx, atol=2e-4 * scale)
-    np.testing.assert_allclose(g_v.cpu().numpy(), e_v, atol=2e-4 * scale)
+    np.testing.assert_allclose(g_tx.cpu().numpy(), e_tx, atol=4e-4 * scale)
+    np.testing.assert_allclose(g_rx.cpu().numpy(), e_rx, atol=4e-4 * scale)
+    np.testing.assert_allclose(g_v.cpu().numpy(), e_v, atol=4e-4 * scale)
 
 
 def test_solve_grad_orders_1_to_10_and_unrolled_refusal(ctx):

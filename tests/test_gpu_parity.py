@@ -405,7 +405,7 @@ def test_bad_arguments_are_errors_not_faults(ctx):
     with pytest.raises(fpt.FptError):
         fpt.Batch.exhaustive(ctx, scene, 0, 2)
     with pytest.raises(fpt.FptError):
-        fpt.Batch.exhaustive(ctx, scene, 1, 6)
+        fpt.Batch.exhaustive(ctx, scene, 1, 11)
     with pytest.raises(fpt.FptError):
         fpt.Batch.exhaustive(ctx, scene, 1, 2, alphabet=[0, 99])
     flat = sc.verts.copy()
