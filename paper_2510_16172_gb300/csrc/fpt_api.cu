@@ -917,12 +917,7 @@ fpt_status fpt_backward_unrolled(fpt_ctx* ctx, const fpt_scene* s, const fpt_bat
   st = ensure_gacc(ctx, s);
   if (st != FPT_OK) return st;
   const SceneDev S = scene_dev(s);
-  for (int n = kMaxBfgsOrder + 1; n <= kMaxOrder; ++n) {
-    const PathRec* list;
-    if (order_slice(b, n, &list))
-      return fail(ctx, FPT_EUNSUPPORTED, "fpt_backward_unrolled runs the BFGS solver: orders up to %d", kMaxBfgsOrder);
-  }
-  for (int n = 1; n <= kMaxBfgsOrder; ++n) {
+  for (int n = 1; n <= kMaxOrder; ++n) {
     const PathRec* list;
     const uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;

@@ -38,12 +38,12 @@ def _dev(x):
     return torch.as_tensor(x, dtype=torch.float32, device="cuda:0")
 
 
-@pytest.mark.parametrize("fp", [1, 4])
-def test_forward_is_the_solver_at_a_fixed_step_count(ctx, fp):
+@pytest.mark.parametrize("fp,lo,hi", [(1, 1, 3), (4, 1, 3), (1, 6, 10)])
+def test_forward_is_the_solver_at_a_fixed_step_count(ctx, fp, lo, hi):
     """The taped forward takes the unified kernel's steps: the same iterates to the bit."""
     sc = scenes.tiny_scene(1, n_rx=2)
     scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
-    batch = fpt.Batch.exhaustive(ctx, scene, 1, 3)
+    batch = fpt.Batch.exhaustive(ctx, scene, lo, hi) if hi <= 3 else fpt.Batch.seeded(ctx, scene, 5, 3000, lo, hi)
     k = 12
     *_, T, st = fpt.backward_unrolled(ctx, scene, batch, k, fp, want_T=True)
     p = fpt.default_params(max_iters=k, fixed_iters=1, fp_iters=fp, polish=0, specialize=0, kink_stop=1e-30)
@@ -98,9 +98,10 @@ def _private_scene(sc, ids, order, ti, ri):
     return scenes.Scene(np.array(types), np.array(verts), np.array(tx), np.array(rx)), nids, idx, idx
 
 
-@pytest.mark.parametrize("k,fp,n_paths,min_frac,max_median", [(4, 1, 300, 0.97, 2e-5), (16, 1, 300, 0.7, 2e-4),
-                                                             (16, 4, 700, 0.7, 2e-4)])
-def test_per_path_gradients_against_the_fp64_autograd_reference(ctx, k, fp, n_paths, min_frac, max_median):
+@pytest.mark.parametrize("k,fp,n_paths,lo,hi,min_frac,max_median", [
+    (4, 1, 300, 1, 3, 0.97, 2e-5), (16, 1, 300, 1, 3, 0.7, 2e-4), (16, 4, 700, 1, 3, 0.7, 2e-4),
+    (4, 1, 200, 6, 8, 0.95, 2e-5), (8, 1, 200, 6, 8, 0.9, 2e-4), (4, 4, 200, 9, 10, 0.95, 2e-5)])
+def test_per_path_gradients_against_the_fp64_autograd_reference(ctx, k, fp, n_paths, lo, hi, min_frac, max_median):
     """Each path's gradient w.r.t. its own geometry against the FP64 reference through the same k steps.
 
     Differentiating BFGS through FP32 iterations is ill-conditioned once steps near the rounding
@@ -108,12 +109,17 @@ def test_per_path_gradients_against_the_fp64_autograd_reference(ctx, k, fp, n_pa
     reference departs from the FP64 one by more than 1e-3 of the gradient on about a fifth of
     these paths at k = 16 while most agree to 1e-5.  The test asks for that distribution: most
     paths within 1e-3 (relative to the path's largest gradient component, at least 1) and a small
-    median.  700 paths put the scene's accumulators in global memory, 300 in shared memory.
+    median.  700 paths put the scene's accumulators in global memory, 300 in shared memory; orders
+    6-10 keep the inverse Hessian and its adjoint in shared memory (a CPU FP32 run of the reference
+    is within 1e-3 on all of those paths).
     """
     import torch
 
     base = scenes.tiny_scene(5, n_rx=2)
-    ids, order, ti, ri = oracle.exhaustive_paths(base, 1, 3)
+    if hi <= 3:
+        ids, order, ti, ri = oracle.exhaustive_paths(base, lo, hi)
+    else:
+        ids, order, ti, ri = oracle.seeded_paths(base, 77, 2000, lo, hi)
     ok = np.nonzero(_no_repeat(ids, order))[0]
     sel = np.sort(np.random.default_rng(k + fp).choice(ok, n_paths, replace=False))
     sc, nids, ti2, ri2 = _private_scene(base, ids[sel], order[sel], ti[sel], ri[sel])
@@ -140,6 +146,7 @@ def test_per_path_gradients_against_the_fp64_autograd_reference(ctx, k, fp, n_pa
 
 
 def test_zero_steps_and_argument_errors(ctx):
+    """k = 0: the gradient of the loss at the start t = 1/2; bad step and round counts are argument errors."""
     import torch
 
     sc = scenes.tiny_scene(0)
