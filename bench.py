@@ -619,12 +619,10 @@ def run_fig3(args, world, rank, local_rank):
                     p = fpt.default_params(max_iters=k, fixed_iters=1, fp_iters=fp)
                     reps = 10 if label == "1000" else 2
                     t_imp = timed(lambda: fpt.solve_grad(ctx, scene, batch, p, dL=ones, out=out), reps)
-                    # the unrolled backward keeps the inverse Hessian and its adjoint in registers: orders 1-5
-                    t_ad = timed(lambda: fpt.backward_unrolled(ctx, scene, batch, k, fp, dL=ones), reps) if n <= 5 \
-                        else None
+                    t_ad = timed(lambda: fpt.backward_unrolled(ctx, scene, batch, k, fp, dL=ones), reps)
                     row = {"n": n, "paths": N, "k": k, "fp_iters": fp, "implicit_ms": t_imp, "ad_ms": t_ad,
-                           "ad_over_implicit": t_ad / t_imp if t_ad else None}
-                    if label == "1000" and t_ad:
+                           "ad_over_implicit": t_ad / t_imp}
+                    if label == "1000":
                         # how far the gradient through the k FP32 steps is from the implicit one
                         _, (_, _, gi) = fpt.solve_grad(ctx, scene, batch, p, dL=ones, out=out)
                         _, _, ga, _, _ = fpt.backward_unrolled(ctx, scene, batch, k, fp, dL=ones)
