@@ -320,6 +320,19 @@ def run_ours(args, world, rank, local_rank):
     f_init = torch.tensor([bfgs_flops_init(3, q) for q in range(4)], dtype=torch.float64, device=dev)
     bfgs_flops = float(((f_init[nq] + f_step[nq] * iters.double()) * run.double()).sum().item())
     del nq, run
+    # obstruction of the step's valid solved paths (post-processing, not part of the timed step)
+    blocked = fpt.occlusion(ctx, scene, batch, out["T"], out["status"], mask)
+    torch.cuda.synchronize(dev)
+    oa, ob = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    oa.record(stream)
+    for _ in range(5):
+        fpt.occlusion(ctx, scene, batch, out["T"], out["status"], mask, out=blocked)
+    ob.record(stream)
+    ob.synchronize()
+    occ = {"ms_per_call": oa.elapsed_time(ob) / 5, "paths_tested": int(fpt.count_status(ctx, out["status"], mask)),
+           "blocked": int((blocked != 0).sum().item()),
+           "kernel": "occlusion_kernel: every segment of each valid solved path against the 32 facades"}
+    del blocked
     names = {fpt.K_BFGS: "bfgs_refill_kernel<3, Q> (8 reflector/edge patterns)",
              fpt.K_POLISH: "polish_ff_kernel<3> + polish64_kernel<3> (rescue)",
              fpt.K_BACKWARD: "backward_kernel<3> + backward_rescue_kernel<3>", fpt.K_OTHER: "backward_finalize_kernel",
@@ -346,7 +359,8 @@ def run_ours(args, world, rank, local_rank):
             "dominant_kernel": names[dom],
             "roofline": roof_bfgs,
             "gpu_launches": int(sum(klaunch)),
-            "clocks": clocks}
+            "clocks": clocks,
+            "occlusion": occ}
     if dom != fpt.K_BFGS:
         line["roofline_note"] = f"dominant kernel is {names[dom]}; roofline reported for the FP32 solver kernel"
 

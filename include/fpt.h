@@ -234,6 +234,22 @@ fpt_status fpt_solve_grad(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch*
                           float* L_out, uint8_t* status_out, uint8_t* iters_out, float* rho_out, float* g_tx,
                           float* g_rx, float* g_vertices);
 
+/* Obstruction of paths by the scene's planar objects (Sec. I: a candidate ray
+ * is discarded when it is obstructed, as well as when an interaction point
+ * falls outside its object).  For every path whose status holds all bits of
+ * status_mask (status device [N], may be NULL when the mask is 0), with points
+ * x_1..x_n from the parameters T [N][n_max][2] (device) and x_0 = TX,
+ * x_{n+1} = RX: segment j (from x_j to x_{j+1}) is blocked when a planar
+ * object other than the two objects at its ends has the segment's ends on
+ * opposite sides of its plane, each more than tol metres from it (tol <= 0:
+ * 1e-4), and the crossing point inside its closed parallelogram.  Edges block
+ * nothing.  blocked_out [N] uint16 (device): bit j set = segment j blocked
+ * (0 for paths not tested and for REPEAT / INVALID_INPUT sequences).  FPT_EINVAL
+ * on missing arguments; FPT_EUNSUPPORTED above 3938 planar objects (their
+ * 52-byte records are staged in shared memory). */
+fpt_status fpt_occlusion(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* batch, const float* T,
+                         const uint8_t* status, uint8_t status_mask, float tol, uint16_t* blocked_out);
+
 /* Gradient by automatic differentiation through the solver's iterations, the
  * alternative the implicit backward is compared with (Sec. IV-B, Fig. 3).
  * Every path of the batch runs exactly `steps` steps of the unified solver of

@@ -14,10 +14,11 @@ from that definition:
     and the crossing point lies in the parallelogram.
 
 blocked_segments() returns, per path, a bit mask (bit j set: segment j is
-blocked) and a margin: the smallest distance, over every object tested, from
-deciding otherwise (the distance of an end from the plane, or of the crossing
-point from the parallelogram's sides along the plane), so that tests can
-leave out the cases a different rounding may decide the other way.
+blocked).  Its `grow` argument widens every parallelogram by that many metres
+along its plane on all sides (negative: shrinks it): the decision is monotone
+in `grow` and in `tol`, so decided() can mark the paths whose masks do not
+change when the points move by a small amount -- the cases that a different
+rounding, or a solution 1e-4 m away, may not decide the other way.
 """
 
 from __future__ import annotations
@@ -51,20 +52,17 @@ def _in_plane_coords(h, b, a1, a2):
     return (g22 * r1 - g12 * r2) / det, (g11 * r2 - g12 * r1) / det
 
 
-def blocked_segments(scene, ids, order, tx_idx, rx_idx, X, tol=1e-4):
-    """Bit masks [M] (uint16) of blocked segments and the decision margins [M] (metres)."""
+def blocked_segments(scene, ids, order, tx_idx, rx_idx, X, tol=1e-4, grow=0.0):
+    """Bit masks [M] (uint16) of blocked segments."""
     ids = np.asarray(ids)
     order = np.asarray(order)
     X = np.asarray(X, dtype=np.float64)
     qidx, b, a1, a2, nrm = _quads(scene)
-    side1 = np.linalg.norm(a1, axis=1)
-    side2 = np.linalg.norm(a2, axis=1)
     # in-plane distance between the sides u = 0 and u = 1 is area / |a2|, between v = 0 and v = 1 area / |a1|
     area = np.linalg.norm(np.cross(a1, a2), axis=1)
-    h_u = area / side2
-    h_v = area / side1
+    gu = grow / (area / np.linalg.norm(a2, axis=1))
+    gv = grow / (area / np.linalg.norm(a1, axis=1))
     masks = np.zeros(len(order), dtype=np.uint16)
-    margins = np.full(len(order), np.inf)
     for p in range(len(order)):
         n = int(order[p])
         pts = np.vstack([scene.tx[tx_idx[p]], X[p, :n], scene.rx[rx_idx[p]]])
@@ -81,21 +79,18 @@ def blocked_segments(scene, ids, order, tx_idx, rx_idx, X, tol=1e-4):
             dP = ((P - b[keep]) * nrm[keep]).sum(-1)
             dQ = ((Q - b[keep]) * nrm[keep]).sum(-1)
             cross = ((dP > tol) & (dQ < -tol)) | ((dP < -tol) & (dQ > tol))
-            plane_m = np.minimum(np.abs(np.abs(dP) - tol), np.abs(np.abs(dQ) - tol))
-            # where the line through P and Q meets the plane (segments parallel to it: nowhere)
-            par = np.abs(dP - dQ) < 1e-300
-            s = dP / np.where(par, 1.0, dP - dQ)
+            s = dP / np.where(cross, dP - dQ, 1.0)
             h = P + s[:, None] * (Q - P)
             u, v = _in_plane_coords(h, b[keep], a1[keep], a2[keep])
-            inside = (u >= 0) & (u <= 1) & (v >= 0) & (v <= 1) & ~par
-            # in-plane distance of that point from the nearest side, metres
-            side_m = np.minimum(np.minimum(np.abs(u), np.abs(1 - u)) * h_u[keep],
-                                np.minimum(np.abs(v), np.abs(1 - v)) * h_v[keep])
-            side_m = np.where(par, np.inf, side_m)
-            # how far each object's decision (cross and inside) is from flipping
-            margin = np.where(cross & inside, np.minimum(plane_m, side_m),
-                              np.where(cross, side_m, np.where(inside, plane_m, np.maximum(plane_m, side_m))))
+            inside = (u >= -gu[keep]) & (u <= 1 + gu[keep]) & (v >= -gv[keep]) & (v <= 1 + gv[keep])
             if np.any(cross & inside):
                 masks[p] |= np.uint16(1 << j)
-            margins[p] = min(margins[p], float(margin.min()))
-    return masks, margins
+    return masks
+
+
+def decided(scene, ids, order, tx_idx, rx_idx, X, tol=1e-4, plane=0.5e-4, side=1e-3):
+    """Paths whose masks stay the same when the plane tolerance moves by +-plane metres and the
+    parallelograms grow or shrink by `side` metres."""
+    most = blocked_segments(scene, ids, order, tx_idx, rx_idx, X, tol - plane, side)
+    least = blocked_segments(scene, ids, order, tx_idx, rx_idx, X, tol + plane, -side)
+    return most == least

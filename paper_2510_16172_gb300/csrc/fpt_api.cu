@@ -102,6 +102,8 @@ struct fpt_scene {
   float* d_rx32 = nullptr;
   double* d_tx64 = nullptr;
   double* d_rx64 = nullptr;
+  float* d_occ = nullptr;  // planar objects as occluders (kOcc floats each)
+  int n_occ = 0;
 };
 
 struct fpt_batch {
@@ -345,7 +347,37 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
     aux[kAux * k + 2] = types[k] == FPT_EDGE ? 1.f : 0.f;
     aux[kAux * k + 3] = 0.f;
   }
+  // occluder records of the planar objects: centred origin, unit normal, dual basis of (a1, a2)
+  std::vector<float> occ;
+  for (int k = 0; k < n_obj; ++k) {
+    if (types[k] != FPT_QUAD) continue;
+    const double* v = verts + 9 * k;
+    double b[3], a1[3], a2[3];
+    for (int c = 0; c < 3; ++c) {
+      b[c] = v[c] - s->centre[c];
+      a1[c] = v[3 + c] - v[c];
+      a2[c] = v[6 + c] - v[c];
+    }
+    double nv[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
+    const double nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+    const double g11 = a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2];
+    const double g12 = a1[0] * a2[0] + a1[1] * a2[1] + a1[2] * a2[2];
+    const double g22 = a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2];
+    const double det = g11 * g22 - g12 * g12;
+    for (int c = 0; c < 3; ++c) occ.push_back((float)b[c]);
+    for (int c = 0; c < 3; ++c) occ.push_back((float)(nv[c] / nn));
+    for (int c = 0; c < 3; ++c) occ.push_back((float)((g22 * a1[c] - g12 * a2[c]) / det));
+    for (int c = 0; c < 3; ++c) occ.push_back((float)((g11 * a2[c] - g12 * a1[c]) / det));
+    int32_t id = k;
+    float idf;
+    std::memcpy(&idf, &id, sizeof(idf));
+    occ.push_back(idf);
+  }
+  s->n_occ = (int)(occ.size() / kOcc);
   cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess && s->n_occ) e = cudaMalloc(&s->d_occ, occ.size() * sizeof(float));
+  if (e == cudaSuccess && s->n_occ)
+    e = cudaMemcpy(s->d_occ, occ.data(), occ.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rec32, rec32.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rec64, rec64.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_aux, aux.size() * sizeof(float));
@@ -372,6 +404,7 @@ void fpt_scene_free(fpt_scene* s) {
   cudaFree(s->d_rx32);
   cudaFree(s->d_tx64);
   cudaFree(s->d_rx64);
+  cudaFree(s->d_occ);
   delete s;
 }
 
@@ -941,6 +974,32 @@ fpt_status fpt_backward_unrolled(fpt_ctx* ctx, const fpt_scene* s, const fpt_bat
   {
     ProfScope ps(ctx, FPT_K_OTHER);
     CUDA_OR_FAIL(ctx, launch_backward_finalize(S, nullptr, ctx->d_gacc, g_tx, g_rx, g_vertices, ctx->stream));
+  }
+  return FPT_OK;
+}
+
+fpt_status fpt_occlusion(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, const float* T, const uint8_t* status,
+                         uint8_t status_mask, float tol, uint16_t* blocked_out) {
+  fpt_status st = check_scene_batch(ctx, s, bc);
+  if (st != FPT_OK) return st;
+  if (!T || !blocked_out) return fail(ctx, FPT_EINVAL, "T and blocked_out are required");
+  if (status_mask && !status) return fail(ctx, FPT_EINVAL, "status_mask needs status");
+  if (!(tol >= 0.f)) return fail(ctx, FPT_EINVAL, "tol must be >= 0");
+  if ((size_t)s->n_occ * kOcc * sizeof(float) > kMaxSmemBytes)
+    return fail(ctx, FPT_EUNSUPPORTED, "%d planar objects exceed the occluder table", s->n_occ);
+  fpt_batch* b = const_cast<fpt_batch*>(bc);
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  st = ensure_buckets(ctx, b, scene_dev(s));
+  if (st != FPT_OK) return st;
+  const SceneDev S = scene_dev(s);
+  const float t = tol > 0.f ? tol : 1e-4f;
+  for (int n = 1; n <= kMaxOrder; ++n) {
+    const PathRec* list;
+    const uint64_t cnt = order_slice(b, n, &list);
+    if (!cnt) continue;
+    ProfScope ps(ctx, FPT_K_OTHER);
+    CUDA_OR_FAIL(ctx, launch_occlusion(S, b->dev, n, list, cnt, T, status, status_mask, s->d_occ, s->n_occ, t,
+                                       blocked_out, ctx->stream, ctx->n_sm));
   }
   return FPT_OK;
 }

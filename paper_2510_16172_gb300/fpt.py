@@ -73,6 +73,7 @@ _SIGS = {
                                  _vp, _vp, _vp, _vp]),
     "fpt_count_status": (C.c_int, [_vp, _vp, C.c_uint64, C.c_uint8, C.POINTER(C.c_uint64)]),
     "fpt_backward_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint8, _vp, _vp, _vp]),
+    "fpt_occlusion": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint8, C.c_float, _vp]),
     "fpt_backward_unrolled": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fpt_tc_gemm_bf16": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
     "fpt_mlp_create": (C.c_int, [_vp, C.c_uint64, C.c_float, C.POINTER(_vp)]),
@@ -403,6 +404,25 @@ def backward_noalloc(ctx: Context, scene: Scene, batch: Batch, T, status=None, d
                                                       _ptr(dX), _ptr(dL), int(dL_status_mask), _ptr(g_tx),
                                                       _ptr(g_rx), _ptr(g_v)))
     return g_tx, g_rx, g_v
+
+
+def occlusion(ctx: Context, scene: Scene, batch: Batch, T, status=None, status_mask: int = 0, tol: float = 0.0,
+              out=None):
+    """fpt_occlusion: per path an int16 bit mask, bit j set when segment j is obstructed."""
+    import torch
+
+    _need_cuda(T, torch.float32, "T")
+    _need_cuda(status, torch.uint8, "status")
+    if out is None:
+        out = torch.zeros(batch.n_paths, dtype=torch.int16, device=T.device)
+    _need_cuda(out, torch.int16, "out")
+    if out.numel() != batch.n_paths or T.numel() != batch.n_paths * batch.n_max * 2:
+        raise FptError("T must be [N, n_max, 2] and out [N] for the batch")
+    if status is not None and status.numel() != batch.n_paths:
+        raise FptError("status must be [N]")
+    _check(ctx.handle, library().fpt_occlusion(ctx.handle, scene.handle, batch.handle, _ptr(T), _ptr(status),
+                                               int(status_mask), float(tol), _ptr(out)))
+    return out
 
 
 def backward_unrolled(ctx: Context, scene: Scene, batch: Batch, steps: int, fp_iters: int = 1, dX=None, dL=None,

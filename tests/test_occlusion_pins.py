@@ -18,9 +18,9 @@ SQUARE = [[0, 0, 0], [1, 0, 0], [0, 1, 0]]  # v0, v1, v3 of the unit square in z
 
 
 def _masks(sc, ids, order, X):
-    m, margin = occlusion.blocked_segments(sc, np.atleast_2d(ids), np.atleast_1d(order), [0] * len(order),
-                                           [0] * len(order), np.asarray(X, dtype=np.float64).reshape(len(order), -1, 3))
-    return m, margin
+    args = (sc, np.atleast_2d(ids), np.atleast_1d(order), [0] * len(np.atleast_1d(order)),
+            [0] * len(np.atleast_1d(order)), np.asarray(X, dtype=np.float64).reshape(len(np.atleast_1d(order)), -1, 3))
+    return occlusion.blocked_segments(*args), occlusion.decided(*args)
 
 
 def test_hand_cases():
@@ -44,8 +44,8 @@ def test_hand_cases():
     assert m[0] == 0
     # now put the wall point low enough that segment 0 crosses z = 0 at x = 0.6, inside the square
     # (0.2, .5, 1) -> (10, .5, z): crossing at 0.2 + 9.8 / (1 - z) = 0.6  =>  z = 1 - 24.5
-    m, margin = _masks(sc, [1], [1], [[10.0, 0.5, -23.5]])
-    assert m[0] == 1 and margin[0] > 0.1
+    m, sure = _masks(sc, [1], [1], [[10.0, 0.5, -23.5]])
+    assert m[0] == 1 and sure[0]
     # an edge in the way blocks nothing
     sc2 = _scene([wall], [0.2, 0.5, 1.0], [0.8, 0.5, -1.0], edges=[[[0, 0.5, 0], [1, 0.5, 0], [0, 0, 0]]])
     m, _ = _masks(sc2, [0], [1], [[10.0, 0.5, -23.5]])
@@ -56,8 +56,8 @@ def test_hand_cases():
     assert m[0] == 0
     # closed boundary: crossing exactly on the side u = 1 blocks
     sc4 = _scene([SQUARE, wall], [1.0, 0.5, 1.0], [0.8, 0.5, -1.0])
-    m, margin = _masks(sc4, [1], [1], [[1.0, 0.5, -1.0]])  # segment 0 straight down through (1, .5, 0)
-    assert m[0] == 1 and margin[0] < 1e-9
+    m, sure = _masks(sc4, [1], [1], [[1.0, 0.5, -1.0]])  # segment 0 straight down through (1, .5, 0)
+    assert m[0] == 1 and not sure[0]
 
 
 def _moller_trumbore(P, Q, a, b, c):
@@ -88,8 +88,8 @@ def test_against_segment_triangle_intersection():
         P, R = rng.uniform(-4, 4, 3), rng.uniform(-4, 4, 3)
         sc = _scene([quad, wall], P, R)
         Xw = np.array([50.0, rng.uniform(-4, 4), rng.uniform(-4, 4)])
-        m, margin = _masks(sc, [1], [1], [Xw])
-        if margin[0] < 1e-6:
+        m, sure = _masks(sc, [1], [1], [Xw])
+        if not sure[0]:
             continue
         checked += 1
         for j, (A, B) in enumerate([(P, Xw), (Xw, R)]):
