@@ -997,9 +997,12 @@ fpt_status fpt_occlusion(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, 
     const PathRec* list;
     const uint64_t cnt = order_slice(b, n, &list);
     if (!cnt) continue;
+    if (cnt > 0xFFFFFFFFull) return fail(ctx, FPT_EUNSUPPORTED, "more than 2^32 paths of one order");
+    st = ensure_rescue(ctx, cnt, n);
+    if (st != FPT_OK) return st;
     ProfScope ps(ctx, FPT_K_OTHER);
     CUDA_OR_FAIL(ctx, launch_occlusion(S, b->dev, n, list, cnt, T, status, status_mask, s->d_occ, s->n_occ, t,
-                                       blocked_out, ctx->stream, ctx->n_sm));
+                                       blocked_out, ctx->d_rescue, ctx->d_rescue_n, ctx->stream, ctx->n_sm));
   }
   return FPT_OK;
 }

@@ -115,9 +115,12 @@ cudaError_t launch_unrolled(int n, const SceneDev& S, const BatchDev& B, int ste
 // Obstruction test (k_occlusion.cu): kOcc floats per planar object: origin b (3,
 // centred), unit normal (3), dual basis d1 (3) and d2 (3), object id (int bits).
 constexpr int kOcc = 13;
+// With status and a non-zero mask the selected paths are listed first (sel: n_local uint32, sel_count: one
+// counter) and the others get a zero mask.
 cudaError_t launch_occlusion(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t n_local,
                              const float* T, const uint8_t* status, uint8_t mask, const float* occ, int n_occ,
-                             float tol, uint16_t* blocked, cudaStream_t stream, int n_sm);
+                             float tol, uint16_t* blocked, uint32_t* sel, unsigned* sel_count, cudaStream_t stream,
+                             int n_sm);
 cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
                                      float* g_rx, float* g_vertices, cudaStream_t stream);
 

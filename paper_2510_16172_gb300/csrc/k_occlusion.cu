@@ -9,26 +9,56 @@
 // parallelogram.  Edges (lines) block nothing.  One thread per path; the
 // occluders' records (centred origin, unit normal and the dual basis that gives
 // the in-plane coordinates u = d1 . (h - b), v = d2 . (h - b)) are staged in
-// shared memory and every thread of a warp walks them in the same order.
+// shared memory and every thread of a warp walks them in the same order.  When
+// only paths with given status bits are tested (typically the few per cent
+// that are valid and solved), a first kernel lists them and writes zero for
+// the rest, so that the test kernel's warps run full.
 #include "fpt_kernels.h"
 
 namespace fpt {
 
+// List the paths of a slice that hold the status bits (local indices); zero the others' masks.
+__global__ void occlusion_select_kernel(BatchDev B, int n, const PathRec* list, uint64_t n_local,
+                                        const uint8_t* __restrict__ status, uint8_t mask,
+                                        uint16_t* __restrict__ blocked, uint32_t* __restrict__ sel,
+                                        unsigned* __restrict__ sel_count) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
+    const uint64_t j = j0 + threadIdx.x;
+    bool take = false;
+    if (j < n_local) {
+      PathDesc d;
+      fetch_path(B, n, list, j, d);
+      take = !(d.flags & ST_SKIP) && (status[d.g] & mask) == mask;
+      if (!take) blocked[d.g] = 0;
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, take);
+    unsigned base = 0;
+    if (lane == 0 && ballot) base = atomicAdd(sel_count, (unsigned)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) sel[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)j;
+  }
+}
+
+// Test the paths of a slice (sel == nullptr) or the listed ones.
 __global__ void __launch_bounds__(kThreads) occlusion_kernel(SceneDev S, BatchDev B, int n, const PathRec* list,
                                                              uint64_t n_local, const float* __restrict__ T,
-                                                             const uint8_t* __restrict__ status, uint8_t mask,
+                                                             const uint32_t* __restrict__ sel,
+                                                             const unsigned* __restrict__ sel_count,
                                                              const float* __restrict__ occ, int n_occ, float tol,
                                                              uint16_t* __restrict__ blocked) {
   extern __shared__ __align__(16) float s_occ[];
   for (int k = threadIdx.x; k < n_occ * kOcc; k += blockDim.x) s_occ[k] = occ[k];
   __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_local; j += stride) {
+  const uint64_t n_iter = sel ? (uint64_t)*sel_count : n_local;
+  for (uint64_t k0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 < n_iter; k0 += stride) {
+    const uint64_t j = sel ? (uint64_t)sel[k0] : k0;
     PathDesc d;
     fetch_path(B, n, list, j, d);
     uint16_t bits = 0;
-    const bool test = !(d.flags & ST_SKIP) && (!status || (status[d.g] & mask) == mask);
-    if (test) {
+    if (!(d.flags & ST_SKIP)) {
       // the points x_0 .. x_{n+1}, relative to the scene centre
       const float2* Tp = reinterpret_cast<const float2*>(T) + d.g * (uint64_t)B.n_max;
       float P[3];
@@ -71,7 +101,21 @@ __global__ void __launch_bounds__(kThreads) occlusion_kernel(SceneDev S, BatchDe
 
 cudaError_t launch_occlusion(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t n_local,
                              const float* T, const uint8_t* status, uint8_t mask, const float* occ, int n_occ,
-                             float tol, uint16_t* blocked, cudaStream_t stream, int n_sm) {
+                             float tol, uint16_t* blocked, uint32_t* sel, unsigned* sel_count, cudaStream_t stream,
+                             int n_sm) {
+  const bool listed = status != nullptr && mask != 0;
+  if (listed) {
+    if (!sel || !sel_count) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(sel_count, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = (n_local + 255) / 256;
+    const unsigned g = (unsigned)(want < (uint64_t)n_sm * 8 ? want : (uint64_t)n_sm * 8);
+    if (g == 0) return cudaSuccess;
+    occlusion_select_kernel<<<g, 256, 0, stream>>>(B, n, list, n_local, status, mask, blocked, sel, sel_count);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = (size_t)n_occ * kOcc * sizeof(float);
   if (smem > kMaxSmemBytes) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
@@ -82,11 +126,13 @@ cudaError_t launch_occlusion(const SceneDev& S, const BatchDev& B, int n, const 
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, occlusion_kernel, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
+  // a listed launch strides over the list; a full grid covers the largest list
   const uint64_t want = (n_local + kThreads - 1) / kThreads;
   const uint64_t cap = (uint64_t)n_sm * (uint64_t)per_sm;
   const unsigned grid = (unsigned)(want < cap ? want : cap);
   if (grid == 0) return cudaSuccess;
-  occlusion_kernel<<<grid, kThreads, smem, stream>>>(S, B, n, list, n_local, T, status, mask, occ, n_occ, tol, blocked);
+  occlusion_kernel<<<grid, kThreads, smem, stream>>>(S, B, n, list, n_local, T, listed ? sel : nullptr,
+                                                     listed ? sel_count : nullptr, occ, n_occ, tol, blocked);
   count_launch();
   return cudaGetLastError();
 }
