@@ -323,8 +323,27 @@ __device__ __forceinline__ bool bfgs_step(PathState<N, Q>& P, const SolveCfg& cf
     qa[jj] = fmaf(q[2], P.z[jj][2], fmaf(q[1], P.z[jj][1], q[0] * P.z[jj][0]));
     qc[jj] = fmaf(q[2], q[2], fmaf(q[1], q[1], q[0] * q[0]));
   }
-  float alpha = fixed_point<N>(P.e, qa, qc, 1.f, cfg.fp_iters);
-  if (!(alpha > 0.f)) alpha = fixed_point<N>(P.e, qa, qc, 0.f, cfg.fp_iters);
+  float alpha;
+  if (cfg.fp_iters == 1) {
+    // one round: the rounds from alpha = 1 and from alpha = 0 side by side, so that the lanes that need
+    // the second (about a third of the steps) do not run it alone; the same values as fixed_point()
+    float n1 = 0.f, d1 = 0.f, n0 = 0.f, d0 = 0.f;
+#pragma unroll
+    for (int jj = 0; jj <= N; ++jj) {
+      const float r1 = rsqrtf(fmaxf(fmaf(1.f, fmaf(1.f, qc[jj], 2.f * qa[jj]), P.e[jj]), 1e-30f));
+      const float r0 = rsqrtf(fmaxf(P.e[jj], 1e-30f));
+      n1 = fmaf(qa[jj], r1, n1);
+      d1 = fmaf(qc[jj], r1, d1);
+      n0 = fmaf(qa[jj], r0, n0);
+      d0 = fmaf(qc[jj], r0, d0);
+    }
+    const float a1 = d1 > 1e-30f ? fminf(-__fdividef(n1, d1), kAlphaMax) : 0.f;
+    const float a0 = d0 > 1e-30f ? fminf(-__fdividef(n0, d0), kAlphaMax) : 0.f;
+    alpha = a1 > 0.f ? a1 : a0;
+  } else {
+    alpha = fixed_point<N>(P.e, qa, qc, 1.f, cfg.fp_iters);
+    if (!(alpha > 0.f)) alpha = fixed_point<N>(P.e, qa, qc, 0.f, cfg.fp_iters);
+  }
   // step and new gradient
   float s[M];
 #pragma unroll
