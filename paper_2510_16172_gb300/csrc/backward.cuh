@@ -43,10 +43,12 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
   __syncthreads();
   const int n_max = B.n_max;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // listed launch: only the paths the select pass found with a cotangent
+  const uint64_t n_iter = cfg.sel ? (uint64_t)*cfg.sel_count : n_local;
   int tiles = 0;
-  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
-    const uint64_t j = j0 + threadIdx.x;
-    const bool have = j < n_local;
+  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_iter; j0 += stride) {
+    const bool have = j0 + threadIdx.x < n_iter;
+    const uint64_t j = have && cfg.sel ? (uint64_t)cfg.sel[j0 + threadIdx.x] : j0 + threadIdx.x;
     PathDesc d;
     float gb[N][9];  // per slot: d/db (3), d/da1 (3), d/da2 (3)
     float gtx[3] = {0.f, 0.f, 0.f}, grx[3] = {0.f, 0.f, 0.f};
@@ -161,6 +163,32 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
   }
 }
 
+// List the paths of a slice that carry a cotangent (no dX: those with a non-zero length cotangent
+// and a status that the backward does not skip), by local index.
+template <int N>
+__global__ void backward_select_kernel(BatchDev B, BackwardCfg cfg, uint64_t n_local, const PathRec* list,
+                                       const uint8_t* __restrict__ status, const float* __restrict__ dLv) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
+    const uint64_t j = j0 + threadIdx.x;
+    bool take = false;
+    if (j < n_local) {
+      PathDesc d;
+      fetch_path_n<N>(B, list, j, d);
+      uint8_t st = d.flags;
+      if (status) st |= status[d.g];
+      if (!(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE)))
+        take = dLv ? dLv[d.g] != 0.f : (cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask);
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, take);
+    unsigned base = 0;
+    if (lane == 0 && ballot) base = atomicAdd(cfg.sel_count, (unsigned)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) cfg.sel[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)j;
+  }
+}
+
 // FP64 pass over the paths whose FP32 pivots failed: FP64 records, segment
 // vectors, Hessian and VJP, summed straight into the FP64 accumulators.
 template <int N>
@@ -244,6 +272,20 @@ cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const Backwa
                                      const float* dX, const float* dL, double* gacc, cudaStream_t stream, int n_sm,
                                      uint32_t* rescue_list, unsigned* rescue_count) {
   BackwardCfg cfg = cfg_in;
+  if (dX != nullptr || cfg.sel == nullptr || cfg.sel_count == nullptr) {
+    cfg.sel = nullptr;  // point cotangents: every path takes part
+    cfg.sel_count = nullptr;
+  } else {
+    cudaError_t e = cudaMemsetAsync(cfg.sel_count, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = (n_local + 255) / 256;
+    const unsigned g = (unsigned)(want < (uint64_t)n_sm * 8 ? want : (uint64_t)n_sm * 8);
+    if (g == 0) return cudaSuccess;
+    backward_select_kernel<N><<<g, 256, 0, stream>>>(B, cfg, n_local, list, status, dL);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const size_t base = (size_t)S.n_obj * (kRec32 + kAux) * sizeof(float);
   const size_t accb = (size_t)(S.n_obj * 9 + 3 * (S.n_tx + S.n_rx)) * sizeof(float);
   size_t smem = base + accb;

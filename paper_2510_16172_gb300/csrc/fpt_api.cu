@@ -924,7 +924,10 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
     st = ensure_rescue(ctx, cnt, n);
     if (st != FPT_OK) return st;
     ProfScope ps(ctx, FPT_K_BACKWARD);
-    CUDA_OR_FAIL(ctx, launch_backward(n, S, b->dev, bc_cfg, cnt, list, T, status, dX, dL, ctx->d_gacc, ctx->stream,
+    BackwardCfg cfg_n = bc_cfg;
+    cfg_n.sel = ctx->d_rescue + 2 * cnt;  // the third list of the scratch (the polish's, free here)
+    cfg_n.sel_count = ctx->d_rescue_n + 2;
+    CUDA_OR_FAIL(ctx, launch_backward(n, S, b->dev, cfg_n, cnt, list, T, status, dX, dL, ctx->d_gacc, ctx->stream,
                                       ctx->n_sm, ctx->d_rescue, ctx->d_rescue_n));
   }
   {

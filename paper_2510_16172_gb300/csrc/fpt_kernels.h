@@ -48,6 +48,10 @@ struct BackwardCfg {
   int acc_in_smem;   // accumulate per CTA in shared memory before the FP64 global sum
   int flush_tiles;   // flush the shared accumulators every this many CTA tiles
   uint8_t dl_mask;   // with no dL array: dL = 1 where (status & dl_mask) == dl_mask (0 = no length term)
+  // scratch for a list of the paths with a cotangent (room for the slice, and its counter): without dX,
+  // a select pass lists them first so the adjoint's warps run full (nullptr: every path is visited)
+  uint32_t* sel = nullptr;
+  unsigned* sel_count = nullptr;
 };
 
 // Per-order launches (n = 1..kMaxOrder).  `list` = nullptr for exhaustive batches.
