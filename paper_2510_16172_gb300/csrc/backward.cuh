@@ -174,12 +174,19 @@ __global__ void backward_select_kernel(BatchDev B, BackwardCfg cfg, uint64_t n_l
     const uint64_t j = j0 + threadIdx.x;
     bool take = false;
     if (j < n_local) {
-      PathDesc d;
-      fetch_path_n<N>(B, list, j, d);
-      uint8_t st = d.flags;
-      if (status) st |= status[d.g];
+      uint64_t g;
+      uint8_t st;
+      if (status) {  // the solver wrote the sequence's REPEAT / INVALID_INPUT bits into its status
+        g = slice_global(B, N, list, j);
+        st = status[g];
+      } else {
+        PathDesc d;
+        fetch_path_n<N>(B, list, j, d);
+        g = d.g;
+        st = d.flags;
+      }
       if (!(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE)))
-        take = dLv ? dLv[d.g] != 0.f : (cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask);
+        take = dLv ? dLv[g] != 0.f : (cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask);
     }
     const unsigned ballot = __ballot_sync(0xffffffffu, take);
     unsigned base = 0;

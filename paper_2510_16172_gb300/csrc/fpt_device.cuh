@@ -232,6 +232,18 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
   finish_desc(B, digits, d);
 }
 
+// Global index g of local index j of an order-n slice, without decoding the
+// sequence (the same g as decode_exhaustive_order / the record's).
+__device__ __forceinline__ uint64_t slice_global(const BatchDev& B, int n, const PathRec* list, uint64_t j) {
+  if (list != nullptr) {
+    const uint2 w = __ldg(reinterpret_cast<const uint2*>(list + j));
+    return (uint64_t)w.x | ((uint64_t)w.y << 32);
+  }
+  const uint64_t kn = B.kpow[n];
+  const uint64_t pair = j / kn;
+  return pair * B.per_pair + B.offset[n] + (j - pair * kn);
+}
+
 // Path source for one per-order launch: exhaustive batches need no list; other
 // batches pass their bucket of decoded path records.
 __device__ __forceinline__ void fetch_path(const BatchDev& B, int n, const PathRec* list, uint64_t j,

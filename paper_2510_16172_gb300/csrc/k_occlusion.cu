@@ -28,10 +28,11 @@ __global__ void occlusion_select_kernel(BatchDev B, int n, const PathRec* list, 
     const uint64_t j = j0 + threadIdx.x;
     bool take = false;
     if (j < n_local) {
-      PathDesc d;
-      fetch_path(B, n, list, j, d);
-      take = !(d.flags & ST_SKIP) && (status[d.g] & mask) == mask;
-      if (!take) blocked[d.g] = 0;
+      // the solver wrote the sequence's REPEAT / INVALID_INPUT bits into its status
+      const uint64_t g = slice_global(B, n, list, j);
+      const uint8_t st = status[g];
+      take = !(st & ST_SKIP) && (st & mask) == mask;
+      if (!take) blocked[g] = 0;
     }
     const unsigned ballot = __ballot_sync(0xffffffffu, take);
     unsigned base = 0;
