@@ -303,7 +303,7 @@ fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uin
 /* ---------------------------------------------------------------------------
  * Learned warm start (the paper names better initial candidates as future work,
  * Sec. V).  A network maps the geometry of a sequence to starting parameters:
- * features (64, BF16) -> 256 -> 256 -> 256 (GELU) -> 8 outputs (t of the first
+ * features (64, BF16) -> 256 -> 256 -> 256 (GELU, tanh form) -> 8 outputs (t of the first
  * four interactions), BF16 weights, FP32 accumulation on the tensor cores,
  * activations rounded to BF16 between layers.  Features of a path of order n,
  * with o = (TX + RX) / 2 and S the model's length scale (metres):

@@ -1,7 +1,7 @@
 """FP64 reference of the warm-start network -- TEST INFRASTRUCTURE ONLY.
 
 Plain numpy, following the network's definition (include/fpt.h): BF16 inputs
-and weights, accumulation (here FP64), bias + exact-erf GELU, activations
+and weights, accumulation (here FP64), bias + GELU in its tanh form, activations
 rounded to BF16 between layers, and for the gradient the same rounding points
 as the definition fixes (dY and dZ enter the products as BF16, bias gradients
 use the unrounded dZ).  With round_bf16=False everything stays FP64, which the
@@ -11,8 +11,6 @@ finite-difference pins use.
 from __future__ import annotations
 
 import numpy as np
-from scipy.special import erf
-
 N_IN, N_H, N_OUT = 64, 256, 16
 SIZES = [("W1", (256, 64)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)), ("b3", (256,)),
          ("W4", (16, 256)), ("b4", (16,))]
@@ -40,12 +38,18 @@ def bf16(x):
     return rounded.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+K0 = np.sqrt(2.0 / np.pi)
+K1 = 0.044715
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+    """GELU, tanh form (Hendrycks and Gimpel): z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))."""
+    return 0.5 * z * (1.0 + np.tanh(K0 * (z + K1 * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+    th = np.tanh(K0 * (z + K1 * z ** 3))
+    return 0.5 * (1.0 + th) + 0.5 * z * (1.0 - th * th) * K0 * (1.0 + 3.0 * K1 * z * z)
 
 
 def features(scene, ids, order, tx_idx, rx_idx, scale):

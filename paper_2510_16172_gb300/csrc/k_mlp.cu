@@ -25,9 +25,27 @@ constexpr int kGemmKC = 64;                  // K per chunk
 constexpr uint32_t kWaitTries = 1u << 24;    // bounded mbarrier polls
 constexpr int ERR_MMA_TIMEOUT = 3;
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// GELU in its tanh form (Hendrycks and Gimpel, arXiv:1606.08415):
+//   gelu(z) = z/2 (1 + tanh(u)),  u = sqrt(2/pi) (z + 0.044715 z^3),
+// with the hardware tanh approximation (PTX tanh.approx.f32, relative error
+// about 2^-11, below the BF16 rounding that follows every activation).  One
+// MUFU operation per activation: the epilogues of the inference kernel
+// evaluate 768 of them per path.
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kGeluK0 = 0.79788456080286536f;  // sqrt(2 / pi)
+constexpr float kGeluK1 = 0.044715f;
+__device__ __forceinline__ float gelu(float z) {
+  const float u = kGeluK0 * fmaf(kGeluK1 * z, z * z, z);
+  return 0.5f * z * (1.f + tanh_approx(u));
+}
 __device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  const float z2 = z * z;
+  const float th = tanh_approx(kGeluK0 * fmaf(kGeluK1 * z, z2, z));
+  return 0.5f * (1.f + th) + 0.5f * z * (1.f - th * th) * kGeluK0 * fmaf(3.f * kGeluK1, z2, 1.f);
 }
 
 // Gather rows [r0, r0 + 128) x k [k0, k0 + 64) of a strided bf16 matrix into a
