@@ -253,7 +253,7 @@ def run_ours(args, world, rank, local_rank):
     scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
     batch = fpt.Batch.exhaustive(ctx, scene, 3, 3, sc.alphabet)
     N = batch.n_paths
-    params = fpt.default_params(max_iters=args.max_iters)
+    params = fpt.default_params(max_iters=args.max_iters, kink_stop=args.kink_stop)
     out = fpt.alloc_outputs(ctx, batch, with_X=False, with_rho=False, with_iters=True)
     grads = (torch.empty((scene.n_tx, 3), device=dev), torch.empty((scene.n_rx, 3), device=dev),
              torch.empty((scene.n_obj, 3, 3), device=dev))
@@ -352,6 +352,7 @@ def run_ours(args, world, rank, local_rank):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.rx_grid == 32 else WORKLOAD + f" (RX grid {args.rx_grid}^2)",
                        "n_paths": N, "init": "plain", "max_bfgs_iters": args.max_iters, "fp_iters": 1,
+                       "kink_stop_m": args.kink_stop,
                        "polish": "1 Newton step, double-float gradient (FP64 for ill-conditioned Hessians)",
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "solved_per_step": solved, "solved_fraction": solved / N, "mean_bfgs_iters": total_iters / max(1, run_paths),
@@ -680,8 +681,8 @@ def e2e(args, sc, ctx, dev, torch, fpt):
         batch = fpt.Batch.exhaustive(ctx, scene, 3, 3, alphabet)
         if out is None:
             out = fpt.alloc_outputs(ctx, batch, with_X=False, with_rho=False, with_iters=False)
-        _, g = fpt.solve_grad(ctx, scene, batch, fpt.default_params(max_iters=args.max_iters), dL_status_mask=mask,
-                              out=out)
+        _, g = fpt.solve_grad(ctx, scene, batch, fpt.default_params(max_iters=args.max_iters, kink_stop=args.kink_stop),
+                              dL_status_mask=mask, out=out)
         L_h.copy_(out["L"], non_blocking=True)
         st_h.copy_(out["status"], non_blocking=True)
         gtx_h.copy_(g[0], non_blocking=True)
@@ -707,7 +708,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--max-iters", type=int, default=32, help="BFGS step cap")
+    ap.add_argument("--max-iters", type=int, default=32,
+                    help="BFGS step cap (32 keeps 99.9 %% of the canyon solves that 40 steps give)")
+    ap.add_argument("--kink-stop", type=float, default=0.01,
+                    help="urban canyon: stop a path whose segment falls below this many metres before converging "
+                         "(1 cm, 1/500 of the smallest facade; loses 96 of 20.5 M solves against 0.1 mm)")
     ap.add_argument("--rx-grid", type=int, default=32, help="RX grid side (32 = the 33.5M-path workload)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain start comparison")
     ap.add_argument("--workload", choices=["canyon", "city", "fig2", "fig3"], default="canyon",

@@ -130,10 +130,12 @@ def test_tiny_scene_parity(ctx, seed):
     check_parity(g, ref)
 
 
-def test_urban_canyon_full_size_sampled(ctx):
-    """33,554,432 order-3 paths on the GPU; 4000 sampled paths re-solved by the oracle."""
+@pytest.mark.parametrize("params", [{}, {"max_iters": 32, "kink_stop": 0.01}], ids=["defaults", "bench"])
+def test_urban_canyon_full_size_sampled(ctx, params):
+    """33,554,432 order-3 paths on the GPU; 4000 sampled paths re-solved by the oracle (library defaults, and the
+    step cap and kink stop the benchmark runs with)."""
     sc = scenes.urban_canyon(0)
-    _, batch, out = gpu_run(ctx, sc, 3, 3)
+    _, batch, out = gpu_run(ctx, sc, 3, 3, fpt.default_params(**params))
     assert batch.n_paths == 32 ** 3 * 1024
     rng = np.random.default_rng(7)
     gidx = np.sort(rng.choice(batch.n_paths, 4000, replace=False))
