@@ -194,6 +194,20 @@ def oracle_rate(sc, n_paths, seed, target_s=None, max_paths=None, decode=None):
     return solved / dt, m, dt, threads
 
 
+def combine_ranks(total_ms, solved, dist, device):
+    """Whole-job figures of a replicated run: the slowest rank's timed total and the sum of the ranks' solved
+    paths (every rank solves its own copy of the workload; nothing else is exchanged)."""
+    if dist is None:
+        return float(total_ms), float(solved)
+    import torch
+
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(solved)], device=device, dtype=torch.float64)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(s.item())
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle on the machine's host cores, rank 0 only."""
     if rank != 0:
@@ -293,15 +307,7 @@ def run_ours(args, world, rank, local_rank):
     iters = out["iters"].to(torch.int64)
     total_iters = int(iters.sum().item())
     run_paths = N - fpt.count_status(ctx, out["status"], fpt.ST_REPEAT)
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        s = torch.tensor([solved], device=dev, dtype=torch.float64)
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        solved_all = float(s.item())
-    else:
-        solved_all = float(solved)
+    total_ms, solved_all = combine_ranks(total_ms, solved, dist, dev)
     value = solved_all * args.steps / (total_ms / 1e3)
 
     # roofline of the dominant kernel (device time per launch from the library's event timing)
@@ -462,7 +468,13 @@ def run_city(args, world, rank, local_rank):
         solved = fpt.count_status(ctx, out["status"], fpt.ST_SOLVED)
         run = (out["status"] & fpt.ST_REPEAT) == 0
         iters = out["iters"].to(torch.int64)
-        res[init] = {"value": solved * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+        dist = None
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        total_ms, solved_all = combine_ranks(total_ms, solved, dist, dev)
+        res[init] = {"value": solved_all * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
                      "solved_per_step": solved, "mean_bfgs_iters": float(iters[run].double().mean()),
                      "kernel_ms": kms, "launches": int(sum(klaunch)), "clocks": clk.summary()}
         if init == 1:
