@@ -789,7 +789,8 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
           CUDA_OR_FAIL(ctx, launch_bfgs(n, -1, S, b->dev, sc, b->small_count[n], b->d_lists + b->small_start[n], T,
                                         status, iters, sq, ctx->n_sm, ctx->d_work + 32));
         }
-        for (int k = 0; k < fpt_ctx::kSide && k < used; ++k) {
+        // join every side stream that waited on the fork, used or not (a stream capture must end joined)
+        for (int k = 0; k < fpt_ctx::kSide; ++k) {
           CUDA_OR_FAIL(ctx, cudaEventRecord(ctx->join_ev[k], ctx->side[k]));
           CUDA_OR_FAIL(ctx, cudaStreamWaitEvent(ctx->stream, ctx->join_ev[k], 0));
         }
