@@ -134,7 +134,7 @@ __device__ __forceinline__ void fetch_path_q(const BatchDev& B, const Tables& tb
   } else if constexpr (kSrc == SRC_PATTERN) {
     decode_exhaustive_pattern<N, Q>(B, tb, j, d);
   } else {
-    decode_exhaustive_order(B, N, j, d);
+    decode_exhaustive_order<N>(B, N, j, d);
   }
 }
 

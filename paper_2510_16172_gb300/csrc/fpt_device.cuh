@@ -129,16 +129,31 @@ __device__ __forceinline__ uint64_t seeded_draw(uint64_t seed, uint64_t g, int s
   return sm64_mix(seed + 0x9E3779B97F4A7C15ULL * (8ULL * g + (uint64_t)s + 1ULL));
 }
 
+// kN > 0: the order is the compile-time kN.  kN = 0: it is known only at run
+// time, and the slot loop runs over compile-time indices guarded by the order,
+// so that the descriptor still stays in registers (as in decode_global).
+template <int kN = 0>
 __device__ __forceinline__ void finish_desc(const BatchDev& B, const int* digits, PathDesc& d) {
   d.flags = 0;
-  for (int j = 0; j < d.n; ++j) {
-    int o = B.alphabet[digits[j]];
-    d.ids[j] = o;
-    if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
+  if constexpr (kN > 0) {
+    for (int j = 0; j < d.n; ++j) {
+      int o = B.alphabet[digits[j]];
+      d.ids[j] = o;
+      if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j)
+      if (j < d.n) {
+        int o = B.alphabet[digits[j]];
+        d.ids[j] = o;
+        if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
+      }
   }
 }
 
-// Exhaustive batch, order n known: local index j over n_pairs * K^n paths.
+// Exhaustive batch, order n known: local index j over n_pairs * K^n paths (kN as in finish_desc).
+template <int kN = 0>
 __device__ __forceinline__ void decode_exhaustive_order(const BatchDev& B, int n, uint64_t j, PathDesc& d) {
   uint64_t kn = B.kpow[n];
   uint64_t pair, r;
@@ -174,7 +189,7 @@ __device__ __forceinline__ void decode_exhaustive_order(const BatchDev& B, int n
         r = qq;
       }
   }
-  finish_desc(B, digits, d);
+  finish_desc<kN>(B, digits, d);
 }
 
 // Any batch: decode global index g.
@@ -190,20 +205,23 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
       d.flags = ST_INVALID;
       const int cap = B.n_max < kMaxOrder ? B.n_max : kMaxOrder;
       d.n = n < 1 ? 1 : (n > cap ? cap : n);
+#pragma unroll
       for (int j = 0; j < kMaxOrder; ++j) d.ids[j] = 0;
       if (d.tx < 0 || d.tx >= B.n_tx) d.tx = 0;
       if (d.rx < 0 || d.rx >= B.n_rx) d.rx = 0;
       return;
     }
-    for (int j = 0; j < n; ++j) {
-      int o = B.ids[g * (uint64_t)B.n_max + j];
-      d.ids[j] = o;
-      if (o < 0 || o >= B.n_alpha) {  // for explicit batches n_alpha holds the object count
-        d.flags |= ST_INVALID;
-        d.ids[j] = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j)
+      if (j < n) {
+        int o = B.ids[g * (uint64_t)B.n_max + j];
+        d.ids[j] = o;
+        if (o < 0 || o >= B.n_alpha) {  // for explicit batches n_alpha holds the object count
+          d.flags |= ST_INVALID;
+          d.ids[j] = 0;
+        }
+        if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
       }
-      if (j > 0 && d.ids[j - 1] == o) d.flags |= ST_REPEAT;
-    }
     return;
   }
   uint64_t pair = g / B.per_pair;
@@ -216,18 +234,21 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
     int n = B.lo + (int)(seeded_draw(B.seed, g, 0) % (uint64_t)(B.hi - B.lo + 1));
     d.n = n;
     digits[0] = (int)(seeded_draw(B.seed, g, 1) % K);
-    for (int j = 1; j < n; ++j)
-      digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + seeded_draw(B.seed, g, j + 1) % (K - 1)) % K);
+#pragma unroll
+    for (int j = 1; j < kMaxOrder; ++j)
+      if (j < n) digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + seeded_draw(B.seed, g, j + 1) % (K - 1)) % K);
   } else {
     int n = B.lo;
     while (n < B.hi && r >= B.offset[n + 1]) ++n;
     d.n = n;
     r -= B.offset[n];
-    for (int q = n - 1; q >= 0; --q) {
-      uint64_t qq = r / K;
-      digits[q] = (int)(r - qq * K);
-      r = qq;
-    }
+#pragma unroll
+    for (int q = kMaxOrder - 1; q >= 0; --q)
+      if (q < n) {
+        uint64_t qq = r / K;
+        digits[q] = (int)(r - qq * K);
+        r = qq;
+      }
   }
   finish_desc(B, digits, d);
 }
@@ -264,7 +285,7 @@ __device__ __forceinline__ void fetch_path_n(const BatchDev& B, const PathRec* l
     load_rec(list, j, d);
     if constexpr (N > kMaxBfgsOrder) decode_global(B, d.g, d);
   } else {
-    decode_exhaustive_order(B, N, j, d);
+    decode_exhaustive_order<N>(B, N, j, d);
   }
 }
 

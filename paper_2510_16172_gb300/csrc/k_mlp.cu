@@ -36,15 +36,17 @@ __device__ __forceinline__ float tanh_approx(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// u = z (K0 + K0 K1 z^2) and gelu = h + h tanh(u) with h = z/2: six operations.
 constexpr float kGeluK0 = 0.79788456080286536f;  // sqrt(2 / pi)
 constexpr float kGeluK1 = 0.044715f;
+constexpr float kGeluK01 = 0.0356774081363001f;  // K0 K1
 __device__ __forceinline__ float gelu(float z) {
-  const float u = kGeluK0 * fmaf(kGeluK1 * z, z * z, z);
-  return 0.5f * z * (1.f + tanh_approx(u));
+  const float h = 0.5f * z;
+  return fmaf(h, tanh_approx(z * fmaf(kGeluK01, z * z, kGeluK0)), h);
 }
 __device__ __forceinline__ float gelu_grad(float z) {
   const float z2 = z * z;
-  const float th = tanh_approx(kGeluK0 * fmaf(kGeluK1 * z, z2, z));
+  const float th = tanh_approx(z * fmaf(kGeluK01, z2, kGeluK0));
   return 0.5f * (1.f + th) + 0.5f * z * (1.f - th * th) * kGeluK0 * fmaf(3.f * kGeluK1, z2, 1.f);
 }
 
@@ -370,46 +372,92 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __r
 }
 
 // learned start: T[g] slot s < min(n, 4) from Y (edges keep t2 = 1/2; non-finite or |t| > 1e3 -> 1/2)
+// Starting parameters of a path of order n from the network's outputs y (slots 1-4; an edge's
+// second parameter -- bit s of `edges` -- and the later slots start at 1/2, and so does an output
+// that is not finite or beyond 1e3, and every slot of an invalid sequence).  The slot loop runs over
+// compile-time indices so that y stays in registers.
+__device__ __forceinline__ void write_start(int n, bool use, unsigned edges, const float (&y)[8], float2* To) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s < n) {
+      float t0 = 0.5f, t1 = 0.5f;
+      if (use) {
+        if (isfinite(y[2 * s]) && fabsf(y[2 * s]) < 1e3f) t0 = y[2 * s];
+        if (!((edges >> s) & 1u) && isfinite(y[2 * s + 1]) && fabsf(y[2 * s + 1]) < 1e3f) t1 = y[2 * s + 1];
+      }
+      To[s] = make_float2(t0, t1);
+    }
+  }
+  for (int s = 4; s < n; ++s) To[s] = make_float2(0.5f, 0.5f);
+}
+
+// bit s: slot s (s < 4) of the path is an edge
+__device__ __forceinline__ unsigned edge_mask(const SceneDev& S, const PathDesc& d) {
+  unsigned m = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (s < d.n && S.aux[kAux * d.ids[s] + 2] != 0.f) m |= 1u << s;
+  return m;
+}
+
 __global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const PathRec* list, uint64_t first, uint64_t count,
                                  const float* __restrict__ Y, float* __restrict__ T) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x) {
     PathDesc d;
     fetch_path(B, n, list, first + k, d);
-    float2* To = reinterpret_cast<float2*>(T) + d.g * (uint64_t)B.n_max;
-    for (int s = 0; s < n; ++s) {
-      float t0 = 0.5f, t1 = 0.5f;
-      if (s < 4 && !(d.flags & ST_INVALID)) {
-        const float y0 = Y[k * kMlpOut + 2 * s], y1 = Y[k * kMlpOut + 2 * s + 1];
-        const bool edge = S.aux[kAux * d.ids[s] + 2] != 0.f;
-        if (isfinite(y0) && fabsf(y0) < 1e3f) t0 = y0;
-        if (!edge && isfinite(y1) && fabsf(y1) < 1e3f) t1 = y1;
-      }
-      To[s] = make_float2(t0, t1);
-    }
+    float y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) y[i] = Y[k * kMlpOut + i];
+    write_start(d.n, !(d.flags & ST_INVALID), edge_mask(S, d), y,
+                reinterpret_cast<float2*>(T) + d.g * (uint64_t)B.n_max);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Fused, persistent inference for the learned start (one CTA per SM).
+// Fused, persistent inference for the learned start (two CTAs per SM).
 //
 // Per tile of 128 paths: features are computed straight into the shared
 // activation tile (K-major, K = 64), then four layers run on the tensor cores
 // with the accumulator in TMEM; each epilogue adds the bias, applies GELU and
 // writes the BF16 activations back into the same tile (K = 256) for the next
-// layer; the last one writes the starting parameters into T.  The weights
-// stream through two 32 KB shared buffers as 13 chunks per tile (64 input
-// columns each, pre-tiled in global memory so that a chunk is one contiguous
-// TMA bulk copy), prefetched one chunk ahead: thread 0 waits for the MMAs that
-// last read a buffer before refilling it.  All waits are bounded.
+// layer; the last one writes the starting parameters into T.  The weights are
+// pre-tiled in global memory as 13 chunks of 64 input columns (K-major core
+// matrices, row groups of 8 outputs contiguous), so the 128-output half of a
+// chunk is one contiguous 16 KB block: they stream through two 16 KB shared
+// buffers as 22 units per tile (a half chunk for layers 1-3, each MMA N = 128
+// into its half of the TMEM accumulator; whole 2 KB chunks for the output
+// layer), prefetched one unit ahead: thread 0 waits for the MMAs that last read
+// a buffer before refilling it.  A CTA's steps are serial -- features, MMAs,
+// CUDA-core epilogue -- so the kernel is sized (99 KB of shared memory, 256
+// TMEM columns, 106 registers) for two CTAs per SM, whose phases interleave.
+// All waits are bounded.
 // ---------------------------------------------------------------------------
 constexpr int kInferThreads = 256;
+constexpr int kInferCtasPerSm = 2;
 constexpr int kChunksPerTile = 13;  // W1: 1, W2: 4, W3: 4, W4: 4 chunks of 64 input columns
+constexpr int kUnitsPerTile = 22;   // streamed units: W1 2 halves, W2 and W3 8 halves each, W4 4 chunks
 
 __host__ __device__ constexpr int chunk_layer(int q) { return q == 0 ? 0 : (q <= 4 ? 1 : (q <= 8 ? 2 : 3)); }
 __host__ __device__ constexpr int chunk_col(int q) { return q == 0 ? 0 : (q - 1) % 4; }
 __host__ __device__ constexpr uint32_t chunk_bytes(int q) { return chunk_layer(q) == 3 ? 16u * 64u * 2u : 256u * 64u * 2u; }
 __host__ __device__ constexpr uint32_t chunk_offset(int q) {
   return q <= 8 ? (uint32_t)q * 32768u : 9u * 32768u + (uint32_t)(q - 9) * 2048u;
+}
+
+// Unit u of a tile: (layer, input-column chunk, output half).  Layers 1-3 go chunk by chunk, both halves
+// of a chunk in turn; the output layer (16 outputs) takes whole chunks.
+__host__ __device__ constexpr int unit_layer(int u) { return u < 2 ? 0 : (u < 10 ? 1 : (u < 18 ? 2 : 3)); }
+__host__ __device__ constexpr int unit_col(int u) {
+  return u < 2 ? 0 : (u < 10 ? (u - 2) / 2 : (u < 18 ? (u - 10) / 2 : u - 18));
+}
+__host__ __device__ constexpr int unit_half(int u) { return u < 18 ? u % 2 : 0; }
+__host__ __device__ constexpr bool unit_ends_layer(int u) { return u == 1 || u == 9 || u == 17 || u == 21; }
+__host__ __device__ constexpr int unit_chunk(int u) {
+  return unit_layer(u) == 0 ? 0 : 1 + (unit_layer(u) - 1) * 4 + unit_col(u);
+}
+__host__ __device__ constexpr uint32_t unit_bytes(int u) { return unit_layer(u) == 3 ? 16u * 64u * 2u : 128u * 64u * 2u; }
+__host__ __device__ constexpr uint32_t unit_offset(int u) {
+  return chunk_offset(unit_chunk(u)) + (uint32_t)unit_half(u) * 16384u;
 }
 
 // bf16 parameter copy ([out][in] per layer) -> chunked K-major tiles
@@ -436,14 +484,32 @@ __global__ void mlp_tile_weights_kernel(const __nv_bfloat16* __restrict__ wb, __
 
 struct InferSmem {
   unsigned char act[128 * 256 * 2];
-  unsigned char wbuf[2][256 * 64 * 2];
+  unsigned char wbuf[2][128 * 64 * 2];
   float bias[3 * 256 + 16];
+  uint64_t row_g[128];     // the tile's paths: global index,
+  uint32_t row_info[128];  // order | (sequence usable) << 8 | edge mask << 16 (order 0: no path)
   uint64_t full[2], done[2], layer;
   uint32_t tmem;
   int fail;
 };
 
-__global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S, BatchDev B, int n,
+// Path source, fixed per launch: kSrcEnum, an exhaustive batch's enumeration of order n; kSrcRec, a
+// bucket of records of order n <= kMaxBfgsOrder (the ids in the record); kSrcRecDecode, a bucket of
+// longer sequences (ids decoded from the global index).
+enum { kSrcEnum = 0, kSrcRec = 1, kSrcRecDecode = 2 };
+
+template <int kSrc>
+__device__ __forceinline__ void infer_fetch(const BatchDev& B, int n, const PathRec* list, uint64_t j, PathDesc& d) {
+  if constexpr (kSrc == kSrcEnum) {
+    decode_exhaustive_order(B, n, j, d);
+  } else {
+    load_rec(list, j, d);
+    if constexpr (kSrc == kSrcRecDecode) decode_global(B, d.g, d);
+  }
+}
+
+template <int kSrc>
+__global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kernel(SceneDev S, BatchDev B, int n,
                                                                      const PathRec* __restrict__ list, uint64_t count,
                                                                      float inv_scale,
                                                                      const __nv_bfloat16* __restrict__ wt,
@@ -454,7 +520,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t n_tiles = (count + 127) / 128;
   const uint64_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const uint64_t total_q = my_tiles * kChunksPerTile;
+  const uint64_t total_q = my_tiles * kUnitsPerTile;
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&sm.full[b], 1);
@@ -481,8 +547,8 @@ __global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S,
   const char* wsrc = reinterpret_cast<const char*>(wt);
   uint32_t full_ph[2] = {0u, 0u}, done_ph[2] = {0u, 0u}, layer_ph = 0u;
   if (tid == 0 && total_q > 0) {
-    tc::mbar_expect_tx(&sm.full[0], chunk_bytes(0));
-    tc::bulk_g2s(sm.wbuf[0], wsrc + chunk_offset(0), chunk_bytes(0), &sm.full[0]);
+    tc::mbar_expect_tx(&sm.full[0], unit_bytes(0));
+    tc::bulk_g2s(sm.wbuf[0], wsrc + unit_offset(0), unit_bytes(0), &sm.full[0]);
   }
   uint64_t q = 0;
   for (uint64_t ti = 0; ti < my_tiles; ++ti) {
@@ -492,11 +558,14 @@ __global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S,
       __nv_bfloat16 f[kMlpIn];
       if (first + tid < count) {
         PathDesc d;
-        fetch_path(B, n, list, first + tid, d);
+        infer_fetch<kSrc>(B, n, list, first + tid, d);
         path_features(S, d, inv_scale, f, nullptr);
+        sm.row_g[tid] = d.g;
+        sm.row_info[tid] = (uint32_t)d.n | (d.flags & ST_INVALID ? 0u : 1u << 8) | (edge_mask(S, d) << 16);
       } else {
 #pragma unroll
         for (int k = 0; k < kMlpIn; ++k) f[k] = __float2bfloat16(0.f);
+        sm.row_info[tid] = 0u;
       }
 #pragma unroll
       for (int g8 = 0; g8 < kMlpIn / 8; ++g8)
@@ -505,9 +574,9 @@ __global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S,
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    for (int lq = 0; lq < kChunksPerTile; ++lq, ++q) {
+    for (int lq = 0; lq < kUnitsPerTile; ++lq, ++q) {
       const int b = (int)(q & 1);
-      const int layer = chunk_layer(lq), c = chunk_col(lq);
+      const int layer = unit_layer(lq), c = unit_col(lq), h = unit_half(lq);
       if (tid == 0) {
         // refill the other buffer with the next chunk once the MMAs that read it (chunk q - 1) are done
         if (q + 1 < total_q) {
@@ -516,28 +585,28 @@ __global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S,
             if (!tc::mbar_wait(&sm.done[nb], done_ph[nb], kWaitTries)) sm.fail = 1;
             done_ph[nb] ^= 1u;
           }
-          const int nq = (lq + 1) % kChunksPerTile;
-          tc::mbar_expect_tx(&sm.full[nb], chunk_bytes(nq));
-          tc::bulk_g2s(sm.wbuf[nb], wsrc + chunk_offset(nq), chunk_bytes(nq), &sm.full[nb]);
+          const int nq = (lq + 1) % kUnitsPerTile;
+          tc::mbar_expect_tx(&sm.full[nb], unit_bytes(nq));
+          tc::bulk_g2s(sm.wbuf[nb], wsrc + unit_offset(nq), unit_bytes(nq), &sm.full[nb]);
         }
         if (!tc::mbar_wait(&sm.full[b], full_ph[b], kWaitTries)) sm.fail = 1;
         full_ph[b] ^= 1u;
         tc::fence_after_sync();
         const uint32_t K_act = layer == 0 ? 64u : 256u;
-        const uint32_t N = layer == 3 ? 16u : 256u;
+        const uint32_t N = layer == 3 ? 16u : 128u;
         const uint32_t a0 = tc::smem_u32(sm.act), w0 = tc::smem_u32(sm.wbuf[b]);
         if (!sm.fail) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(c * 8 + 2 * kk) * 128u, 128u, (K_act / 8u) * 128u);
             const uint64_t bd = tc::smem_desc(w0 + (uint32_t)(2 * kk) * 128u, 128u, 8u * 128u);
-            tc::mma_bf16(tmem, ad, bd, tc::idesc_bf16(128, N), (c > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_bf16(tmem + (uint32_t)h * 128u, ad, bd, tc::idesc_bf16(128, N), (c > 0 || kk > 0) ? 1u : 0u);
           }
         }
         tc::mma_commit(&sm.done[b]);
-        if (layer == 0 || c == 3) tc::mma_commit(&sm.layer);
+        if (unit_ends_layer(lq)) tc::mma_commit(&sm.layer);
       }
-      if (!(layer == 0 || c == 3)) continue;
+      if (!unit_ends_layer(lq)) continue;
       // end of a layer: wait for its MMAs, then the epilogue
       if (!tc::mbar_wait(&sm.layer, layer_ph, kWaitTries)) sm.fail = 1;
       layer_ph ^= 1u;
@@ -546,32 +615,32 @@ __global__ void __launch_bounds__(kInferThreads, 1) mlp_infer_kernel(SceneDev S,
       const int row = rg * 32 + lane;
       if (layer < 3) {
         const int c0 = (warp >> 2) * 128;
-        for (int cc = c0; cc < c0 + 128; cc += 16) {
-          float v[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(rg * 32) << 16) + (uint32_t)cc, v);
-          __nv_bfloat16 h[16];
+        const float* bias = sm.bias + layer * 256;
+        for (int cc = c0; cc < c0 + 128; cc += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(rg * 32) << 16) + (uint32_t)cc, v);
 #pragma unroll
-          for (int k = 0; k < 16; ++k) h[k] = __float2bfloat16(gelu(v[k] + sm.bias[layer * 256 + cc + k]));
-          *reinterpret_cast<uint4*>(sm.act + tc::kmajor_offset(row, cc, 256)) = reinterpret_cast<uint4*>(h)[0];
-          *reinterpret_cast<uint4*>(sm.act + tc::kmajor_offset(row, cc + 8, 256)) = reinterpret_cast<uint4*>(h)[1];
+          for (int g8 = 0; g8 < 4; ++g8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int c = g8 * 8 + 2 * k;
+              const __nv_bfloat162 p = __floats2bfloat162_rn(gelu(v[c] + bias[cc + c]), gelu(v[c + 1] + bias[cc + c + 1]));
+              w[k] = *reinterpret_cast<const uint32_t*>(&p);
+            }
+            *reinterpret_cast<uint4*>(sm.act + tc::kmajor_offset(row, cc + g8 * 8, 256)) = make_uint4(w[0], w[1], w[2], w[3]);
+          }
         }
       } else if (warp < 4) {
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(rg * 32) << 16), v);
-        if (first + row < count) {
-          PathDesc d;
-          fetch_path(B, n, list, first + row, d);
-          float2* To = reinterpret_cast<float2*>(T) + d.g * (uint64_t)B.n_max;
-          for (int s = 0; s < n; ++s) {
-            float t0 = 0.5f, t1 = 0.5f;
-            if (s < 4 && !(d.flags & ST_INVALID)) {
-              const float y0 = v[2 * s] + sm.bias[768 + 2 * s], y1 = v[2 * s + 1] + sm.bias[768 + 2 * s + 1];
-              const bool edge = S.aux[kAux * d.ids[s] + 2] != 0.f;
-              if (isfinite(y0) && fabsf(y0) < 1e3f) t0 = y0;
-              if (!edge && isfinite(y1) && fabsf(y1) < 1e3f) t1 = y1;
-            }
-            To[s] = make_float2(t0, t1);
-          }
+        const uint32_t info = sm.row_info[row];
+        if (info & 0xFFu) {
+          float y[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) y[i] = v[i] + sm.bias[768 + i];
+          write_start((int)(info & 0xFFu), (info >> 8) & 1u, info >> 16, y,
+                      reinterpret_cast<float2*>(T) + sm.row_g[row] * (uint64_t)B.n_max);
         }
       }
       tc::fence_async_smem();
@@ -603,13 +672,18 @@ cudaError_t launch_mlp_infer(const SceneDev& S, const BatchDev& B, int n, const 
   static bool attr = false;
   const int smem = (int)sizeof(InferSmem);
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+    for (auto k : {mlp_infer_kernel<kSrcEnum>, mlp_infer_kernel<kSrcRec>, mlp_infer_kernel<kSrcRecDecode>}) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+    }
     attr = true;
   }
   const uint64_t tiles = (count + 127) / 128;
-  const unsigned grid = (unsigned)(tiles < (uint64_t)n_sm ? tiles : (uint64_t)n_sm);
-  mlp_infer_kernel<<<grid, kInferThreads, smem, stream>>>(S, B, n, list, count, inv_scale, wt, params, T, err);
+  const uint64_t cap = (uint64_t)n_sm * kInferCtasPerSm;
+  const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+  auto kern = list == nullptr ? mlp_infer_kernel<kSrcEnum>
+                              : (n > kMaxBfgsOrder ? mlp_infer_kernel<kSrcRecDecode> : mlp_infer_kernel<kSrcRec>);
+  kern<<<grid, kInferThreads, smem, stream>>>(S, B, n, list, count, inv_scale, wt, params, T, err);
   count_launch();
   return cudaGetLastError();
 }
