@@ -577,34 +577,39 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
     for (int lq = 0; lq < kUnitsPerTile; ++lq, ++q) {
       const int b = (int)(q & 1);
       const int layer = unit_layer(lq), c = unit_col(lq), h = unit_half(lq);
-      if (tid == 0) {
-        // refill the other buffer with the next chunk once the MMAs that read it (chunk q - 1) are done
-        if (q + 1 < total_q) {
-          const int nb = b ^ 1;
-          if (q >= 1) {
-            if (!tc::mbar_wait(&sm.done[nb], done_ph[nb], kWaitTries)) sm.fail = 1;
-            done_ph[nb] ^= 1u;
+      // warp 0 issues the copies and MMAs: lane 0 works while its warp-mates wait at the warp
+      // barrier, so that their mbarrier polls below never hold up the issuing lane
+      if (warp == 0) {
+        if (lane == 0) {
+          // refill the other buffer with the next chunk once the MMAs that read it (chunk q - 1) are done
+          if (q + 1 < total_q) {
+            const int nb = b ^ 1;
+            if (q >= 1) {
+              if (!tc::mbar_wait(&sm.done[nb], done_ph[nb], kWaitTries)) sm.fail = 1;
+              done_ph[nb] ^= 1u;
+            }
+            const int nq = (lq + 1) % kUnitsPerTile;
+            tc::mbar_expect_tx(&sm.full[nb], unit_bytes(nq));
+            tc::bulk_g2s(sm.wbuf[nb], wsrc + unit_offset(nq), unit_bytes(nq), &sm.full[nb]);
           }
-          const int nq = (lq + 1) % kUnitsPerTile;
-          tc::mbar_expect_tx(&sm.full[nb], unit_bytes(nq));
-          tc::bulk_g2s(sm.wbuf[nb], wsrc + unit_offset(nq), unit_bytes(nq), &sm.full[nb]);
-        }
-        if (!tc::mbar_wait(&sm.full[b], full_ph[b], kWaitTries)) sm.fail = 1;
-        full_ph[b] ^= 1u;
-        tc::fence_after_sync();
-        const uint32_t K_act = layer == 0 ? 64u : 256u;
-        const uint32_t N = layer == 3 ? 16u : 128u;
-        const uint32_t a0 = tc::smem_u32(sm.act), w0 = tc::smem_u32(sm.wbuf[b]);
-        if (!sm.fail) {
+          if (!tc::mbar_wait(&sm.full[b], full_ph[b], kWaitTries)) sm.fail = 1;
+          full_ph[b] ^= 1u;
+          tc::fence_after_sync();
+          const uint32_t K_act = layer == 0 ? 64u : 256u;
+          const uint32_t N = layer == 3 ? 16u : 128u;
+          const uint32_t a0 = tc::smem_u32(sm.act), w0 = tc::smem_u32(sm.wbuf[b]);
+          if (!sm.fail) {
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(c * 8 + 2 * kk) * 128u, 128u, (K_act / 8u) * 128u);
-            const uint64_t bd = tc::smem_desc(w0 + (uint32_t)(2 * kk) * 128u, 128u, 8u * 128u);
-            tc::mma_bf16(tmem + (uint32_t)h * 128u, ad, bd, tc::idesc_bf16(128, N), (c > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(c * 8 + 2 * kk) * 128u, 128u, (K_act / 8u) * 128u);
+              const uint64_t bd = tc::smem_desc(w0 + (uint32_t)(2 * kk) * 128u, 128u, 8u * 128u);
+              tc::mma_bf16(tmem + (uint32_t)h * 128u, ad, bd, tc::idesc_bf16(128, N), (c > 0 || kk > 0) ? 1u : 0u);
+            }
           }
+          tc::mma_commit(&sm.done[b]);
+          if (unit_ends_layer(lq)) tc::mma_commit(&sm.layer);
         }
-        tc::mma_commit(&sm.done[b]);
-        if (unit_ends_layer(lq)) tc::mma_commit(&sm.layer);
+        __syncwarp();
       }
       if (!unit_ends_layer(lq)) continue;
       // end of a layer: wait for its MMAs, then the epilogue
