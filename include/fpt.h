@@ -122,6 +122,9 @@ void fpt_default_params(fpt_solve_params* p);
  * device workspace.  Returns FPT_ECUDA if the device cannot be used. */
 fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream);
 void fpt_destroy(fpt_ctx* ctx);
+/* Switch the context's stream.  No synchronisation (legal inside a stream
+ * capture): work issued on the old stream, uploads included, must be complete
+ * (fpt_sync) or otherwise ordered before the new stream's next use. */
 fpt_status fpt_set_stream(fpt_ctx* ctx, void* cuda_stream);
 /* Message for the last error on this context (static storage, never NULL). */
 const char* fpt_last_error(const fpt_ctx* ctx);
@@ -133,12 +136,17 @@ fpt_status fpt_sync(fpt_ctx* ctx);
  * FPT_EDGE); verts: host double [n_obj][3][3].  The library builds object
  * records in FP32 (hi + lo parts) and FP64 on the device, relative to the
  * scene centre.  FPT_EINVAL on non-finite vertices, a zero-area plane or a
- * zero-length edge (< 1e-9 m), or n_obj outside [1, 65535].  Synchronous. */
+ * zero-length edge (< 1e-9 m), or n_obj outside [1, 65535].  The records
+ * are built on the host and copied asynchronously on the context's stream
+ * (ordered before every later call on it; the host inputs may be reused on
+ * return, the scene keeps its own copies until fpt_scene_free). */
 fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* verts, int32_t n_obj,
                             fpt_scene** out);
 void fpt_scene_free(fpt_scene* scene);
 /* TX and RX positions (x_0 and x_{n+1} of Eq. 2): host double [n][3].
- * Copied to the device.  FPT_EINVAL on non-finite input or n < 1. */
+ * Copied to the device asynchronously on the context's stream, as the scene.
+ * Replacing the endpoints of a scene frees its old device copies first (which
+ * waits for the device).  FPT_EINVAL on non-finite input or n < 1. */
 fpt_status fpt_set_endpoints(fpt_scene* scene, const double* tx, int32_t n_tx, const double* rx, int32_t n_rx);
 
 /* Candidate sequences (Sec. III).
@@ -156,8 +164,9 @@ fpt_status fpt_set_endpoints(fpt_scene* scene, const double* tx, int32_t n_tx, c
  * FPT_EINVAL on lo < 1, hi > 10, lo > hi, empty alphabet or ids out of range
  * (host-checked arrays only).  A batch records the object types of the
  * scene it was built for; calls that pass a scene with other types return
- * FPT_EINVAL.  Seeded and explicit batches are bucketed on the device by
- * (order, interaction-type pattern) on their first use (synchronous). */
+ * FPT_EINVAL.  The alphabet tables are copied asynchronously on the
+ * context's stream.  Seeded and explicit batches are bucketed on the device
+ * by (order, interaction-type pattern) on their first use (synchronous). */
 fpt_status fpt_batch_exhaustive(fpt_ctx* ctx, const fpt_scene* scene, const int32_t* alphabet, int32_t n_alpha,
                                 int32_t order_lo, int32_t order_hi, fpt_batch** out);
 fpt_status fpt_batch_seeded(fpt_ctx* ctx, const fpt_scene* scene, const int32_t* alphabet, int32_t n_alpha,

@@ -104,6 +104,10 @@ struct fpt_scene {
   double* d_rx64 = nullptr;
   float* d_occ = nullptr;  // planar objects as occluders (kOcc floats each)
   int n_occ = 0;
+  // host sources of the asynchronous uploads, kept until the device buffers are freed (cudaFree
+  // waits for the device, so no copy from them is still pending when they go)
+  std::vector<float> h_rec32, h_aux, h_reclo, h_occ, h_tx32, h_rx32;
+  std::vector<double> h_rec64, h_tx64, h_rx64;
 };
 
 struct fpt_batch {
@@ -112,6 +116,7 @@ struct fpt_batch {
   int32_t* d_alphabet = nullptr;
   int32_t* d_type_pos = nullptr;  // alphabet positions of the reflectors, then of the edges
   std::vector<uint8_t> types;     // object types of the scene the batch was built for
+  std::vector<int32_t> h_alphabet, h_type_pos;  // host sources of the uploads (as in fpt_scene)
   // (order, pattern) buckets of seeded / explicit batches (built on first use)
   bool bucketed = false;
   PathRec* d_lists = nullptr;
@@ -261,6 +266,8 @@ void fpt_destroy(fpt_ctx* ctx) {
 
 fpt_status fpt_set_stream(fpt_ctx* ctx, void* cuda_stream) {
   if (!ctx) return FPT_EINVAL;
+  // no synchronisation here (the call is legal inside a stream capture): the caller orders the old
+  // stream's work, uploads included, before the new stream's
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   return FPT_OK;
 }
@@ -311,8 +318,12 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
   s->n_obj = n_obj;
   s->types.assign(types, types + n_obj);
   for (int c = 0; c < 3; ++c) s->centre[c] = 0.5 * (lo[c] + hi[c]);
-  std::vector<float> rec32((size_t)n_obj * kRec32), aux((size_t)n_obj * kAux), reclo((size_t)n_obj * kRecLo);
-  std::vector<double> rec64((size_t)n_obj * kRec64);
+  std::vector<float>&rec32 = s->h_rec32, &aux = s->h_aux, &reclo = s->h_reclo;
+  std::vector<double>& rec64 = s->h_rec64;
+  rec32.assign((size_t)n_obj * kRec32, 0.f);
+  aux.assign((size_t)n_obj * kAux, 0.f);
+  reclo.assign((size_t)n_obj * kRecLo, 0.f);
+  rec64.assign((size_t)n_obj * kRec64, 0.0);
   for (int k = 0; k < n_obj; ++k) {
     const double* v = verts + 9 * k;
     double b[3], a1[3], a2[3];
@@ -348,7 +359,7 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
     aux[kAux * k + 3] = 0.f;
   }
   // occluder records of the planar objects: centred origin, unit normal, dual basis of (a1, a2)
-  std::vector<float> occ;
+  std::vector<float>& occ = s->h_occ;
   for (int k = 0; k < n_obj; ++k) {
     if (types[k] != FPT_QUAD) continue;
     const double* v = verts + 9 * k;
@@ -377,15 +388,21 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess && s->n_occ) e = cudaMalloc(&s->d_occ, occ.size() * sizeof(float));
   if (e == cudaSuccess && s->n_occ)
-    e = cudaMemcpy(s->d_occ, occ.data(), occ.size() * sizeof(float), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(s->d_occ, occ.data(), occ.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rec32, rec32.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rec64, rec64.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_aux, aux.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_reclo, reclo.size() * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemcpy(s->d_reclo, reclo.data(), reclo.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(s->d_rec32, rec32.data(), rec32.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(s->d_rec64, rec64.data(), rec64.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(s->d_aux, aux.data(), aux.size() * sizeof(float), cudaMemcpyHostToDevice);
+  // copies on the context's stream, ordered before every later call on it, with no wait for the
+  // device; their host sources live in the scene until it is freed
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_reclo, reclo.data(), reclo.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_rec32, rec32.data(), rec32.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_rec64, rec64.data(), rec64.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_aux, aux.data(), aux.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) {
     fpt_scene_free(s);
     return fail(ctx, FPT_ECUDA, "scene upload: %s", cudaGetErrorString(e));
@@ -408,23 +425,27 @@ void fpt_scene_free(fpt_scene* s) {
   delete s;
 }
 
-static cudaError_t upload_points(const double* p, int n, const double* centre, float** d32, double** d64) {
-  std::vector<float> h32((size_t)n * kEnd32);
-  std::vector<double> h64((size_t)n * 3);
+// Upload points (recentred, FP32 pairs and FP64) asynchronously on `stream`.  h32 / h64 hold the host
+// sources until the next upload or the scene's release; the old device buffers are freed first
+// (cudaFree waits for the device), so no copy from the old sources is pending when they are refilled.
+static cudaError_t upload_points(const double* p, int n, const double* centre, float** d32, double** d64,
+                                 std::vector<float>& h32, std::vector<double>& h64, cudaStream_t stream) {
+  cudaFree(*d32);
+  cudaFree(*d64);
+  *d32 = nullptr;
+  *d64 = nullptr;
+  h32.assign((size_t)n * kEnd32, 0.f);
+  h64.assign((size_t)n * 3, 0.0);
   for (int i = 0; i < n; ++i)
     for (int c = 0; c < 3; ++c) {
       double x = p[3 * i + c] - centre[c];
       h64[3 * i + c] = x;
       split(x, h32[kEnd32 * i + c], h32[kEnd32 * i + 3 + c]);
     }
-  cudaFree(*d32);
-  cudaFree(*d64);
-  *d32 = nullptr;
-  *d64 = nullptr;
   cudaError_t e = cudaMalloc(d32, h32.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(d64, h64.size() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemcpy(*d32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(*d64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(*d32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(*d64, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice, stream);
   return e;
 }
 
@@ -437,8 +458,8 @@ fpt_status fpt_set_endpoints(fpt_scene* s, const double* tx, int32_t n_tx, const
   for (int i = 0; i < 3 * n_rx; ++i)
     if (!std::isfinite(rx[i])) return fail(ctx, FPT_EINVAL, "non-finite RX");
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
-  CUDA_OR_FAIL(ctx, upload_points(tx, n_tx, s->centre, &s->d_tx32, &s->d_tx64));
-  CUDA_OR_FAIL(ctx, upload_points(rx, n_rx, s->centre, &s->d_rx32, &s->d_rx64));
+  CUDA_OR_FAIL(ctx, upload_points(tx, n_tx, s->centre, &s->d_tx32, &s->d_tx64, s->h_tx32, s->h_tx64, ctx->stream));
+  CUDA_OR_FAIL(ctx, upload_points(rx, n_rx, s->centre, &s->d_rx32, &s->d_rx64, s->h_rx32, s->h_rx64, ctx->stream));
   s->n_tx = n_tx;
   s->n_rx = n_rx;
   return FPT_OK;
@@ -449,7 +470,8 @@ fpt_status fpt_set_endpoints(fpt_scene* s, const double* tx, int32_t n_tx, const
 // ---------------------------------------------------------------------------
 static fpt_status make_alphabet(fpt_ctx* ctx, const fpt_scene* s, const int32_t* alphabet, int32_t n_alpha,
                                 fpt_batch* b) {
-  std::vector<int32_t> a;
+  std::vector<int32_t>& a = b->h_alphabet;
+  a.clear();
   if (alphabet) {
     if (n_alpha < 1) return fail(ctx, FPT_EINVAL, "empty alphabet");
     a.assign(alphabet, alphabet + n_alpha);
@@ -460,18 +482,21 @@ static fpt_status make_alphabet(fpt_ctx* ctx, const fpt_scene* s, const int32_t*
   }
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   CUDA_OR_FAIL(ctx, cudaMalloc(&b->d_alphabet, a.size() * sizeof(int32_t)));
-  CUDA_OR_FAIL(ctx, cudaMemcpy(b->d_alphabet, a.data(), a.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(ctx, cudaMemcpyAsync(b->d_alphabet, a.data(), a.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                    ctx->stream));
   b->dev.alphabet = b->d_alphabet;
   b->dev.n_alpha = (int)a.size();
   // positions of the reflectors, then of the edges: the exhaustive enumeration by pattern
-  std::vector<int32_t> pos;
+  std::vector<int32_t>& pos = b->h_type_pos;
+  pos.clear();
   for (int pass = 0; pass < 2; ++pass)
     for (size_t k = 0; k < a.size(); ++k)
       if ((s->types[a[k]] == FPT_QUAD) == (pass == 0)) pos.push_back((int32_t)k);
   b->dev.n_alpha_quad = 0;
   for (int32_t o : a) b->dev.n_alpha_quad += s->types[o] == FPT_QUAD;
   CUDA_OR_FAIL(ctx, cudaMalloc(&b->d_type_pos, pos.size() * sizeof(int32_t)));
-  CUDA_OR_FAIL(ctx, cudaMemcpy(b->d_type_pos, pos.data(), pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(ctx, cudaMemcpyAsync(b->d_type_pos, pos.data(), pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                    ctx->stream));
   b->dev.type_pos = b->d_type_pos;
   b->types = s->types;
   return FPT_OK;

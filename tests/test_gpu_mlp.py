@@ -133,20 +133,29 @@ def test_learned_start_keeps_parity(ctx):
         check_parity(to_np(out), oracle_solve(sc, ids, order, ti, ri))
 
 
-@pytest.mark.parametrize("seed", [41, 42])
-def test_fused_inference_start_matches_reference(ctx, seed):
-    """The fused tensor-core inference writes the network's prediction as the start (checked with no BFGS steps)."""
+@pytest.mark.parametrize("seed,kind,lo,hi", [(41, "seeded", 1, 5), (42, "seeded", 1, 5), (43, "exhaustive", 1, 3),
+                                              (44, "seeded", 6, 8)])
+def test_fused_inference_start_matches_reference(ctx, seed, kind, lo, hi):
+    """The fused tensor-core inference writes the network's prediction as the start (checked with no BFGS
+    steps), for each path source: bucket records of orders 1-5 (9000 paths, ragged last tile), an
+    exhaustive batch's enumeration, and records of orders 6-8 (ids decoded again; slots 5+ start at 1/2)."""
     params = numpy_params(seed)
     net = fpt.Mlp(ctx, 0, SCALE)
     net.set_params(params)
     net.attach()
     sc = scenes.tiny_scene(seed, n_rx=3)
     scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
-    batch = fpt.Batch.seeded(ctx, scene, seed, 3000, 1, 5)  # 9000 paths: ragged last tile, orders 1-5
+    if kind == "seeded":
+        batch = fpt.Batch.seeded(ctx, scene, seed, 3000, lo, hi)
+        ids, order, ti, ri = oracle.seeded_paths(sc, seed, 3000, lo, hi)
+    else:
+        batch = fpt.Batch.exhaustive(ctx, scene, lo, hi)
+        ids, order, ti, ri = oracle.exhaustive_paths(sc, lo, hi)
     out = fpt.solve(ctx, scene, batch, fpt.default_params(init_mode=1, max_iters=0, polish=0))
     ctx.sync()
     T = out["T"].cpu().numpy()
-    ids, order, ti, ri = oracle.seeded_paths(sc, seed, 3000, 1, 5)
+    keep = (out["status"].cpu().numpy() & fpt.ST_REPEAT) == 0  # repeats are not solved
+    assert keep.sum() > 1000
     Fo, _ = mo.features(sc, ids, order, ti, ri, SCALE)
     Y = mo.forward(params.astype(np.float64), mo.bf16(Fo))["Y"]
     expect = np.full(T.shape, 0.5)
@@ -155,6 +164,6 @@ def test_fused_inference_start_matches_reference(ctx, seed):
             expect[p, s, 0] = Y[p, 2 * s]
             if sc.types[ids[p, s]] == scenes.QUAD:
                 expect[p, s, 1] = Y[p, 2 * s + 1]
-    used = np.arange(T.shape[1])[None, :] < order[:, None]
+    used = (np.arange(T.shape[1])[None, :] < order[:, None]) & keep[:, None]
     err = np.abs(T - expect)[used]
     assert err.max() <= 5e-3 * max(1.0, np.abs(Y).max()), err.max()
