@@ -434,12 +434,10 @@ __global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const PathRec* l
 // ---------------------------------------------------------------------------
 constexpr int kInferThreads = 256;
 constexpr int kInferCtasPerSm = 2;
-constexpr int kChunksPerTile = 13;  // W1: 1, W2: 4, W3: 4, W4: 4 chunks of 64 input columns
-constexpr int kUnitsPerTile = 22;   // streamed units: W1 2 halves, W2 and W3 8 halves each, W4 4 chunks
+constexpr int kUnitsPerTile = 22;  // streamed units: W1 2 halves, W2 and W3 8 halves each, W4 4 chunks
 
-__host__ __device__ constexpr int chunk_layer(int q) { return q == 0 ? 0 : (q <= 4 ? 1 : (q <= 8 ? 2 : 3)); }
-__host__ __device__ constexpr int chunk_col(int q) { return q == 0 ? 0 : (q - 1) % 4; }
-__host__ __device__ constexpr uint32_t chunk_bytes(int q) { return chunk_layer(q) == 3 ? 16u * 64u * 2u : 256u * 64u * 2u; }
+// Chunk q of the tiled weights (W1: 0; W2: 1-4; W3: 5-8; W4: 9-12; 64 input columns each):
+// 32 KB for the 256-output layers, 2 KB for the output layer.
 __host__ __device__ constexpr uint32_t chunk_offset(int q) {
   return q <= 8 ? (uint32_t)q * 32768u : 9u * 32768u + (uint32_t)(q - 9) * 2048u;
 }
@@ -459,6 +457,14 @@ __host__ __device__ constexpr uint32_t unit_bytes(int u) { return unit_layer(u) 
 __host__ __device__ constexpr uint32_t unit_offset(int u) {
   return chunk_offset(unit_chunk(u)) + (uint32_t)unit_half(u) * 16384u;
 }
+// the units of a tile cover the tiled weights once, back to back
+__host__ __device__ constexpr bool units_tile_weights() {
+  for (int u = 0; u + 1 < kUnitsPerTile; ++u)
+    if (unit_offset(u) + unit_bytes(u) != unit_offset(u + 1)) return false;
+  return unit_offset(kUnitsPerTile - 1) + unit_bytes(kUnitsPerTile - 1) == kMlpTiledBytes &&
+         kMlpTiledBytes == 2u * (kMlpHidden * kMlpIn + 2 * kMlpHidden * kMlpHidden + kMlpOut * kMlpHidden);
+}
+static_assert(units_tile_weights(), "weight units");
 
 // bf16 parameter copy ([out][in] per layer) -> chunked K-major tiles
 __global__ void mlp_tile_weights_kernel(const __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt) {
