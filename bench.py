@@ -730,7 +730,8 @@ def e2e(args, sc, ctx, dev, torch, fpt):
         batch.close()
         scene.close()
     return {"value": solved / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": 1e3 * dt / steps, "pipelined": "outputs double-buffered; copies overlap the next step"}
+            "ms_per_step": 1e3 * dt / steps, "pipelined": "outputs double-buffered; copies overlap the next step",
+            "l2": "not flushed: every step writes ~1 GB of outputs (T, L, status), far more than L2"}
 
 
 def main():
