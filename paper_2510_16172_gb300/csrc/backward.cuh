@@ -199,14 +199,11 @@ __global__ void backward_select_kernel(BatchDev B, BackwardCfg cfg, uint64_t n_l
 // FP64 pass over the paths whose FP32 pivots failed: FP64 records, segment
 // vectors, Hessian and VJP, summed straight into the FP64 accumulators.
 template <int N>
-__global__ void __launch_bounds__(kThreads) backward_rescue_kernel(SceneDev S, BatchDev B, BackwardCfg cfg,
-                                                                   const PathRec* __restrict__ list,
-                                                                   const float* __restrict__ T,
-                                                                   const uint8_t* __restrict__ status,
-                                                                   const float* __restrict__ dX,
-                                                                   const float* __restrict__ dLv, double* gacc,
-                                                                   const uint32_t* __restrict__ rescue_list,
-                                                                   const unsigned* __restrict__ rescue_count) {
+__global__ void __launch_bounds__(kThreads, kLongOrderMinBlocks<N>)
+    backward_rescue_kernel(SceneDev S, BatchDev B, BackwardCfg cfg, const PathRec* __restrict__ list,
+        const float* __restrict__ T, const uint8_t* __restrict__ status, const float* __restrict__ dX,
+        const float* __restrict__ dLv, double* gacc, const uint32_t* __restrict__ rescue_list,
+        const unsigned* __restrict__ rescue_count) {
   const uint64_t n = *rescue_count;
   const int n_max = B.n_max;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {

@@ -130,7 +130,7 @@ __device__ __forceinline__ void fetch_path_q(const BatchDev& B, const Tables& tb
                                              PathDesc& d) {
   if constexpr (kSrc == SRC_LIST) {
     load_rec(list, j, d);
-    if constexpr (N > kMaxBfgsOrder) decode_global(B, d.g, d);  // longer records keep g, not the ids
+    if constexpr (N > kMaxBfgsOrder) decode_global<N>(B, d.g, d);  // longer records keep g, not the ids
   } else if constexpr (kSrc == SRC_PATTERN) {
     decode_exhaustive_pattern<N, Q>(B, tb, j, d);
   } else {

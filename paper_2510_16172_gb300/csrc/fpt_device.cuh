@@ -129,13 +129,15 @@ __device__ __forceinline__ uint64_t seeded_draw(uint64_t seed, uint64_t g, int s
   return sm64_mix(seed + 0x9E3779B97F4A7C15ULL * (8ULL * g + (uint64_t)s + 1ULL));
 }
 
-// kN > 0: the order is the compile-time kN.  kN = 0: it is known only at run
-// time, and the slot loop runs over compile-time indices guarded by the order,
-// so that the descriptor still stays in registers (as in decode_global).
-template <int kN = 0>
+// kExact: the order d.n is the compile-time kN.  Otherwise it is known only at
+// run time and at most kN (kMaxOrder when kN = 0): the slot loop runs over
+// compile-time indices guarded by the order, so that the descriptor still stays
+// in registers (as in decode_global).
+template <int kN = 0, bool kExact = false>
 __device__ __forceinline__ void finish_desc(const BatchDev& B, const int* digits, PathDesc& d) {
+  constexpr int kSlotsMax = kN > 0 ? kN : kMaxOrder;
   d.flags = 0;
-  if constexpr (kN > 0) {
+  if constexpr (kExact) {
     for (int j = 0; j < d.n; ++j) {
       int o = B.alphabet[digits[j]];
       d.ids[j] = o;
@@ -143,7 +145,7 @@ __device__ __forceinline__ void finish_desc(const BatchDev& B, const int* digits
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < kMaxOrder; ++j)
+    for (int j = 0; j < kSlotsMax; ++j)
       if (j < d.n) {
         int o = B.alphabet[digits[j]];
         d.ids[j] = o;
@@ -189,11 +191,15 @@ __device__ __forceinline__ void decode_exhaustive_order(const BatchDev& B, int n
         r = qq;
       }
   }
-  finish_desc<kN>(B, digits, d);
+  finish_desc<kN, (kN > 0)>(B, digits, d);
 }
 
-// Any batch: decode global index g.
+// Any batch: decode global index g.  kN > 0: the caller knows that the order is
+// at most kN (a kernel compiled for order kN over a bucket of that order), so
+// the slot loops stop there; kN = 0: any order up to kMaxOrder.
+template <int kN = 0>
 __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, PathDesc& d) {
+  constexpr int kSlotsMax = kN > 0 ? kN : kMaxOrder;
   d.g = g;
   if (B.mode == BATCH_EXPLICIT) {
     int n = B.order[g];
@@ -212,7 +218,7 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
       return;
     }
 #pragma unroll
-    for (int j = 0; j < kMaxOrder; ++j)
+    for (int j = 0; j < kSlotsMax; ++j)
       if (j < n) {
         int o = B.ids[g * (uint64_t)B.n_max + j];
         d.ids[j] = o;
@@ -235,7 +241,7 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
     d.n = n;
     digits[0] = (int)(seeded_draw(B.seed, g, 1) % K);
 #pragma unroll
-    for (int j = 1; j < kMaxOrder; ++j)
+    for (int j = 1; j < kSlotsMax; ++j)
       if (j < n) digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + seeded_draw(B.seed, g, j + 1) % (K - 1)) % K);
   } else {
     int n = B.lo;
@@ -243,14 +249,14 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
     d.n = n;
     r -= B.offset[n];
 #pragma unroll
-    for (int q = kMaxOrder - 1; q >= 0; --q)
+    for (int q = kSlotsMax - 1; q >= 0; --q)
       if (q < n) {
         uint64_t qq = r / K;
         digits[q] = (int)(r - qq * K);
         r = qq;
       }
   }
-  finish_desc(B, digits, d);
+  finish_desc<kN>(B, digits, d);
 }
 
 // Global index g of local index j of an order-n slice, without decoding the
@@ -283,7 +289,7 @@ template <int N>
 __device__ __forceinline__ void fetch_path_n(const BatchDev& B, const PathRec* list, uint64_t j, PathDesc& d) {
   if (list != nullptr) {
     load_rec(list, j, d);
-    if constexpr (N > kMaxBfgsOrder) decode_global(B, d.g, d);
+    if constexpr (N > kMaxBfgsOrder) decode_global<N>(B, d.g, d);
   } else {
     decode_exhaustive_order<N>(B, N, j, d);
   }

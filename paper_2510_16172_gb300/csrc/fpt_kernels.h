@@ -9,6 +9,12 @@
 namespace fpt {
 
 constexpr int kThreads = 128;  // threads per CTA for all path kernels
+// Minimum CTAs per SM for the launch bounds of the per-order kernels that spill at orders above
+// kMaxBfgsOrder (unrolled AD, FP64 polish, FP64 adjoint): 1 there, so that ptxas gives them the
+// full 255 registers instead of settling on a smaller budget and spilling more; unspecified (0)
+// at the register-resident orders.
+template <int N>
+constexpr int kLongOrderMinBlocks = N > kMaxBfgsOrder ? 1 : 0;
 constexpr size_t kMaxSmemBytes = 200 * 1024;  // dynamic shared memory a path kernel may request
 
 // Kernels launched by the calling thread; the API's profiler reads the

@@ -521,14 +521,11 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
 // FP64 polish (validation mode: polish_fp64 = 1)
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kThreads) polish64_kernel(SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local,
-                                                            const PathRec* __restrict__ list, float* __restrict__ T,
-                                                            float* __restrict__ X, float* __restrict__ Lout,
-                                                            uint8_t* __restrict__ status, float* __restrict__ rho_out,
-                                                            uint8_t* __restrict__ mask_out,
-                                                            float* __restrict__ bdist_out, int use_smem,
-                                                            const uint32_t* __restrict__ rescue_list,
-                                                            const unsigned* __restrict__ rescue_count) {
+__global__ void __launch_bounds__(kThreads, kLongOrderMinBlocks<N>)
+    polish64_kernel(SceneDev S, BatchDev B, PolishCfg cfg, uint64_t n_local, const PathRec* __restrict__ list,
+        float* __restrict__ T, float* __restrict__ X, float* __restrict__ Lout, uint8_t* __restrict__ status,
+        float* __restrict__ rho_out, uint8_t* __restrict__ mask_out, float* __restrict__ bdist_out, int use_smem,
+        const uint32_t* __restrict__ rescue_list, const unsigned* __restrict__ rescue_count) {
   constexpr int M = 2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const double* rec64 = S.rec64;

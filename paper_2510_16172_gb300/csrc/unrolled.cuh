@@ -157,13 +157,10 @@ __device__ __forceinline__ void grad_reverse(const Geo<N>& G, const float (&t)[N
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads) unrolled_grad_kernel(SceneDev S, BatchDev B, int K, int R,
-                                                                  uint64_t n_local, const PathRec* __restrict__ list,
-                                                                  const float* __restrict__ dX,
-                                                                  const float* __restrict__ dLv, float dl_all,
-                                                                  double* gacc, float* __restrict__ tape,
-                                                                  float* __restrict__ T_out,
-                                                                  uint8_t* __restrict__ status_out, bool sm) {
+__global__ void __launch_bounds__(kThreads, kLongOrderMinBlocks<N>)
+    unrolled_grad_kernel(SceneDev S, BatchDev B, int K, int R, uint64_t n_local, const PathRec* __restrict__ list,
+        const float* __restrict__ dX, const float* __restrict__ dLv, float dl_all, double* gacc,
+        float* __restrict__ tape, float* __restrict__ T_out, uint8_t* __restrict__ status_out, bool sm) {
   constexpr unsigned Q = kAllQuads<N>;
   constexpr int M = 2 * N;
   constexpr int HP = M * (M + 1) / 2;
