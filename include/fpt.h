@@ -56,7 +56,7 @@ typedef enum {
   FPT_ENOMEM = 2,       /* device or host allocation failed */
   FPT_ECUDA = 3,        /* a CUDA runtime call failed */
   FPT_EDEVICE = 4,      /* a kernel reported an error through the device error word */
-  FPT_EUNSUPPORTED = 5  /* valid request outside what this build supports */
+  FPT_EUNSUPPORTED = 5  /* valid request outside what the library supports */
 } fpt_status;
 
 enum { FPT_QUAD = 0, FPT_EDGE = 1 };
