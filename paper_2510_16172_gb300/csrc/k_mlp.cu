@@ -371,7 +371,6 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __r
     dst[i] = __float2bfloat16(src[i]);
 }
 
-// learned start: T[g] slot s < min(n, 4) from Y (edges keep t2 = 1/2; non-finite or |t| > 1e3 -> 1/2)
 // Starting parameters of a path of order n from the network's outputs y (slots 1-4; an edge's
 // second parameter -- bit s of `edges` -- and the later slots start at 1/2, and so does an output
 // that is not finite or beyond 1e3, and every slot of an invalid sequence).  The slot loop runs over
@@ -400,6 +399,7 @@ __device__ __forceinline__ unsigned edge_mask(const SceneDev& S, const PathDesc&
   return m;
 }
 
+// learned start from unfused network outputs Y [count][16] (local indices first .. first + count)
 __global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const PathRec* list, uint64_t first, uint64_t count,
                                  const float* __restrict__ Y, float* __restrict__ T) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x) {
@@ -426,11 +426,11 @@ __global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const PathRec* l
 // chunk is one contiguous 16 KB block: they stream through two 16 KB shared
 // buffers as 22 units per tile (a half chunk for layers 1-3, each MMA N = 128
 // into its half of the TMEM accumulator; whole 2 KB chunks for the output
-// layer), prefetched one unit ahead: thread 0 waits for the MMAs that last read
-// a buffer before refilling it.  A CTA's steps are serial -- features, MMAs,
-// CUDA-core epilogue -- so the kernel is sized (99 KB of shared memory, 256
-// TMEM columns, 106 registers) for two CTAs per SM, whose phases interleave.
-// All waits are bounded.
+// layer), prefetched one unit ahead: lane 0 of warp 0 waits for the MMAs that
+// last read a buffer before refilling it.  A CTA's steps are serial -- features,
+// MMAs, CUDA-core epilogue -- so the kernel is sized (103 KB of shared memory,
+// 256 TMEM columns, at most 117 registers) for two CTAs per SM, whose phases
+// interleave.  All waits are bounded.
 // ---------------------------------------------------------------------------
 constexpr int kInferThreads = 256;
 constexpr int kInferCtasPerSm = 2;
