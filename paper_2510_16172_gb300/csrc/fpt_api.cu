@@ -318,7 +318,9 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
   s->n_obj = n_obj;
   s->types.assign(types, types + n_obj);
   for (int c = 0; c < 3; ++c) s->centre[c] = 0.5 * (lo[c] + hi[c]);
-  std::vector<float>&rec32 = s->h_rec32, &aux = s->h_aux, &reclo = s->h_reclo;
+  std::vector<float>& rec32 = s->h_rec32;
+  std::vector<float>& aux = s->h_aux;
+  std::vector<float>& reclo = s->h_reclo;
   std::vector<double>& rec64 = s->h_rec64;
   rec32.assign((size_t)n_obj * kRec32, 0.f);
   aux.assign((size_t)n_obj * kAux, 0.f);
