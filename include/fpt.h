@@ -160,7 +160,9 @@ fpt_status fpt_set_endpoints(fpt_scene* scene, const double* tx, int32_t n_tx, c
  *   h(g,s) is splitmix64's output function applied to
  *   seed + 0x9E3779B97F4A7C15 * (8 g + s + 1).
  * Explicit: caller-owned device arrays ids [n][n_max] (object ids),
- *   order [n], tx_idx [n], rx_idx [n].
+ *   order [n], tx_idx [n], rx_idx [n]; n = 0 is an empty batch (the arrays
+ *   may then be NULL): every call on it succeeds, writes no per-path output
+ *   (those pointers may be NULL too) and returns zero gradients.
  * FPT_EINVAL on lo < 1, hi > 10, lo > hi, empty alphabet or ids out of range
  * (host-checked arrays only).  A batch records the object types of the
  * scene it was built for; calls that pass a scene with other types return

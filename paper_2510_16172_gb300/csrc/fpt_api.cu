@@ -587,7 +587,8 @@ fpt_status fpt_batch_seeded(fpt_ctx* ctx, const fpt_scene* s, const int32_t* alp
 fpt_status fpt_batch_explicit(fpt_ctx* ctx, const fpt_scene* s, const int32_t* ids_dev, const uint8_t* order_dev,
                               const int32_t* tx_idx_dev, const int32_t* rx_idx_dev, uint64_t n, int32_t n_max,
                               fpt_batch** out) {
-  if (!ctx || !s || !out || !ids_dev || !order_dev || !tx_idx_dev || !rx_idx_dev)
+  // an empty batch (n = 0) is legal and its device arrays may be NULL
+  if (!ctx || !s || !out || (n > 0 && (!ids_dev || !order_dev || !tx_idx_dev || !rx_idx_dev)))
     return fail(ctx, FPT_EINVAL, "null argument");
   *out = nullptr;
   if (n_max < 1 || n_max > kMaxOrder) return fail(ctx, FPT_EINVAL, "n_max %d outside [1, %d]", n_max, kMaxOrder);
@@ -741,7 +742,7 @@ static fpt_status solve_impl(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* 
                              const GradCfg* grad) {
   fpt_status st = check_scene_batch(ctx, s, bc);
   if (st != FPT_OK) return st;
-  if (!T || !status) return fail(ctx, FPT_EINVAL, "T_out and status_out are required");
+  if (bc->dev.n_paths > 0 && (!T || !status)) return fail(ctx, FPT_EINVAL, "T_out and status_out are required");
   fpt_solve_params p;
   fpt_default_params(&p);
   if (prm) p = *prm;
@@ -872,7 +873,7 @@ fpt_status fpt_solve_grad(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc,
   if (st != FPT_OK) return st;
   if (prm && prm->polish_fp64) return fail(ctx, FPT_EUNSUPPORTED, "fpt_solve_grad runs the double-float polish");
   if (prm && prm->polish < 1) return fail(ctx, FPT_EINVAL, "fpt_solve_grad needs polish >= 1");
-  if (!status) return fail(ctx, FPT_EINVAL, "status_out is required");
+  if (!status && bc->dev.n_paths > 0) return fail(ctx, FPT_EINVAL, "status_out is required");
   if (!(prm && prm->fuse_adjoint)) {
     // the adjoint kernels after the solve, with the cotangents given here
     st = fpt_solve(ctx, s, bc, prm, T, X, L, status, iters, rho);
@@ -904,7 +905,7 @@ fpt_status fpt_validity(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
                         float* bdist, float* rho) {
   fpt_status st = check_scene_batch(ctx, s, bc);
   if (st != FPT_OK) return st;
-  if (!T) return fail(ctx, FPT_EINVAL, "T is required");
+  if (!T && bc->dev.n_paths > 0) return fail(ctx, FPT_EINVAL, "T is required");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   st = ensure_buckets(ctx, b, scene_dev(s));
@@ -932,7 +933,7 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
                         float* g_vertices) {
   fpt_status st = check_scene_batch(ctx, s, bc);
   if (st != FPT_OK) return st;
-  if (!T) return fail(ctx, FPT_EINVAL, "T is required");
+  if (!T && bc->dev.n_paths > 0) return fail(ctx, FPT_EINVAL, "T is required");
   fpt_batch* b = const_cast<fpt_batch*>(bc);
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   st = ensure_buckets(ctx, b, scene_dev(s));
@@ -942,7 +943,8 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   const SceneDev S = scene_dev(s);
   fpt_solve_params p;
   fpt_default_params(&p);
-  if (!dL && dL_status_mask && !status) return fail(ctx, FPT_EINVAL, "dL_status_mask needs status");
+  if (!dL && dL_status_mask && !status && bc->dev.n_paths > 0)
+    return fail(ctx, FPT_EINVAL, "dL_status_mask needs status");
   BackwardCfg bc_cfg{p.cond_fp64, p.deg_tol, 1, 64, dL ? (uint8_t)0 : dL_status_mask};
   for (int n = 1; n <= kMaxOrder; ++n) {
     const PathRec* list;
@@ -1013,8 +1015,8 @@ fpt_status fpt_occlusion(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, 
                          uint8_t status_mask, float tol, uint16_t* blocked_out) {
   fpt_status st = check_scene_batch(ctx, s, bc);
   if (st != FPT_OK) return st;
-  if (!T || !blocked_out) return fail(ctx, FPT_EINVAL, "T and blocked_out are required");
-  if (status_mask && !status) return fail(ctx, FPT_EINVAL, "status_mask needs status");
+  if (bc->dev.n_paths > 0 && (!T || !blocked_out)) return fail(ctx, FPT_EINVAL, "T and blocked_out are required");
+  if (status_mask && !status && bc->dev.n_paths > 0) return fail(ctx, FPT_EINVAL, "status_mask needs status");
   if (!(tol >= 0.f)) return fail(ctx, FPT_EINVAL, "tol must be >= 0");
   if ((size_t)s->n_occ * kOcc * sizeof(float) > kMaxSmemBytes)
     return fail(ctx, FPT_EUNSUPPORTED, "%d planar objects exceed the occluder table", s->n_occ);
@@ -1043,8 +1045,9 @@ fpt_status fpt_backward_noalloc(fpt_ctx* ctx, const fpt_scene* s, const fpt_batc
                                 float* g_tx, float* g_rx, float* g_vertices) {
   fpt_status st = check_scene_batch(ctx, s, b);
   if (st != FPT_OK) return st;
-  if (!T) return fail(ctx, FPT_EINVAL, "T is required");
-  if (!dL && dL_status_mask && !status) return fail(ctx, FPT_EINVAL, "dL_status_mask needs status");
+  if (!T && b->dev.n_paths > 0) return fail(ctx, FPT_EINVAL, "T is required");
+  if (!dL && dL_status_mask && !status && b->dev.n_paths > 0)
+    return fail(ctx, FPT_EINVAL, "dL_status_mask needs status");
   const long long need = 9LL * s->n_obj + 3LL * (s->n_tx + s->n_rx);
   if (need > kNoAllocMaxAcc)
     return fail(ctx, FPT_EINVAL, "fpt_backward_noalloc: 9 n_obj + 3 (n_tx + n_rx) = %lld exceeds its limit %d", need,
@@ -1069,7 +1072,7 @@ fpt_status fpt_backward_noalloc(fpt_ctx* ctx, const fpt_scene* s, const fpt_batc
 }
 
 fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uint8_t mask, uint64_t* count) {
-  if (!ctx || !status || !count) return fail(ctx, FPT_EINVAL, "null argument");
+  if (!ctx || !count || (!status && n > 0)) return fail(ctx, FPT_EINVAL, "null argument");
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   unsigned long long h = 0;
   CUDA_OR_FAIL(ctx, cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned long long), ctx->stream));

@@ -443,3 +443,33 @@ def test_fixed_point_rounds_reach_the_oracle_in_fewer_steps(ctx):
     assert np.array_equal(o1["T"], o_unified["T"])
     e_late, _ = err(32, 1, 2)
     assert e_late < 1e-5
+
+
+def test_empty_explicit_batch(ctx):
+    """A batch of zero paths: every call succeeds, writes nothing per path and returns zero gradients."""
+    import torch
+
+    sc = scenes.tiny_scene(2, n_rx=2)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    dev = torch.device("cuda", 0)
+    batch = fpt.Batch.explicit(ctx, scene, torch.empty((0, 3), dtype=torch.int32, device=dev),
+                               torch.empty(0, dtype=torch.uint8, device=dev), torch.empty(0, dtype=torch.int32, device=dev),
+                               torch.empty(0, dtype=torch.int32, device=dev))
+    assert batch.n_paths == 0
+    out = fpt.solve(ctx, scene, batch)
+    assert out["T"].shape == (0, 3, 2) and out["status"].shape == (0,)
+    mask = fpt.ST_VALID | fpt.ST_SOLVED
+    out, (g_tx, g_rx, g_v) = fpt.solve_grad(ctx, scene, batch, dL_status_mask=mask)
+    ctx.sync()
+    assert fpt.count_status(ctx, out["status"], mask) == 0
+    for g in (g_tx, g_rx, g_v):
+        assert g.numel() > 0 and not g.any()
+    g_tx, g_rx, g_v = fpt.backward(ctx, scene, batch, out["T"], out["status"], dL_status_mask=mask)
+    ctx.sync()
+    assert not (g_tx.any() or g_rx.any() or g_v.any())
+    m, bd, rho = fpt.validity(ctx, scene, batch, out["T"])
+    assert m.numel() == 0
+    assert fpt.occlusion(ctx, scene, batch, out["T"], out["status"], mask).numel() == 0
+    ids, order, ti, ri = fpt.enumerate(ctx, batch)
+    ctx.sync()
+    assert ids.shape == (0, 3) and order.numel() == 0
