@@ -473,3 +473,52 @@ def test_empty_explicit_batch(ctx):
     ids, order, ti, ri = fpt.enumerate(ctx, batch)
     ctx.sync()
     assert ids.shape == (0, 3) and order.numel() == 0
+
+
+def test_degenerate_geometries_are_never_solved(ctx):
+    """Endpoints on an object, on an edge's line and at the same point: the minimisers with a
+    zero-length segment (kinks of L, DEGENERATE in the oracle) are never reported SOLVED, nothing
+    turns non-finite, and the regular cases still meet the oracle."""
+    quad = np.array([[0.0, 0.0, 0.0], [10.0, 0.0, 0.0], [0.0, 10.0, 0.0]])  # the plane z = 0
+    edge = np.array([[0.0, 12.0, 0.0], [0.0, 12.0, 10.0], [0.0, 0.0, 0.0]])  # the line x = 0, y = 12
+    types = np.array([scenes.QUAD, scenes.EDGE], dtype=np.uint8)
+    verts = np.stack([quad, edge])
+    tx = np.array([[5.0, 5.0, 0.0],       # on the plane
+                   [0.0, 12.0, 4.0],      # on the edge
+                   [3.0, 4.0, 2.0]])      # regular
+    rx = np.array([[5.0, 5.0, 3.0], [3.0, 4.0, 2.0]])  # the second RX coincides with the third TX
+    sc = scenes.Scene(types, verts, tx, rx)
+    _, batch, out = gpu_run(ctx, sc, 1, 2)
+    g = to_np(out)
+    ids, order, ti, ri = oracle.exhaustive_paths(sc, 1, 2)
+    ref = oracle_solve(sc, ids, order, ti, ri)
+    gst, ost = g["status"].astype(np.int32), ref["status"]
+    assert not (gst & fpt.ST_NONFINITE).any()
+    deg = (ost & oracle.DEGENERATE) > 0
+    assert deg.sum() >= 3
+    assert not ((gst & fpt.ST_SOLVED) > 0)[deg].any()
+    assert regular(ost).sum() >= 8
+    check_parity(g, ref, min_solved_frac=0.9)
+
+
+def test_largest_scene_uses_the_full_16_bit_object_ids(ctx):
+    """65,535 objects (the most a scene holds: bucket records keep 16-bit ids): seeded sequences
+    over all of them meet the oracle; one object more is an argument error."""
+    rng = np.random.default_rng(17)
+    K = 65535
+    types = (rng.random(K) < 0.3).astype(np.uint8)  # ~30 % edges
+    verts = np.zeros((K, 3, 3))
+    for k in range(K):
+        verts[k] = scenes.random_edge(rng, 1, 3, 1, 9) if types[k] else scenes.random_rectangle(rng, 1, 4, 1, 9)
+    tx = rng.uniform(0, 10, (1, 3))
+    rx = rng.uniform(0, 10, (2, 3))
+    sc = scenes.Scene(types, verts, tx, rx)
+    scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
+    batch = fpt.Batch.seeded(ctx, scene, 5, 1500, 1, 3)
+    out = to_np(fpt.solve(ctx, scene, batch))
+    ctx.sync()
+    ids, order, ti, ri = oracle.seeded_paths(sc, 5, 1500, 1, 3)
+    assert ids.max() > 60000
+    check_parity(out, oracle_solve(sc, ids, order, ti, ri), min_solved_frac=0.98)
+    with pytest.raises(fpt.FptError):
+        fpt.Scene(ctx, np.zeros(K + 1, dtype=np.uint8), np.concatenate([verts, verts[:1]]))
