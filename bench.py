@@ -414,10 +414,15 @@ CITY_WORKLOAD = ("ragged city: 256 objects (154 facades 5-30 m, 102 of their edg
                  "100,000,000 seeded sequences of order 1-5; learned start (the network trained here on the solver's "
                  "solutions of 50 random 10 m scenes), FP32 BFGS + Eq.6 fixed point, double-float Newton polish, "
                  "validity, implicit backward of the sum of valid path lengths (one fpt_solve_grad call)")
+CITY_WORKLOAD_PLAIN = ("ragged city: 256 objects (154 facades 5-30 m, 102 of their edges, 500 x 500 x 60 m), 1 TX x 16 "
+                       "RX, seeded sequences of order 1-5; plain start, FP32 BFGS + Eq.6 fixed point, double-float "
+                       "Newton polish, validity, implicit backward of the sum of valid path lengths (one fpt_solve_grad "
+                       "call)")
 
 
 def run_city(args, world, rank, local_rank):
-    """The ragged large batch: seeded orders 1-5 on a city, learned start; the plain start alongside."""
+    """The ragged large batch: seeded orders 1-5 on a city, learned start; the plain start alongside
+    (with --no-learned: the plain start alone, no network trained)."""
     import numpy as np
     import torch
 
@@ -427,12 +432,16 @@ def run_city(args, world, rank, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     ctx = fpt.Context(local_rank)
-    t0 = time.perf_counter()
-    X, T, G = warmstart.make_dataset(ctx)
-    net, hist = warmstart.train(ctx, X, T, G, epochs=6)
-    del X, T, G
-    train_s = time.perf_counter() - t0
-    net.attach()
+    learned = not args.no_learned
+    train_s, hist = None, None
+    if learned:
+        t0 = time.perf_counter()
+        X, T, G = warmstart.make_dataset(ctx)
+        net, hist = warmstart.train(ctx, X, T, G, epochs=6)
+        del X, T, G
+        train_s = time.perf_counter() - t0
+        net.attach()
+    main = 1 if learned else 0
     sc = scenes.city(0, n_rx=16)
     scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
     per_pair = args.city_paths // (len(sc.tx) * len(sc.rx))
@@ -445,7 +454,7 @@ def run_city(args, world, rank, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     res = {}
-    for init in (1, 0):
+    for init in ((1, 0) if learned else (0,)):
         params = fpt.default_params(max_iters=args.max_iters, init_mode=init)
         for _ in range(args.warmup):
             fpt.solve_grad(ctx, scene, batch, params, dL_status_mask=mask, out=out, grads=grads)
@@ -477,7 +486,7 @@ def run_city(args, world, rank, local_rank):
         res[init] = {"value": solved_all * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
                      "solved_per_step": solved, "mean_bfgs_iters": float(iters[run].double().mean()),
                      "kernel_ms": kms, "launches": int(sum(klaunch)), "clocks": clk.summary()}
-        if init == 1:
+        if init == main:
             # algorithmic BFGS flops of this step: per path, its (order, reflector count)'s count per step
             ids, order, _, _ = fpt.enumerate(ctx, batch)
             is_quad = torch.tensor(np.asarray(sc.types) == scenes.QUAD, device=dev)
@@ -497,7 +506,7 @@ def run_city(args, world, rank, local_rank):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
-    L = res[1]
+    L = res[main]
     bfgs_ms = L["kernel_ms"][fpt.K_BFGS] / args.steps
     roof = {"kernel": "bfgs_refill_kernel<n, Q> (orders 1-5, reflector/edge patterns)", "bound": "alu",
             "achieved": L["bfgs_flops"] / (bfgs_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -508,15 +517,16 @@ def run_city(args, world, rank, local_rank):
     line = {"metric": METRIC, "value": L["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": L["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": CITY_WORKLOAD, "n_paths": N, "init": "learned", "max_bfgs_iters": args.max_iters,
+            "config": {"workload": CITY_WORKLOAD if learned else CITY_WORKLOAD_PLAIN, "n_paths": N,
+                       "init": "learned" if learned else "plain", "max_bfgs_iters": args.max_iters,
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "solved_per_step": L["solved_per_step"], "mean_bfgs_iters": L["mean_bfgs_iters"],
             "kernel_ms_per_step": {names[k]: L["kernel_ms"][k] / args.steps for k in range(fpt.K_COUNT)},
-            "roofline": roof, "gpu_launches": L["launches"], "clocks": L["clocks"],
-            "plain_start": {"value": res[0]["value"], "ms_per_step": res[0]["ms_per_step"],
-                            "solved_per_step": res[0]["solved_per_step"],
-                            "mean_bfgs_iters": res[0]["mean_bfgs_iters"]},
-            "network": {"train_s": train_s, "train_loss_per_epoch": hist}}
+            "roofline": roof, "gpu_launches": L["launches"], "clocks": L["clocks"]}
+    if learned:
+        line["plain_start"] = {"value": res[0]["value"], "ms_per_step": res[0]["ms_per_step"],
+                               "solved_per_step": res[0]["solved_per_step"], "mean_bfgs_iters": res[0]["mean_bfgs_iters"]}
+        line["network"] = {"train_s": train_s, "train_loss_per_epoch": hist}
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
 
@@ -749,7 +759,8 @@ def main():
                     help="urban canyon: stop a path whose segment falls below this many metres before converging "
                          "(1 cm, 1/500 of the smallest facade; loses 96 of 20.5 M solves against 0.1 mm)")
     ap.add_argument("--rx-grid", type=int, default=32, help="RX grid side (32 = the 33.5M-path workload)")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain start comparison")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="canyon: skip the learned-vs-plain start comparison; city: the plain start alone")
     ap.add_argument("--workload", choices=["canyon", "city", "fig2", "fig3"], default="canyon",
                     help="canyon: the 33.5M-path urban canyon (default); city: the 100M-path ragged city batch; "
                          "fig2: point error against solver time by iteration budget; fig3: gradient time, implicit vs AD "
