@@ -318,14 +318,19 @@ def run_ours(args, world, rank, local_rank):
     # algorithmic flops of the pattern kernels: per path, its pattern's count per step x its steps
     ids = fpt.enumerate(ctx, batch)[0]
     is_quad = torch.tensor(np.asarray(sc.types) == scenes.QUAD, device=dev)
-    nq = is_quad[ids.long()].sum(dim=1)
-    del ids
+    qbits = is_quad[ids.long()].to(torch.int64)
+    pattern = qbits[:, 0] | (qbits[:, 1] << 1) | (qbits[:, 2] << 2)  # bit i: slot i is a reflector
+    nq = qbits.sum(dim=1)
+    del ids, qbits
     run = (out["status"] & fpt.ST_REPEAT) == 0
     f_step = torch.tensor([bfgs_flops_per_iter(3, params.fp_iters, q) for q in range(4)], dtype=torch.float64,
                           device=dev)
     f_init = torch.tensor([bfgs_flops_init(3, q) for q in range(4)], dtype=torch.float64, device=dev)
-    bfgs_flops = float(((f_init[nq] + f_step[nq] * iters.double()) * run.double()).sum().item())
-    del nq, run
+    per_path = (f_init[nq] + f_step[nq] * iters.double()) * run.double()
+    bfgs_flops = float(per_path.sum().item())
+    # the static count per pattern kernel (one launch each per step), for comparison with executed FP32 ops
+    flops_by_pattern = {int(q): float(per_path[pattern == q].sum().item()) for q in range(8)}
+    del nq, run, per_path, pattern
     # obstruction of the step's valid solved paths (post-processing, not part of the timed step)
     blocked = fpt.occlusion(ctx, scene, batch, out["T"], out["status"], mask)
     torch.cuda.synchronize(dev)
@@ -365,6 +370,7 @@ def run_ours(args, world, rank, local_rank):
             "kernel_ms_per_step": {names[k]: kms[k] / args.steps for k in range(fpt.K_COUNT) if klaunch[k]},
             "dominant_kernel": names[dom],
             "roofline": roof_bfgs,
+            "bfgs_flops_by_pattern": flops_by_pattern,
             "gpu_launches": int(sum(klaunch)),
             "clocks": clocks,
             "occlusion": occ}
@@ -380,12 +386,26 @@ def run_ours(args, world, rank, local_rank):
                                 "sample": f"{m} seeded uniformly sampled paths of the workload, FP64 damped Newton "
                                           f"+ implicit VJP, {dt:.1f} s on {threads} threads"}
     if rank == 0 and world == 1 and not args.no_learned:
-        line["learned_vs_plain"] = learned_vs_plain(ctx, fpt)
+        line["learned_vs_plain"], net = learned_vs_plain(ctx, fpt, args.epochs)
+        if not args.no_city:
+            # config 5, the ragged city batch, from the network just trained (learned) and from t = 1/2
+            net.attach()
+            m = measure_city(ctx, dev, args, args.city_steps, 2, True)
+            L, P = m["res"][1], m["res"][0]
+            line["ragged_city"] = {
+                "workload": CITY_WORKLOAD, "n_paths": m["n_paths"], "steps": args.city_steps, "warmup": 2,
+                "learned": {k: L[k] for k in ("value", "ms_per_step", "solved_per_step", "mean_bfgs_iters",
+                                              "kernel_ms_per_step", "launches")},
+                "plain": {k: P[k] for k in ("value", "ms_per_step", "solved_per_step", "mean_bfgs_iters",
+                                            "kernel_ms_per_step", "launches")},
+                "unit": UNIT, "roofline": m["roofline"], "clocks": L["clocks"],
+                "launch_structure": "one launch per (order, reflector/edge pattern) bucket, on four streams"}
+        net.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def learned_vs_plain(ctx, fpt):
+def learned_vs_plain(ctx, fpt, epochs):
     """The learned start against the plain one (same solver, same unseen scenes).
 
     The network (64-256-256-256-8, GELU, BF16 weights, FP32 accumulation) is
@@ -398,16 +418,16 @@ def learned_vs_plain(ctx, fpt):
     from paper_2510_16172_gb300 import warmstart
 
     t0 = time.perf_counter()
-    net, ev = warmstart.run(ctx, per_pair_train=200_000, per_pair_eval=200_000, epochs=6)
-    net.close()
+    net, ev = warmstart.run(ctx, per_pair_train=200_000, per_pair_eval=200_000, epochs=epochs)
     res = {"workload": "train: 50 seeded 10 m scenes (8 quads + 4 edges) x 200,000 seeded order-1..4 sequences, "
-                       "solved paths as targets, 6 epochs of Adam; eval: 10 unseen scenes x 200,000 sequences",
+                       f"solved paths as targets, {epochs} epochs of Adam; eval: 10 unseen scenes x 200,000 "
+                       "sequences",
            "train_samples": ev["train_samples"], "train_loss_per_epoch": ev["train_loss_per_epoch"],
            "train_s": ev["train_s"], "plain": ev["plain"], "learned": ev["learned"],
            "learned_over_plain_solves_per_s": ev["learned"]["solves_per_s"] / ev["plain"]["solves_per_s"],
            "learned_over_plain_iterations": ev["learned"]["mean_bfgs_iters"] / ev["plain"]["mean_bfgs_iters"],
            "wall_s": time.perf_counter() - t0}
-    return res
+    return res, net
 
 
 CITY_WORKLOAD = ("ragged city: 256 objects (154 facades 5-30 m, 102 of their edges, 500 x 500 x 60 m), 1 TX x 16 RX, "
@@ -420,28 +440,17 @@ CITY_WORKLOAD_PLAIN = ("ragged city: 256 objects (154 facades 5-30 m, 102 of the
                        "call)")
 
 
-def run_city(args, world, rank, local_rank):
-    """The ragged large batch: seeded orders 1-5 on a city, learned start; the plain start alongside
-    (with --no-learned: the plain start alone, no network trained)."""
+def measure_city(ctx, dev, args, steps, warmup, learned, dist=None):
+    """The ragged large batch (config 5): 100,000,000 seeded sequences of order 1-5 on the 256-object city, one
+    fpt_solve_grad per step (solve and implicit backward of the sum of the valid solved lengths), timed with
+    CUDA events (L2 flushed between steps) from the learned start (when `learned`: the network attached to ctx)
+    and from the plain start.  Returns per start the whole-job solves/s, ms per step, solved paths, mean BFGS
+    steps, kernel ms per class and launches, and the BFGS roofline of the main start."""
     import numpy as np
     import torch
 
-    from paper_2510_16172_gb300 import build, fpt, scenes, warmstart
+    from paper_2510_16172_gb300 import fpt, scenes
 
-    build.build()
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    ctx = fpt.Context(local_rank)
-    learned = not args.no_learned
-    train_s, hist = None, None
-    if learned:
-        t0 = time.perf_counter()
-        X, T, G = warmstart.make_dataset(ctx)
-        net, hist = warmstart.train(ctx, X, T, G, epochs=6)
-        del X, T, G
-        train_s = time.perf_counter() - t0
-        net.attach()
-    main = 1 if learned else 0
     sc = scenes.city(0, n_rx=16)
     scene = fpt.Scene(ctx, sc.types, sc.verts, sc.tx, sc.rx)
     per_pair = args.city_paths // (len(sc.tx) * len(sc.rx))
@@ -453,18 +462,21 @@ def run_city(args, world, rank, local_rank):
     mask = fpt.ST_VALID | fpt.ST_SOLVED
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    main = 1 if learned else 0
     res = {}
     for init in ((1, 0) if learned else (0,)):
         params = fpt.default_params(max_iters=args.max_iters, init_mode=init)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fpt.solve_grad(ctx, scene, batch, params, dL_status_mask=mask, out=out, grads=grads)
         ctx.sync()
         fpt.profile_enable(ctx, True)
         fpt.profile_read(ctx, reset=True)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         with ClockSampler(gpu_identifier(torch, dev)) as clk:
+            if dist:
+                dist.barrier()
             torch.cuda.synchronize(dev)
-            for k in range(args.steps):
+            for k in range(steps):
                 flush.zero_()
                 ev[k][0].record(stream)
                 fpt.solve_grad(ctx, scene, batch, params, dL_status_mask=mask, out=out, grads=grads)
@@ -477,13 +489,10 @@ def run_city(args, world, rank, local_rank):
         solved = fpt.count_status(ctx, out["status"], fpt.ST_SOLVED)
         run = (out["status"] & fpt.ST_REPEAT) == 0
         iters = out["iters"].to(torch.int64)
-        dist = None
-        if world > 1:
-            import torch.distributed as dist
-
+        if dist:
             dist.barrier()
         total_ms, solved_all = combine_ranks(total_ms, solved, dist, dev)
-        res[init] = {"value": solved_all * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+        res[init] = {"value": solved_all * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
                      "solved_per_step": solved, "mean_bfgs_iters": float(iters[run].double().mean()),
                      "kernel_ms": kms, "launches": int(sum(klaunch)), "clocks": clk.summary()}
         if init == main:
@@ -502,38 +511,75 @@ def run_city(args, world, rank, local_rank):
                 flops += float(((f_init[nq] + f_step[nq] * iters[sel].double()) * r).sum().item())
             del ids, order
             res[init]["bfgs_flops"] = flops
+    del out, batch, scene
     peaks = measured_peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     L = res[main]
-    bfgs_ms = L["kernel_ms"][fpt.K_BFGS] / args.steps
+    bfgs_ms = L["kernel_ms"][fpt.K_BFGS] / steps
     roof = {"kernel": "bfgs_refill_kernel<n, Q> (orders 1-5, reflector/edge patterns)", "bound": "alu",
             "achieved": L["bfgs_flops"] / (bfgs_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz", "traffic": None}
     roof["frac"] = roof["achieved"] / roof["peak"]
     names = {fpt.K_BFGS: "bfgs", fpt.K_POLISH: "polish", fpt.K_BACKWARD: "backward", fpt.K_OTHER: "finalize",
              fpt.K_MLP: "mlp_infer_kernel (learned start)"}
+    for r in res.values():
+        r["kernel_ms_per_step"] = {names[k]: r["kernel_ms"][k] / steps for k in range(fpt.K_COUNT)}
+        del r["kernel_ms"]
+    return {"n_paths": N, "res": res, "roofline": roof, "main": main}
+
+
+def run_city(args, world, rank, local_rank):
+    """The ragged large batch: seeded orders 1-5 on a city, learned start; the plain start alongside
+    (with --no-learned: the plain start alone, no network trained)."""
+    import torch
+
+    from paper_2510_16172_gb300 import build, fpt, warmstart
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ctx = fpt.Context(local_rank)
+    learned = not args.no_learned
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    train_s, hist = None, None
+    if learned:
+        t0 = time.perf_counter()
+        X, T, G = warmstart.make_dataset(ctx)
+        net, hist = warmstart.train(ctx, X, T, G, epochs=args.epochs)
+        del X, T, G
+        train_s = time.perf_counter() - t0
+        net.attach()
+    m = measure_city(ctx, dev, args, args.steps, args.warmup, learned, dist)
+    L = m["res"][m["main"]]
     line = {"metric": METRIC, "value": L["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": L["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": CITY_WORKLOAD if learned else CITY_WORKLOAD_PLAIN, "n_paths": N,
+            "config": {"workload": CITY_WORKLOAD if learned else CITY_WORKLOAD_PLAIN, "n_paths": m["n_paths"],
                        "init": "learned" if learned else "plain", "max_bfgs_iters": args.max_iters,
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "solved_per_step": L["solved_per_step"], "mean_bfgs_iters": L["mean_bfgs_iters"],
-            "kernel_ms_per_step": {names[k]: L["kernel_ms"][k] / args.steps for k in range(fpt.K_COUNT)},
-            "roofline": roof, "gpu_launches": L["launches"], "clocks": L["clocks"]}
+            "kernel_ms_per_step": L["kernel_ms_per_step"],
+            "roofline": m["roofline"], "gpu_launches": L["launches"], "clocks": L["clocks"]}
     if learned:
-        line["plain_start"] = {"value": res[0]["value"], "ms_per_step": res[0]["ms_per_step"],
-                               "solved_per_step": res[0]["solved_per_step"], "mean_bfgs_iters": res[0]["mean_bfgs_iters"]}
+        P = m["res"][0]
+        line["plain_start"] = {"value": P["value"], "ms_per_step": P["ms_per_step"],
+                               "solved_per_step": P["solved_per_step"], "mean_bfgs_iters": P["mean_bfgs_iters"],
+                               "kernel_ms_per_step": P["kernel_ms_per_step"]}
         line["network"] = {"train_s": train_s, "train_loss_per_epoch": hist}
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
+        from paper_2510_16172_gb300 import scenes
 
-        rate, m, dt, threads = oracle_rate(sc, N, 1, target_s=args.cpu_seconds,
-                                           decode=lambda g: oracle.seeded_paths(sc, 5, per_pair, 1, 5, g))
+        sc = scenes.city(0, n_rx=16)
+        per_pair = args.city_paths // (len(sc.tx) * len(sc.rx))
+        rate, mm, dt, threads = oracle_rate(sc, m["n_paths"], 1, target_s=args.cpu_seconds,
+                                            decode=lambda g: oracle.seeded_paths(sc, 5, per_pair, 1, 5, g))
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"{m} uniformly sampled paths of the batch, FP64 damped Newton + implicit "
+                                "sample": f"{mm} uniformly sampled paths of the batch, FP64 damped Newton + implicit "
                                           f"VJP, {dt:.1f} s on {threads} threads"}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -677,10 +723,11 @@ def run_fig3(args, world, rank, local_rank):
 
 
 def e2e(args, sc, ctx, dev, torch, fpt):
-    """Same metric through the public API: host scene/endpoints in, host lengths/status/gradients out.
+    """Same metric through the public API: host scene/endpoints in, host parameters/lengths/status/gradients out.
 
     Every step uploads its scene and endpoints from pinned host memory, builds the batch, runs
-    fpt_solve_grad and copies L, status and the gradients back to pinned host memory.  The device
+    fpt_solve_grad and copies the solved parameters T (the interaction points are x_i = A_i t_i + b_i),
+    the lengths, the status and the gradients back to pinned host memory.  The device
     outputs are double-buffered: step k's device-to-host copy runs on a copy stream while step k + 1
     computes (a serving loop's pipeline); the timed region ends when the last step's results are on
     the host.  Scenes and batches are released, and the solved paths counted on the host, after the
@@ -695,6 +742,7 @@ def e2e(args, sc, ctx, dev, torch, fpt):
     steps = max(3, min(10, args.steps // 2))
     total = args.warmup + steps
     L_h = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(2)]
+    T_h = [torch.empty((N, 3, 2), dtype=torch.float32).pin_memory() for _ in range(2)]
     st_h = [torch.empty(N, dtype=torch.uint8).pin_memory() for _ in range(total)]
     g_h = [(torch.empty((len(sc.tx), 3), dtype=torch.float32).pin_memory(),
             torch.empty((len(sc.rx), 3), dtype=torch.float32).pin_memory(),
@@ -702,7 +750,7 @@ def e2e(args, sc, ctx, dev, torch, fpt):
     mask = fpt.ST_VALID | fpt.ST_SOLVED
     params = fpt.default_params(max_iters=args.max_iters, kink_stop=args.kink_stop)
     h2d = types.numel() + verts.numel() * 8 + tx.numel() * 8 + rx.numel() * 8 + alphabet.size * 4
-    d2h = N * 4 + N + sum(t.numel() * 4 for t in g_h[0])
+    d2h = T_h[0].numel() * 4 + N * 4 + N + sum(t.numel() * 4 for t in g_h[0])
     copy_stream = torch.cuda.Stream(dev)
     outs = [None, None]
     grads = [None, None]
@@ -728,6 +776,7 @@ def e2e(args, sc, ctx, dev, torch, fpt):
         done[b].record(ctx.stream)
         with torch.cuda.stream(copy_stream):
             copy_stream.wait_event(done[b])
+            T_h[b].copy_(outs[b]["T"], non_blocking=True)
             L_h[b].copy_(outs[b]["L"], non_blocking=True)
             st_h[k].copy_(outs[b]["status"], non_blocking=True)
             for h, d in zip(g_h[b], grads[b]):
@@ -741,6 +790,7 @@ def e2e(args, sc, ctx, dev, torch, fpt):
         scene.close()
     return {"value": solved / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": 1e3 * dt / steps, "pipelined": "outputs double-buffered; copies overlap the next step",
+            "d2h": "T [N,3,2] (the solved parameters), L [N], status [N] and the TX/RX/vertex gradients, every step",
             "l2": "not flushed: every step writes ~1 GB of outputs (T, L, status), far more than L2"}
 
 
@@ -766,6 +816,9 @@ def main():
                          "fig2: point error against solver time by iteration budget; fig3: gradient time, implicit vs AD "
                          "through the iterations")
     ap.add_argument("--city-paths", type=int, default=100_000_000)
+    ap.add_argument("--city-steps", type=int, default=5, help="timed steps of the city leg of the default run")
+    ap.add_argument("--no-city", action="store_true", help="canyon run: skip the ragged city leg")
+    ap.add_argument("--epochs", type=int, default=6, help="training epochs of the warm-start network")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -128,6 +128,16 @@ void fpt_destroy(fpt_ctx* ctx);
 fpt_status fpt_set_stream(fpt_ctx* ctx, void* cuda_stream);
 /* Message for the last error on this context (static storage, never NULL). */
 const char* fpt_last_error(const fpt_ctx* ctx);
+/* How the backward calls (fpt_backward, fpt_solve_grad, fpt_backward_noalloc)
+ * sum the per-path gradient terms of Sec. III-D over paths.  smem = 1 (the
+ * default): each CTA adds its paths' terms into FP32 partial sums in shared
+ * memory and adds those into the FP64 totals every flush_tiles of its tiles
+ * of 128 paths (64 by default) and when it ends; a smaller flush_tiles puts
+ * fewer terms into each FP32 partial sum (more accurate, more global
+ * atomics).  smem = 0: every term is added straight into the FP64 totals.
+ * Scenes whose partial sums do not fit shared memory always use smem = 0.
+ * FPT_EINVAL unless flush_tiles >= 1 and smem is 0 or 1. */
+fpt_status fpt_set_accumulation(fpt_ctx* ctx, int32_t flush_tiles, int32_t smem);
 /* Wait for the stream, then check the device error word: FPT_EDEVICE if a
  * kernel flagged an error since the last check (the word is then cleared). */
 fpt_status fpt_sync(fpt_ctx* ctx);
@@ -143,11 +153,44 @@ fpt_status fpt_sync(fpt_ctx* ctx);
 fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* verts, int32_t n_obj,
                             fpt_scene** out);
 void fpt_scene_free(fpt_scene* scene);
+/* Scene from a caller-owned DEVICE array verts [n_obj][3][3] FP32 (layout of
+ * fpt_scene_upload) and host types [n_obj].  The records are built by a kernel
+ * on the context's stream (as fpt_scene_update_vertices), relative to `centre`
+ * (host double[3]; NULL = the origin), which the library cannot take from
+ * device data without waiting for it; nothing waits for the device.
+ * FPT_EINVAL on bad types, a non-finite centre or n_obj outside [1, 65535];
+ * non-finite or degenerate objects set the device error word (FPT_EDEVICE at
+ * fpt_sync).  The scene has no endpoints until fpt_set_endpoints[_device]. */
+fpt_status fpt_scene_upload_device(fpt_ctx* ctx, const uint8_t* types, const float* verts, int32_t n_obj,
+                                   const double* centre, fpt_scene** out);
 /* TX and RX positions (x_0 and x_{n+1} of Eq. 2): host double [n][3].
  * Copied to the device asynchronously on the context's stream, as the scene.
  * Replacing the endpoints of a scene frees its old device copies first (which
  * waits for the device).  FPT_EINVAL on non-finite input or n < 1. */
 fpt_status fpt_set_endpoints(fpt_scene* scene, const double* tx, int32_t n_tx, const double* rx, int32_t n_rx);
+
+/* TX and RX positions from caller-owned DEVICE arrays: tx [n_tx][3], rx
+ * [n_rx][3] FP32 (for example torch tensors that an optimisation loop updates
+ * from the gradients of Sec. III-D).  A kernel on the context's stream builds
+ * the endpoint records from them (each FP32 value taken exactly, relative to
+ * the scene centre); nothing passes through host memory and the call does not
+ * wait for the device, except when a count exceeds what the scene's endpoint
+ * buffers already hold (the first call, or more endpoints than before: the
+ * buffers are then reallocated).  The arrays are read when the stream reaches
+ * the call and may change afterwards.  FPT_EINVAL on null pointers or n < 1;
+ * non-finite coordinates set the device error word (FPT_EDEVICE at fpt_sync).
+ * Batches are tied to the counts n_tx, n_rx as with fpt_set_endpoints. */
+fpt_status fpt_set_endpoints_device(fpt_scene* scene, const float* tx, int32_t n_tx, const float* rx, int32_t n_rx);
+/* Replace the geometry of every object from a caller-owned DEVICE array verts
+ * [n_obj][3][3] FP32 (plane: v0, v1, v3; edge: e0, e1, unused), in the layout
+ * of fpt_scene_upload.  Object types and the scene centre stay those of the
+ * upload.  The records (Sec. III-B, Eq. 3), side heights and occluder records
+ * are rebuilt in place by a kernel on the context's stream: no allocation, no
+ * wait for the device; calls already issued on the stream use the old
+ * geometry, later calls the new.  Non-finite vertices, zero-area planes and
+ * zero-length edges (< 1e-9 m) set the device error word (FPT_EDEVICE at
+ * fpt_sync) instead of being refused. */
+fpt_status fpt_scene_update_vertices(fpt_scene* scene, const float* verts);
 
 /* Candidate sequences (Sec. III).
  * Exhaustive: for every (tx, rx) pair, every ordered sequence over the
@@ -219,7 +262,9 @@ fpt_status fpt_validity(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* b
  * path: v = A^T dX + dL grad_T L, solve H u = -v with the block-tridiagonal
  * Hessian H (FP32; FP64 if ill-conditioned), then u^T d(grad_T L)/dtheta plus
  * the explicit terms.  Paths with status REPEAT/DEGENERATE/NONFINITE/
- * INVALID_INPUT in `status` (device [N], may be NULL) contribute nothing.
+ * INVALID_INPUT in `status` (device [N], may be NULL) contribute nothing,
+ * and so do paths whose cotangents are all zero (skipped) and paths whose
+ * Hessian is singular in FP64 too (counted by fpt_backward_dropped).
  * Gradients are summed over paths into device outputs that the call
  * overwrites (any may be NULL): g_tx [n_tx][3], g_rx [n_rx][3],
  * g_vertices [n_obj][3][3] (plane: v0, v1, v3; edge: e0, e1, zeros).
@@ -298,14 +343,22 @@ fpt_status fpt_backward_unrolled(fpt_ctx* ctx, const fpt_scene* scene, const fpt
  * larger inputs return FPT_EINVAL with a message.  Seeded and explicit
  * batches must already be bucketed (any earlier fpt_solve or fpt_backward
  * on the batch does that).
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  Every call reuses the same array and clears the sums it needs;
- * calls that overlap on the GPU (different streams or contexts, same device)
- * race on it and must be serialised by the caller. */
+ * The array's device address is looked up, with the device current, when a
+ * context is created on that device (fpt_create) and cached; a device reset
+ * (cudaDeviceReset) can move the array, so create a new context after one
+ * before calling this again.  Every call reuses the same array and clears the
+ * sums it needs; calls that overlap on the GPU (different streams or
+ * contexts, same device) race on it and must be serialised by the caller. */
 fpt_status fpt_backward_noalloc(fpt_ctx* ctx, const fpt_scene* scene, const fpt_batch* batch, const float* T,
                                 const uint8_t* status, const float* dX, const float* dL, uint8_t dL_status_mask,
                                 float* g_tx, float* g_rx, float* g_vertices);
+
+/* Paths left out of the sums of the most recent fpt_backward, fpt_solve_grad
+ * or fpt_backward_noalloc call on this context because their Hessian failed
+ * the pivot test in FP32 and again in FP64 (singular: such a path has no
+ * well-defined implicit gradient and contributes nothing).  Synchronises the
+ * context's stream. */
+fpt_status fpt_backward_dropped(fpt_ctx* ctx, uint64_t* count);
 
 /* Number of paths whose status has all bits of `mask` set (device status
  * [n]; result written to *count on the host after a stream sync). */
@@ -365,6 +418,31 @@ fpt_status fpt_mlp_loss_grad(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const fl
  * loss of this batch; *loss (host, may be NULL) receives the batch loss. */
 fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const float* T, const float* G, uint64_t B,
                               float lr, float* loss);
+/* Training schedule of fpt_mlp_train. */
+typedef struct {
+  int32_t epochs;     /* passes over the samples (>= 1) */
+  int32_t batch;      /* samples per Adam step (>= 128); the last partial batch of an epoch is left out */
+  float lr;           /* learning rate of the first epoch (> 0) */
+  float lr_decay;     /* factor applied to the learning rate after every epoch (> 0; 0.5 halves it) */
+  uint64_t seed;      /* seed of the sample order: every epoch visits the samples in a new pseudo-random order */
+  int32_t reserved[4]; /* must be zero */
+} fpt_train_params;
+/* Train the network on n samples (device arrays as for fpt_mlp_loss_grad: X
+ * bf16 [n][64], targets T [n][8], Gram matrices G [n][4][3]): for every epoch
+ * a seeded permutation of the samples (a Feistel-network permutation drawn
+ * from seed and epoch, evaluated on the device), then floor(n / batch) Adam
+ * steps on consecutive slices of it; everything runs on the context's stream
+ * without waiting for the device.  loss_per_epoch (host [epochs], may be
+ * NULL) receives each epoch's mean batch loss (the call then synchronises
+ * once at its end).  FPT_EINVAL on bad parameters or n < batch. */
+fpt_status fpt_mlp_train(fpt_ctx* ctx, fpt_mlp* mlp, const void* X, const float* T, const float* G, uint64_t n,
+                         const fpt_train_params* params, float* loss_per_epoch);
+/* The learned start of every path of a batch: T_out [N][n_max][2] (device)
+ * receives the starting parameters fpt_solve uses with init_mode = 1 and this
+ * network (the first min(n, 4) interactions from the network, an edge's
+ * second parameter, later interactions and non-finite outputs at 1/2, unused
+ * slots 0), computed by the fused tensor-core inference kernel. */
+fpt_status fpt_mlp_infer(fpt_ctx* ctx, fpt_mlp* mlp, const fpt_scene* scene, const fpt_batch* batch, float* T_out);
 /* Network used by fpt_solve when init_mode = 1 (NULL detaches).  The network's
  * prediction seeds the first min(n, 4) interactions of each path; further
  * interactions, edges' second coordinate and non-finite predictions use the

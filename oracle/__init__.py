@@ -282,13 +282,14 @@ def reduce_gradients(scene, ids, order, tx_idx, rx_idx, dtheta):
     g_tx = np.zeros((len(scene.tx), 3))
     g_rx = np.zeros((len(scene.rx), 3))
     g_obj = np.zeros((K, 3, 3))  # (b, a1, a2)
-    n_max = ids.shape[1]
-    for p in range(len(order)):
-        d = dtheta[p]
-        g_tx[tx_idx[p]] += d[0:3]
-        g_rx[rx_idx[p]] += d[3:6]
-        for i in range(order[p]):
-            g_obj[ids[p, i]] += d[6 + 9 * i: 15 + 9 * i].reshape(3, 3)
+    order = np.asarray(order)
+    dtheta = np.asarray(dtheta, dtype=np.float64)
+    # plain sums over paths (np.add.at adds repeated indices one by one)
+    np.add.at(g_tx, np.asarray(tx_idx), dtheta[:, 0:3])
+    np.add.at(g_rx, np.asarray(rx_idx), dtheta[:, 3:6])
+    for i in range(ids.shape[1]):
+        on = order > i
+        np.add.at(g_obj, np.asarray(ids)[on, i], dtheta[on, 6 + 9 * i: 15 + 9 * i].reshape(-1, 3, 3))
     g_vert = np.zeros((K, 3, 3))
     gb, ga1, ga2 = g_obj[:, 0], g_obj[:, 1], g_obj[:, 2]
     quad = scene.types == QUAD

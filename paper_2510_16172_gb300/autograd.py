@@ -9,7 +9,14 @@ Forward runs fpt_solve on every exhaustive candidate sequence; backward runs
 fpt_backward with the incoming cotangents of X and L (Sec. III-D: solve
 H u = -v per path, then u^T d(grad_T L)/d(theta) plus the explicit terms).
 Paths that are repeats, degenerate, non-finite or invalid carry no gradient.
-Marshalling only: both directions run in libfpt.so.
+
+The geometry stays on the GPU: the solver keeps one scene whose records are
+rebuilt from the CUDA tensors by the library's kernels (fpt_scene_upload_device
+on the first call, then fpt_scene_update_vertices and fpt_set_endpoints_device),
+so no call copies TX, RX or vertices to the host or waits for the device.  A
+backward whose forward is not the most recent one first restores that
+forward's geometry (saved on the device).  Marshalling only: both directions
+run in libfpt.so.
 """
 
 from __future__ import annotations
@@ -23,22 +30,24 @@ from . import fpt
 class _FermatPathsFn(torch.autograd.Function):
     @staticmethod
     def forward(fctx, tx, rx, verts, solver):
-        scene = fpt.Scene(solver.ctx, solver.types, verts.detach().cpu().double().numpy(),
-                          tx.detach().cpu().double().numpy(), rx.detach().cpu().double().numpy())
-        batch = fpt.Batch.exhaustive(solver.ctx, scene, solver.order_lo, solver.order_hi, solver.alphabet)
+        geo = tuple(t.detach().to(device=solver.device, dtype=torch.float32).contiguous() for t in (tx, rx, verts))
+        scene, batch, version = solver._load(*geo)
         out = fpt.solve(solver.ctx, scene, batch, solver.params)
-        fctx.scene, fctx.batch, fctx.solver = scene, batch, solver
+        fctx.solver, fctx.version = solver, version
         fctx.in_meta = [(t.dtype, t.device) for t in (tx, rx, verts)]
-        fctx.save_for_backward(out["T"], out["status"])
+        fctx.save_for_backward(out["T"], out["status"], *geo)
         fctx.mark_non_differentiable(out["status"])
         return out["X"], out["L"], out["status"]
 
     @staticmethod
     def backward(fctx, dX, dL, _dstatus):
-        T, status = fctx.saved_tensors
+        T, status, tx, rx, verts = fctx.saved_tensors
+        solver = fctx.solver
+        if solver.version != fctx.version:  # a later forward replaced the geometry: restore this one's
+            solver._load(tx, rx, verts)
         dX = dX.contiguous().float() if dX is not None else None
         dL = dL.contiguous().float() if dL is not None else None
-        g_tx, g_rx, g_v = fpt.backward(fctx.solver.ctx, fctx.scene, fctx.batch, T, status, dX, dL)
+        g_tx, g_rx, g_v = fpt.backward(solver.ctx, solver.scene, solver.batch, T, status, dX, dL)
         outs = []
         for g, (dt, dev) in zip((g_tx, g_rx, g_v), fctx.in_meta):
             outs.append(g.to(device=dev, dtype=dt))
@@ -46,14 +55,38 @@ class _FermatPathsFn(torch.autograd.Function):
 
 
 class FermatSolver:
-    """Differentiable batched Fermat path solve over all sequences of order lo..hi."""
+    """Differentiable batched Fermat path solve over all sequences of order lo..hi.
 
-    def __init__(self, types, order_lo=1, order_hi=2, alphabet=None, params=None, device=0):
+    centre: the point (3 floats, metres) the library recentres the geometry on for FP32
+    precision; None = the origin.
+    """
+
+    def __init__(self, types, order_lo=1, order_hi=2, alphabet=None, params=None, device=0, centre=None):
         self.ctx = fpt.Context(device)
+        self.device = torch.device("cuda", device)
         self.types = np.ascontiguousarray(types, dtype=np.uint8)
         self.order_lo, self.order_hi = order_lo, order_hi
         self.alphabet = alphabet
         self.params = params if params is not None else fpt.default_params()
+        self.centre = None if centre is None else np.asarray(centre, dtype=np.float64).reshape(3)
+        self.scene = None
+        self.batch = None
+        self.version = 0
+
+    def _load(self, tx, rx, verts):
+        """Put this geometry (CUDA float32 tensors) into the solver's scene; returns (scene, batch, version)."""
+        if self.scene is None:
+            self.scene = fpt.Scene(self.ctx, self.types, verts, centre=self.centre)
+        else:
+            self.scene.update_vertices(verts)
+        counts = (self.scene.n_tx, self.scene.n_rx)
+        self.scene.set_endpoints(tx, rx)
+        if self.batch is None or counts != (self.scene.n_tx, self.scene.n_rx):
+            if self.batch is not None:
+                self.batch.close()
+            self.batch = fpt.Batch.exhaustive(self.ctx, self.scene, self.order_lo, self.order_hi, self.alphabet)
+        self.version += 1
+        return self.scene, self.batch, self.version
 
     def __call__(self, tx, rx, verts):
         return _FermatPathsFn.apply(tx, rx, verts, self)

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
       // a path with no cotangent contributes exactly zero: skip it
       if (use) {
         dl = dLv ? dLv[d.g] : ((cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask) ? 1.f : 0.f);
-        use = dX != nullptr || dl != 0.f;
+        use = dl != 0.f || has_point_cotangent<N>(dX, d.g, n_max);
       }
     } else {
       d.tx = d.rx = 0;
@@ -241,9 +241,18 @@ __global__ void __launch_bounds__(kThreads, kLongOrderMinBlocks<N>)
         z[jj][c] = x;
       }
     const double dl = dLv ? (double)dLv[g] : ((cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask) ? 1.0 : 0.0);
-    if (!dX && dl == 0.0) continue;  // no cotangent: the path contributes exactly zero
+    bool any = dl != 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) any = any || dx[i][c] != 0.0;
+    if (!any) continue;  // no cotangent: the path contributes exactly zero
     double gb[N][9], gtx[3], grx[3];
-    if (!path_vjp<double, N>(z, a, t, edge, dx, dl, 1e-10, gb, gtx, grx)) continue;
+    if (!path_vjp<double, N>(z, a, t, edge, dx, dl, 1e-10, gb, gtx, grx)) {
+      // singular even in FP64: the path is left out of the sums and counted
+      if (cfg.dropped) atomicAdd(cfg.dropped, 1u);
+      continue;
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll

@@ -88,20 +88,18 @@ template <int N, unsigned Q>
 __device__ __forceinline__ void decode_exhaustive_pattern(const BatchDev& B, const Tables& tb, uint64_t j,
                                                           PathDesc& d) {
   const uint32_t nq = (uint32_t)B.n_alpha_quad, ne = (uint32_t)(B.n_alpha - B.n_alpha_quad);
-  uint32_t cnt = 1;
-#pragma unroll
-  for (int i = 0; i < N; ++i) cnt *= Pat<N, Q>::quad(i) ? nq : ne;
+  const uint32_t cnt = B.fd_pat.d;
   const uint32_t j32 = (uint32_t)j;
-  const uint32_t pair = j32 / cnt;
+  const uint32_t pair = fdiv(j32, B.fd_pat);
   uint32_t r = j32 - pair * cnt;
   d.n = N;
-  d.tx = (int)(pair / (uint32_t)B.n_rx);
+  d.tx = (int)fdiv(pair, B.fd_rx);
   d.rx = (int)(pair - (uint32_t)d.tx * (uint32_t)B.n_rx);
   int pos[N];
 #pragma unroll
   for (int i = N - 1; i >= 0; --i) {
     const uint32_t base = Pat<N, Q>::quad(i) ? nq : ne;
-    const uint32_t q = r / base;
+    const uint32_t q = fdiv(r, Pat<N, Q>::quad(i) ? B.fd_quad : B.fd_edge);
     pos[i] = tb.type_pos[(Pat<N, Q>::quad(i) ? 0u : nq) + (r - q * base)];
     r = q;
   }
@@ -503,17 +501,19 @@ __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, 
 // of its warp's chunk (chunks of cfg.chunk paths are claimed from a global
 // counter), so lanes do not idle behind the warp's slowest path.  To amortise
 // the divergent start-up code, lanes refill only when at least cfg.refill of
-// them are free, or when none is busy.  The chunk is sized per launch so that
+// them are free, or when none is busy; a finished path stays in its lane's
+// registers until then, so that writing it out shares that divergent pass.  The chunk is sized per launch so that
 // every warp claims several chunks (a short tail) but few atomics are needed.
 
-// CTAs per SM that the register allocation of the refill kernels targets
-// (1: no constraint beyond kThreads).  A build-time tuning constant.
-#ifndef FPT_BFGS_MIN_CTAS
-#define FPT_BFGS_MIN_CTAS 1
-#endif
+// CTAs per SM that the register allocation of the refill kernels targets: four up to
+// order 3, whose kernels all fit 128 registers without spilling (left to itself, ptxas
+// gives some order-3 pattern kernels 137 and so only three CTAs per SM); no constraint
+// beyond kThreads for the longer orders, which need 168-255.
+template <int N>
+constexpr int kBfgsMinCtas = N <= 3 ? 4 : 1;
 
 template <int N, unsigned Q, int kSrc>
-__global__ void __launch_bounds__(kThreads, FPT_BFGS_MIN_CTAS) bfgs_refill_kernel(SceneDev S, BatchDev B, SolveCfg cfg, uint64_t n_local,
+__global__ void __launch_bounds__(kThreads, kBfgsMinCtas<N>) bfgs_refill_kernel(SceneDev S, BatchDev B, SolveCfg cfg, uint64_t n_local,
                                                                const PathRec* __restrict__ list,
                                                                float* __restrict__ T_out,
                                                                uint8_t* __restrict__ status_out,
@@ -529,10 +529,15 @@ __global__ void __launch_bounds__(kThreads, FPT_BFGS_MIN_CTAS) bfgs_refill_kerne
   PathState<N, Q> P;
   if constexpr (kSmemHFloats<N, Q> > 0) P.H.p = s_tab + threadIdx.x;
   bool active = false;
+  bool owed = false;  // the lane's finished path is written out at the next refill (one divergent pass for both)
   for (;;) {
     unsigned free_mask = __ballot_sync(full, !active);
     const int n_free = __popc(free_mask);
     if (more && (n_free >= cfg.refill || n_free == 32)) {
+      if (owed) {
+        path_finish<N, Q>(P, B.n_max, T_out, status_out, iters_out);
+        owed = false;
+      }
       // hand out paths to free lanes, claiming new chunks as needed
       while (more && free_mask) {
         if (next >= end) {
@@ -571,10 +576,11 @@ __global__ void __launch_bounds__(kThreads, FPT_BFGS_MIN_CTAS) bfgs_refill_kerne
       continue;
     }
     if (active && bfgs_step<N, Q>(P, cfg)) {
-      path_finish<N, Q>(P, B.n_max, T_out, status_out, iters_out);
       active = false;
+      owed = true;
     }
   }
+  if (owed) path_finish<N, Q>(P, B.n_max, T_out, status_out, iters_out);
 }
 
 // Arguments of one BFGS launch over a slice of paths.
@@ -630,9 +636,16 @@ cudaError_t launch_bfgs_nq(const BfgsLaunch& a) {
     if (e != cudaSuccess) return e;
     // at least ~8 chunks per warp, in whole warps of paths
     SolveCfg cfg = a.cfg;
+    BatchDev B = a.B;
+    if constexpr (kSrc == SRC_PATTERN) {
+      uint64_t cnt = 1;
+      for (int i = 0; i < N; ++i)
+        cnt *= Pat<N, Q>::quad(i) ? (uint64_t)a.B.n_alpha_quad : (uint64_t)(a.B.n_alpha - a.B.n_alpha_quad);
+      B.fd_pat = make_fastdiv(cnt);
+    }
     const uint64_t per = a.n_local / ((uint64_t)grid * (kThreads / 32) * 8);
     cfg.chunk = (int)(per >= (uint64_t)kMaxChunk ? kMaxChunk : (per < 32 ? 32 : per / 32 * 32));
-    bfgs_refill_kernel<N, Q, kSrc><<<grid, kThreads, smem, a.stream>>>(a.S, a.B, cfg, a.n_local, a.list, a.T,
+    bfgs_refill_kernel<N, Q, kSrc><<<grid, kThreads, smem, a.stream>>>(a.S, B, cfg, a.n_local, a.list, a.T,
                                                                        a.status, a.iters, use_smem, a.work);
     count_launch();
   } else {

@@ -45,8 +45,10 @@ struct fpt_ctx {
   float* d_step = nullptr;                 // first Newton steps of the second polish pass's paths
   size_t rescue_cap = 0;
   size_t step_cap = 0;                     // floats of d_step
-  unsigned* d_rescue_n = nullptr;
+  unsigned* d_rescue_n = nullptr;          // counters: FP64 polish, FP64 adjoint, selected paths, dropped paths
   fpt_mlp* init_mlp = nullptr;             // network for init_mode = 1
+  int acc_flush_tiles = 64;                // backward sums: CTA tiles between flushes of the FP32 partial sums
+  int acc_smem = 1;                        // backward sums: 1 = FP32 partial sums per CTA, 0 = straight to FP64
   char msg[512] = "ok";
   // kernel timing
   bool prof = false;
@@ -104,6 +106,10 @@ struct fpt_scene {
   double* d_rx64 = nullptr;
   float* d_occ = nullptr;  // planar objects as occluders (kOcc floats each)
   int n_occ = 0;
+  uint8_t* d_types = nullptr;      // object types and occluder slots (-1: edge), for records built on the device
+  int32_t* d_occ_slot = nullptr;
+  int tx_cap = 0, rx_cap = 0;      // endpoints the device buffers hold
+  std::vector<int32_t> h_occ_slot;
   // host sources of the asynchronous uploads, kept until the device buffers are freed (cudaFree
   // waits for the device, so no copy from them is still pending when they go)
   std::vector<float> h_rec32, h_aux, h_reclo, h_occ, h_tx32, h_rx32;
@@ -160,6 +166,11 @@ struct fpt_mlp {
   __nv_bfloat16* d_wt = nullptr;  // BF16 weights pre-tiled for the fused inference kernel
   bool wt_stale = true;
   float* d_loss = nullptr;
+  // fpt_mlp_train: one shuffled mini-batch and the per-epoch mean losses
+  __nv_bfloat16* d_Xb = nullptr;
+  float *d_Tb = nullptr, *d_Gb = nullptr, *d_hist = nullptr;
+  uint64_t train_cap = 0;
+  size_t hist_cap = 0;
   // activations / gradients for a batch of up to cap rows
   uint64_t cap = 0;
   __nv_bfloat16 *d_H1 = nullptr, *d_H2 = nullptr, *d_H3 = nullptr, *d_dZa = nullptr, *d_dZb = nullptr,
@@ -231,7 +242,10 @@ fpt_status fpt_create(fpt_ctx** out, int device, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_rescue_n, 3 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_rescue_n, 4 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_rescue_n, 0, 4 * sizeof(unsigned));
+  // the fixed array of fpt_backward_noalloc: its address on this device, looked up again for every context
+  if (e == cudaSuccess) e = noalloc_lookup(device);
   if (e != cudaSuccess) {
     fpt_destroy(ctx);
     return FPT_ECUDA;
@@ -273,6 +287,15 @@ fpt_status fpt_set_stream(fpt_ctx* ctx, void* cuda_stream) {
 }
 
 const char* fpt_last_error(const fpt_ctx* ctx) { return ctx ? ctx->msg : "null context"; }
+
+fpt_status fpt_set_accumulation(fpt_ctx* ctx, int32_t flush_tiles, int32_t smem) {
+  if (!ctx) return FPT_EINVAL;
+  if (flush_tiles < 1 || (smem != 0 && smem != 1))
+    return fail(ctx, FPT_EINVAL, "fpt_set_accumulation: flush_tiles must be >= 1 and smem 0 or 1");
+  ctx->acc_flush_tiles = flush_tiles;
+  ctx->acc_smem = smem;
+  return FPT_OK;
+}
 
 fpt_status fpt_sync(fpt_ctx* ctx) {
   if (!ctx) return FPT_EINVAL;
@@ -387,7 +410,17 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
     occ.push_back(idf);
   }
   s->n_occ = (int)(occ.size() / kOcc);
+  s->h_occ_slot.assign(n_obj, -1);
+  for (int k = 0, q = 0; k < n_obj; ++k)
+    if (types[k] == FPT_QUAD) s->h_occ_slot[k] = q++;
   cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_types, (size_t)n_obj);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_occ_slot, (size_t)n_obj * sizeof(int32_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_types, s->types.data(), (size_t)n_obj, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_occ_slot, s->h_occ_slot.data(), (size_t)n_obj * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        ctx->stream);
   if (e == cudaSuccess && s->n_occ) e = cudaMalloc(&s->d_occ, occ.size() * sizeof(float));
   if (e == cudaSuccess && s->n_occ)
     e = cudaMemcpyAsync(s->d_occ, occ.data(), occ.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
@@ -413,6 +446,52 @@ fpt_status fpt_scene_upload(fpt_ctx* ctx, const uint8_t* types, const double* ve
   return FPT_OK;
 }
 
+fpt_status fpt_scene_upload_device(fpt_ctx* ctx, const uint8_t* types, const float* verts, int32_t n_obj,
+                                   const double* centre, fpt_scene** out) {
+  if (!ctx || !types || !verts || !out) return fail(ctx, FPT_EINVAL, "null argument");
+  *out = nullptr;
+  if (n_obj < 1 || n_obj > 65535) return fail(ctx, FPT_EINVAL, "n_obj %d outside [1, 65535]", n_obj);
+  for (int k = 0; k < n_obj; ++k)
+    if (types[k] != FPT_QUAD && types[k] != FPT_EDGE) return fail(ctx, FPT_EINVAL, "object %d: bad type", k);
+  if (centre)
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(centre[c])) return fail(ctx, FPT_EINVAL, "non-finite centre");
+  fpt_scene* s = new (std::nothrow) fpt_scene();
+  if (!s) return FPT_ENOMEM;
+  s->ctx = ctx;
+  s->n_obj = n_obj;
+  s->types.assign(types, types + n_obj);
+  for (int c = 0; c < 3; ++c) s->centre[c] = centre ? centre[c] : 0.0;
+  s->h_occ_slot.assign(n_obj, -1);
+  int n_occ = 0;
+  for (int k = 0; k < n_obj; ++k)
+    if (types[k] == FPT_QUAD) s->h_occ_slot[k] = n_occ++;
+  s->n_occ = n_occ;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_types, (size_t)n_obj);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_occ_slot, (size_t)n_obj * sizeof(int32_t));
+  if (e == cudaSuccess && n_occ) e = cudaMalloc(&s->d_occ, (size_t)n_occ * kOcc * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_rec32, (size_t)n_obj * kRec32 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_rec64, (size_t)n_obj * kRec64 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_aux, (size_t)n_obj * kAux * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_reclo, (size_t)n_obj * kRecLo * sizeof(float));
+  // the type tables' host sources stay in the scene until it is freed
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_types, s->types.data(), (size_t)n_obj, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_occ_slot, s->h_occ_slot.data(), (size_t)n_obj * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess)
+    e = launch_object_records(n_obj, s->d_types, s->d_occ_slot, verts, s->centre, s->d_rec32, s->d_reclo, s->d_rec64,
+                              s->d_aux, s->d_occ, ctx->d_err, ctx->stream);
+  if (e != cudaSuccess) {
+    fpt_scene_free(s);
+    return fail(ctx, FPT_ECUDA, "device scene upload: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return FPT_OK;
+}
+
 void fpt_scene_free(fpt_scene* s) {
   if (!s) return;
   cudaFree(s->d_rec32);
@@ -424,6 +503,8 @@ void fpt_scene_free(fpt_scene* s) {
   cudaFree(s->d_tx64);
   cudaFree(s->d_rx64);
   cudaFree(s->d_occ);
+  cudaFree(s->d_types);
+  cudaFree(s->d_occ_slot);
   delete s;
 }
 
@@ -462,8 +543,46 @@ fpt_status fpt_set_endpoints(fpt_scene* s, const double* tx, int32_t n_tx, const
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   CUDA_OR_FAIL(ctx, upload_points(tx, n_tx, s->centre, &s->d_tx32, &s->d_tx64, s->h_tx32, s->h_tx64, ctx->stream));
   CUDA_OR_FAIL(ctx, upload_points(rx, n_rx, s->centre, &s->d_rx32, &s->d_rx64, s->h_rx32, s->h_rx64, ctx->stream));
+  s->n_tx = s->tx_cap = n_tx;
+  s->n_rx = s->rx_cap = n_rx;
+  return FPT_OK;
+}
+
+// Device buffers for n endpoints: kept when they already hold n, reallocated otherwise (cudaFree waits
+// for the device, so a pending copy from an earlier host upload into the old buffer has finished).
+static cudaError_t endpoint_buffers(int n, int* cap, float** d32, double** d64) {
+  if (n <= *cap && *d32 && *d64) return cudaSuccess;
+  cudaFree(*d32);
+  cudaFree(*d64);
+  *d32 = nullptr;
+  *d64 = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(d32, (size_t)n * kEnd32 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(d64, (size_t)n * 3 * sizeof(double));
+  if (e == cudaSuccess) *cap = n;
+  return e;
+}
+
+fpt_status fpt_set_endpoints_device(fpt_scene* s, const float* tx, int32_t n_tx, const float* rx, int32_t n_rx) {
+  if (!s || !tx || !rx) return s ? fail(s->ctx, FPT_EINVAL, "null argument") : FPT_EINVAL;
+  fpt_ctx* ctx = s->ctx;
+  if (n_tx < 1 || n_rx < 1) return fail(ctx, FPT_EINVAL, "need at least one TX and one RX");
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  CUDA_OR_FAIL(ctx, endpoint_buffers(n_tx, &s->tx_cap, &s->d_tx32, &s->d_tx64));
+  CUDA_OR_FAIL(ctx, endpoint_buffers(n_rx, &s->rx_cap, &s->d_rx32, &s->d_rx64));
+  CUDA_OR_FAIL(ctx, launch_endpoint_records(tx, n_tx, s->centre, s->d_tx32, s->d_tx64, ctx->d_err, ctx->stream));
+  CUDA_OR_FAIL(ctx, launch_endpoint_records(rx, n_rx, s->centre, s->d_rx32, s->d_rx64, ctx->d_err, ctx->stream));
   s->n_tx = n_tx;
   s->n_rx = n_rx;
+  return FPT_OK;
+}
+
+fpt_status fpt_scene_update_vertices(fpt_scene* s, const float* verts) {
+  if (!s || !verts) return s ? fail(s->ctx, FPT_EINVAL, "null argument") : FPT_EINVAL;
+  fpt_ctx* ctx = s->ctx;
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  CUDA_OR_FAIL(ctx, launch_object_records(s->n_obj, s->d_types, s->d_occ_slot, verts, s->centre, s->d_rec32,
+                                          s->d_reclo, s->d_rec64, s->d_aux, s->d_occ, ctx->d_err, ctx->stream));
   return FPT_OK;
 }
 
@@ -502,6 +621,15 @@ static fpt_status make_alphabet(fpt_ctx* ctx, const fpt_scene* s, const int32_t*
   b->dev.type_pos = b->d_type_pos;
   b->types = s->types;
   return FPT_OK;
+}
+
+// Reciprocals of the exhaustive decoders' divisors (FastDiv).
+static void set_reciprocals(BatchDev& d) {
+  d.fd_rx = make_fastdiv((uint64_t)d.n_rx);
+  d.fd_alpha = make_fastdiv((uint64_t)d.n_alpha);
+  d.fd_quad = make_fastdiv((uint64_t)d.n_alpha_quad);
+  d.fd_edge = make_fastdiv((uint64_t)(d.n_alpha - d.n_alpha_quad));
+  for (int n = 0; n <= kMaxOrder; ++n) d.fd_kpow[n] = make_fastdiv(d.kpow[n]);
 }
 
 static fpt_status check_orders(fpt_ctx* ctx, int lo, int hi) {
@@ -549,6 +677,7 @@ fpt_status fpt_batch_exhaustive(fpt_ctx* ctx, const fpt_scene* s, const int32_t*
   }
   d.per_pair = acc;
   d.n_paths = acc * (uint64_t)s->n_tx * (uint64_t)s->n_rx;
+  set_reciprocals(d);
   *out = b;
   return FPT_OK;
 }
@@ -580,6 +709,7 @@ fpt_status fpt_batch_seeded(fpt_ctx* ctx, const fpt_scene* s, const int32_t* alp
   d.seed = seed;
   d.per_pair = per_pair;
   d.n_paths = per_pair * (uint64_t)s->n_tx * (uint64_t)s->n_rx;
+  set_reciprocals(b->dev);
   *out = b;
   return FPT_OK;
 }
@@ -611,6 +741,7 @@ fpt_status fpt_batch_explicit(fpt_ctx* ctx, const fpt_scene* s, const int32_t* i
   d.tx_idx = tx_idx_dev;
   d.rx_idx = rx_idx_dev;
   b->types = s->types;
+  set_reciprocals(b->dev);
   *out = b;
   return FPT_OK;
 }
@@ -892,7 +1023,10 @@ fpt_status fpt_solve_grad(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc,
   gc.cond_adj = p.cond_fp64;
   gc.deg_tol = prm ? prm->deg_tol : p.deg_tol;
   gc.gacc = ctx->d_gacc;
-  gc.flush_tiles = 64;
+  gc.flush_tiles = ctx->acc_flush_tiles;
+  gc.acc_in_smem = ctx->acc_smem;
+  gc.dropped = ctx->d_rescue_n + 3;
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(gc.dropped, 0, sizeof(unsigned), ctx->stream));
   st = solve_impl(ctx, s, bc, prm, T, X, L, status, iters, rho, &gc);
   if (st != FPT_OK) return st;
   const SceneDev S = scene_dev(s);
@@ -945,7 +1079,9 @@ fpt_status fpt_backward(fpt_ctx* ctx, const fpt_scene* s, const fpt_batch* bc, c
   fpt_default_params(&p);
   if (!dL && dL_status_mask && !status && bc->dev.n_paths > 0)
     return fail(ctx, FPT_EINVAL, "dL_status_mask needs status");
-  BackwardCfg bc_cfg{p.cond_fp64, p.deg_tol, 1, 64, dL ? (uint8_t)0 : dL_status_mask};
+  BackwardCfg bc_cfg{p.cond_fp64, p.deg_tol, ctx->acc_smem, ctx->acc_flush_tiles, dL ? (uint8_t)0 : dL_status_mask};
+  bc_cfg.dropped = ctx->d_rescue_n + 3;
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(bc_cfg.dropped, 0, sizeof(unsigned), ctx->stream));
   for (int n = 1; n <= kMaxOrder; ++n) {
     const PathRec* list;
     uint64_t cnt = order_slice(b, n, &list);
@@ -1065,9 +1201,21 @@ fpt_status fpt_backward_noalloc(fpt_ctx* ctx, const fpt_scene* s, const fpt_batc
   CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
   fpt_solve_params p;
   fpt_default_params(&p);
-  BackwardCfg cfg{p.cond_fp64, p.deg_tol, 1, 64, dL ? (uint8_t)0 : dL_status_mask};
+  BackwardCfg cfg{p.cond_fp64, p.deg_tol, ctx->acc_smem, ctx->acc_flush_tiles, dL ? (uint8_t)0 : dL_status_mask};
+  cfg.dropped = ctx->d_rescue_n + 3;  // context memory, allocated by fpt_create
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(cfg.dropped, 0, sizeof(unsigned), ctx->stream));
   CUDA_OR_FAIL(ctx, launch_backward_noalloc(ctx->device, scene_dev(s), b->dev, cfg, lists, counts, T, status, dX, dL,
                                             g_tx, g_rx, g_vertices, ctx->stream, ctx->n_sm));
+  return FPT_OK;
+}
+
+fpt_status fpt_backward_dropped(fpt_ctx* ctx, uint64_t* count) {
+  if (!ctx || !count) return fail(ctx, FPT_EINVAL, "null argument");
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  unsigned h = 0;
+  CUDA_OR_FAIL(ctx, cudaMemcpyAsync(&h, ctx->d_rescue_n + 3, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  *count = h;
   return FPT_OK;
 }
 
@@ -1305,7 +1453,7 @@ void fpt_mlp_free(fpt_mlp* m) {
   if (m->ctx && m->ctx->init_mlp == m) m->ctx->init_mlp = nullptr;
   mlp_free_ws(m);
   for (void* p : {(void*)m->d_w, (void*)m->d_m, (void*)m->d_v, (void*)m->d_g, (void*)m->d_wb, (void*)m->d_wt,
-                  (void*)m->d_loss})
+                  (void*)m->d_loss, (void*)m->d_Xb, (void*)m->d_Tb, (void*)m->d_Gb, (void*)m->d_hist})
     cudaFree(p);
   delete m;
 }
@@ -1444,6 +1592,89 @@ fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* m, const void* X, const flo
   if (loss) {
     CUDA_OR_FAIL(ctx, cudaMemcpyAsync(loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return FPT_OK;
+}
+
+fpt_status fpt_mlp_train(fpt_ctx* ctx, fpt_mlp* m, const void* X, const float* T, const float* G, uint64_t n,
+                         const fpt_train_params* prm, float* loss_per_epoch) {
+  if (!ctx || !m || !prm) return fail(ctx, FPT_EINVAL, "null argument");
+  if (m->ctx != ctx) return fail(ctx, FPT_EINVAL, "network belongs to another context");
+  const fpt_train_params p = *prm;
+  if (p.epochs < 1 || p.batch < 128 || !(p.lr > 0.f) || !(p.lr_decay > 0.f))
+    return fail(ctx, FPT_EINVAL, "fpt_mlp_train: epochs >= 1, batch >= 128, lr > 0 and lr_decay > 0 required");
+  if ((uint64_t)p.batch > n) return fail(ctx, FPT_EINVAL, "fpt_mlp_train: fewer samples (%llu) than one batch",
+                                         (unsigned long long)n);
+  if (!X || !T || !G) return fail(ctx, FPT_EINVAL, "fpt_mlp_train: X, T and G are required");
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  const uint64_t B = (uint64_t)p.batch;
+  fpt_status st = mlp_ensure_ws(ctx, m, B, true);
+  if (st != FPT_OK) return st;
+  if (B > m->train_cap || (size_t)p.epochs > m->hist_cap) {
+    cudaFree(m->d_Xb);
+    cudaFree(m->d_Tb);
+    cudaFree(m->d_Gb);
+    cudaFree(m->d_hist);
+    m->d_Xb = nullptr;
+    m->d_Tb = m->d_Gb = m->d_hist = nullptr;
+    m->train_cap = m->hist_cap = 0;
+    cudaError_t e = cudaMalloc(&m->d_Xb, B * kMlpIn * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_Tb, B * 8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_Gb, B * 12 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_hist, (size_t)p.epochs * sizeof(float));
+    if (e != cudaSuccess) return fail(ctx, FPT_ENOMEM, "fpt_mlp_train: batch buffers: %s", cudaGetErrorString(e));
+    m->train_cap = B;
+    m->hist_cap = (size_t)p.epochs;
+  }
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(m->d_hist, 0, (size_t)p.epochs * sizeof(float), ctx->stream));
+  const uint64_t steps = n / B;  // the last partial batch of every epoch is left out
+  const __nv_bfloat16* Xs = static_cast<const __nv_bfloat16*>(X);
+  float lr = p.lr;
+  for (int ep = 0; ep < p.epochs; ++ep) {
+    // a new seeded order of the samples every epoch (splitmix64 of seed and epoch)
+    uint64_t s0 = p.seed + 0x9E3779B97F4A7C15ULL * (uint64_t)(ep + 1);
+    const uint64_t key = sm64_next(s0);
+    for (uint64_t k = 0; k < steps; ++k) {
+      CUDA_OR_FAIL(ctx, launch_mlp_gather(Xs, T, G, n, k * B, B, key, m->d_Xb, m->d_Tb, m->d_Gb, ctx->stream));
+      st = fpt_mlp_train_step(ctx, m, m->d_Xb, m->d_Tb, m->d_Gb, B, lr, nullptr);
+      if (st != FPT_OK) return st;
+      CUDA_OR_FAIL(ctx, launch_mlp_accumulate(m->d_hist + ep, m->d_loss, 1.f / (float)steps, ctx->stream));
+    }
+    lr *= p.lr_decay;
+  }
+  if (loss_per_epoch) {
+    CUDA_OR_FAIL(ctx, cudaMemcpyAsync(loss_per_epoch, m->d_hist, (size_t)p.epochs * sizeof(float),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return FPT_OK;
+}
+
+fpt_status fpt_mlp_infer(fpt_ctx* ctx, fpt_mlp* m, const fpt_scene* s, const fpt_batch* bc, float* T) {
+  fpt_status st = check_scene_batch(ctx, s, bc);
+  if (st != FPT_OK) return st;
+  if (!m) return fail(ctx, FPT_EINVAL, "null network");
+  if (m->ctx != ctx) return fail(ctx, FPT_EINVAL, "network belongs to another context");
+  if (!T && bc->dev.n_paths > 0) return fail(ctx, FPT_EINVAL, "T_out is required");
+  fpt_batch* b = const_cast<fpt_batch*>(bc);
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  st = ensure_buckets(ctx, b, scene_dev(s));
+  if (st != FPT_OK) return st;
+  const SceneDev S = scene_dev(s);
+  if (b->dev.n_paths == 0) return FPT_OK;
+  // slots past a path's order stay zero
+  CUDA_OR_FAIL(ctx, cudaMemsetAsync(T, 0, b->dev.n_paths * (uint64_t)b->dev.n_max * 2 * sizeof(float), ctx->stream));
+  if (m->wt_stale) {
+    CUDA_OR_FAIL(ctx, launch_mlp_tile_weights(m->d_wb, m->d_wt, ctx->stream));
+    m->wt_stale = false;
+  }
+  for (int n = 1; n <= kMaxOrder; ++n) {
+    const PathRec* list;
+    const uint64_t cnt = order_slice(b, n, &list);
+    if (!cnt) continue;
+    ProfScope ps(ctx, FPT_K_MLP);
+    CUDA_OR_FAIL(ctx, launch_mlp_infer(S, b->dev, n, list, cnt, 1.f / m->scale, m->d_wt, m->d_w, T, ctx->d_err,
+                                       ctx->stream, ctx->n_sm));
   }
   return FPT_OK;
 }

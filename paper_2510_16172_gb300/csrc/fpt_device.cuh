@@ -25,6 +25,8 @@ constexpr uint8_t ST_SKIP = ST_REPEAT | ST_INVALID;  // never solved
 
 // device error word codes
 constexpr int ERR_NONE = 0, ERR_BAD_ORDER = 1, ERR_SMEM = 2;
+// (3: a tensor-core wait ran out, k_mlp.cu)  4: non-finite or degenerate device-side geometry
+constexpr int ERR_BAD_GEOMETRY = 4;
 
 struct SceneDev {
   int n_obj;
@@ -43,6 +45,24 @@ struct SceneDev {
 
 enum BatchMode { BATCH_EXHAUSTIVE = 0, BATCH_SEEDED = 1, BATCH_EXPLICIT = 2 };
 
+// Division of 32-bit values by a divisor fixed per batch or launch, through a precomputed 64-bit
+// reciprocal m = ceil(2^64 / d): floor(x / d) = floor(x m / 2^64) for every x < 2^32 and 2 <= d < 2^32,
+// since x m / 2^64 exceeds x / d by less than x / 2^64 < 2^-32 <= 1 / d and so never reaches the next
+// integer.  A multiply-high replaces the long instruction sequence of an integer division.
+struct FastDiv {
+  uint64_t m;  // ceil(2^64 / d) (0 when d <= 1)
+  uint32_t d;
+};
+__host__ __device__ inline FastDiv make_fastdiv(uint64_t d) {
+  FastDiv f;
+  f.d = d > 0xFFFFFFFFull ? 0u : (uint32_t)d;  // divisors of 2^32 or more are never used on the fast path
+  f.m = f.d <= 1 ? 0ull : ~0ull / f.d + 1ull;
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
+  return f.d <= 1 ? x : (uint32_t)__umul64hi((unsigned long long)x, (unsigned long long)f.m);
+}
+
 struct BatchDev {
   int mode;
   int n_alpha;
@@ -60,6 +80,10 @@ struct BatchDev {
   const int32_t* rx_idx;    // explicit [n]
   const int32_t* type_pos;  // exhaustive: alphabet positions of the reflectors, then of the edges (ascending)
   int n_alpha_quad;         // exhaustive: reflectors in the alphabet
+  // reciprocals for the exhaustive decoders: n_rx, n_alpha, the alphabet's reflectors and edges, K^n
+  FastDiv fd_rx, fd_alpha, fd_quad, fd_edge;
+  FastDiv fd_kpow[kMaxOrder + 1];
+  FastDiv fd_pat;  // set per pattern launch: sequences of the launch's pattern per (tx, rx) pair
 };
 
 // Interaction-type pattern of a sequence of order n: bit i set = slot i is a
@@ -160,16 +184,17 @@ __device__ __forceinline__ void decode_exhaustive_order(const BatchDev& B, int n
   uint64_t kn = B.kpow[n];
   uint64_t pair, r;
   if (j <= 0xFFFFFFFFull && kn <= 0xFFFFFFFFull) {  // one order holds at most 2^32 paths: the usual case
-    const uint32_t p32 = (uint32_t)j / (uint32_t)kn;
+    const uint32_t p32 = fdiv((uint32_t)j, B.fd_kpow[n]);
     pair = p32;
     r = (uint32_t)j - p32 * (uint32_t)kn;
+    d.tx = (int)fdiv(p32, B.fd_rx);
   } else {
     pair = j / kn;
     r = j - pair * kn;
+    d.tx = (int)(pair / (uint64_t)B.n_rx);
   }
   d.g = pair * B.per_pair + B.offset[n] + r;
   d.n = n;
-  d.tx = (int)(pair / (uint64_t)B.n_rx);
   d.rx = (int)(pair - (uint64_t)d.tx * (uint64_t)B.n_rx);
   int digits[kMaxOrder];
   const uint64_t K = (uint64_t)B.n_alpha;
@@ -178,7 +203,7 @@ __device__ __forceinline__ void decode_exhaustive_order(const BatchDev& B, int n
 #pragma unroll
     for (int q = kMaxOrder - 1; q >= 0; --q)
       if (q < n) {
-        uint32_t qq = r32 / K32;
+        uint32_t qq = fdiv(r32, B.fd_alpha);
         digits[q] = (int)(r32 - qq * K32);
         r32 = qq;
       }

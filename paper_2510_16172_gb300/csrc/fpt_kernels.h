@@ -58,6 +58,8 @@ struct BackwardCfg {
   // a select pass lists them first so the adjoint's warps run full (nullptr: every path is visited)
   uint32_t* sel = nullptr;
   unsigned* sel_count = nullptr;
+  // counter of the paths whose Hessian also fails the FP64 pivot test (left out of the sums; nullptr: not counted)
+  unsigned* dropped = nullptr;
 };
 
 // Per-order launches (n = 1..kMaxOrder).  `list` = nullptr for exhaustive batches.
@@ -79,6 +81,8 @@ struct GradCfg {
   uint32_t* rescue_list;    // paths whose adjoint runs in the FP64 pass (n_local entries)
   unsigned* rescue_count;
   int flush_tiles;          // flush the shared accumulators every this many CTA tiles
+  int acc_in_smem = 1;      // 0: every path's terms go straight into the FP64 accumulators
+  unsigned* dropped = nullptr;  // as BackwardCfg::dropped
 };
 
 // Double-float polish, then an FP64 pass over the paths whose FP32 pivots failed
@@ -103,6 +107,8 @@ cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const B
 constexpr int kNoAllocMaxAcc = 1 << 16;      // 9 n_obj + 3 (n_tx + n_rx) FP64 accumulators
 constexpr int kNoAllocMaxSlice = 1 << 20;    // paths of one order in the batch
 constexpr int kNoAllocMaxDevices = 64;
+// Look up (again) the device address of the fixed scratch array on `device` (current).
+cudaError_t noalloc_lookup(int device);
 cudaError_t launch_backward_noalloc(int device, const SceneDev& S, const BatchDev& B, const BackwardCfg& cfg,
                                     const PathRec* const* lists, const uint64_t* counts, const float* T,
                                     const uint8_t* status, const float* dX, const float* dL, float* g_tx, float* g_rx,
@@ -131,6 +137,14 @@ cudaError_t launch_occlusion(const SceneDev& S, const BatchDev& B, int n, const 
                              const float* T, const uint8_t* status, uint8_t mask, const float* occ, int n_occ,
                              float tol, uint16_t* blocked, uint32_t* sel, unsigned* sel_count, cudaStream_t stream,
                              int n_sm);
+// Records from caller-owned device FP32 coordinates (k_scene.cu): endpoints p [n][3] -> kEnd32 FP32 and
+// 3 FP64 values each; objects verts [n_obj][3][3] -> FP32, low-part, FP64, aux and occluder records.
+// Non-finite or degenerate input sets ERR_BAD_GEOMETRY in *err.
+cudaError_t launch_endpoint_records(const float* p, int n, const double* centre, float* rec32, double* rec64,
+                                    int* err, cudaStream_t stream);
+cudaError_t launch_object_records(int n_obj, const uint8_t* types, const int32_t* occ_slot, const float* verts,
+                                  const double* centre, float* rec32, float* reclo, double* rec64, float* aux,
+                                  float* occ, int* err, cudaStream_t stream);
 cudaError_t launch_backward_finalize(const SceneDev& S, const uint8_t* types, const double* gacc, float* g_tx,
                                      float* g_rx, float* g_vertices, cudaStream_t stream);
 

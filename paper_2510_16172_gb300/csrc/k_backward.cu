@@ -97,8 +97,9 @@ cudaError_t launch_backward(int n, const SceneDev& S, const BatchDev& B, const B
 // the list of the FP64 pass.  It exists once per GPU that loads the library
 // and lives until the process exits.  Host code must not pass the symbol
 // itself to a kernel (on the host it names a host-side stand-in): its device
-// address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, and cached.
+// address is looked up with cudaGetSymbolAddress, with that device current,
+// whenever a context is created on the device (noalloc_lookup), and cached; a
+// device reset can move the array, and the next context looks it up again.
 // ---------------------------------------------------------------------------
 constexpr size_t kNoAllocAccBytes = (size_t)kNoAllocMaxAcc * sizeof(double);
 constexpr size_t kNoAllocCountBytes = 256;
@@ -108,15 +109,29 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 static std::mutex g_noalloc_mutex;
 static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
+// The calling thread has `device` current.
+cudaError_t noalloc_lookup(int device) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return cudaSuccess;  // such devices cannot use the array
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  g_noalloc_addr[device] = p;
+  return cudaSuccess;
+}
+
 static cudaError_t noalloc_scratch(int device, unsigned char** out) {
   if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // the calling thread has `device` current
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[device] = p;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_addr[device]) {
+      *out = static_cast<unsigned char*>(g_noalloc_addr[device]);
+      return cudaSuccess;
+    }
   }
+  cudaError_t e = noalloc_lookup(device);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   *out = static_cast<unsigned char*>(g_noalloc_addr[device]);
   return cudaSuccess;
 }

@@ -670,6 +670,81 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// ---------------------------------------------------------------------------
+// Training data order: a seeded pseudo-random permutation of [0, n) per epoch, evaluated index by index
+// (a four-round Feistel network on 2h-bit words, 2^(2h) >= n, with cycle walking back into [0, n)), and
+// the gather of one mini-batch's rows into contiguous buffers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t feistel(uint64_t x, int h, uint64_t key) {
+  const uint64_t mask = (1ULL << h) - 1ULL;
+  uint64_t l = x >> h, r = x & mask;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t f = mix64(r ^ (key + 0x9E3779B97F4A7C15ULL * (uint64_t)(k + 1))) & mask;
+    const uint64_t nl = r;
+    r = l ^ f;
+    l = nl;
+  }
+  return (l << h) | r;
+}
+
+// Position k of the permutation of [0, n) drawn by `key` (n >= 1).  The walk stays on k's cycle of the
+// Feistel permutation, which holds k itself, so it returns a value below n; the bound only guards the loop.
+__device__ __forceinline__ uint64_t perm_index(uint64_t k, uint64_t n, int h, uint64_t key) {
+  uint64_t x = k;
+  for (int i = 0; i < (1 << 20); ++i) {
+    x = feistel(x, h, key);
+    if (x < n) return x;
+  }
+  return k;
+}
+
+__global__ void mlp_gather_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ T,
+                                  const float* __restrict__ G, uint64_t n, uint64_t first, uint64_t B, int h,
+                                  uint64_t key, __nv_bfloat16* __restrict__ Xb, float* __restrict__ Tb,
+                                  float* __restrict__ Gb) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t src = perm_index(first + i, n, h, key);
+    const uint4* xs = reinterpret_cast<const uint4*>(X + src * kMlpIn);
+    uint4* xd = reinterpret_cast<uint4*>(Xb + i * kMlpIn);
+#pragma unroll
+    for (int q = 0; q < kMlpIn / 8; ++q) xd[q] = xs[q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Tb[i * 8 + q] = T[src * 8 + q];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) Gb[i * 12 + q] = G[src * 12 + q];
+  }
+}
+
+// dst += w * src (one value: a batch's loss into its epoch's mean)
+__global__ void mlp_accumulate_kernel(float* dst, const float* src, float w) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst += w * *src;
+}
+
+cudaError_t launch_mlp_gather(const __nv_bfloat16* X, const float* T, const float* G, uint64_t n, uint64_t first,
+                              uint64_t B, uint64_t key, __nv_bfloat16* Xb, float* Tb, float* Gb,
+                              cudaStream_t stream) {
+  int h = 1;
+  while ((1ULL << (2 * h)) < n) ++h;
+  const uint64_t want = (B + 255) / 256;
+  mlp_gather_kernel<<<(unsigned)(want < 4096 ? (want ? want : 1) : 4096), 256, 0, stream>>>(X, T, G, n, first, B, h,
+                                                                                           key, Xb, Tb, Gb);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_accumulate(float* dst, const float* src, float w, cudaStream_t stream) {
+  mlp_accumulate_kernel<<<1, 32, 0, stream>>>(dst, src, w);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mlp_tile_weights(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t stream) {
   mlp_tile_weights_kernel<<<128, 256, 0, stream>>>(wb, wt);
   count_launch();

@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
           // the FP64 polish decides this path's status; the FP64 adjoint pass reads it
           gc.rescue_list[atomicAdd(gc.rescue_count, 1u)] = (uint32_t)j;
         } else if (!(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE)) &&
-                   (gc.dX != nullptr ||
+                   (has_point_cotangent<N>(gc.dX, g, n_max) ||
                     (gc.dL ? gc.dL[g] != 0.f : (gc.dl_mask && (st & gc.dl_mask) == gc.dl_mask)))) {
           // (a path with no cotangent contributes exactly zero and is skipped)
           if (fact_ok && adj_ok) {
@@ -722,7 +722,7 @@ cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const PolishCf
   if (smemff <= 160 * 1024) {
     use_smem = kSmemRecords;
     sff = smemff;
-    if (grad) {
+    if (grad && grad->acc_in_smem) {
       const size_t acc = (size_t)(9 * S.n_obj + 3 * (S.n_tx + S.n_rx)) * sizeof(float);
       if (sff + acc <= 160 * 1024) {
         use_smem |= kSmemAcc;
@@ -777,7 +777,8 @@ cudaError_t launch_polish_n(const SceneDev& S, const BatchDev& B, const PolishCf
   e = cudaGetLastError();
   if (e != cudaSuccess || !grad) return e;
   // FP64 adjoint for the paths the fused kernel listed (final T and status are in place)
-  const BackwardCfg bc{gc.cond_adj, gc.deg_tol, 0, 0, gc.dL ? (uint8_t)0 : gc.dl_mask};
+  BackwardCfg bc{gc.cond_adj, gc.deg_tol, 0, 0, gc.dL ? (uint8_t)0 : gc.dl_mask};
+  bc.dropped = gc.dropped;
   return launch_backward_rescue(N, S, B, bc, n_local, list, T, status, gc.dX, gc.dL, gc.gacc, stream, n_sm,
                                 gc.rescue_list, gc.rescue_count);
 }

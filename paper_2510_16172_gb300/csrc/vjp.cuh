@@ -11,6 +11,18 @@
 
 namespace fpt {
 
+// A path carries a point cotangent when one of its dX entries is non-zero.  A path whose
+// cotangents are all zero contributes exactly zero to the sums, so the adjoint skips it.
+template <int N>
+__device__ __forceinline__ bool has_point_cotangent(const float* __restrict__ dX, uint64_t g, int n_max) {
+  if (!dX) return false;
+  const float* p = dX + g * (uint64_t)n_max * 3;
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < 3 * N; ++k) any = any || p[k] != 0.f;
+  return any;
+}
+
 // Warp-aggregated accumulate of `cnt` values into acc[base + k] (or, without
 // shared accumulators, into gacc[gbase + k]).  Lanes with base < 0 add
 // nothing.  If every adding lane has the same base the warp sums its values

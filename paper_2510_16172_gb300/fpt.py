@@ -47,6 +47,11 @@ class SolveParams(C.Structure):
                 ("reserved", C.c_int32 * 4)]
 
 
+class TrainParams(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("lr_decay", C.c_float),
+                ("seed", C.c_uint64), ("reserved", C.c_int32 * 4)]
+
+
 # every symbol declared in include/fpt.h with (restype, argtypes)
 _vp = C.c_void_p
 _SIGS = {
@@ -55,10 +60,15 @@ _SIGS = {
     "fpt_destroy": (None, [_vp]),
     "fpt_set_stream": (C.c_int, [_vp, _vp]),
     "fpt_last_error": (C.c_char_p, [_vp]),
+    "fpt_set_accumulation": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "fpt_backward_dropped": (C.c_int, [_vp, C.POINTER(C.c_uint64)]),
     "fpt_sync": (C.c_int, [_vp]),
     "fpt_scene_upload": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.POINTER(_vp)]),
     "fpt_scene_free": (None, [_vp]),
+    "fpt_scene_upload_device": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, C.POINTER(_vp)]),
     "fpt_set_endpoints": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.c_int32]),
+    "fpt_set_endpoints_device": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.c_int32]),
+    "fpt_scene_update_vertices": (C.c_int, [_vp, _vp]),
     "fpt_batch_exhaustive": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(_vp)]),
     "fpt_batch_seeded": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32,
                                    C.POINTER(_vp)]),
@@ -86,6 +96,8 @@ _SIGS = {
     "fpt_mlp_forward": (C.c_int, [_vp, _vp, _vp, C.c_uint64, _vp]),
     "fpt_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, C.POINTER(C.c_float), _vp]),
     "fpt_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, C.c_float, C.POINTER(C.c_float)]),
+    "fpt_mlp_train": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, C.POINTER(TrainParams), _vp]),
+    "fpt_mlp_infer": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "fpt_set_init_mlp": (C.c_int, [_vp, _vp]),
     "fpt_profile_enable": (C.c_int, [_vp, C.c_int]),
     "fpt_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
@@ -136,6 +148,10 @@ def _check(ctx_handle, rc):
         raise FptError(f"{_ERRORS.get(rc, rc)}: {msg.decode() if msg else ''}")
 
 
+def _is_cuda_tensor(x) -> bool:
+    return getattr(x, "is_cuda", False) is True
+
+
 def _need_cuda(t, dtype, name):
     import torch
 
@@ -171,6 +187,10 @@ class Context:
     def sync(self):
         _check(self.handle, library().fpt_sync(self.handle))
 
+    def set_accumulation(self, flush_tiles: int = 64, smem: int = 1):
+        """fpt_set_accumulation: how the backward calls sum the per-path gradient terms."""
+        _check(self.handle, library().fpt_set_accumulation(self.handle, int(flush_tiles), int(smem)))
+
     def close(self):
         if getattr(self, "handle", None):
             library().fpt_destroy(self.handle)
@@ -186,13 +206,26 @@ class Context:
 class Scene:
     """fpt_scene_upload + fpt_set_endpoints (host float64 inputs)."""
 
-    def __init__(self, ctx: Context, types, verts, tx=None, rx=None):
+    def __init__(self, ctx: Context, types, verts, tx=None, rx=None, centre=None):
+        """Host float64 vertices: fpt_scene_upload.  A CUDA float32 tensor [n_obj, 3, 3]:
+        fpt_scene_upload_device, recentred on `centre` (host, 3 floats; None = origin)."""
         self.ctx = ctx
         self.types = np.ascontiguousarray(types, dtype=np.uint8)
-        self.verts = np.ascontiguousarray(verts, dtype=np.float64).reshape(-1, 3, 3)
         h = _vp()
-        _check(ctx.handle, library().fpt_scene_upload(ctx.handle, _ptr(self.types), _ptr(self.verts),
-                                                      len(self.types), C.byref(h)))
+        if _is_cuda_tensor(verts):
+            import torch
+
+            _need_cuda(verts, torch.float32, "verts")
+            if verts.numel() != 9 * len(self.types):
+                raise FptError("verts must be [n_obj, 3, 3]")
+            self.verts = verts
+            c = None if centre is None else np.ascontiguousarray(centre, dtype=np.float64).reshape(3)
+            _check(ctx.handle, library().fpt_scene_upload_device(ctx.handle, _ptr(self.types), _ptr(verts),
+                                                                 len(self.types), _ptr(c), C.byref(h)))
+        else:
+            self.verts = np.ascontiguousarray(verts, dtype=np.float64).reshape(-1, 3, 3)
+            _check(ctx.handle, library().fpt_scene_upload(ctx.handle, _ptr(self.types), _ptr(self.verts),
+                                                          len(self.types), C.byref(h)))
         self.handle = h
         self.n_tx = self.n_rx = 0
         if tx is not None:
@@ -203,10 +236,32 @@ class Scene:
         return len(self.types)
 
     def set_endpoints(self, tx, rx):
+        """Host float64 arrays: fpt_set_endpoints.  CUDA float32 tensors [n, 3]: fpt_set_endpoints_device
+        (the records are built on the device; the tensors are read when the stream reaches the call)."""
+        if _is_cuda_tensor(tx) or _is_cuda_tensor(rx):
+            import torch
+
+            _need_cuda(tx, torch.float32, "tx")
+            _need_cuda(rx, torch.float32, "rx")
+            if tx.dim() != 2 or tx.shape[1] != 3 or rx.dim() != 2 or rx.shape[1] != 3:
+                raise FptError("tx and rx must be [n, 3]")
+            _check(self.ctx.handle, library().fpt_set_endpoints_device(self.handle, _ptr(tx), tx.shape[0], _ptr(rx),
+                                                                       rx.shape[0]))
+            self.n_tx, self.n_rx = int(tx.shape[0]), int(rx.shape[0])
+            return
         tx = np.ascontiguousarray(np.atleast_2d(tx), dtype=np.float64)
         rx = np.ascontiguousarray(np.atleast_2d(rx), dtype=np.float64)
         _check(self.ctx.handle, library().fpt_set_endpoints(self.handle, _ptr(tx), len(tx), _ptr(rx), len(rx)))
         self.n_tx, self.n_rx = len(tx), len(rx)
+
+    def update_vertices(self, verts):
+        """fpt_scene_update_vertices from a CUDA float32 tensor [n_obj, 3, 3] (types and centre unchanged)."""
+        import torch
+
+        _need_cuda(verts, torch.float32, "verts")
+        if verts.numel() != 9 * self.n_obj:
+            raise FptError("verts must be [n_obj, 3, 3]")
+        _check(self.ctx.handle, library().fpt_scene_update_vertices(self.handle, _ptr(verts)))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -540,6 +595,33 @@ class Mlp:
                                                               C.byref(loss) if want_loss else None))
         return float(loss.value) if want_loss else None
 
+    def train(self, X, T, G, epochs: int, batch: int = 8192, lr: float = 1e-3, lr_decay: float = 0.5,
+              seed: int = 0):
+        """fpt_mlp_train: the whole schedule in the library (seeded shuffles, Adam steps); returns the
+        per-epoch mean loss."""
+        import torch
+
+        _need_cuda(X, torch.bfloat16, "X")
+        _need_cuda(T, torch.float32, "T")
+        _need_cuda(G, torch.float32, "G")
+        p = TrainParams(int(epochs), int(batch), float(lr), float(lr_decay), int(seed))
+        hist = (C.c_float * int(epochs))()
+        _check(self.ctx.handle, library().fpt_mlp_train(self.ctx.handle, self.handle, _ptr(X), _ptr(T), _ptr(G),
+                                                         X.shape[0], C.byref(p), hist))
+        return [float(v) for v in hist]
+
+    def infer(self, scene: "Scene", batch: "Batch", out=None):
+        """fpt_mlp_infer: the learned start T [N, n_max, 2] of every path of the batch."""
+        import torch
+
+        if out is None:
+            out = torch.empty((batch.n_paths, batch.n_max, 2), dtype=torch.float32,
+                              device=torch.device("cuda", self.ctx.device))
+        _need_cuda(out, torch.float32, "out")
+        _check(self.ctx.handle, library().fpt_mlp_infer(self.ctx.handle, self.handle, scene.handle, batch.handle,
+                                                         _ptr(out)))
+        return out
+
     def attach(self):
         """Use this network for fpt_solve with init_mode = 1."""
         _check(self.ctx.handle, library().fpt_set_init_mlp(self.ctx.handle, self.handle))
@@ -570,6 +652,13 @@ def tc_gemm_bf16(ctx: Context, A, W, bias=None, out=None):
     C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=A.device)
     _check(ctx.handle, library().fpt_tc_gemm_bf16(ctx.handle, M, N, K, _ptr(A), _ptr(W), _ptr(bias), _ptr(C)))
     return C
+
+
+def backward_dropped(ctx: Context) -> int:
+    """fpt_backward_dropped: paths of the last backward call left out as singular in FP64 too."""
+    n = C.c_uint64(0)
+    _check(ctx.handle, library().fpt_backward_dropped(ctx.handle, C.byref(n)))
+    return int(n.value)
 
 
 def count_status(ctx: Context, status, mask: int) -> int:

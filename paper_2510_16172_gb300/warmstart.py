@@ -44,24 +44,14 @@ def make_dataset(ctx, seeds=TRAIN_SEEDS, per_pair=200_000, order_lo=1, order_hi=
     return torch.cat(Xs).contiguous(), torch.cat(Ts).contiguous(), torch.cat(Gs).contiguous()
 
 
-def train(ctx, X, T, G, epochs=3, batch=8192, lr=1e-3, seed=0, log=None):
-    """Adam on shuffled mini-batches; returns the network and the per-epoch mean loss."""
-    import torch
-
+def train(ctx, X, T, G, epochs=3, batch=8192, lr=1e-3, lr_decay=0.5, seed=0, log=None):
+    """Adam on shuffled mini-batches (fpt_mlp_train: the schedule runs in the library); returns the network
+    and the per-epoch mean batch loss."""
     net = fpt.Mlp(ctx, seed, LENGTH_SCALE)
-    n = X.shape[0] // batch * batch
-    g = torch.Generator(device=X.device).manual_seed(seed)
-    history = []
-    for ep in range(epochs):
-        perm = torch.randperm(X.shape[0], generator=g, device=X.device)[:n]
-        Xp, Tp, Gp = X[perm].contiguous(), T[perm].contiguous(), G[perm].contiguous()
-        rate = lr * (0.5 ** ep)
-        for k in range(0, n, batch):
-            net.train_step(Xp[k:k + batch], Tp[k:k + batch], Gp[k:k + batch], rate, want_loss=False)
-        m = min(n, 65536)
-        history.append(net.loss_grad(X[:m], T[:m], G[:m])[0])
-        if log:
-            log(f"epoch {ep}: loss {history[-1]:.5f}")
+    history = net.train(X, T, G, epochs, batch=batch, lr=lr, lr_decay=lr_decay, seed=seed)
+    if log:
+        for ep, v in enumerate(history):
+            log(f"epoch {ep}: loss {v:.5f}")
     return net, history
 
 

@@ -47,15 +47,28 @@ def test_noalloc_backward_matches_backward_twice(ctx, workload):
     dX = torch.as_tensor(dX, dtype=torch.float32, device="cuda")
     dL = torch.as_tensor(dL, dtype=torch.float32, device="cuda")
     mask = fpt.ST_VALID | fpt.ST_SOLVED
+    # the caller owns the outputs, as a caller that cannot allocate would
+    got = (torch.empty((scene.n_tx, 3), dtype=torch.float32, device="cuda"),
+           torch.empty((scene.n_rx, 3), dtype=torch.float32, device="cuda"),
+           torch.empty((scene.n_obj, 3, 3), dtype=torch.float32, device="cuda"))
     for k in range(2):  # two calls in a row: the fixed array keeps the previous call's contents
         ref = fpt.backward(ctx, scene, batch, out["T"], out["status"], dX, dL)
-        got = fpt.backward_noalloc(ctx, scene, batch, out["T"], out["status"], dX, dL)
+        fpt.backward_noalloc(ctx, scene, batch, out["T"], out["status"], dX, dL, out=got)
         ctx.sync()
         compare(got, ref)
         ref = fpt.backward(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask)
-        got = fpt.backward_noalloc(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask)
+        fpt.backward_noalloc(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask, out=got)
         ctx.sync()
         compare(got, ref)
+    # further calls take no device memory: the free memory the driver reports stays the same
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in range(3):
+        fpt.backward_noalloc(ctx, scene, batch, out["T"], out["status"], dX, dL, out=got)
+        fpt.backward_noalloc(ctx, scene, batch, out["T"], out["status"], None, None, dL_status_mask=mask, out=got)
+    ctx.sync()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_backward_rejects_sizes_beyond_its_limit(ctx):
