@@ -157,7 +157,8 @@ def kernel_source_hash() -> str:
 # DRAM traffic per launch from an ncu capture (profiles/), valid for the kernel sources with this hash.
 NCU_TRAFFIC = {
     # DRAM read + write of one step's bfgs_refill_kernel<3, Q> launches, ncu capture of these sources
-    ("5df8c896b36b", "bfgs"): 559.5e6,
+    # (profiles/launch_list_urban_canyon_33M.md)
+    ("39df173948b3", "bfgs"): 570.1e6,
 }
 
 
@@ -423,7 +424,9 @@ def learned_vs_plain(ctx, fpt, epochs):
                        f"solved paths as targets, {epochs} epochs of Adam; eval: 10 unseen scenes x 200,000 "
                        "sequences",
            "train_samples": ev["train_samples"], "train_loss_per_epoch": ev["train_loss_per_epoch"],
-           "train_s": ev["train_s"], "plain": ev["plain"], "learned": ev["learned"],
+           "train_s": ev["train_s"],
+           "train_tflops": MLP_TRAIN_FLOP * (ev["train_samples"] // 8192) * 8192 * epochs / ev["train_s"] / 1e12,
+           "plain": ev["plain"], "learned": ev["learned"],
            "learned_over_plain_solves_per_s": ev["learned"]["solves_per_s"] / ev["plain"]["solves_per_s"],
            "learned_over_plain_iterations": ev["learned"]["mean_bfgs_iters"] / ev["plain"]["mean_bfgs_iters"],
            "wall_s": time.perf_counter() - t0}
@@ -722,6 +725,51 @@ def run_fig3(args, world, rank, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# algorithmic work of one training sample of the 64-256-256-256-16 network: the forward pass (2 flop per
+# multiply-add), the back-propagation to the inputs of layers 2-4 and the weight gradients of all four
+MLP_MACS = 64 * 256 + 2 * 256 * 256 + 256 * 16
+MLP_TRAIN_FLOP = 2 * MLP_MACS + 2 * (MLP_MACS - 64 * 256) + 2 * MLP_MACS
+
+
+def run_train(args, world, rank, local_rank):
+    """Training throughput of the warm-start network (fpt_mlp_train: seeded shuffles, forward, loss,
+    backward and Adam on the tensor cores) on the solver's solutions of 10 random 10 m scenes, per batch
+    size: one timed epoch after one untimed one, CUDA events on the context's stream."""
+    import torch
+
+    from paper_2510_16172_gb300 import build, fpt, warmstart
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ctx = fpt.Context(local_rank)
+    X, T, G = warmstart.make_dataset(ctx, seeds=tuple(range(1000, 1010)), per_pair=100_000)
+    rows = []
+    stream = torch.cuda.current_stream(dev)
+    for batch in (int(v) for v in args.train_batches.split(",")):
+        net = fpt.Mlp(ctx, 0, warmstart.LENGTH_SCALE)
+        net.train(X, T, G, max(1, args.warmup), batch=batch, lr=1e-3, lr_decay=1.0, seed=1)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.train(X, T, G, args.steps, batch=batch, lr=1e-3, lr_decay=1.0, seed=2)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        samples = (X.shape[0] // batch) * batch * args.steps
+        rows.append({"batch": batch, "epochs": args.steps, "ms": ms, "samples": samples,
+                     "tflops": MLP_TRAIN_FLOP * samples / (ms * 1e-3) / 1e12})
+        net.close()
+    peaks = measured_peaks()
+    line = {"metric": "warm-start network training throughput (fpt_mlp_train)", "unit": "TFLOP/s",
+            "config": {"workload": f"{X.shape[0]} samples (solver solutions of 10 random 10 m scenes), "
+                                   "64-256-256-256-16 GELU, BF16 operands, FP32 accumulation and Adam",
+                       "flop_per_sample": MLP_TRAIN_FLOP},
+            "peak_bf16_sustained_tflops": peaks.get("bf16_tflops_sustained"), "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def e2e(args, sc, ctx, dev, torch, fpt):
     """Same metric through the public API: host scene/endpoints in, host parameters/lengths/status/gradients out.
 
@@ -811,14 +859,15 @@ def main():
     ap.add_argument("--rx-grid", type=int, default=32, help="RX grid side (32 = the 33.5M-path workload)")
     ap.add_argument("--no-learned", action="store_true",
                     help="canyon: skip the learned-vs-plain start comparison; city: the plain start alone")
-    ap.add_argument("--workload", choices=["canyon", "city", "fig2", "fig3"], default="canyon",
+    ap.add_argument("--workload", choices=["canyon", "city", "fig2", "fig3", "train"], default="canyon",
                     help="canyon: the 33.5M-path urban canyon (default); city: the 100M-path ragged city batch; "
                          "fig2: point error against solver time by iteration budget; fig3: gradient time, implicit vs AD "
-                         "through the iterations")
+                         "through the iterations; train: warm-start network training throughput (--steps epochs)")
     ap.add_argument("--city-paths", type=int, default=100_000_000)
     ap.add_argument("--city-steps", type=int, default=5, help="timed steps of the city leg of the default run")
     ap.add_argument("--no-city", action="store_true", help="canyon run: skip the ragged city leg")
     ap.add_argument("--epochs", type=int, default=6, help="training epochs of the warm-start network")
+    ap.add_argument("--train-batches", default="8192,16384,65536", help="train workload: batch sizes to time")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -838,6 +887,8 @@ def main():
         run_fig2(args, world, rank, local_rank)
     elif args.workload == "fig3":
         run_fig3(args, world, rank, local_rank)
+    elif args.workload == "train":
+        run_train(args, world, rank, local_rank)
     else:
         run_ours(args, world, rank, local_rank)
     if world > 1:

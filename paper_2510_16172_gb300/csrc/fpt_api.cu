@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "fpt.h"
@@ -165,6 +166,10 @@ struct fpt_mlp {
   __nv_bfloat16* d_wb = nullptr;  // BF16 copy used by the tensor cores
   __nv_bfloat16* d_wt = nullptr;  // BF16 weights pre-tiled for the fused inference kernel
   bool wt_stale = true;
+  __nv_bfloat16* d_wtT = nullptr;  // BF16 W^T of layers 2-4 (the backward's dH = dZ W), refreshed when stale
+  float* d_splitws = nullptr;      // split-K partial products of the weight gradients
+  size_t splitws_cap = 0;          // floats
+  bool wtT_stale = true;
   float* d_loss = nullptr;
   // fpt_mlp_train: one shuffled mini-batch and the per-epoch mean losses
   __nv_bfloat16* d_Xb = nullptr;
@@ -175,6 +180,9 @@ struct fpt_mlp {
   uint64_t cap = 0;
   __nv_bfloat16 *d_H1 = nullptr, *d_H2 = nullptr, *d_H3 = nullptr, *d_dZa = nullptr, *d_dZb = nullptr,
                 *d_dYb = nullptr, *d_X = nullptr;
+  // transposed copies for the weight gradients dW = dZ^T act (K-major operands): act^T, dZ^T, dY^T
+  __nv_bfloat16 *d_Ht1 = nullptr, *d_Ht2 = nullptr, *d_Ht3 = nullptr, *d_Xt = nullptr, *d_dZta = nullptr,
+                *d_dZtb = nullptr, *d_dYt = nullptr;
   float *d_Z1 = nullptr, *d_Z2 = nullptr, *d_Z3 = nullptr, *d_dZf = nullptr, *d_Y = nullptr, *d_dY = nullptr;
 };
 
@@ -1239,9 +1247,11 @@ fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uin
 static void mlp_free_ws(fpt_mlp* m) {
   for (void* p : {(void*)m->d_H1, (void*)m->d_H2, (void*)m->d_H3, (void*)m->d_dZa, (void*)m->d_dZb, (void*)m->d_dYb,
                   (void*)m->d_X, (void*)m->d_Z1, (void*)m->d_Z2, (void*)m->d_Z3, (void*)m->d_dZf, (void*)m->d_Y,
-                  (void*)m->d_dY})
+                  (void*)m->d_dY, (void*)m->d_Ht1, (void*)m->d_Ht2, (void*)m->d_Ht3, (void*)m->d_Xt, (void*)m->d_dZta,
+                  (void*)m->d_dZtb, (void*)m->d_dYt})
     cudaFree(p);
   m->d_H1 = m->d_H2 = m->d_H3 = m->d_dZa = m->d_dZb = m->d_dYb = m->d_X = nullptr;
+  m->d_Ht1 = m->d_Ht2 = m->d_Ht3 = m->d_Xt = m->d_dZta = m->d_dZtb = m->d_dYt = nullptr;
   m->d_Z1 = m->d_Z2 = m->d_Z3 = m->d_dZf = m->d_Y = m->d_dY = nullptr;
   m->cap = 0;
 }
@@ -1268,6 +1278,13 @@ static fpt_status mlp_ensure_ws(fpt_ctx* ctx, fpt_mlp* m, uint64_t B, bool train
     bf(&m->d_dZb, H);
     bf(&m->d_dYb, want * kMlpOut);
     f32(&m->d_dY, want * kMlpOut);
+    bf(&m->d_Ht1, H);
+    bf(&m->d_Ht2, H);
+    bf(&m->d_Ht3, H);
+    bf(&m->d_Xt, want * kMlpIn);
+    bf(&m->d_dZta, H);
+    bf(&m->d_dZtb, H);
+    bf(&m->d_dYt, want * kMlpOut);
   }
   if (e != cudaSuccess) {
     mlp_free_ws(m);
@@ -1314,6 +1331,12 @@ static fpt_status mlp_forward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16
     g.H = H[l];
     g.shm = kMlpHidden;
     g.shn = 1;
+    if (train) {  // H^T [256][B]: the K-major operand of the next layer's weight gradient
+      __nv_bfloat16* Ht[3] = {m->d_Ht1, m->d_Ht2, m->d_Ht3};
+      g.Ht = Ht[l];
+      g.shtm = 1;
+      g.shtn = Bi;
+    }
     CUDA_OR_FAIL(ctx, launch_gemm(g, 1, ctx->stream));
     in = H[l];
   }
@@ -1326,30 +1349,57 @@ static fpt_status mlp_forward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16
   return FPT_OK;
 }
 
-// loss and gradient (into m->d_g) of a batch; loss accumulated in m->d_loss
+// loss and gradient (into m->d_g) of a batch; loss accumulated in m->d_loss.  Every GEMM reads K-major
+// operands: the weight gradients dW = dZ^T act take the transposed copies written by the epilogues, the
+// back-propagation dH = dZ W the transposed BF16 weights.
+static int split_k(const fpt_ctx* ctx, int B, int m_tiles) {
+  // enough CTAs to cover the SMs, at least four 64-wide K chunks per split
+  int ks = (2 * ctx->n_sm + m_tiles - 1) / m_tiles;
+  const int max_ks = B / 256 > 1 ? B / 256 : 1;
+  return ks < 1 ? 1 : (ks > max_ks ? max_ks : ks);
+}
+
 static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16* X, const float* T, const float* G,
                                     uint64_t B) {
   const int Bi = (int)B;
-  const int ks = Bi >= 2048 ? Bi / 1024 : 1;  // split the batch reduction of the weight gradients
-  const __nv_bfloat16* W = m->d_wb;
   CUDA_OR_FAIL(ctx, cudaMemsetAsync(m->d_g, 0, kMlpParams * sizeof(float), ctx->stream));
   CUDA_OR_FAIL(ctx, cudaMemsetAsync(m->d_loss, 0, sizeof(float), ctx->stream));
+  if (m->wtT_stale) {
+    CUDA_OR_FAIL(ctx, launch_mlp_transpose_weights(m->d_wb, m->d_wtT, ctx->stream));
+    m->wtT_stale = false;
+  }
+  const __nv_bfloat16* Wt2 = m->d_wtT;
+  const __nv_bfloat16* Wt3 = m->d_wtT + 256 * 256;
+  const __nv_bfloat16* Wt4 = m->d_wtT + 2 * 256 * 256;
+  // weight gradients: split-K partial products in a workspace, then one reduction into m->d_g
+  const int ks = split_k(ctx, Bi, 2);
+  const size_t ws_need = (size_t)ks * kMlpHidden * kMlpHidden;
+  if (ws_need > m->splitws_cap) {
+    cudaFree(m->d_splitws);
+    m->d_splitws = nullptr;
+    m->splitws_cap = 0;
+    CUDA_OR_FAIL(ctx, cudaMalloc(&m->d_splitws, ws_need * sizeof(float)));
+    m->splitws_cap = ws_need;
+  }
+  auto weight_grad = [&](int M, int N, const __nv_bfloat16* At, const __nv_bfloat16* Bt, float* dst, long long scm,
+                         long long scn) -> fpt_status {
+    GemmArgs g = gemm_args(M, N, Bi, At, Bi, 1, Bt, Bi, 1, EPI_SPLIT, ctx->d_err);
+    g.C = m->d_splitws;
+    CUDA_OR_FAIL(ctx, launch_gemm(g, ks, ctx->stream));
+    CUDA_OR_FAIL(ctx, launch_splitk_reduce(m->d_splitws, ks, M, N, dst, scm, scn, ctx->stream));
+    return FPT_OK;
+  };
   fpt_status st = mlp_forward_impl(ctx, m, X, B, m->d_Y, true);
   if (st != FPT_OK) return st;
-  CUDA_OR_FAIL(ctx, launch_mlp_loss(G, m->d_Y, T, B, m->d_dY, m->d_dYb, m->d_loss, ctx->stream));
-  // last layer: dW4^T[in][out] = sum_b H3[b][in] dY[b][out]; db4 = sum_b dY
+  CUDA_OR_FAIL(ctx, launch_bf16_transpose(X, Bi, kMlpIn, m->d_Xt, ctx->stream));
+  CUDA_OR_FAIL(ctx, launch_mlp_loss(G, m->d_Y, T, B, m->d_dY, m->d_dYb, m->d_dYt, m->d_loss, ctx->stream));
+  // last layer: dW4^T [in][out] = H3^T dY (sum over the batch); db4 = sum_b dY
+  st = weight_grad(kMlpHidden, kMlpOut, m->d_Ht3, m->d_dYt, m->d_g + kOffW4, 1, kMlpHidden);
+  if (st != FPT_OK) return st;
+  CUDA_OR_FAIL(ctx, launch_colsum(m->d_dY, B, kMlpOut, m->d_g + kOffB4, ctx->stream));
+  // dZ3 = (dY W4) * gelu'(Z3), and its transpose
   {
-    GemmArgs g = gemm_args(kMlpHidden, kMlpOut, Bi, m->d_H3, 1, kMlpHidden, m->d_dYb, 1, kMlpOut, EPI_ATOMIC, ctx->d_err);
-    g.C = m->d_g + kOffW4;
-    g.scm = 1;
-    g.scn = kMlpHidden;
-    CUDA_OR_FAIL(ctx, launch_gemm(g, ks, ctx->stream));
-    CUDA_OR_FAIL(ctx, launch_colsum(m->d_dY, B, kMlpOut, m->d_g + kOffB4, ctx->stream));
-  }
-  // dZ3 = (dY W4) * gelu'(Z3)
-  {
-    GemmArgs g = gemm_args(Bi, kMlpHidden, kMlpOut, m->d_dYb, kMlpOut, 1, W + kOffW4, 1, kMlpHidden, EPI_GELU_GRAD,
-                           ctx->d_err);
+    GemmArgs g = gemm_args(Bi, kMlpHidden, kMlpOut, m->d_dYb, kMlpOut, 1, Wt4, kMlpOut, 1, EPI_GELU_GRAD, ctx->d_err);
     g.Zin = m->d_Z3;
     g.szm = kMlpHidden;
     g.szn = 1;
@@ -1359,25 +1409,25 @@ static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat1
     g.H = m->d_dZa;
     g.shm = kMlpHidden;
     g.shn = 1;
+    g.Ht = m->d_dZta;
+    g.shtm = 1;
+    g.shtn = Bi;
     CUDA_OR_FAIL(ctx, launch_gemm(g, 1, ctx->stream));
   }
-  const __nv_bfloat16* acts[3] = {X, m->d_H1, m->d_H2};  // inputs of layers 1..3
+  const __nv_bfloat16* acts_t[3] = {m->d_Xt, m->d_Ht1, m->d_Ht2};  // inputs of layers 1..3, transposed
+  const __nv_bfloat16* wts[3] = {nullptr, Wt2, Wt3};
   const float* Zs[2] = {m->d_Z1, m->d_Z2};
   const int offW[3] = {kOffW1, kOffW2, kOffW3}, offB[3] = {kOffB1, kOffB2, kOffB3};
-  __nv_bfloat16* dZ = m->d_dZa;
-  __nv_bfloat16* dZn = m->d_dZb;
+  __nv_bfloat16 *dZ = m->d_dZa, *dZn = m->d_dZb, *dZt = m->d_dZta, *dZtn = m->d_dZtb;
   for (int l = 2; l >= 0; --l) {
     const int K_in = l == 0 ? kMlpIn : kMlpHidden;
     CUDA_OR_FAIL(ctx, launch_colsum(m->d_dZf, B, kMlpHidden, m->d_g + offB[l], ctx->stream));
-    // dW_l[out][in] = sum_b dZ[b][out] act[b][in]
-    GemmArgs gw = gemm_args(kMlpHidden, K_in, Bi, dZ, 1, kMlpHidden, acts[l], 1, K_in, EPI_ATOMIC, ctx->d_err);
-    gw.C = m->d_g + offW[l];
-    gw.scm = K_in;
-    gw.scn = 1;
-    CUDA_OR_FAIL(ctx, launch_gemm(gw, ks, ctx->stream));
+    // dW_l [out][in] = dZ^T [out][b] act^T [in][b]
+    st = weight_grad(kMlpHidden, K_in, dZt, acts_t[l], m->d_g + offW[l], K_in, 1);
+    if (st != FPT_OK) return st;
     if (l == 0) break;
-    // dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
-    GemmArgs gd = gemm_args(Bi, kMlpHidden, kMlpHidden, dZ, kMlpHidden, 1, W + offW[l], 1, kMlpHidden, EPI_GELU_GRAD,
+    // dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1}) = dZ_l [b][out] (W_l^T)[in][out], and its transpose
+    GemmArgs gd = gemm_args(Bi, kMlpHidden, kMlpHidden, dZ, kMlpHidden, 1, wts[l], kMlpHidden, 1, EPI_GELU_GRAD,
                             ctx->d_err);
     gd.Zin = Zs[l - 1];
     gd.szm = kMlpHidden;
@@ -1388,10 +1438,12 @@ static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat1
     gd.H = dZn;
     gd.shm = kMlpHidden;
     gd.shn = 1;
+    gd.Ht = dZtn;
+    gd.shtm = 1;
+    gd.shtn = Bi;
     CUDA_OR_FAIL(ctx, launch_gemm(gd, 1, ctx->stream));
-    __nv_bfloat16* tmp = dZ;
-    dZ = dZn;
-    dZn = tmp;
+    std::swap(dZ, dZn);
+    std::swap(dZt, dZtn);
   }
   return FPT_OK;
 }
@@ -1420,6 +1472,7 @@ fpt_status fpt_mlp_create(fpt_ctx* ctx, uint64_t seed, float length_scale, fpt_m
     if (e == cudaSuccess) e = cudaMalloc(p, kMlpParams * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->d_wb, kMlpParams * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->d_wt, kMlpTiledBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_wtT, kMlpWtElems * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->d_loss, sizeof(float));
   if (e != cudaSuccess) {
     fpt_mlp_free(m);
@@ -1453,7 +1506,8 @@ void fpt_mlp_free(fpt_mlp* m) {
   if (m->ctx && m->ctx->init_mlp == m) m->ctx->init_mlp = nullptr;
   mlp_free_ws(m);
   for (void* p : {(void*)m->d_w, (void*)m->d_m, (void*)m->d_v, (void*)m->d_g, (void*)m->d_wb, (void*)m->d_wt,
-                  (void*)m->d_loss, (void*)m->d_Xb, (void*)m->d_Tb, (void*)m->d_Gb, (void*)m->d_hist})
+                  (void*)m->d_loss, (void*)m->d_Xb, (void*)m->d_Tb, (void*)m->d_Gb, (void*)m->d_hist, (void*)m->d_wtT,
+                  (void*)m->d_splitws})
     cudaFree(p);
   delete m;
 }
@@ -1481,6 +1535,7 @@ fpt_status fpt_mlp_set_params(fpt_mlp* m, const float* host) {
   CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));
   m->step = 0;
   m->wt_stale = true;
+  m->wtT_stale = true;
   return FPT_OK;
 }
 
@@ -1589,6 +1644,7 @@ fpt_status fpt_mlp_train_step(fpt_ctx* ctx, fpt_mlp* m, const void* X, const flo
   const float c1 = 1.f - std::pow(0.9f, (float)m->step), c2 = 1.f - std::pow(0.999f, (float)m->step);
   CUDA_OR_FAIL(ctx, launch_adam(m->d_w, m->d_m, m->d_v, m->d_g, kMlpParams, lr, c1, c2, m->d_wb, ctx->stream));
   m->wt_stale = true;
+  m->wtT_stale = true;
   if (loss) {
     CUDA_OR_FAIL(ctx, cudaMemcpyAsync(loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OR_FAIL(ctx, cudaStreamSynchronize(ctx->stream));

@@ -6,13 +6,17 @@
 // activations are rounded to BF16 between layers.
 //
 // gemm_kernel: D[M x N] = sum_k A(m, k) B(n, k) for one 128-row tile per CTA,
-// N <= 256, K in chunks of 64.  Operands are gathered from global memory with
-// arbitrary element strides into the canonical K-major shared-memory layout
-// (tc.cuh), so transposed operands of the backward pass need no copies.  One
-// thread issues four 128 x N x 16 MMAs per chunk and commits them to an
-// mbarrier; the epilogue reads the accumulator from TMEM (one warp per 32 rows)
-// and applies: plain store, atomic add (split-K over the batch), bias + GELU
-// with a BF16 activation, or the GELU derivative for the backward pass.
+// N <= 256, K in chunks of 64 (split over gridDim.y).  Operands whose rows are
+// contiguous and 16-byte aligned are copied with cp.async into the canonical
+// K-major shared-memory layout (tc.cuh), two chunks in flight; other strides
+// are gathered element by element.  The training pass keeps every operand
+// K-major: its epilogues also write the transposes that the weight gradients
+// read.  One thread issues four 128 x N x 16 MMAs per chunk and commits them
+// to the chunk's mbarrier; the epilogue reads the accumulator from TMEM (one
+// warp per 32 rows), stages it in shared memory so that every store is
+// coalesced, and applies: plain store, split-K partial store, atomic add,
+// bias + GELU with a BF16 activation (and its transpose), or the GELU
+// derivative for the backward pass (and its transpose).
 #include <cuda_bf16.h>
 
 #include "fpt_kernels.h"
@@ -82,13 +86,117 @@ __device__ __forceinline__ void load_tile(unsigned char* tile, const __nv_bfloat
   }
 }
 
-constexpr int kGemmSmem = 128 * kGemmKC * 2 + 256 * kGemmKC * 2;  // A and B tiles (48 KB)
+// 16 bytes global -> shared, asynchronous (cp.async), the bytes past src_bytes (0..16) zero-filled.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int kPending>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(kPending) : "memory");
+}
+
+// Rows [r0, r0 + rows) x k [k0, k0 + 64) of a row-major bf16 matrix whose rows start on 16-byte
+// boundaries into the K-major tile layout, with asynchronous 16-byte copies (zero outside rows < R,
+// k < K).  Consecutive threads take consecutive 16-byte pieces of a row: a warp reads four whole rows.
+__device__ __forceinline__ void load_tile_async(unsigned char* tile, const __nv_bfloat16* src, long long s_r, int R,
+                                                int K, int r0, int k0, int rows) {
+  for (int idx = threadIdx.x; idx < rows * (kGemmKC / 8); idx += blockDim.x) {
+    const int r = idx / (kGemmKC / 8), kg = idx % (kGemmKC / 8);
+    const int gr = r0 + r, gk = k0 + kg * 8;
+    const int valid = gr < R ? min(max(K - gk, 0), 8) : 0;
+    const __nv_bfloat16* p = valid ? src + (long long)gr * s_r + gk : src;
+    cp_async16(tile + tc::kmajor_offset(r, kg * 8, kGemmKC), p, (uint32_t)valid * 2u);
+  }
+}
+
+// Operands that the pipelined path takes: unit stride along k, rows 16-byte aligned.
+__host__ __device__ inline bool gemm_vectorised(const GemmArgs& g) {
+  const bool a = g.sak == 1 && (g.sam % 8) == 0 && (reinterpret_cast<uintptr_t>(g.A) & 15) == 0;
+  const bool b = g.sbk == 1 && (g.sbn % 8) == 0 && (reinterpret_cast<uintptr_t>(g.B) & 15) == 0;
+  return a && b;
+}
+
+constexpr int kGemmStages = 2;                                      // K chunks in flight
+constexpr int kGemmTileA = 128 * kGemmKC * 2;                       // 16 KB
+constexpr int kGemmStageBytes = kGemmTileA + 256 * kGemmKC * 2;     // A + B (N <= 256): 48 KB
+constexpr int kGemmSmem = kGemmStages * kGemmStageBytes;            // 96 KB: two CTAs per SM
+// Epilogue staging: each warp's 32 accumulator rows, 64 columns at a time, in a private slab of the
+// (by then idle) pipeline buffers; rows padded to 65 floats so that both the row-wise and the
+// column-wise passes hit 32 different banks.
+constexpr int kEpiCols = 64, kEpiStride = kEpiCols + 1;
+static_assert(4 * 32 * kEpiStride * 4 <= kGemmSmem, "epilogue slabs");
+
+// Epilogue of one warp's 32 accumulator rows (TMEM lanes 32 w .. 32 w + 31, matrix rows mrow0 ..).  Per
+// 64-column slab: (a) the accumulator (+ bias) goes from TMEM to the warp's staging slab, lane = row;
+// (b) row by row, consecutive lanes on consecutive columns, the row-major outputs are formed and stored
+// (coalesced; Zin read the same way), and the final value is kept in the slab; (c) column by column,
+// consecutive lanes on consecutive rows, the transposed copy Ht is stored (coalesced too).
+__device__ __forceinline__ void gemm_epilogue_staged(const GemmArgs& g, uint32_t tmem_warp, int mrow0, int lane,
+                                                     int n_pad, float* slab) {
+  for (int c0 = 0; c0 < n_pad; c0 += kEpiCols) {
+    const int cols = min(kEpiCols, n_pad - c0);
+    for (int cc = 0; cc < cols; cc += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem_warp + (uint32_t)(c0 + cc), v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int n = c0 + cc + q;
+        float x = v[q];
+        if ((g.op == EPI_STORE || g.op == EPI_BIAS_GELU) && g.bias && n < g.N) x += g.bias[n];
+        slab[lane * kEpiStride + cc + q] = x;
+      }
+    }
+    __syncwarp();
+    for (int r = 0; r < 32; ++r) {
+      const int m = mrow0 + r;
+      if (m >= g.M) break;  // r is the same for the whole warp
+      for (int cc = lane; cc < cols; cc += 32) {
+        const int n = c0 + cc;
+        if (n >= g.N) continue;
+        const float x = slab[r * kEpiStride + cc];
+        float y = x;
+        switch (g.op) {
+          case EPI_STORE:
+            g.C[(long long)m * g.scm + (long long)n * g.scn] = x;
+            break;
+          case EPI_ATOMIC:
+            atomicAdd(g.C + (long long)m * g.scm + (long long)n * g.scn, x);
+            break;
+          case EPI_SPLIT:
+            g.C[((long long)blockIdx.y * g.M + m) * g.N + n] = x;
+            break;
+          case EPI_BIAS_GELU:
+            if (g.C) g.C[(long long)m * g.scm + (long long)n * g.scn] = x;
+            y = __bfloat162float(__float2bfloat16(gelu(x)));
+            g.H[(long long)m * g.shm + (long long)n * g.shn] = __float2bfloat16(y);
+            break;
+          case EPI_GELU_GRAD:
+            y = x * gelu_grad(g.Zin[(long long)m * g.szm + (long long)n * g.szn]);
+            if (g.C) g.C[(long long)m * g.scm + (long long)n * g.scn] = y;
+            g.H[(long long)m * g.shm + (long long)n * g.shn] = __float2bfloat16(y);
+            break;
+        }
+        slab[r * kEpiStride + cc] = y;
+      }
+    }
+    __syncwarp();
+    if (g.Ht) {
+      const int m = mrow0 + lane;
+      for (int cc = 0; cc < cols; ++cc) {
+        const int n = c0 + cc;
+        if (n < g.N && m < g.M)
+          g.Ht[(long long)m * g.shtm + (long long)n * g.shtn] = __float2bfloat16(slab[lane * kEpiStride + cc]);
+      }
+    }
+    __syncwarp();
+  }
+}
 
 __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char gemm_smem[];
-  unsigned char* sA = gemm_smem;
-  unsigned char* sB = gemm_smem + 128 * kGemmKC * 2;
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[kGemmStages];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -98,8 +206,9 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
   // K range of this split
   const int k_per = ((g.K + gridDim.y * kGemmKC - 1) / (gridDim.y * kGemmKC)) * kGemmKC;
   const int kb = blockIdx.y * k_per, ke = min(g.K, kb + k_per);
+  const int n_chunks = ke > kb ? (ke - kb + kGemmKC - 1) / kGemmKC : 0;
   if (threadIdx.x == 0) {
-    tc::mbar_init(&bar, 1);
+    for (int s = 0; s < kGemmStages; ++s) tc::mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -112,70 +221,91 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = tc::idesc_bf16(128, n_pad);
-  uint32_t phase = 0;
-  int issued = 0;
-  for (int k0 = kb; k0 < ke; k0 += kGemmKC) {
-    load_tile(sA, g.A, g.sam, g.sak, g.M, g.K, m0, k0, 128);
-    load_tile(sB, g.B, g.sbn, g.sbk, g.N, g.K, 0, k0, n_pad);
-    tc::fence_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-#pragma unroll
-      for (int kk = 0; kk < kGemmKC / 16; ++kk) {
-        const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, (kGemmKC / 8) * 128);
-        const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, (kGemmKC / 8) * 128);
-        tc::mma_bf16(tmem, ad, bd, idesc, (issued | kk) ? 1u : 0u);
-      }
-      tc::mma_commit(&bar);
-    }
-    issued = 1;
-    // the tiles are reused by the next chunk: wait until the MMAs have read them
-    if (!tc::mbar_wait(&bar, phase, kWaitTries)) atomicExch(&s_fail, 1);
-    phase ^= 1u;
+  auto stage_a = [&](int s) { return gemm_smem + s * kGemmStageBytes; };
+  auto stage_b = [&](int s) { return gemm_smem + s * kGemmStageBytes + kGemmTileA; };
+  auto issue = [&](int c) {  // one thread: the four MMAs of chunk c, then its commit
+    const int s = c % kGemmStages;
     tc::fence_after_sync();
-    __syncthreads();
-    if (s_fail) break;
+    const uint32_t a0 = tc::smem_u32(stage_a(s)), b0 = tc::smem_u32(stage_b(s));
+#pragma unroll
+    for (int kk = 0; kk < kGemmKC / 16; ++kk) {
+      const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, (kGemmKC / 8) * 128);
+      const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, (kGemmKC / 8) * 128);
+      tc::mma_bf16(tmem, ad, bd, idesc, (c | kk) ? 1u : 0u);
+    }
+    tc::mma_commit(&bar[s]);
+  };
+  // chunk c's MMAs have completed: its stage barrier's phase number c / kGemmStages.  A thread whose
+  // bounded wait runs out sets s_fail, which every thread reads only after the next barrier.
+  auto wait_chunk = [&](int c) {
+    if (tc::mbar_wait(&bar[c % kGemmStages], (uint32_t)((c / kGemmStages) & 1), kWaitTries)) return true;
+    atomicExch(&s_fail, 1);
+    return false;
+  };
+  if (gemm_vectorised(g)) {
+    // pipelined: chunks load (cp.async, one commit group per chunk) kGemmStages - 1 ahead of the MMAs
+    for (int c = 0; c < kGemmStages - 1; ++c) {
+      if (c < n_chunks) {
+        load_tile_async(stage_a(c), g.A, g.sam, g.M, g.K, m0, kb + c * kGemmKC, 128);
+        load_tile_async(stage_b(c), g.B, g.sbn, g.N, g.K, 0, kb + c * kGemmKC, n_pad);
+      }
+      cp_async_commit();
+    }
+    for (int c = 0; c < n_chunks; ++c) {
+      cp_async_wait<kGemmStages - 2>();  // this thread's copies of chunk c (group c) have landed
+      tc::fence_async_smem();
+      __syncthreads();
+      if (s_fail) break;  // the same value for every thread after the barrier
+      if (threadIdx.x == 0) issue(c);
+      // refill the stage of chunk c - 1 with chunk c + kGemmStages - 1 once chunk c - 1's MMAs, queued ahead
+      // of chunk c's, have read it
+      const int cn = c + kGemmStages - 1;
+      if (cn < n_chunks && (c == 0 || wait_chunk(c - 1))) {
+        const int sn = cn % kGemmStages;
+        load_tile_async(stage_a(sn), g.A, g.sam, g.M, g.K, m0, kb + cn * kGemmKC, 128);
+        load_tile_async(stage_b(sn), g.B, g.sbn, g.N, g.K, 0, kb + cn * kGemmKC, n_pad);
+      }
+      cp_async_commit();
+    }
+    cp_async_wait<0>();
+  } else {
+    // element gathers from arbitrary strides: one stage, each chunk waited for before the next
+    for (int c = 0; c < n_chunks; ++c) {
+      load_tile(stage_a(0), g.A, g.sam, g.sak, g.M, g.K, m0, kb + c * kGemmKC, 128);
+      load_tile(stage_b(0), g.B, g.sbn, g.sbk, g.N, g.K, 0, kb + c * kGemmKC, n_pad);
+      tc::fence_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int s = c % kGemmStages;
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_u32(stage_a(0)), b0 = tc::smem_u32(stage_b(0));
+#pragma unroll
+        for (int kk = 0; kk < kGemmKC / 16; ++kk) {
+          const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, (kGemmKC / 8) * 128);
+          const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, (kGemmKC / 8) * 128);
+          tc::mma_bf16(tmem, ad, bd, idesc, (c | kk) ? 1u : 0u);
+        }
+        tc::mma_commit(&bar[s]);
+      }
+      wait_chunk(c);  // the tile is reused by the next chunk
+      tc::fence_after_sync();
+      __syncthreads();
+      if (s_fail) break;
+    }
   }
+  __syncthreads();
+  if (n_chunks > 0 && !s_fail) wait_chunk(n_chunks - 1);  // the last commit: every MMA has completed
+  tc::fence_after_sync();
+  __syncthreads();
   if (s_fail) {
     if (threadIdx.x == 0 && g.err) atomicCAS(g.err, 0, ERR_MMA_TIMEOUT);
     // give MMAs still in flight a (bounded) chance to finish before TMEM is freed
-    tc::mbar_wait(&bar, phase, kWaitTries);
-  } else if (issued) {
-    // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31
-    const int m = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < n_pad; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (m < g.M) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int n = c0 + q;
-          if (n >= g.N) continue;
-          float x = v[q];
-          switch (g.op) {
-            case EPI_STORE:
-              if (g.bias) x += g.bias[n];
-              g.C[(long long)m * g.scm + (long long)n * g.scn] = x;
-              break;
-            case EPI_ATOMIC:
-              atomicAdd(g.C + (long long)m * g.scm + (long long)n * g.scn, x);
-              break;
-            case EPI_BIAS_GELU: {
-              if (g.bias) x += g.bias[n];
-              if (g.C) g.C[(long long)m * g.scm + (long long)n * g.scn] = x;
-              g.H[(long long)m * g.shm + (long long)n * g.shn] = __float2bfloat16(gelu(x));
-            } break;
-            case EPI_GELU_GRAD: {
-              const float dz = x * gelu_grad(g.Zin[(long long)m * g.szm + (long long)n * g.szn]);
-              if (g.C) g.C[(long long)m * g.scm + (long long)n * g.scn] = dz;
-              g.H[(long long)m * g.shm + (long long)n * g.shn] = __float2bfloat16(dz);
-            } break;
-          }
-        }
-      }
-    }
+    if (n_chunks > 0) tc::mbar_wait(&bar[(n_chunks - 1) % kGemmStages], (uint32_t)(((n_chunks - 1) / kGemmStages) & 1),
+                                    kWaitTries);
+  } else if (n_chunks > 0) {
+    // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31; the pipeline buffers are idle now
+    float* slab = reinterpret_cast<float*>(gemm_smem) + warp * 32 * kEpiStride;
+    gemm_epilogue_staged(g, tmem + ((uint32_t)(warp * 32) << 16), m0 + warp * 32, lane, n_pad, slab);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -314,7 +444,7 @@ __global__ void mlp_features_kernel(SceneDev S, BatchDev B, int n, const PathRec
 // loss (1/B) sum_b sum_s dy_s^T G_s dy_s (G_s = A_s^T A_s / S^2 per slot, zero for unused slots) and dY
 __global__ void mlp_loss_kernel(const float* __restrict__ G, const float* __restrict__ Y,
                                 const float* __restrict__ T, uint64_t B, float* __restrict__ dY,
-                                __nv_bfloat16* __restrict__ dYb, float* loss) {
+                                __nv_bfloat16* __restrict__ dYb, __nv_bfloat16* __restrict__ dYt, float* loss) {
   float acc = 0.f;
   const float w = 2.f / (float)B;
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (uint64_t)gridDim.x * blockDim.x) {
@@ -335,6 +465,7 @@ __global__ void mlp_loss_kernel(const float* __restrict__ G, const float* __rest
     for (int k = 0; k < kMlpOut; ++k) {
       dY[b * kMlpOut + k] = g[k];
       dYb[b * kMlpOut + k] = __float2bfloat16(g[k]);
+      if (dYt) dYt[(uint64_t)k * B + b] = __float2bfloat16(g[k]);
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -363,6 +494,38 @@ __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float*
     const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
     w[i] = wi;
     wb[i] = __float2bfloat16(wi);
+  }
+}
+
+// dst [C][R] = src [R][C]^T through a 32 x 32 shared-memory tile (both sides coalesced)
+__global__ void bf16_transpose_kernel(const __nv_bfloat16* __restrict__ src, int R, int C,
+                                      __nv_bfloat16* __restrict__ dst) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < C) tile[i][threadIdx.x] = src[(long long)r * C + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < R && c < C) dst[(long long)c * R + r] = tile[threadIdx.x][i];
+  }
+}
+
+// W^T of layers 2, 3 (256 x 256) and 4 (16 x 256 -> 256 x 16), back to back in wt
+__global__ void mlp_transpose_weights_kernel(const __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt) {
+  const int n2 = 256 * 256, n4 = 16 * 256;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * n2 + n4; idx += gridDim.x * blockDim.x) {
+    if (idx < 2 * n2) {
+      const int l = idx / n2, e = idx % n2;  // wt element (in = e / 256, out = e % 256)
+      const int in = e / 256, out = e % 256;
+      wt[idx] = wb[(l == 0 ? kOffW2 : kOffW3) + out * 256 + in];
+    } else {
+      const int e = idx - 2 * n2;  // (in = e / 16, out = e % 16)
+      const int in = e / 16, out = e % 16;
+      wt[idx] = wb[kOffW4 + out * 256 + in];
+    }
   }
 }
 
@@ -602,15 +765,17 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
           full_ph[b] ^= 1u;
           tc::fence_after_sync();
           const uint32_t K_act = layer == 0 ? 64u : 256u;
-          const uint32_t N = layer == 3 ? 16u : 128u;
           const uint32_t a0 = tc::smem_u32(sm.act), w0 = tc::smem_u32(sm.wbuf[b]);
           if (!sm.fail) {
+            // the unit's first descriptors; each next K = 16 step starts 256 bytes further, i.e. 16 more
+            // in the 14-bit start-address field (shared addresses stay below 2^18: the field never carries)
+            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(c * 8) * 128u, 128u, (K_act / 8u) * 128u);
+            const uint64_t bd = tc::smem_desc(w0, 128u, 8u * 128u);
+            const uint32_t idesc = layer == 3 ? tc::idesc_bf16(128, 16) : tc::idesc_bf16(128, 128);
+            const uint32_t d = tmem + (uint32_t)h * 128u;
+            tc::mma_bf16(d, ad, bd, idesc, c > 0 ? 1u : 0u);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(c * 8 + 2 * kk) * 128u, 128u, (K_act / 8u) * 128u);
-              const uint64_t bd = tc::smem_desc(w0 + (uint32_t)(2 * kk) * 128u, 128u, 8u * 128u);
-              tc::mma_bf16(tmem + (uint32_t)h * 128u, ad, bd, tc::idesc_bf16(128, N), (c > 0 || kk > 0) ? 1u : 0u);
-            }
+            for (int kk = 1; kk < 4; ++kk) tc::mma_bf16(d, ad + 16u * kk, bd + 16u * kk, idesc, 1u);
           }
           tc::mma_commit(&sm.done[b]);
           if (unit_ends_layer(lq)) tc::mma_commit(&sm.layer);
@@ -788,8 +953,8 @@ cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, con
 }
 
 cudaError_t launch_mlp_loss(const float* G, const float* Y, const float* T, uint64_t B, float* dY,
-                            __nv_bfloat16* dYb, float* loss, cudaStream_t stream) {
-  mlp_loss_kernel<<<grid_1d(B, 256, 1024), 256, 0, stream>>>(G, Y, T, B, dY, dYb, loss);
+                            __nv_bfloat16* dYb, __nv_bfloat16* dYt, float* loss, cudaStream_t stream) {
+  mlp_loss_kernel<<<grid_1d(B, 256, 1024), 256, 0, stream>>>(G, Y, T, B, dY, dYb, dYt, loss);
   count_launch();
   return cudaGetLastError();
 }
@@ -804,6 +969,39 @@ cudaError_t launch_colsum(const float* A, uint64_t B, int N, float* out, cudaStr
 cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float c1, float c2,
                         __nv_bfloat16* wb, cudaStream_t stream) {
   adam_kernel<<<grid_1d(n, 256, 1024), 256, 0, stream>>>(w, m, v, g, n, lr, c1, c2, wb);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, int M, int N, float* dst, long long scm,
+                                     long long scn) {
+  const long long MN = (long long)M * N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int s = 0; s < splits; ++s) acc += ws[s * MN + e];
+    dst[(e / N) * scm + (e % N) * scn] += acc;
+  }
+}
+
+cudaError_t launch_splitk_reduce(const float* ws, int splits, int M, int N, float* dst, long long scm, long long scn,
+                                 cudaStream_t stream) {
+  const long long MN = (long long)M * N;
+  const unsigned grid = (unsigned)((MN + 255) / 256 < 1024 ? (MN + 255) / 256 : 1024);
+  splitk_reduce_kernel<<<grid, 256, 0, stream>>>(ws, splits, M, N, dst, scm, scn);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bf16_transpose(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t stream) {
+  if (R < 1 || C < 1) return cudaSuccess;
+  dim3 grid((C + 31) / 32, (R + 31) / 32);
+  bf16_transpose_kernel<<<grid, dim3(32, 8), 0, stream>>>(src, R, C, dst);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_transpose_weights(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t stream) {
+  mlp_transpose_weights_kernel<<<264, 512, 0, stream>>>(wb, wt);
   count_launch();
   return cudaGetLastError();
 }

@@ -15,7 +15,10 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 256 * 64, kOffW2 = kOffB1 + 256, kOf
               kOffW3 = kOffB2 + 256, kOffB3 = kOffW3 + 256 * 256, kOffW4 = kOffB3 + 256, kOffB4 = kOffW4 + 16 * 256,
               kMlpParams = kOffB4 + 16;
 
-enum EpilogueOp { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_GELU = 2, EPI_GELU_GRAD = 3 };
+// EPI_SPLIT: split-K partial product, split s stored plainly at C + s M N ([M][N] row-major), summed by
+// launch_splitk_reduce (contended atomics on the same few outputs were the slowest part of the weight
+// gradients)
+enum EpilogueOp { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_GELU = 2, EPI_GELU_GRAD = 3, EPI_SPLIT = 4 };
 
 // D[M x N] = sum_k A(m, k) B(n, k); A(m, k) = A[m * sam + k * sak], B(n, k) = B[n * sbn + k * sbk].
 struct GemmArgs {
@@ -30,16 +33,26 @@ struct GemmArgs {
   long long scm, scn;
   __nv_bfloat16* H;       // BF16 output: activation (EPI_BIAS_GELU) or dZ (EPI_GELU_GRAD)
   long long shm, shn;
+  __nv_bfloat16* Ht;      // optional second copy of H with its own strides (the transpose, for the backward)
+  long long shtm, shtn;
   const float* Zin;       // pre-activation for EPI_GELU_GRAD
   long long szm, szn;
   int* err;               // device error word (MMA completion timeout)
 };
 
 cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream);
+// dst[m * scm + n * scn] += sum over s < splits of ws[s][m][n]  (ws: splits x M x N floats)
+cudaError_t launch_splitk_reduce(const float* ws, int splits, int M, int N, float* dst, long long scm, long long scn,
+                                 cudaStream_t stream);
+// dst [C][R] = src [R][C]^T (bf16)
+cudaError_t launch_bf16_transpose(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t stream);
+// The transposed BF16 weights of layers 2-4 (W^T [in][out]) from the BF16 parameter copy.
+constexpr int kMlpWtElems = 256 * 256 + 256 * 256 + 256 * 16;
+cudaError_t launch_mlp_transpose_weights(const __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t stream);
 cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t first,
                                 uint64_t count, float inv_scale, __nv_bfloat16* X, float* G, cudaStream_t stream);
 cudaError_t launch_mlp_loss(const float* G, const float* Y, const float* T, uint64_t B, float* dY,
-                            __nv_bfloat16* dYb, float* loss, cudaStream_t stream);
+                            __nv_bfloat16* dYb, __nv_bfloat16* dYt, float* loss, cudaStream_t stream);
 cudaError_t launch_colsum(const float* A, uint64_t B, int N, float* out, cudaStream_t stream);
 cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float c1, float c2,
                         __nv_bfloat16* wb, cudaStream_t stream);

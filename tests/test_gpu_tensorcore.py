@@ -1,4 +1,8 @@
-"""Tensor-core (tcgen05) GEMM of the warm-start network against a plain FP32 product (GPU)."""
+"""Tensor-core (tcgen05) GEMM of the warm-start network against a plain FP32 product (GPU).
+
+Row lengths that are multiples of 8 elements take the pipelined path (asynchronous 16-byte copies, three
+64-wide K chunks in flight, ragged edges zero-filled); others (K = 100) the element-gather path.
+"""
 
 import numpy as np
 import pytest
@@ -17,7 +21,7 @@ def ctx():
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (1, 16, 16), (300, 200, 100), (1000, 64, 256), (129, 256, 256),
-                                   (4096, 16, 256)])
+                                   (4096, 16, 256), (256, 256, 4096), (200, 48, 1000), (130, 256, 136)])
 def test_tc_gemm_matches_fp32_product(ctx, M, N, K):
     import torch
 
