@@ -1356,7 +1356,11 @@ static int split_k(const fpt_ctx* ctx, int B, int m_tiles) {
   // enough CTAs to cover the SMs, at least four 64-wide K chunks per split
   int ks = (2 * ctx->n_sm + m_tiles - 1) / m_tiles;
   const int max_ks = B / 256 > 1 ? B / 256 : 1;
-  return ks < 1 ? 1 : (ks > max_ks ? max_ks : ks);
+  ks = ks < 1 ? 1 : (ks > max_ks ? max_ks : ks);
+  // the GEMM gives each split ceil(B / (ks 64)) chunks of 64: count only the splits that get some,
+  // so that every split the reduction sums has written its partial product
+  const int per = (B + ks * 64 - 1) / (ks * 64) * 64;
+  return (B + per - 1) / per;
 }
 
 static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16* X, const float* T, const float* G,

@@ -5,19 +5,17 @@
 // the solver.  Weights are BF16, accumulation FP32 in tensor memory,
 // activations are rounded to BF16 between layers.
 //
-// gemm_kernel: D[M x N] = sum_k A(m, k) B(n, k) for one 128-row tile per CTA,
-// N <= 256, K in chunks of 64 (split over gridDim.y).  Operands whose rows are
-// contiguous and 16-byte aligned are copied with cp.async into the canonical
-// K-major shared-memory layout (tc.cuh), two chunks in flight; other strides
-// are gathered element by element.  The training pass keeps every operand
-// K-major: its epilogues also write the transposes that the weight gradients
-// read.  One thread issues four 128 x N x 16 MMAs per chunk and commits them
-// to the chunk's mbarrier; the epilogue reads the accumulator from TMEM (one
-// warp per 32 rows), stages it in shared memory so that every store is
-// coalesced, and applies: plain store, split-K partial store, atomic add,
-// bias + GELU with a BF16 activation (and its transpose), or the GELU
-// derivative for the backward pass (and its transpose).
+// GEMMs D[M x N] = sum_k A(m, k) B(n, k), N <= 256, K in chunks of 64.  Operands whose rows are
+// contiguous and 16-byte aligned go to gemm_ws_kernel: persistent, one CTA per SM over (128-row tile,
+// K split) items, the chunks loaded by TMA into a four-stage ring (128-byte swizzled K-major tiles), one
+// thread issuing the MMAs into two TMEM accumulators, eight epilogue warps storing from registers.
+// Other strides (and the atomic epilogue) take gemm_kernel, one tile per CTA with the operands gathered
+// element by element.  The training pass keeps every operand K-major: its epilogues also write the
+// transposes that the weight gradients read.  Epilogues: plain store, split-K partial store, atomic add,
+// bias + GELU with a BF16 activation (and its transpose), or the GELU derivative for the backward pass
+// (and its transpose).
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "fpt_kernels.h"
 #include "mlp.h"
@@ -134,7 +132,7 @@ static_assert(4 * 32 * kEpiStride * 4 <= kGemmSmem, "epilogue slabs");
 // (coalesced; Zin read the same way), and the final value is kept in the slab; (c) column by column,
 // consecutive lanes on consecutive rows, the transposed copy Ht is stored (coalesced too).
 __device__ __forceinline__ void gemm_epilogue_staged(const GemmArgs& g, uint32_t tmem_warp, int mrow0, int lane,
-                                                     int n_pad, float* slab) {
+                                                     int n_pad, float* slab, int split) {
   for (int c0 = 0; c0 < n_pad; c0 += kEpiCols) {
     const int cols = min(kEpiCols, n_pad - c0);
     for (int cc = 0; cc < cols; cc += 16) {
@@ -165,7 +163,7 @@ __device__ __forceinline__ void gemm_epilogue_staged(const GemmArgs& g, uint32_t
             atomicAdd(g.C + (long long)m * g.scm + (long long)n * g.scn, x);
             break;
           case EPI_SPLIT:
-            g.C[((long long)blockIdx.y * g.M + m) * g.N + n] = x;
+            g.C[((long long)split * g.M + m) * g.N + n] = x;
             break;
           case EPI_BIAS_GELU:
             if (g.C) g.C[(long long)m * g.scm + (long long)n * g.scn] = x;
@@ -305,11 +303,347 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
   } else if (n_chunks > 0) {
     // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31; the pipeline buffers are idle now
     float* slab = reinterpret_cast<float*>(gemm_smem) + warp * 32 * kEpiStride;
-    gemm_epilogue_staged(g, tmem + ((uint32_t)(warp * 32) << 16), m0 + warp * 32, lane, n_pad, slab);
+    gemm_epilogue_staged(g, tmem + ((uint32_t)(warp * 32) << 16), m0 + warp * 32, lane, n_pad, slab, (int)blockIdx.y);
   }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised GEMM for operands whose rows are contiguous and 16-byte aligned.
+// One CTA per SM (256 threads) takes work items (a 128-row tile and a K split) in turn:
+//   warp 0     producer: cp.async copies of each 64-wide K chunk into a ring of kWsStages stages
+//              (A 16 KB + B up to 32 KB); once a chunk's copies have landed (it runs one chunk
+//              behind the newest, so two are in flight) each lane fences them for the tensor core
+//              and arrives on the stage's `full` barrier;
+//   warp 1     MMA issuer (lane 0): per chunk four 128 x N x 16 tcgen05 MMAs into one of two TMEM
+//              accumulators (256 columns each), committed to the stage's `empty` barrier; after a
+//              tile's last chunk, a commit to the accumulator's `acc_full` barrier;
+//   warps 4-7  epilogue: drain an accumulator (TMEM lanes 32 (w % 4) ..) through the staged,
+//              coalesced epilogue while the next tile's MMAs fill the other, then arrive on its
+//              `acc_empty` barrier.
+// Every wait is bounded; a timeout sets the CTA's fail flag, which every role polls and leaves on.
+// ---------------------------------------------------------------------------
+// ---- persistent warp-specialised GEMM (TMA operands) -------------------------------------------------
+// One CTA per SM walks the (128-row tile, K split) items.  Warp 0 (one thread) loads each 64-wide K chunk
+// of A (128 rows) and B (n_pad rows) with one TMA tile load per operand into a ring of kWsStages stages,
+// in the 128-byte swizzled K-major layout; rows past M or N and k past K arrive as zeros.  Warp 1 (one
+// thread) issues four 128 x n_pad x 16 MMAs per chunk into one of two TMEM accumulators (columns 0-255,
+// 256-511), releases the chunk's stage by a commit to `empty` and announces a finished tile by a commit
+// to `acc_full`.  Warps 2-9 are the epilogue: two warps per 32-lane quarter of TMEM (a warp may read the
+// quarter given by its index mod 4), each on every other group of 16 columns; every lane owns one output
+// row and stores its 16 columns with 16-byte vector stores (the transposed copy with one store per column,
+// consecutive lanes on consecutive rows).  They hand the accumulator back through `acc_empty`, so the
+// MMAs of the tile after next may start while this tile's epilogue runs.
+constexpr int kWsStages = 4;
+constexpr int kWsEpiWarps = 8;
+constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
+constexpr int kWsTileA = 128 * 128;                       // 128 rows x 128 bytes
+constexpr int kWsStageBytes = kWsTileA + 256 * 128;       // + B, up to 256 rows: 48 KB
+constexpr int kWsSmem = kWsStages * kWsStageBytes + 1024;  // + slack to align the ring to 1024 bytes
+
+struct WsItem {
+  int m0, kb, ke, split;
+};
+__device__ __forceinline__ WsItem ws_item(const GemmArgs& g, int item, int m_tiles, int k_per) {
+  WsItem w;
+  w.m0 = (item % m_tiles) * 128;
+  w.split = item / m_tiles;
+  w.kb = w.split * k_per;
+  w.ke = min(g.K, w.kb + k_per);
+  return w;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// Which outputs may use 16-byte vector accesses (unit stride along n, row strides and bases aligned).
+struct EpiVec {
+  bool c, h, z, bias;
+};
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+__device__ __forceinline__ EpiVec epi_vec(const GemmArgs& g) {
+  EpiVec v;
+  v.c = g.op == EPI_SPLIT ? (g.N % 4 == 0 && aligned16(g.C)) : (g.scn == 1 && g.scm % 4 == 0 && aligned16(g.C));
+  v.h = g.shn == 1 && g.shm % 8 == 0 && aligned16(g.H);
+  v.z = g.szn == 1 && g.szm % 4 == 0 && aligned16(g.Zin);
+  v.bias = aligned16(g.bias);
+  return v;
+}
+
+__device__ __forceinline__ void store16_f32(float* p, const float (&x)[16], bool vec, int nv, long long sn) {
+  if (vec) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (i < nv) p[i * sn] = x[i];
+  }
+}
+__device__ __forceinline__ void store16_bf16(__nv_bfloat16* p, const float (&x)[16], bool vec, int nv, long long sn) {
+  if (vec) {
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    uint4* q = reinterpret_cast<uint4*>(p);
+    q[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    q[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (i < nv) p[i * sn] = __float2bfloat16(x[i]);
+  }
+}
+
+// One warp's share of a finished 128 x n_pad accumulator: its lane quarter, column groups j0, j0 + 2, ...
+// m = this lane's output row.
+template <int OP>
+__device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev, uint32_t tacc, int m, int j0,
+                                            int n_groups, int split) {
+  const bool row = m < g.M;
+  for (int j = j0; j < n_groups; j += 2) {
+    const int n0 = 16 * j;
+    float x[16];
+    __syncwarp();
+    tc::tmem_ld16(tacc + (uint32_t)n0, x);
+    if (!row) continue;
+    const int nv = min(16, g.N - n0);
+    const bool full = nv == 16;
+    if ((OP == EPI_STORE || OP == EPI_BIAS_GELU) && g.bias) {
+      if (full && ev.bias) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 b = __ldg(reinterpret_cast<const float4*>(g.bias + n0) + i);
+          x[4 * i] += b.x;
+          x[4 * i + 1] += b.y;
+          x[4 * i + 2] += b.z;
+          x[4 * i + 3] += b.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (i < nv) x[i] += g.bias[n0 + i];
+      }
+    }
+    if (OP == EPI_SPLIT) {
+      store16_f32(g.C + ((long long)split * g.M + m) * g.N + n0, x, full && ev.c, nv, 1);
+      continue;
+    }
+    if (OP == EPI_STORE) {
+      store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
+      continue;
+    }
+    if (OP == EPI_GELU_GRAD) {
+      const float* zp = g.Zin + (long long)m * g.szm + (long long)n0 * g.szn;
+      float z[16];
+      if (full && ev.z) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(zp) + i);
+          z[4 * i] = t.x;
+          z[4 * i + 1] = t.y;
+          z[4 * i + 2] = t.z;
+          z[4 * i + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = i < nv ? zp[i * g.szn] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[i] *= gelu_grad(z[i]);
+      if (g.C) store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
+    } else {  // EPI_BIAS_GELU: the pre-activation, then the BF16 activation
+      if (g.C) store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[i] = gelu(x[i]);
+    }
+    store16_bf16(g.H + (long long)m * g.shm + (long long)n0 * g.shn, x, full && ev.h, nv, g.shn);
+    if (g.Ht) {
+      __nv_bfloat16* tp = g.Ht + (long long)m * g.shtm + (long long)n0 * g.shtn;
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (i < nv) tp[i * g.shtn] = __float2bfloat16(x[i]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWsThreads, 1)
+    gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g,
+                   int m_tiles, int n_items, int k_per) {
+  extern __shared__ unsigned char ws_raw[];
+  __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], acc_full[2], acc_empty[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  __shared__ int s_last_q;             // the MMA thread's last committed chunk (-1: none)
+  __shared__ int s_armed[kWsStages];   // each stage's last phase handed to the TMA engine (-1: none)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned all = 0xffffffffu;
+  const int n_pad = (g.N + 15) & ~15;
+  unsigned char* ring = ws_raw + ((1024u - (tc::smem_u32(ws_raw) & 1023u)) & 1023u);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWsStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+      s_armed[s] = -1;
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kWsEpiWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+    s_last_q = -1;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&s_tmem, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  auto stage_a = [&](int s) { return ring + s * kWsStageBytes; };
+  auto stage_b = [&](int s) { return ring + s * kWsStageBytes + kWsTileA; };
+  auto failed = [&]() { return *reinterpret_cast<volatile int*>(&s_fail) != 0; };
+
+  if (warp == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      const uint32_t tx_bytes = (uint32_t)(128 + n_pad) * 128u;
+      int q = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
+        const WsItem w = ws_item(g, item, m_tiles, k_per);
+        for (int k0 = w.kb; k0 < w.ke; k0 += kGemmKC, ++q) {
+          const int s = q % kWsStages, u = q / kWsStages;
+          if (u > 0) {  // the stage's previous chunk has been read by its MMAs
+            ok = !failed() && tc::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), kWaitTries);
+            if (!ok) break;
+          }
+          tc::mbar_expect_tx(&full[s], tx_bytes);
+          s_armed[s] = u;
+          tc::tma_load_2d(stage_a(s), &tmA, k0, w.m0, &full[s]);
+          tc::tma_load_2d(stage_b(s), &tmB, k0, 0, &full[s]);
+        }
+      }
+      if (!ok) atomicExch(&s_fail, 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int q = 0, i = 0;
+      bool ok = true;
+      const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)n_pad);
+      for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x, ++i) {
+        const WsItem w = ws_item(g, item, m_tiles, k_per);
+        const int b = i & 1, v = i >> 1;
+        if (v > 0) ok = !failed() && tc::mbar_wait(&acc_empty[b], (uint32_t)((v - 1) & 1), kWaitTries);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(b * 256);
+        for (int k0 = w.kb, c = 0; k0 < w.ke; k0 += kGemmKC, ++q, ++c) {
+          const int s = q % kWsStages, u = q / kWsStages;
+          ok = !failed() && tc::mbar_wait(&full[s], (uint32_t)(u & 1), kWaitTries);
+          if (!ok) break;
+          tc::fence_after_sync();
+          const uint64_t ad = tc::smem_desc_sw128(tc::smem_u32(stage_a(s)));
+          const uint64_t bd = tc::smem_desc_sw128(tc::smem_u32(stage_b(s)));
+#pragma unroll
+          for (int kk = 0; kk < kGemmKC / 16; ++kk)
+            tc::mma_bf16(d, ad + 2u * kk, bd + 2u * kk, idesc, (c | kk) ? 1u : 0u);
+          tc::mma_commit(&empty[s]);
+          s_last_q = q;
+        }
+        if (!ok) break;
+        tc::mma_commit(&acc_full[b]);
+      }
+      if (!ok) atomicExch(&s_fail, 1);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue ----
+    const int quarter = warp & 3;            // the TMEM lanes this warp may read
+    const int j0 = (warp - 2) >> 2;          // its column groups: j0, j0 + 2, ...
+    const int n_groups = n_pad / 16;
+    const EpiVec ev = epi_vec(g);
+    int i = 0;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++i) {
+      const WsItem w = ws_item(g, item, m_tiles, k_per);
+      const int b = i & 1, v = i >> 1;
+      const bool ok = __all_sync(all, !failed() && tc::mbar_wait(&acc_full[b], (uint32_t)(v & 1), kWaitTries));
+      if (!ok) {
+        if (lane == 0) atomicExch(&s_fail, 1);
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t tacc = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+      const int m = w.m0 + quarter * 32 + lane;
+      switch (g.op) {
+        case EPI_STORE:
+          ws_epilogue<EPI_STORE>(g, ev, tacc, m, j0, n_groups, w.split);
+          break;
+        case EPI_SPLIT:
+          ws_epilogue<EPI_SPLIT>(g, ev, tacc, m, j0, n_groups, w.split);
+          break;
+        case EPI_BIAS_GELU:
+          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, j0, n_groups, w.split);
+          break;
+        default:
+          ws_epilogue<EPI_GELU_GRAD>(g, ev, tacc, m, j0, n_groups, w.split);
+          break;
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (s_fail && threadIdx.x == 0) {
+    if (g.err) atomicCAS(g.err, 0, ERR_MMA_TIMEOUT);
+    // let the copies and MMAs already issued finish (bounded) before shared and tensor memory go away
+    for (int s = 0; s < kWsStages; ++s)
+      if (s_armed[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)(s_armed[s] & 1), kWaitTries);
+    const int q = s_last_q;
+    if (q >= 0) tc::mbar_wait(&empty[q % kWsStages], (uint32_t)((q / kWsStages) & 1), kWaitTries);
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// The {k, row} view of a row-major BF16 matrix (rows x K, row stride ld elements) in 64 x box_rows boxes
+// with 128-byte swizzling; elements outside the matrix read as zero.
+static bool encode_operand(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, long long ld, int box_rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2u};
+  const cuuint32_t box[2] = {(cuuint32_t)kGemmKC, (cuuint32_t)box_rows};
+  const cuuint32_t elem[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, elem,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
@@ -317,8 +651,28 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem);
     if (e != cudaSuccess) return e;
     attr = true;
+  }
+  if (gemm_vectorised(g) && g.op != EPI_ATOMIC) {
+    const int n_pad = (g.N + 15) & ~15;
+    CUtensorMap tmA, tmB;
+    if (encode_operand(&tmA, g.A, g.M, g.K, g.sam, 128) && encode_operand(&tmB, g.B, g.N, g.K, g.sbn, n_pad)) {
+      // persistent: one CTA per SM over the (tile, split) items
+      const int m_tiles = (g.M + 127) / 128;
+      const int k_per = ((g.K + k_split * kGemmKC - 1) / (k_split * kGemmKC)) * kGemmKC;
+      const int splits = (g.K + k_per - 1) / k_per;
+      const int n_items = m_tiles * splits;
+      int dev = 0, n_sm = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      const int grid = n_items < n_sm ? n_items : n_sm;
+      gemm_ws_kernel<<<grid, kWsThreads, kWsSmem, stream>>>(tmA, tmB, g, m_tiles, n_items, k_per);
+      count_launch();
+      return cudaGetLastError();
+    }
   }
   dim3 grid((g.M + 127) / 128, k_split);
   gemm_kernel<<<grid, 128, kGemmSmem, stream>>>(g);

@@ -39,6 +39,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// Descriptor of a K-major operand in the 128-byte swizzled layout that a TMA tile load with
+// 128-byte swizzling and a 64-element (128-byte) inner box writes: rows of 128 bytes, atoms of 8 rows
+// (1024 bytes, stride 1024 along M or N), the tile base 1024-byte aligned.  The leading byte offset is
+// not used by swizzled K-major layouts.  The 16-element K slice kk of a 64-wide chunk starts 32 kk bytes
+// into each row: the descriptor's start address plus 2 kk.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;  // swizzling mode: 128 bytes
+  return d;
+}
+
 // Instruction descriptor of kind::f16: BF16 A and B, FP32 accumulator, both
 // operands K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
@@ -73,6 +88,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 // Arm the barrier for `bytes` of incoming transactions (one arrival).
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// One box of a 2-D tensor map (coordinates x along the contiguous dimension, y along rows) into shared
+// memory by the TMA engine; the box's bytes complete transactions on the barrier.  x times the element
+// size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst_smem, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst_smem)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // Global -> shared copy by the TMA engine; completes `bytes` transactions on the barrier.

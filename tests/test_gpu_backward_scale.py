@@ -66,6 +66,44 @@ def assert_sums_close(got, want, what, per_array=True):
         assert err <= REL * scale, f"{what}: {name} gradient off by {err:.3e} (scale {scale:.3e})"
 
 
+# Per-path error of the FP32 adjoint (block LDL^T of the Eq. 12 system, then Eq. 13), measured on the
+# GB300 against the oracle's FP64 VJP at the GPU's own parameters, over 20,000 regular tiny-scene paths of
+# orders 1-3 with segments above 10 cm: median 2.2e-7, 99th percentile 1.2e-5, largest 3.1e-4 of the
+# path's largest gradient entry.  A sum over many paths then differs from the oracle's by at most
+# PATH_EPS times the sum of its paths' largest entries, whatever the order of summation.
+PATH_EPS = 1e-3
+
+
+def path_magnitude_bounds(sc, ids, order, tx_idx, rx_idx, dtheta):
+    """For every TX, RX and vertex entry, PATH_EPS times the sum over the paths that contribute to it of
+    each path's largest |gradient| entry (the vertex chain rule of oracle.reduce_gradients taken with
+    absolute values: v0 collects the b, a1 and a2 parameters of its object)."""
+    m = np.abs(np.asarray(dtheta, dtype=np.float64)).max(axis=1)
+    K = sc.n_obj
+    b_tx = np.zeros(len(sc.tx))
+    b_rx = np.zeros(len(sc.rx))
+    b_obj = np.zeros(K)
+    np.add.at(b_tx, np.asarray(tx_idx), m)
+    np.add.at(b_rx, np.asarray(rx_idx), m)
+    for i in range(ids.shape[1]):
+        on = np.asarray(order) > i
+        np.add.at(b_obj, np.asarray(ids)[on, i], m[on])
+    quad = sc.types == scenes.QUAD
+    b_v = np.zeros((K, 3))
+    b_v[:, 0] = np.where(quad, 3.0, 2.0) * b_obj
+    b_v[:, 1] = b_obj
+    b_v[:, 2] = np.where(quad, b_obj, 0.0)
+    return (PATH_EPS * b_tx[:, None] + 1e-6, PATH_EPS * b_rx[:, None] + 1e-6, PATH_EPS * b_v[:, :, None] + 1e-6)
+
+
+def assert_within_path_bounds(got, want, bounds, what):
+    for name, g, e, b in zip(("TX", "RX", "vertices"), got, want, bounds):
+        g = g.cpu().numpy().astype(np.float64)
+        over = np.abs(g - e) / b
+        k = np.unravel_index(np.argmax(over), over.shape)
+        assert over[k] <= 1.0, f"{what}: {name} gradient {k} off by {abs(g - e)[k]:.3e}, bound {np.broadcast_to(b, g.shape)[k]:.3e}"
+
+
 def sampled_backward_case(ctx, sc, scene, batch, decode, params, seed):
     """Solve the whole batch on the GPU, then check fpt_backward, its listed form and fpt_solve_grad
     against the oracle's VJP sums (see the module docstring)."""
@@ -188,8 +226,10 @@ def test_backward_sums_by_flush_interval(ctx):
     shared-memory partial sums flushed after every tile, every two tiles, every 64 (the default) or not
     used at all.  The reference is the oracle's FP64 VJP (Eq. 12-13) evaluated at the GPU's own solution
     (the oracle's solver run for zero steps from it), so the comparison sees the backward's arithmetic
-    and its summation, not the solve's tolerance; every setting agrees with it, and with the sums taken
-    straight in FP64 to FP32 summation."""
+    and its summation, not the solve's tolerance.  Every setting agrees with it within the per-path FP32
+    adjoint error (PATH_EPS of each contributing path's largest entry), and with the sums taken straight
+    in FP64 to 1e-5 of the largest entry: the FP32 partial sums add nothing visible to the adjoint's own
+    rounding."""
     import torch
 
     sc = scenes.tiny_scene(3, n_rx=128)
@@ -215,6 +255,7 @@ def test_backward_sums_by_flush_interval(ctx):
     ref = oracle.solve(sc, ids, order, ti, ri, solver=oracle.BFGS, max_iters=0, T_start=T_gpu, dX=dX, dL=dL)
     assert np.array_equal(ref["T"][w], T_gpu[w])  # the oracle evaluated at the GPU's parameters
     want = oracle.reduce_gradients(sc, ids, order, ti, ri, ref["dtheta"] * w[:, None])
+    bounds = path_magnitude_bounds(sc, ids, order, ti, ri, ref["dtheta"] * w[:, None])
     dev = out["T"].device
     dXd = torch.as_tensor(dX, dtype=torch.float32, device=dev)
     dLd = torch.as_tensor(dL, dtype=torch.float32, device=dev)
@@ -222,18 +263,17 @@ def test_backward_sums_by_flush_interval(ctx):
     try:
         for flush, smem in ((1, 0), (1, 1), (2, 1), (64, 1)):
             ctx.set_accumulation(flush, smem)
-            # bound: 2e-4 of the largest gradient entry, as in the other tiny-scene backward tests
             got = fpt.backward(ctx, scene, batch, out["T"], out["status"], dXd, dLd)
             ctx.sync()
-            assert_sums_close(got, want, f"fpt_backward, flush {flush}, smem {smem}", per_array=False)
+            assert_within_path_bounds(got, want, bounds, f"fpt_backward, flush {flush}, smem {smem}")
             results[(flush, smem)] = [g.cpu().numpy().astype(np.float64) for g in got]
             got = fpt.backward_noalloc(ctx, scene, batch, out["T"], out["status"], dXd, dLd)
             ctx.sync()
-            assert_sums_close(got, want, f"fpt_backward_noalloc, flush {flush}, smem {smem}", per_array=False)
+            assert_within_path_bounds(got, want, bounds, f"fpt_backward_noalloc, flush {flush}, smem {smem}")
             # the fused adjoint runs at the polish's own (equally solved) point
             _, got = fpt.solve_grad(ctx, scene, batch, fpt.default_params(fuse_adjoint=1), dX=dXd, dL=dLd)
             ctx.sync()
-            assert_sums_close(got, want, f"fpt_solve_grad fused, flush {flush}, smem {smem}", per_array=False)
+            assert_within_path_bounds(got, want, bounds, f"fpt_solve_grad fused, flush {flush}, smem {smem}")
     finally:
         ctx.set_accumulation(64, 1)
     # FP32 partial sums of up to 64 tiles against sums taken in FP64 path by path

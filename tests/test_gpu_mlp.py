@@ -83,6 +83,33 @@ def test_forward_and_gradient_match_reference(ctx):
     assert np.all(g[mo.N_PARAMS - 16 - 8 * 256 - 8:mo.N_PARAMS - 16] == 0)
 
 
+def test_gradient_at_a_large_ragged_batch(ctx):
+    """40,001 random samples: 313 row tiles, so every CTA of the persistent GEMM runs two or three tiles
+    through both TMEM accumulators and wraps its four-stage operand ring; the weight gradients split K
+    (the batch) over 126 slices.  Forward, loss and gradient against the FP64 reference with the same
+    BF16 roundings."""
+    import torch
+
+    rng = np.random.default_rng(11)
+    n = 40001
+    Xo = mo.bf16(rng.uniform(-1.0, 1.0, (n, 64)))
+    G = rng.normal(0.0, 1.0, (n, 4, 3))
+    T = rng.uniform(-0.5, 1.5, (n, 8))
+    params = numpy_params(7)
+    net = fpt.Mlp(ctx, 0, SCALE)
+    net.set_params(params)
+    X = torch.as_tensor(Xo, dtype=torch.float32).to(torch.bfloat16).cuda()
+    Y = net.forward(X).cpu().numpy()
+    Yo = mo.forward(params.astype(np.float64), Xo)["Y"]
+    assert np.abs(Y - Yo).max() <= 5e-3 * max(1.0, np.abs(Yo).max())
+    loss, g = net.loss_grad(X, torch.as_tensor(T, dtype=torch.float32, device="cuda"),
+                            torch.as_tensor(G, dtype=torch.float32, device="cuda"))
+    lo, go = mo.loss_grad(params.astype(np.float64), Xo, T, G)
+    assert abs(loss - lo) <= 2e-3 * abs(lo)
+    g = g.cpu().numpy()
+    assert np.abs(g - go).max() <= 3e-3 * np.abs(go).max(), (np.abs(g - go).max(), np.abs(go).max())
+
+
 def training_set(ctx, seeds, per_pair=20000):
     """Features and solver outputs (solved paths only) for seeded order 1-4 sequences on tiny scenes."""
     import torch
