@@ -183,7 +183,7 @@ struct fpt_mlp {
   // transposed copies for the weight gradients dW = dZ^T act (K-major operands): act^T, dZ^T, dY^T
   __nv_bfloat16 *d_Ht1 = nullptr, *d_Ht2 = nullptr, *d_Ht3 = nullptr, *d_Xt = nullptr, *d_dZta = nullptr,
                 *d_dZtb = nullptr, *d_dYt = nullptr;
-  float *d_Z1 = nullptr, *d_Z2 = nullptr, *d_Z3 = nullptr, *d_dZf = nullptr, *d_Y = nullptr, *d_dY = nullptr;
+  float *d_Z1 = nullptr, *d_Z2 = nullptr, *d_Z3 = nullptr, *d_Y = nullptr, *d_dY = nullptr;
 };
 
 static fpt_status mlp_ensure_ws(fpt_ctx* ctx, fpt_mlp* m, uint64_t B, bool train);
@@ -1246,13 +1246,13 @@ fpt_status fpt_count_status(fpt_ctx* ctx, const uint8_t* status, uint64_t n, uin
 // ---------------------------------------------------------------------------
 static void mlp_free_ws(fpt_mlp* m) {
   for (void* p : {(void*)m->d_H1, (void*)m->d_H2, (void*)m->d_H3, (void*)m->d_dZa, (void*)m->d_dZb, (void*)m->d_dYb,
-                  (void*)m->d_X, (void*)m->d_Z1, (void*)m->d_Z2, (void*)m->d_Z3, (void*)m->d_dZf, (void*)m->d_Y,
+                  (void*)m->d_X, (void*)m->d_Z1, (void*)m->d_Z2, (void*)m->d_Z3, (void*)m->d_Y,
                   (void*)m->d_dY, (void*)m->d_Ht1, (void*)m->d_Ht2, (void*)m->d_Ht3, (void*)m->d_Xt, (void*)m->d_dZta,
                   (void*)m->d_dZtb, (void*)m->d_dYt})
     cudaFree(p);
   m->d_H1 = m->d_H2 = m->d_H3 = m->d_dZa = m->d_dZb = m->d_dYb = m->d_X = nullptr;
   m->d_Ht1 = m->d_Ht2 = m->d_Ht3 = m->d_Xt = m->d_dZta = m->d_dZtb = m->d_dYt = nullptr;
-  m->d_Z1 = m->d_Z2 = m->d_Z3 = m->d_dZf = m->d_Y = m->d_dY = nullptr;
+  m->d_Z1 = m->d_Z2 = m->d_Z3 = m->d_Y = m->d_dY = nullptr;
   m->cap = 0;
 }
 
@@ -1273,7 +1273,6 @@ static fpt_status mlp_ensure_ws(fpt_ctx* ctx, fpt_mlp* m, uint64_t B, bool train
     f32(&m->d_Z1, H);
     f32(&m->d_Z2, H);
     f32(&m->d_Z3, H);
-    f32(&m->d_dZf, H);
     bf(&m->d_dZa, H);
     bf(&m->d_dZb, H);
     bf(&m->d_dYb, want * kMlpOut);
@@ -1401,15 +1400,13 @@ static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat1
   st = weight_grad(kMlpHidden, kMlpOut, m->d_Ht3, m->d_dYt, m->d_g + kOffW4, 1, kMlpHidden);
   if (st != FPT_OK) return st;
   CUDA_OR_FAIL(ctx, launch_colsum(m->d_dY, B, kMlpOut, m->d_g + kOffB4, ctx->stream));
-  // dZ3 = (dY W4) * gelu'(Z3), and its transpose
+  // dZ3 = (dY W4) * gelu'(Z3), its transpose, and db3 = sum_b dZ3 (column sums in the epilogue)
   {
     GemmArgs g = gemm_args(Bi, kMlpHidden, kMlpOut, m->d_dYb, kMlpOut, 1, Wt4, kMlpOut, 1, EPI_GELU_GRAD, ctx->d_err);
     g.Zin = m->d_Z3;
     g.szm = kMlpHidden;
     g.szn = 1;
-    g.C = m->d_dZf;
-    g.scm = kMlpHidden;
-    g.scn = 1;
+    g.colsum = m->d_g + kOffB3;
     g.H = m->d_dZa;
     g.shm = kMlpHidden;
     g.shn = 1;
@@ -1425,20 +1422,17 @@ static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat1
   __nv_bfloat16 *dZ = m->d_dZa, *dZn = m->d_dZb, *dZt = m->d_dZta, *dZtn = m->d_dZtb;
   for (int l = 2; l >= 0; --l) {
     const int K_in = l == 0 ? kMlpIn : kMlpHidden;
-    CUDA_OR_FAIL(ctx, launch_colsum(m->d_dZf, B, kMlpHidden, m->d_g + offB[l], ctx->stream));
     // dW_l [out][in] = dZ^T [out][b] act^T [in][b]
     st = weight_grad(kMlpHidden, K_in, dZt, acts_t[l], m->d_g + offW[l], K_in, 1);
     if (st != FPT_OK) return st;
     if (l == 0) break;
-    // dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1}) = dZ_l [b][out] (W_l^T)[in][out], and its transpose
+    // dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1}) = dZ_l [b][out] (W_l^T)[in][out], its transpose and db_{l-1}
     GemmArgs gd = gemm_args(Bi, kMlpHidden, kMlpHidden, dZ, kMlpHidden, 1, wts[l], kMlpHidden, 1, EPI_GELU_GRAD,
                             ctx->d_err);
     gd.Zin = Zs[l - 1];
     gd.szm = kMlpHidden;
     gd.szn = 1;
-    gd.C = m->d_dZf;
-    gd.scm = kMlpHidden;
-    gd.scn = 1;
+    gd.colsum = m->d_g + offB[l - 1];
     gd.H = dZn;
     gd.shm = kMlpHidden;
     gd.shn = 1;

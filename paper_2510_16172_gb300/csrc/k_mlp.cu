@@ -180,6 +180,15 @@ __device__ __forceinline__ void gemm_epilogue_staged(const GemmArgs& g, uint32_t
       }
     }
     __syncwarp();
+    if (g.op == EPI_GELU_GRAD && g.colsum) {  // this warp's rows of each column (rows past M hold no value)
+      const int rows = min(32, g.M - mrow0);
+      for (int cc = lane; cc < cols; cc += 32) {
+        if (c0 + cc >= g.N) continue;
+        float acc = 0.f;
+        for (int r = 0; r < rows; ++r) acc += slab[r * kEpiStride + cc];
+        atomicAdd(g.colsum + c0 + cc, acc);
+      }
+    }
     if (g.Ht) {
       const int m = mrow0 + lane;
       for (int cc = 0; cc < cols; ++cc) {
@@ -359,6 +368,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
 // Which outputs may use 16-byte vector accesses (unit stride along n, row strides and bases aligned).
 struct EpiVec {
   bool c, h, z, bias;
@@ -404,15 +415,95 @@ __device__ __forceinline__ void store16_bf16(__nv_bfloat16* p, const float (&x)[
 
 // One warp's share of a finished 128 x n_pad accumulator: its lane quarter, column groups j0, j0 + 2, ...
 // m = this lane's output row.
+// Sum of x[i] over the warp's 32 lanes for each of the 16 columns i: a transposing butterfly (16 shuffles).
+// Returns the sum of column ((lane >> 1) & 8) | ((lane >> 1) & 4) | ((lane >> 1) & 2) | ((lane >> 1) & 1),
+// i.e. column lane / 2 in bit-reversed halves: lane bits 4, 3, 2, 1 select column bits 3, 2, 1, 0.
+__device__ __forceinline__ float warp_colsum16(const float (&x)[16], int lane) {
+  float a[8], b[4], c[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float send = h16 ? x[i] : x[i + 8];
+    const float keep = h16 ? x[i + 8] : x[i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = h8 ? a[i] : a[i + 4];
+    const float keep = h8 ? a[i + 4] : a[i];
+    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h4 ? b[i] : b[i + 2];
+    const float keep = h4 ? b[i + 2] : b[i];
+    c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const float d = (h2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h2 ? c[0] : c[1], 2);
+  return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+__device__ __forceinline__ int warp_colsum16_column(int lane) {
+  return ((lane >> 1) & 8) | ((lane >> 1) & 4) | ((lane >> 1) & 2) | ((lane >> 1) & 1);
+}
+
+// Z[m][n0 .. n0 + 15] (zero past N or M) into registers; 16-byte loads when aligned and whole.
+__device__ __forceinline__ void load_z16(const GemmArgs& g, const EpiVec& ev, int m, bool row, int n0, float (&z)[16]) {
+  const float* zp = g.Zin + (long long)m * g.szm + (long long)n0 * g.szn;
+  const int nv = min(16, g.N - n0);
+  if (row && nv == 16 && ev.z) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(zp) + i);
+      z[4 * i] = t.x;
+      z[4 * i + 1] = t.y;
+      z[4 * i + 2] = t.z;
+      z[4 * i + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = row && i < nv ? zp[i * g.szn] : 0.f;
+  }
+}
+
 template <int OP>
 __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev, uint32_t tacc, int m, int j0,
-                                            int n_groups, int split) {
+                                            int n_groups, int split, float* s_col) {
   const bool row = m < g.M;
+  float zq[16];  // the pre-activations of the next column group (EPI_GELU_GRAD with column sums)
+  if (OP == EPI_GELU_GRAD && s_col && j0 < n_groups) load_z16(g, ev, m, row, 16 * j0, zq);
   for (int j = j0; j < n_groups; j += 2) {
     const int n0 = 16 * j;
     float x[16];
     __syncwarp();
     tc::tmem_ld16(tacc + (uint32_t)n0, x);
+    if (OP == EPI_GELU_GRAD && s_col) {
+      // dZ = acc * gelu'(Z) for every lane (zero past M), the warp's column sums, then the stores.  The
+      // pre-activations of this group were loaded during the previous group (z); the next group's are
+      // requested now, before this group's arithmetic.
+      const int nv = min(16, g.N - n0);
+      float z[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) z[i] = zq[i];
+      if (j + 2 < n_groups) load_z16(g, ev, m, row, 16 * (j + 2), zq);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[i] = row ? x[i] * gelu_grad(z[i]) : 0.f;
+      const float cs = warp_colsum16(x, lane_id());
+      if ((lane_id() & 1) == 0) {
+        const int c = warp_colsum16_column(lane_id());
+        if (c < nv) atomicAdd(s_col + n0 + c, cs);
+      }
+      if (!row) continue;
+      const bool full = nv == 16;
+      if (g.C) store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
+      store16_bf16(g.H + (long long)m * g.shm + (long long)n0 * g.shn, x, full && ev.h, nv, g.shn);
+      if (g.Ht) {
+        __nv_bfloat16* tp = g.Ht + (long long)m * g.shtm + (long long)n0 * g.shtn;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (i < nv) tp[i * g.shtn] = __float2bfloat16(x[i]);
+      }
+      continue;
+    }
     if (!row) continue;
     const int nv = min(16, g.N - n0);
     const bool full = nv == 16;
@@ -483,6 +574,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   __shared__ int s_fail;
   __shared__ int s_last_q;             // the MMA thread's last committed chunk (-1: none)
   __shared__ int s_armed[kWsStages];   // each stage's last phase handed to the TMA engine (-1: none)
+  __shared__ float s_col[256];         // this CTA's column sums (EPI_GELU_GRAD with colsum)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned all = 0xffffffffu;
   const int n_pad = (g.N + 15) & ~15;
@@ -501,6 +593,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     s_fail = 0;
     s_last_q = -1;
   }
+  const bool want_col = g.op == EPI_GELU_GRAD && g.colsum != nullptr;
+  if (want_col)
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_col[k] = 0.f;
   if (warp == 0) {
     tc::tmem_alloc(&s_tmem, 512);
     tc::tmem_relinquish();
@@ -588,16 +683,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       const int m = w.m0 + quarter * 32 + lane;
       switch (g.op) {
         case EPI_STORE:
-          ws_epilogue<EPI_STORE>(g, ev, tacc, m, j0, n_groups, w.split);
+          ws_epilogue<EPI_STORE>(g, ev, tacc, m, j0, n_groups, w.split, nullptr);
           break;
         case EPI_SPLIT:
-          ws_epilogue<EPI_SPLIT>(g, ev, tacc, m, j0, n_groups, w.split);
+          ws_epilogue<EPI_SPLIT>(g, ev, tacc, m, j0, n_groups, w.split, nullptr);
           break;
         case EPI_BIAS_GELU:
-          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, j0, n_groups, w.split);
+          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, j0, n_groups, w.split, nullptr);
           break;
         default:
-          ws_epilogue<EPI_GELU_GRAD>(g, ev, tacc, m, j0, n_groups, w.split);
+          ws_epilogue<EPI_GELU_GRAD>(g, ev, tacc, m, j0, n_groups, w.split, want_col ? s_col : nullptr);
           break;
       }
       tc::fence_before_sync();
@@ -616,6 +711,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (q >= 0) tc::mbar_wait(&empty[q % kWsStages], (uint32_t)((q / kWsStages) & 1), kWaitTries);
   }
   __syncthreads();
+  if (want_col && !s_fail)
+    for (int k = threadIdx.x; k < g.N; k += blockDim.x) atomicAdd(g.colsum + k, s_col[k]);
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
@@ -827,13 +924,32 @@ __global__ void mlp_loss_kernel(const float* __restrict__ G, const float* __rest
 }
 
 // out[n] += sum_b A[b][n]  (bias gradients), A: [B][N] row-major
+// out[n] += sum_b A[b][n]: each thread one column and a strided set of rows (four sums in flight), then
+// the block's row lanes combined in shared memory and one atomic per column and block.
 __global__ void colsum_kernel(const float* __restrict__ A, uint64_t B, int N, float* out) {
+  __shared__ float part[256];
   const int n = threadIdx.x % N;
   const int lanes = blockDim.x / N;
-  float acc = 0.f;
-  for (uint64_t b = (uint64_t)blockIdx.x * lanes + threadIdx.x / N; b < B; b += (uint64_t)gridDim.x * lanes)
-    acc += A[b * N + n];
-  if (threadIdx.x < lanes * N) atomicAdd(out + n, acc);
+  const int rl = threadIdx.x / N;
+  const uint64_t step = (uint64_t)gridDim.x * lanes;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  uint64_t b = (uint64_t)blockIdx.x * lanes + rl;
+  if (rl < lanes) {
+    for (; b + 3 * step < B; b += 4 * step) {
+      a0 += A[b * N + n];
+      a1 += A[(b + step) * N + n];
+      a2 += A[(b + 2 * step) * N + n];
+      a3 += A[(b + 3 * step) * N + n];
+    }
+    for (; b < B; b += step) a0 += A[b * N + n];
+  }
+  part[threadIdx.x] = rl < lanes ? (a0 + a1) + (a2 + a3) : 0.f;
+  __syncthreads();
+  if (threadIdx.x < N) {
+    float acc = 0.f;
+    for (int r = 0; r < lanes; ++r) acc += part[r * N + threadIdx.x];
+    atomicAdd(out + threadIdx.x, acc);
+  }
 }
 
 __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
@@ -1314,8 +1430,17 @@ cudaError_t launch_mlp_loss(const float* G, const float* Y, const float* T, uint
 }
 
 cudaError_t launch_colsum(const float* A, uint64_t B, int N, float* out, cudaStream_t stream) {
-  const int threads = N >= 256 ? N : (256 / N) * N;
-  colsum_kernel<<<grid_1d(B, threads / N, 256), threads, 0, stream>>>(A, B, N, out);
+  if (N < 1 || N > 256) return cudaErrorInvalidValue;
+  const int threads = (256 / N) * N;
+  int dev = 0, n_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t rows_per_block = (uint64_t)(threads / N) * 16;  // at least 16 rows per thread
+  uint64_t blocks = (B + rows_per_block - 1) / rows_per_block;
+  if (blocks > (uint64_t)(4 * n_sm)) blocks = 4 * n_sm;
+  if (blocks < 1) blocks = 1;
+  colsum_kernel<<<(unsigned)blocks, 256, 0, stream>>>(A, B, N, out);
   count_launch();
   return cudaGetLastError();
 }
@@ -1327,8 +1452,38 @@ cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, flo
   return cudaGetLastError();
 }
 
+// dst[m][n] += sum over s of ws[s][m][n].  Each thread takes four consecutive entries (one 16-byte load per
+// split) over one of gridDim.y groups of splits, with two sums in flight, and adds its partial sums to dst.
 __global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, int M, int N, float* dst, long long scm,
                                      long long scn) {
+  const long long MN = (long long)M * N, n4 = MN / 4;
+  const int groups = gridDim.y;
+  const int s_lo = (int)((long long)blockIdx.y * splits / groups), s_hi = (int)((long long)(blockIdx.y + 1) * splits / groups);
+  const float4* w4 = reinterpret_cast<const float4*>(ws);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    int s = s_lo;
+    for (; s + 1 < s_hi; s += 2) {
+      const float4 u = w4[s * n4 + q], v = w4[(s + 1) * n4 + q];
+      a.x += u.x; a.y += u.y; a.z += u.z; a.w += u.w;
+      b.x += v.x; b.y += v.y; b.z += v.z; b.w += v.w;
+    }
+    if (s < s_hi) {
+      const float4 u = w4[s * n4 + q];
+      a.x += u.x; a.y += u.y; a.z += u.z; a.w += u.w;
+    }
+    const float r[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long e = 4 * q + i;
+      atomicAdd(dst + (e / N) * scm + (e % N) * scn, r[i]);
+    }
+  }
+}
+
+// The same for any M x N (one entry per thread, every split).
+__global__ void splitk_reduce1_kernel(const float* __restrict__ ws, int splits, int M, int N, float* dst, long long scm,
+                                      long long scn) {
   const long long MN = (long long)M * N;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (long long)gridDim.x * blockDim.x) {
     float acc = 0.f;
@@ -1340,8 +1495,15 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, i
 cudaError_t launch_splitk_reduce(const float* ws, int splits, int M, int N, float* dst, long long scm, long long scn,
                                  cudaStream_t stream) {
   const long long MN = (long long)M * N;
-  const unsigned grid = (unsigned)((MN + 255) / 256 < 1024 ? (MN + 255) / 256 : 1024);
-  splitk_reduce_kernel<<<grid, 256, 0, stream>>>(ws, splits, M, N, dst, scm, scn);
+  if (MN % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0) {
+    const long long n4 = MN / 4;
+    const unsigned gx = (unsigned)((n4 + 255) / 256 < 1024 ? (n4 + 255) / 256 : 1024);
+    const unsigned gy = splits < 8 ? (unsigned)splits : 8u;
+    splitk_reduce_kernel<<<dim3(gx, gy), 256, 0, stream>>>(ws, splits, M, N, dst, scm, scn);
+  } else {
+    const unsigned grid = (unsigned)((MN + 255) / 256 < 1024 ? (MN + 255) / 256 : 1024);
+    splitk_reduce1_kernel<<<grid, 256, 0, stream>>>(ws, splits, M, N, dst, scm, scn);
+  }
   count_launch();
   return cudaGetLastError();
 }

@@ -37,6 +37,7 @@ struct GemmArgs {
   long long shtm, shtn;
   const float* Zin;       // pre-activation for EPI_GELU_GRAD
   long long szm, szn;
+  float* colsum;          // EPI_GELU_GRAD: the column sums of the FP32 result are added here ([N]), or null
   int* err;               // device error word (MMA completion timeout)
 };
 
