@@ -7,8 +7,9 @@
 //
 // GEMMs D[M x N] = sum_k A(m, k) B(n, k), N <= 256, K in chunks of 64.  Operands whose rows are
 // contiguous and 16-byte aligned go to gemm_ws_kernel: persistent, one CTA per SM over (128-row tile,
-// K split) items, the chunks loaded by TMA into a four-stage ring (128-byte swizzled K-major tiles), one
-// thread issuing the MMAs into two TMEM accumulators, eight epilogue warps storing from registers.
+// K split) items, the chunks loaded by TMA into a two-stage ring (128-byte swizzled K-major tiles), one
+// thread issuing the MMAs into two TMEM accumulators, twelve epilogue warps staging the outputs in shared
+// memory for TMA tensor stores.
 // Other strides (and the atomic epilogue) take gemm_kernel, one tile per CTA with the operands gathered
 // element by element.  The training pass keeps every operand K-major: its epilogues also write the
 // transposes that the weight gradients read.  Epilogues: plain store, split-K partial store, atomic add,
@@ -319,38 +320,27 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
   if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
-// ---------------------------------------------------------------------------
-// Persistent, warp-specialised GEMM for operands whose rows are contiguous and 16-byte aligned.
-// One CTA per SM (256 threads) takes work items (a 128-row tile and a K split) in turn:
-//   warp 0     producer: cp.async copies of each 64-wide K chunk into a ring of kWsStages stages
-//              (A 16 KB + B up to 32 KB); once a chunk's copies have landed (it runs one chunk
-//              behind the newest, so two are in flight) each lane fences them for the tensor core
-//              and arrives on the stage's `full` barrier;
-//   warp 1     MMA issuer (lane 0): per chunk four 128 x N x 16 tcgen05 MMAs into one of two TMEM
-//              accumulators (256 columns each), committed to the stage's `empty` barrier; after a
-//              tile's last chunk, a commit to the accumulator's `acc_full` barrier;
-//   warps 4-7  epilogue: drain an accumulator (TMEM lanes 32 (w % 4) ..) through the staged,
-//              coalesced epilogue while the next tile's MMAs fill the other, then arrive on its
-//              `acc_empty` barrier.
-// Every wait is bounded; a timeout sets the CTA's fail flag, which every role polls and leaves on.
-// ---------------------------------------------------------------------------
 // ---- persistent warp-specialised GEMM (TMA operands) -------------------------------------------------
 // One CTA per SM walks the (128-row tile, K split) items.  Warp 0 (one thread) loads each 64-wide K chunk
 // of A (128 rows) and B (n_pad rows) with one TMA tile load per operand into a ring of kWsStages stages,
 // in the 128-byte swizzled K-major layout; rows past M or N and k past K arrive as zeros.  Warp 1 (one
 // thread) issues four 128 x n_pad x 16 MMAs per chunk into one of two TMEM accumulators (columns 0-255,
 // 256-511), releases the chunk's stage by a commit to `empty` and announces a finished tile by a commit
-// to `acc_full`.  Warps 2-9 are the epilogue: two warps per 32-lane quarter of TMEM (a warp may read the
-// quarter given by its index mod 4), each on every other group of 16 columns; every lane owns one output
-// row and stores its 16 columns with 16-byte vector stores (the transposed copy with one store per column,
-// consecutive lanes on consecutive rows).  They hand the accumulator back through `acc_empty`, so the
-// MMAs of the tile after next may start while this tile's epilogue runs.
-constexpr int kWsStages = 4;
-constexpr int kWsEpiWarps = 8;
+// to `acc_full`.  Warps 2-13 are the epilogue: three warps per 32-lane quarter of TMEM (a warp may read the
+// quarter given by its index mod 4), each on every third group of 16 columns, one output row per lane.
+// Each 32 x 16 group is staged in shared memory and written by TMA tensor stores (full lines, no
+// per-lane store traffic); outputs whose strides a tensor map cannot describe are stored by the lanes.
+// The warps hand the accumulator back through `acc_empty`, so the MMAs of the tile after next may start
+// while this tile's epilogue runs.  Every wait is bounded; a timeout sets the CTA's fail flag, which every
+// role polls and leaves on.
+constexpr int kWsStages = 2;
+constexpr int kWsEpiWarps = 12;
+constexpr int kWsGroupStride = kWsEpiWarps / 4;  // epilogue warps per 32-lane quarter of TMEM
 constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
 constexpr int kWsTileA = 128 * 128;                       // 128 rows x 128 bytes
 constexpr int kWsStageBytes = kWsTileA + 256 * 128;       // + B, up to 256 rows: 48 KB
-constexpr int kWsSmem = kWsStages * kWsStageBytes + 1024;  // + slack to align the ring to 1024 bytes
+// the ring, two 4 KB output staging buffers per epilogue warp, slack to align the ring to 1024 bytes
+constexpr int kWsSmem = kWsStages * kWsStageBytes + kWsEpiWarps * 2 * 4096 + 1024;
 
 struct WsItem {
   int m0, kb, ke, split;
@@ -413,8 +403,6 @@ __device__ __forceinline__ void store16_bf16(__nv_bfloat16* p, const float (&x)[
   }
 }
 
-// One warp's share of a finished 128 x n_pad accumulator: its lane quarter, column groups j0, j0 + 2, ...
-// m = this lane's output row.
 // Sum of x[i] over the warp's 32 lanes for each of the 16 columns i: a transposing butterfly (16 shuffles).
 // Returns the sum of column ((lane >> 1) & 8) | ((lane >> 1) & 4) | ((lane >> 1) & 2) | ((lane >> 1) & 1),
 // i.e. column lane / 2 in bit-reversed halves: lane bits 4, 3, 2, 1 select column bits 3, 2, 1, 0.
@@ -465,48 +453,47 @@ __device__ __forceinline__ void load_z16(const GemmArgs& g, const EpiVec& ev, in
   }
 }
 
+// Staging of one warp's 32 x 16 output group for the TMA tensor stores (two buffers per warp, used in
+// turn): the FP32 box in the 64-byte swizzled layout (row r, 16-byte chunk c at r 64 + 16 (c ^ (r / 2 mod 4))),
+// the BF16 box in the 32-byte swizzled layout (r 32 + 16 (c ^ (r / 4 mod 2))), the transposed BF16 box
+// plainly (column n of the group at n 64, row r at 2 r).  Consecutive lanes (rows) hit different banks
+// in all three.
+constexpr int kStgC = 0, kStgH = 2048, kStgHt = 3072, kStgBytes = 4096;
+constexpr int kOutC = 1, kOutH = 2, kOutHt = 4;  // outputs that go through TMA stores
+
+struct OutMaps {
+  const CUtensorMap* c;
+  const CUtensorMap* h;
+  const CUtensorMap* ht;
+  int flags;
+};
+
+// One warp's share of a finished 128 x n_pad accumulator: its lane quarter, column groups j0, j0 + kWsGroupStride, ...
+// m = this lane's output row, mrow0 = the warp's first row.  Each output goes out through a TMA store of the
+// staged group when its tensor map exists (flags), else with this lane's own stores.  gi counts the warp's
+// groups (it picks the staging buffer).  For EPI_GELU_GRAD the pre-activations of the next group are
+// loaded while the current one is worked on, and the column sums of dZ are added to s_col.
 template <int OP>
-__device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev, uint32_t tacc, int m, int j0,
-                                            int n_groups, int split, float* s_col) {
+__device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev, uint32_t tacc, int m, int mrow0,
+                                            int j0, int n_groups, int split, float* s_col, const OutMaps& om,
+                                            unsigned char* stg, int& gi) {
+  const int lane = lane_id();
   const bool row = m < g.M;
-  float zq[16];  // the pre-activations of the next column group (EPI_GELU_GRAD with column sums)
-  if (OP == EPI_GELU_GRAD && s_col && j0 < n_groups) load_z16(g, ev, m, row, 16 * j0, zq);
-  for (int j = j0; j < n_groups; j += 2) {
+  const bool has_c = OP == EPI_STORE || OP == EPI_SPLIT || g.C != nullptr;
+  const bool has_h = OP == EPI_BIAS_GELU || OP == EPI_GELU_GRAD;
+  const bool has_ht = has_h && g.Ht != nullptr;
+  const bool tma_c = has_c && (om.flags & kOutC), tma_h = has_h && (om.flags & kOutH),
+             tma_ht = has_ht && (om.flags & kOutHt);
+  const bool any_tma = tma_c || tma_h || tma_ht;
+  float zq[16];  // the pre-activations of the next column group (EPI_GELU_GRAD)
+  if (OP == EPI_GELU_GRAD && j0 < n_groups) load_z16(g, ev, m, row, 16 * j0, zq);
+  for (int j = j0; j < n_groups; j += kWsGroupStride) {
     const int n0 = 16 * j;
+    const int nv = min(16, g.N - n0);
+    const bool full = nv == 16;
     float x[16];
     __syncwarp();
     tc::tmem_ld16(tacc + (uint32_t)n0, x);
-    if (OP == EPI_GELU_GRAD && s_col) {
-      // dZ = acc * gelu'(Z) for every lane (zero past M), the warp's column sums, then the stores.  The
-      // pre-activations of this group were loaded during the previous group (z); the next group's are
-      // requested now, before this group's arithmetic.
-      const int nv = min(16, g.N - n0);
-      float z[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) z[i] = zq[i];
-      if (j + 2 < n_groups) load_z16(g, ev, m, row, 16 * (j + 2), zq);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) x[i] = row ? x[i] * gelu_grad(z[i]) : 0.f;
-      const float cs = warp_colsum16(x, lane_id());
-      if ((lane_id() & 1) == 0) {
-        const int c = warp_colsum16_column(lane_id());
-        if (c < nv) atomicAdd(s_col + n0 + c, cs);
-      }
-      if (!row) continue;
-      const bool full = nv == 16;
-      if (g.C) store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
-      store16_bf16(g.H + (long long)m * g.shm + (long long)n0 * g.shn, x, full && ev.h, nv, g.shn);
-      if (g.Ht) {
-        __nv_bfloat16* tp = g.Ht + (long long)m * g.shtm + (long long)n0 * g.shtn;
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (i < nv) tp[i * g.shtn] = __float2bfloat16(x[i]);
-      }
-      continue;
-    }
-    if (!row) continue;
-    const int nv = min(16, g.N - n0);
-    const bool full = nv == 16;
     if ((OP == EPI_STORE || OP == EPI_BIAS_GELU) && g.bias) {
       if (full && ev.bias) {
 #pragma unroll
@@ -523,51 +510,96 @@ __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev,
           if (i < nv) x[i] += g.bias[n0 + i];
       }
     }
-    if (OP == EPI_SPLIT) {
-      store16_f32(g.C + ((long long)split * g.M + m) * g.N + n0, x, full && ev.c, nv, 1);
-      continue;
-    }
-    if (OP == EPI_STORE) {
-      store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
-      continue;
-    }
+    float h[16];  // the BF16 output (rounded when stored): the activation, or dZ
     if (OP == EPI_GELU_GRAD) {
-      const float* zp = g.Zin + (long long)m * g.szm + (long long)n0 * g.szn;
       float z[16];
-      if (full && ev.z) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(zp) + i);
-          z[4 * i] = t.x;
-          z[4 * i + 1] = t.y;
-          z[4 * i + 2] = t.z;
-          z[4 * i + 3] = t.w;
+      for (int i = 0; i < 16; ++i) z[i] = zq[i];
+      if (j + kWsGroupStride < n_groups) load_z16(g, ev, m, row, 16 * (j + kWsGroupStride), zq);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[i] = row ? x[i] * gelu_grad(z[i]) : 0.f;
+      if (s_col) {
+        const float cs = warp_colsum16(x, lane);
+        if ((lane & 1) == 0) {
+          const int c = warp_colsum16_column(lane);
+          if (c < nv) atomicAdd(s_col + n0 + c, cs);
         }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) z[i] = i < nv ? zp[i * g.szn] : 0.f;
       }
 #pragma unroll
-      for (int i = 0; i < 16; ++i) x[i] *= gelu_grad(z[i]);
-      if (g.C) store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
-    } else {  // EPI_BIAS_GELU: the pre-activation, then the BF16 activation
-      if (g.C) store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
+      for (int i = 0; i < 16; ++i) h[i] = x[i];
+    } else if (OP == EPI_BIAS_GELU) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) x[i] = gelu(x[i]);
+      for (int i = 0; i < 16; ++i) h[i] = gelu(x[i]);
     }
-    store16_bf16(g.H + (long long)m * g.shm + (long long)n0 * g.shn, x, full && ev.h, nv, g.shn);
-    if (g.Ht) {
-      __nv_bfloat16* tp = g.Ht + (long long)m * g.shtm + (long long)n0 * g.shtn;
+    // this lane's own stores for the outputs without a tensor map
+    if (row) {
+      if (has_c && !tma_c) {
+        if (OP == EPI_SPLIT)
+          store16_f32(g.C + ((long long)split * g.M + m) * g.N + n0, x, full && ev.c, nv, 1);
+        else
+          store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
+      }
+      if (has_h && !tma_h) store16_bf16(g.H + (long long)m * g.shm + (long long)n0 * g.shn, h, full && ev.h, nv, g.shn);
+      if (has_ht && !tma_ht) {
+        __nv_bfloat16* tp = g.Ht + (long long)m * g.shtm + (long long)n0 * g.shtn;
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (i < nv) tp[i * g.shtn] = __float2bfloat16(x[i]);
+        for (int i = 0; i < 16; ++i)
+          if (i < nv) tp[i * g.shtn] = __float2bfloat16(h[i]);
+      }
+    }
+    if (!any_tma) continue;
+    // the staged group: wait until the engine has read this buffer's previous group, fill it, store it
+    unsigned char* buf = stg + (gi & 1) * kStgBytes;
+    ++gi;
+    if (lane == 0) tc::bulk_wait_read<1>();
+    __syncwarp();
+    if (tma_c) {
+      unsigned char* cb = buf + kStgC + lane * 64;
+      const int sw = (lane >> 1) & 3;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<float4*>(cb + 16 * (c ^ sw)) = make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+    }
+    if (tma_h) {
+      unsigned char* hb = buf + kStgH + lane * 32;
+      const int sw = (lane >> 2) & 1;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(h[8 * c + 2 * i], h[8 * c + 2 * i + 1]);
+          w[i] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(hb + 16 * (c ^ sw)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    if (tma_ht) {
+      __nv_bfloat16* tb = reinterpret_cast<__nv_bfloat16*>(buf + kStgHt) + lane;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) tb[32 * i] = __float2bfloat16(h[i]);
+    }
+    tc::fence_async_smem();
+    __syncwarp();
+    if (lane == 0 && mrow0 < g.M) {
+      if (tma_c) {
+        if (OP == EPI_SPLIT)
+          tc::tma_store_3d(om.c, buf + kStgC, n0, mrow0, split);
+        else
+          tc::tma_store_2d(om.c, buf + kStgC, n0, mrow0);
+      }
+      if (tma_h) tc::tma_store_2d(om.h, buf + kStgH, n0, mrow0);
+      if (tma_ht) tc::tma_store_2d(om.ht, buf + kStgHt, mrow0, n0);
+      tc::bulk_commit();
     }
   }
 }
 
 __global__ void __launch_bounds__(kWsThreads, 1)
-    gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g,
-                   int m_tiles, int n_items, int k_per) {
+    gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH,
+                   const __grid_constant__ CUtensorMap tmHt, int out_flags, GemmArgs g, int m_tiles, int n_items,
+                   int k_per) {
   extern __shared__ unsigned char ws_raw[];
   __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t s_tmem;
@@ -666,9 +698,12 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   } else {
     // ---- epilogue ----
     const int quarter = warp & 3;            // the TMEM lanes this warp may read
-    const int j0 = (warp - 2) >> 2;          // its column groups: j0, j0 + 2, ...
+    const int j0 = (warp - 2) >> 2;          // its column groups: j0, j0 + kWsGroupStride, ...
     const int n_groups = n_pad / 16;
     const EpiVec ev = epi_vec(g);
+    const OutMaps om{&tmC, &tmH, &tmHt, out_flags};
+    unsigned char* stg = ring + kWsStages * kWsStageBytes + (warp - 2) * 2 * kStgBytes;
+    int gi = 0;
     int i = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++i) {
       const WsItem w = ws_item(g, item, m_tiles, k_per);
@@ -680,25 +715,30 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       }
       tc::fence_after_sync();
       const uint32_t tacc = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-      const int m = w.m0 + quarter * 32 + lane;
+      const int mrow0 = w.m0 + quarter * 32;
+      const int m = mrow0 + lane;
       switch (g.op) {
         case EPI_STORE:
-          ws_epilogue<EPI_STORE>(g, ev, tacc, m, j0, n_groups, w.split, nullptr);
+          ws_epilogue<EPI_STORE>(g, ev, tacc, m, mrow0, j0, n_groups, w.split, nullptr, om, stg, gi);
           break;
         case EPI_SPLIT:
-          ws_epilogue<EPI_SPLIT>(g, ev, tacc, m, j0, n_groups, w.split, nullptr);
+          ws_epilogue<EPI_SPLIT>(g, ev, tacc, m, mrow0, j0, n_groups, w.split, nullptr, om, stg, gi);
           break;
         case EPI_BIAS_GELU:
-          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, j0, n_groups, w.split, nullptr);
+          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, mrow0, j0, n_groups, w.split, nullptr, om, stg, gi);
           break;
         default:
-          ws_epilogue<EPI_GELU_GRAD>(g, ev, tacc, m, j0, n_groups, w.split, want_col ? s_col : nullptr);
+          ws_epilogue<EPI_GELU_GRAD>(g, ev, tacc, m, mrow0, j0, n_groups, w.split, want_col ? s_col : nullptr, om,
+                                     stg, gi);
           break;
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
+    // every TMA store of this warp has completed before its staging buffers go away
+    if (lane == 0) tc::bulk_wait_all();
+    __syncwarp();
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -729,18 +769,61 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// The {k, row} view of a row-major BF16 matrix (rows x K, row stride ld elements) in 64 x box_rows boxes
-// with 128-byte swizzling; elements outside the matrix read as zero.
-static bool encode_operand(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, long long ld, int box_rows) {
+// A tiled tensor map of `rank` dimensions (dims innermost first, strides in bytes for dimensions 1..),
+// elements outside the tensor read as zero and are not written.
+static bool encode_map(CUtensorMap* map, CUtensorMapDataType type, int rank, const void* base, const cuuint64_t* dims,
+                       const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapSwizzle swizzle) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  for (int d = 0; d + 1 < rank; ++d)
+    if (strides[d] % 16 != 0) return false;
+  const cuuint32_t elem[3] = {1, 1, 1};
+  return enc(map, type, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, elem,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The {k, row} view of a row-major BF16 matrix (rows x K, row stride ld elements) in 64 x box_rows boxes
+// with 128-byte swizzling.
+static bool encode_operand(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, long long ld, int box_rows) {
   const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 2u};
   const cuuint32_t box[2] = {(cuuint32_t)kGemmKC, (cuuint32_t)box_rows};
-  const cuuint32_t elem[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, elem,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode_map(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+// Tensor maps of the epilogue's outputs (32-row x 16-column boxes, laid out as the staging buffers are);
+// returns the kOut* flags of the outputs that have one.
+static int encode_outputs(const GemmArgs& g, int splits, CUtensorMap* tmC, CUtensorMap* tmH, CUtensorMap* tmHt) {
+  int flags = 0;
+  if (g.op == EPI_SPLIT) {
+    const cuuint64_t dims[3] = {(cuuint64_t)g.N, (cuuint64_t)g.M, (cuuint64_t)splits};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.N * 4u, (cuuint64_t)g.M * g.N * 4u};
+    const cuuint32_t box[3] = {16, 32, 1};
+    if (encode_map(tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g.C, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B))
+      flags |= kOutC;
+  } else if (g.C && g.scn == 1) {
+    const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.scm * 4u};
+    const cuuint32_t box[2] = {16, 32};
+    if (encode_map(tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g.C, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B))
+      flags |= kOutC;
+  }
+  if ((g.op == EPI_BIAS_GELU || g.op == EPI_GELU_GRAD) && g.H && g.shn == 1) {
+    const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.shm * 2u};
+    const cuuint32_t box[2] = {16, 32};
+    if (encode_map(tmH, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.H, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_32B))
+      flags |= kOutH;
+  }
+  if ((g.op == EPI_BIAS_GELU || g.op == EPI_GELU_GRAD) && g.Ht && g.shtm == 1) {
+    const cuuint64_t dims[2] = {(cuuint64_t)g.M, (cuuint64_t)g.N};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.shtn * 2u};
+    const cuuint32_t box[2] = {32, 16};
+    if (encode_map(tmHt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.Ht, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE))
+      flags |= kOutHt;
+  }
+  return flags;
 }
 
 cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
@@ -766,7 +849,10 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
       if (e != cudaSuccess) return e;
       const int grid = n_items < n_sm ? n_items : n_sm;
-      gemm_ws_kernel<<<grid, kWsThreads, kWsSmem, stream>>>(tmA, tmB, g, m_tiles, n_items, k_per);
+      CUtensorMap tmC{}, tmH{}, tmHt{};
+      const int out_flags = encode_outputs(g, splits, &tmC, &tmH, &tmHt);
+      gemm_ws_kernel<<<grid, kWsThreads, kWsSmem, stream>>>(tmA, tmB, tmC, tmH, tmHt, out_flags, g, m_tiles, n_items,
+                                                            k_per);
       count_launch();
       return cudaGetLastError();
     }
