@@ -175,6 +175,7 @@ struct fpt_mlp {
   __nv_bfloat16* d_Xb = nullptr;
   float *d_Tb = nullptr, *d_Gb = nullptr, *d_hist = nullptr;
   uint64_t train_cap = 0;
+  bool xt_ready = false;  // d_Xt already holds the transpose of d_Xb (written by the shuffle gather)
   size_t hist_cap = 0;
   // activations / gradients for a batch of up to cap rows
   uint64_t cap = 0;
@@ -1352,8 +1353,9 @@ static fpt_status mlp_forward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16
 // operands: the weight gradients dW = dZ^T act take the transposed copies written by the epilogues, the
 // back-propagation dH = dZ W the transposed BF16 weights.
 static int split_k(const fpt_ctx* ctx, int B, int m_tiles) {
-  // enough CTAs to cover the SMs, at least four 64-wide K chunks per split
-  int ks = (2 * ctx->n_sm + m_tiles - 1) / m_tiles;
+  // one (row tile, K split) item per SM (the persistent GEMM then keeps one partial product per CTA), at
+  // least four 64-wide K chunks per split
+  int ks = ctx->n_sm / m_tiles;
   const int max_ks = B / 256 > 1 ? B / 256 : 1;
   ks = ks < 1 ? 1 : (ks > max_ks ? max_ks : ks);
   // the GEMM gives each split ceil(B / (ks 64)) chunks of 64: count only the splits that get some,
@@ -1394,7 +1396,7 @@ static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat1
   };
   fpt_status st = mlp_forward_impl(ctx, m, X, B, m->d_Y, true);
   if (st != FPT_OK) return st;
-  CUDA_OR_FAIL(ctx, launch_bf16_transpose(X, Bi, kMlpIn, m->d_Xt, ctx->stream));
+  if (!(m->xt_ready && X == m->d_Xb)) CUDA_OR_FAIL(ctx, launch_bf16_transpose(X, Bi, kMlpIn, m->d_Xt, ctx->stream));
   CUDA_OR_FAIL(ctx, launch_mlp_loss(G, m->d_Y, T, B, m->d_dY, m->d_dYb, m->d_dYt, m->d_loss, ctx->stream));
   // last layer: dW4^T [in][out] = H3^T dY (sum over the batch); db4 = sum_b dY
   st = weight_grad(kMlpHidden, kMlpOut, m->d_Ht3, m->d_dYt, m->d_g + kOffW4, 1, kMlpHidden);
@@ -1689,8 +1691,11 @@ fpt_status fpt_mlp_train(fpt_ctx* ctx, fpt_mlp* m, const void* X, const float* T
     uint64_t s0 = p.seed + 0x9E3779B97F4A7C15ULL * (uint64_t)(ep + 1);
     const uint64_t key = sm64_next(s0);
     for (uint64_t k = 0; k < steps; ++k) {
-      CUDA_OR_FAIL(ctx, launch_mlp_gather(Xs, T, G, n, k * B, B, key, m->d_Xb, m->d_Tb, m->d_Gb, ctx->stream));
+      CUDA_OR_FAIL(ctx, launch_mlp_gather(Xs, T, G, n, k * B, B, key, m->d_Xb, m->d_Tb, m->d_Gb, m->d_Xt,
+                                          ctx->stream));
+      m->xt_ready = true;
       st = fpt_mlp_train_step(ctx, m, m->d_Xb, m->d_Tb, m->d_Gb, B, lr, nullptr);
+      m->xt_ready = false;
       if (st != FPT_OK) return st;
       CUDA_OR_FAIL(ctx, launch_mlp_accumulate(m->d_hist + ep, m->d_loss, 1.f / (float)steps, ctx->stream));
     }

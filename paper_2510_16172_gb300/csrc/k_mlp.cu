@@ -979,30 +979,86 @@ __global__ void mlp_features_kernel(SceneDev S, BatchDev B, int n, const PathRec
 }
 
 // loss (1/B) sum_b sum_s dy_s^T G_s dy_s (G_s = A_s^T A_s / S^2 per slot, zero for unused slots) and dY
+// Per sample: d = Y[:8] - T, the Gram-weighted loss sum_s d_s^T G_s d_s and its gradient dY = (2 / B) G d
+// (the padded outputs 8..15 get zero), in FP32, BF16 and transposed BF16.  vec: the rows of G, Y, T and the
+// outputs start on 16-byte boundaries (16-byte loads and stores).
 __global__ void mlp_loss_kernel(const float* __restrict__ G, const float* __restrict__ Y,
                                 const float* __restrict__ T, uint64_t B, float* __restrict__ dY,
-                                __nv_bfloat16* __restrict__ dYb, __nv_bfloat16* __restrict__ dYt, float* loss) {
+                                __nv_bfloat16* __restrict__ dYb, __nv_bfloat16* __restrict__ dYt, float* loss,
+                                int vec) {
   float acc = 0.f;
   const float w = 2.f / (float)B;
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (uint64_t)gridDim.x * blockDim.x) {
+    float gm[12], y[8], t[8];
+    if (vec) {
+      const float4* gp = reinterpret_cast<const float4*>(G + b * 12);
+      const float4* yp = reinterpret_cast<const float4*>(Y + b * kMlpOut);
+      const float4* tp = reinterpret_cast<const float4*>(T + b * 8);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float4 v = __ldg(gp + q);
+        gm[4 * q] = v.x;
+        gm[4 * q + 1] = v.y;
+        gm[4 * q + 2] = v.z;
+        gm[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float4 v = yp[q], u = __ldg(tp + q);
+        y[4 * q] = v.x;
+        y[4 * q + 1] = v.y;
+        y[4 * q + 2] = v.z;
+        y[4 * q + 3] = v.w;
+        t[4 * q] = u.x;
+        t[4 * q + 1] = u.y;
+        t[4 * q + 2] = u.z;
+        t[4 * q + 3] = u.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) gm[q] = G[b * 12 + q];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        y[q] = Y[b * kMlpOut + q];
+        t[q] = T[b * 8 + q];
+      }
+    }
     float g[kMlpOut];
 #pragma unroll
     for (int k = 0; k < kMlpOut; ++k) g[k] = 0.f;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      const float g11 = G[b * 12 + 3 * s], g12 = G[b * 12 + 3 * s + 1], g22 = G[b * 12 + 3 * s + 2];
-      const float d0 = Y[b * kMlpOut + 2 * s] - T[b * 8 + 2 * s];
-      const float d1 = Y[b * kMlpOut + 2 * s + 1] - T[b * 8 + 2 * s + 1];
+      const float g11 = gm[3 * s], g12 = gm[3 * s + 1], g22 = gm[3 * s + 2];
+      const float d0 = y[2 * s] - t[2 * s];
+      const float d1 = y[2 * s + 1] - t[2 * s + 1];
       const float m0 = g11 * d0 + g12 * d1, m1 = g12 * d0 + g22 * d1;
       acc += d0 * m0 + d1 * m1;
       g[2 * s] = w * m0;
       g[2 * s + 1] = w * m1;
     }
+    if (vec) {
+      float4* dp = reinterpret_cast<float4*>(dY + b * kMlpOut);
 #pragma unroll
-    for (int k = 0; k < kMlpOut; ++k) {
-      dY[b * kMlpOut + k] = g[k];
-      dYb[b * kMlpOut + k] = __float2bfloat16(g[k]);
-      if (dYt) dYt[(uint64_t)k * B + b] = __float2bfloat16(g[k]);
+      for (int q = 0; q < 4; ++q) dp[q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+      uint32_t wv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(g[2 * q], g[2 * q + 1]);
+        wv[q] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      uint4* bp = reinterpret_cast<uint4*>(dYb + b * kMlpOut);
+      bp[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      bp[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kMlpOut; ++k) {
+        dY[b * kMlpOut + k] = g[k];
+        dYb[b * kMlpOut + k] = __float2bfloat16(g[k]);
+      }
+    }
+    if (dYt) {
+#pragma unroll
+      for (int k = 0; k < kMlpOut; ++k) dYt[(uint64_t)k * B + b] = __float2bfloat16(g[k]);
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -1426,20 +1482,44 @@ __device__ __forceinline__ uint64_t perm_index(uint64_t k, uint64_t n, int h, ui
   return k;
 }
 
+// Row i of the batch = sample perm(first + i): X (128 bytes), T (32) and G (48) copied with 16-byte loads
+// and stores; with Xt, also the transposed features Xt[k][i] (consecutive threads, consecutive i).
 __global__ void mlp_gather_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ T,
                                   const float* __restrict__ G, uint64_t n, uint64_t first, uint64_t B, int h,
                                   uint64_t key, __nv_bfloat16* __restrict__ Xb, float* __restrict__ Tb,
-                                  float* __restrict__ Gb) {
+                                  float* __restrict__ Gb, __nv_bfloat16* __restrict__ Xt, int vec_tg) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t src = perm_index(first + i, n, h, key);
     const uint4* xs = reinterpret_cast<const uint4*>(X + src * kMlpIn);
     uint4* xd = reinterpret_cast<uint4*>(Xb + i * kMlpIn);
+    uint4 xv[kMlpIn / 8];
 #pragma unroll
-    for (int q = 0; q < kMlpIn / 8; ++q) xd[q] = xs[q];
+    for (int q = 0; q < kMlpIn / 8; ++q) xv[q] = __ldg(xs + q);
+    if (vec_tg) {
+      const float4* ts = reinterpret_cast<const float4*>(T + src * 8);
+      const float4* gs = reinterpret_cast<const float4*>(G + src * 12);
+      float4* td = reinterpret_cast<float4*>(Tb + i * 8);
+      float4* gd = reinterpret_cast<float4*>(Gb + i * 12);
+      const float4 t0 = __ldg(ts), t1 = __ldg(ts + 1);
+      const float4 g0 = __ldg(gs), g1 = __ldg(gs + 1), g2 = __ldg(gs + 2);
+      td[0] = t0;
+      td[1] = t1;
+      gd[0] = g0;
+      gd[1] = g1;
+      gd[2] = g2;
+    } else {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) Tb[i * 8 + q] = T[src * 8 + q];
+      for (int q = 0; q < 8; ++q) Tb[i * 8 + q] = T[src * 8 + q];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) Gb[i * 12 + q] = G[src * 12 + q];
+      for (int q = 0; q < 12; ++q) Gb[i * 12 + q] = G[src * 12 + q];
+    }
+#pragma unroll
+    for (int q = 0; q < kMlpIn / 8; ++q) xd[q] = xv[q];
+    if (Xt) {
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(xv);
+#pragma unroll
+      for (int k = 0; k < kMlpIn; ++k) Xt[(uint64_t)k * B + i] = e[k];
+    }
   }
 }
 
@@ -1449,13 +1529,15 @@ __global__ void mlp_accumulate_kernel(float* dst, const float* src, float w) {
 }
 
 cudaError_t launch_mlp_gather(const __nv_bfloat16* X, const float* T, const float* G, uint64_t n, uint64_t first,
-                              uint64_t B, uint64_t key, __nv_bfloat16* Xb, float* Tb, float* Gb,
+                              uint64_t B, uint64_t key, __nv_bfloat16* Xb, float* Tb, float* Gb, __nv_bfloat16* Xt,
                               cudaStream_t stream) {
   int h = 1;
   while ((1ULL << (2 * h)) < n) ++h;
   const uint64_t want = (B + 255) / 256;
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const int vec_tg = a16(T) && a16(G) && a16(Tb) && a16(Gb);
   mlp_gather_kernel<<<(unsigned)(want < 4096 ? (want ? want : 1) : 4096), 256, 0, stream>>>(X, T, G, n, first, B, h,
-                                                                                           key, Xb, Tb, Gb);
+                                                                                           key, Xb, Tb, Gb, Xt, vec_tg);
   count_launch();
   return cudaGetLastError();
 }
@@ -1510,7 +1592,9 @@ cudaError_t launch_mlp_features(const SceneDev& S, const BatchDev& B, int n, con
 
 cudaError_t launch_mlp_loss(const float* G, const float* Y, const float* T, uint64_t B, float* dY,
                             __nv_bfloat16* dYb, __nv_bfloat16* dYt, float* loss, cudaStream_t stream) {
-  mlp_loss_kernel<<<grid_1d(B, 256, 1024), 256, 0, stream>>>(G, Y, T, B, dY, dYb, dYt, loss);
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const int vec = a16(G) && a16(Y) && a16(T) && a16(dY) && a16(dYb);
+  mlp_loss_kernel<<<grid_1d(B, 256, 1024), 256, 0, stream>>>(G, Y, T, B, dY, dYb, dYt, loss, vec);
   count_launch();
   return cudaGetLastError();
 }

@@ -66,7 +66,8 @@ cudaError_t launch_mlp_infer(const SceneDev& S, const BatchDev& B, int n, const 
 // Rows perm(first .. first + B - 1) of (X [n][64], T [n][8], G [n][12]) into (Xb, Tb, Gb), perm = the
 // seeded permutation of [0, n) drawn by key.
 cudaError_t launch_mlp_gather(const __nv_bfloat16* X, const float* T, const float* G, uint64_t n, uint64_t first,
-                              uint64_t B, uint64_t key, __nv_bfloat16* Xb, float* Tb, float* Gb, cudaStream_t stream);
+                              uint64_t B, uint64_t key, __nv_bfloat16* Xb, float* Tb, float* Gb, __nv_bfloat16* Xt,
+                              cudaStream_t stream);
 cudaError_t launch_mlp_accumulate(float* dst, const float* src, float w, cudaStream_t stream);
 cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t first,
                              uint64_t count, const float* Y, float* T, cudaStream_t stream);

@@ -246,6 +246,30 @@ def test_mlp_train_native_schedule(ctx):
     assert abs(runs[0][0][-1] - runs[1][0][-1]) <= 1e-3 * runs[0][0][-1]
 
 
+def test_mlp_train_full_batch_epoch_is_one_step(ctx):
+    """One epoch of fpt_mlp_train with the batch = every sample is one Adam step on a shuffled copy of the
+    whole set, so it equals one fpt_mlp_train_step on the unshuffled set up to the summation order.  Adam's
+    first step moves each weight by +-lr (sign of its gradient), so the layers agree entry by entry except
+    where a gradient is at the rounding level: a wrong shuffle of X, T, G or of the transposed features the
+    library gathers for the first layer's weight gradient would flip about half of them."""
+    from paper_2510_16172_gb300 import warmstart
+
+    X, T, G = warmstart.make_dataset(ctx, [33, 34], 20000)
+    n = min(X.shape[0], 16384) // 8 * 8
+    X, T, G = X[:n].contiguous(), T[:n].contiguous(), G[:n].contiguous()
+    lr = 1e-3
+    a = fpt.Mlp(ctx, 7, SCALE)
+    b = fpt.Mlp(ctx, 7, SCALE)
+    a.train(X, T, G, epochs=1, batch=n, lr=lr, lr_decay=1.0, seed=3)
+    b.train_step(X, T, G, lr, want_loss=False)
+    pa, pb = mo.unpack(a.get_params()), mo.unpack(b.get_params())
+    for name in ("W1", "b1", "W2", "W3", "W4"):
+        flips = np.mean(np.abs(pa[name] - pb[name]) > lr)
+        assert flips <= 0.01, (name, flips)
+    a.close()
+    b.close()
+
+
 def test_learned_start_saves_steps_on_unseen_scenes(ctx):
     """What the trained network gains (config 4 in small): trained by the library's tensor-core kernels on
     the solver's own solutions of seeded order-1..4 sequences on 20 random 10 m scenes, it starts the solver
