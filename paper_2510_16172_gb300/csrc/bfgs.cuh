@@ -538,37 +538,40 @@ __global__ void __launch_bounds__(kThreads, kBfgsMinCtas<N>) bfgs_refill_kernel(
         path_finish<N, Q>(P, B.n_max, T_out, status_out, iters_out);
         owed = false;
       }
-      // hand out paths to free lanes, claiming new chunks as needed
-      while (more && free_mask) {
-        if (next >= end) {
-          unsigned long long base = 0;
-          if (lane == 0) base = atomicAdd(work, (unsigned long long)cfg.chunk);
-          base = __shfl_sync(full, base, 0);
-          if (base >= n_local) {
-            more = false;
-            break;
-          }
-          next = base;
-          end = base + cfg.chunk < n_local ? base + cfg.chunk : n_local;
+      // hand out paths to the free lanes in one pass: the rest of the warp's chunk, then (claimed first)
+      // the next chunk.  A lane whose new path needs no solving (a repeat) writes it out and stays free
+      // until the next refill rather than costing the warp another pass.
+      const uint64_t want = (uint64_t)n_free;
+      const uint64_t avail = end - next;
+      uint64_t nb = 0, ne = 0;  // the newly claimed chunk, if any
+      if (avail < want) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(work, (unsigned long long)cfg.chunk);
+        base = __shfl_sync(full, base, 0);
+        if (base >= n_local) {
+          more = false;
+        } else {
+          nb = base;
+          ne = base + cfg.chunk < n_local ? base + cfg.chunk : n_local;
         }
-        const uint64_t avail = end - next;
-        const int take = (int)(avail < (uint64_t)__popc(free_mask) ? avail : (uint64_t)__popc(free_mask));
-        const bool mine = (free_mask >> lane) & 1u;
-        const int rank = __popc(free_mask & lt_mask);
-        bool got = mine && rank < take;
-        const unsigned got_mask = __ballot_sync(full, got);
-        if (got) {
-          const uint64_t j = next + (uint64_t)rank;
-          if (path_start<N, Q, kSrc>(P, B, tb, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr)) {
-            active = true;
-          } else {
-            path_finish<N, Q>(P, B.n_max, T_out, status_out, iters_out);
-          }
+      }
+      const uint64_t have = avail + (ne - nb);
+      const uint64_t take = have < want ? have : want;
+      const bool mine = (free_mask >> lane) & 1u;
+      const uint64_t rank = (uint64_t)__popc(free_mask & lt_mask);
+      if (mine && rank < take) {
+        const uint64_t j = rank < avail ? next + rank : nb + (rank - avail);
+        if (path_start<N, Q, kSrc>(P, B, tb, list, j, cfg.max_iters, cfg.init_from_T ? T_out : nullptr)) {
+          active = true;
+        } else {
+          path_finish<N, Q>(P, B.n_max, T_out, status_out, iters_out);
         }
-        next += (uint64_t)take;
-        free_mask &= ~got_mask;
-        // lanes whose new path needs no solving are free again
-        free_mask |= __ballot_sync(full, got && !active);
+      }
+      if (take <= avail) {
+        next += take;
+      } else {
+        next = nb + (take - avail);
+        end = ne;
       }
     }
     if (!__any_sync(full, active)) {
