@@ -250,6 +250,33 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+
+def library_defaults_leg(ctx, scene, batch, out, grads, mask, flush, stream, torch, fpt, dev, steps=5, warmup=2):
+    """The same canyon step (solve, polish, validity, implicit backward of the valid solved lengths) with the
+    library's default solver settings instead of the benchmark's step cap and kink stop; timed the same way
+    (CUDA events, L2 flushed between steps), outside the headline's timed region."""
+    p = fpt.default_params()
+
+    def step():
+        fpt.solve_grad(ctx, scene, batch, p, dL_status_mask=mask, out=out, grads=grads)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    solved = fpt.count_status(ctx, out["status"], fpt.ST_SOLVED)
+    # kink_stop 0 selects the library's default, one tenth of the degeneracy tolerance
+    kink = float(p.kink_stop) if p.kink_stop > 0 else 0.1 * float(p.deg_tol)
+    return {"value": solved / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "solved_per_step": solved, "steps": steps,
+            "max_bfgs_iters": int(p.max_iters), "kink_stop_m": kink}
+
 def run_ours(args, world, rank, local_rank):
     import numpy as np
     import torch
@@ -377,6 +404,9 @@ def run_ours(args, world, rank, local_rank):
             "occlusion": occ}
     if dom != fpt.K_BFGS:
         line["roofline_note"] = f"dominant kernel is {names[dom]}; roofline reported for the FP32 solver kernel"
+    if world == 1:
+        line["at_library_defaults"] = library_defaults_leg(ctx, scene, batch, out, grads, mask, flush, stream, torch,
+                                                           fpt, dev)
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
