@@ -98,18 +98,24 @@ def _private_scene(sc, ids, order, ti, ri):
     return scenes.Scene(np.array(types), np.array(verts), np.array(tx), np.array(rx)), nids, idx, idx
 
 
-@pytest.mark.parametrize("k,fp,n_paths,lo,hi,min_frac,max_median", [
-    (4, 1, 300, 1, 3, 0.97, 2e-5), (16, 1, 300, 1, 3, 0.7, 2e-4), (16, 4, 700, 1, 3, 0.7, 2e-4),
-    (4, 1, 200, 6, 8, 0.95, 2e-5), (8, 1, 200, 6, 8, 0.9, 2e-4), (4, 4, 200, 9, 10, 0.95, 2e-5)])
-def test_per_path_gradients_against_the_fp64_autograd_reference(ctx, k, fp, n_paths, lo, hi, min_frac, max_median):
+# (k, Eq. 6 rounds, paths, orders, fraction within 1e-3, fraction within 1e-2, median bound).  Measured on the
+# GB300 with these seeds (the gradients are deterministic: every path has its own objects): 100 % within 1e-3
+# at k = 4 and at orders 6-10; at k = 16, 87.3 % / 96.0 % (one round) and 84.0 % / 93.6 % (four rounds) within
+# 1e-3 / 1e-2; medians 9e-7 to 1.4e-5.  A CPU FP32 run of the reference reaches 86 % and 80 % within 1e-3 at
+# k = 16, so the bounds sit just below what any FP32 evaluation of these iterations gets.
+@pytest.mark.parametrize("k,fp,n_paths,lo,hi,min_frac,min_frac2,max_median", [
+    (4, 1, 300, 1, 3, 0.99, 1.0, 5e-6), (16, 1, 300, 1, 3, 0.82, 0.93, 5e-5), (16, 4, 700, 1, 3, 0.78, 0.90, 6e-5),
+    (4, 1, 200, 6, 8, 0.99, 1.0, 8e-6), (8, 1, 200, 6, 8, 0.98, 1.0, 5e-5), (4, 4, 200, 9, 10, 0.99, 1.0, 5e-6)])
+def test_per_path_gradients_against_the_fp64_autograd_reference(ctx, k, fp, n_paths, lo, hi, min_frac, min_frac2,
+                                                                  max_median):
     """Each path's gradient w.r.t. its own geometry against the FP64 reference through the same k steps.
 
     Differentiating BFGS through FP32 iterations is ill-conditioned once steps near the rounding
     level enter the inverse-Hessian updates (rho = 1 / s.y): a CPU FP32 run of the same autograd
-    reference departs from the FP64 one by more than 1e-3 of the gradient on about a fifth of
-    these paths at k = 16 while most agree to 1e-5.  The test asks for that distribution: most
-    paths within 1e-3 (relative to the path's largest gradient component, at least 1) and a small
-    median.  700 paths put the scene's accumulators in global memory, 300 in shared memory; orders
+    reference departs from the FP64 one by more than 1e-3 of the gradient on 14-20 % of these
+    paths at k = 16 while most agree to 1e-5.  The test asks for that distribution: fractions of
+    the paths within 1e-3 and within 1e-2 (relative to the path's largest gradient component, at
+    least 1) and a small median.  700 paths put the scene's accumulators in global memory, 300 in shared memory; orders
     6-10 keep the inverse Hessian and its adjoint in shared memory (a CPU FP32 run of the reference
     is within 1e-3 on all of those paths).
     """
@@ -142,6 +148,7 @@ def test_per_path_gradients_against_the_fp64_autograd_reference(ctx, k, fp, n_pa
         rel[p] = np.abs(got - ref).max() / max(np.abs(ref).max(), 1.0)
     rel[~np.isfinite(rel)] = np.inf
     assert (rel < 1e-3).mean() >= min_frac, (np.sort(rel)[::-1][:10], (rel < 1e-3).mean())
+    assert (rel < 1e-2).mean() >= min_frac2, (np.sort(rel)[::-1][:10], (rel < 1e-2).mean())
     assert np.median(rel) < max_median, np.median(rel)
 
 
