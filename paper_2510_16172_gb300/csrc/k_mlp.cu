@@ -1196,41 +1196,34 @@ __global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const PathRec* l
 // with the accumulator in TMEM; each epilogue adds the bias, applies GELU and
 // writes the BF16 activations back into the same tile (K = 256) for the next
 // layer; the last one writes the starting parameters into T.  The weights are
-// pre-tiled in global memory as 13 chunks of 64 input columns (K-major core
-// matrices, row groups of 8 outputs contiguous), so the 128-output half of a
-// chunk is one contiguous 16 KB block: they stream through two 16 KB shared
-// buffers as 22 units per tile (a half chunk for layers 1-3, each MMA N = 128
-// into its half of the TMEM accumulator; whole 2 KB chunks for the output
-// layer), prefetched one unit ahead: lane 0 of warp 0 waits for the MMAs that
-// last read a buffer before refilling it.  A CTA's steps are serial -- features,
+// pre-tiled in global memory as 22 units, each K-major in core matrices: for
+// layers 1-3 all 256 outputs x 32 input columns (16 KB, two MMAs with N = 256
+// into the whole TMEM accumulator; an MMA costs about the same time whatever
+// its N, so the widest one wastes least), for the output layer 16 outputs x 64
+// columns (2 KB, four MMAs).  They stream through two 16 KB shared buffers,
+// prefetched one unit ahead: lane 0 of warp 0 waits for the MMAs that last read
+// a buffer before refilling it.  A CTA's steps are serial -- features,
 // MMAs, CUDA-core epilogue -- so the kernel is sized (103 KB of shared memory,
 // 256 TMEM columns, at most 117 registers) for two CTAs per SM, whose phases
 // interleave.  All waits are bounded.
 // ---------------------------------------------------------------------------
 constexpr int kInferThreads = 256;
 constexpr int kInferCtasPerSm = 2;
-constexpr int kUnitsPerTile = 22;  // streamed units: W1 2 halves, W2 and W3 8 halves each, W4 4 chunks
+constexpr int kUnitsPerTile = 22;  // streamed units: W1 2 K-halves, W2 and W3 8 each, W4 4 chunks
 
-// Chunk q of the tiled weights (W1: 0; W2: 1-4; W3: 5-8; W4: 9-12; 64 input columns each):
-// 32 KB for the 256-output layers, 2 KB for the output layer.
-__host__ __device__ constexpr uint32_t chunk_offset(int q) {
-  return q <= 8 ? (uint32_t)q * 32768u : 9u * 32768u + (uint32_t)(q - 9) * 2048u;
-}
-
-// Unit u of a tile: (layer, input-column chunk, output half).  Layers 1-3 go chunk by chunk, both halves
-// of a chunk in turn; the output layer (16 outputs) takes whole chunks.
+// One K = 16 MMA (M = 128) occupies an SM's tensor pipe for about the same time whatever N is (measured on
+// the GB300: ~131 cycles for N = 64, 128 and 256), so the hidden layers run with N = 256: a unit of W1-W3
+// is all 256 outputs x 32 input columns (16 KB, two MMAs); the output layer (16 outputs) takes whole
+// 64-column chunks (2 KB, four MMAs).
 __host__ __device__ constexpr int unit_layer(int u) { return u < 2 ? 0 : (u < 10 ? 1 : (u < 18 ? 2 : 3)); }
-__host__ __device__ constexpr int unit_col(int u) {
-  return u < 2 ? 0 : (u < 10 ? (u - 2) / 2 : (u < 18 ? (u - 10) / 2 : u - 18));
+// first input column of unit u within its layer
+__host__ __device__ constexpr int unit_k0(int u) {
+  return u < 2 ? 32 * u : (u < 10 ? 32 * (u - 2) : (u < 18 ? 32 * (u - 10) : 64 * (u - 18)));
 }
-__host__ __device__ constexpr int unit_half(int u) { return u < 18 ? u % 2 : 0; }
 __host__ __device__ constexpr bool unit_ends_layer(int u) { return u == 1 || u == 9 || u == 17 || u == 21; }
-__host__ __device__ constexpr int unit_chunk(int u) {
-  return unit_layer(u) == 0 ? 0 : 1 + (unit_layer(u) - 1) * 4 + unit_col(u);
-}
-__host__ __device__ constexpr uint32_t unit_bytes(int u) { return unit_layer(u) == 3 ? 16u * 64u * 2u : 128u * 64u * 2u; }
+__host__ __device__ constexpr uint32_t unit_bytes(int u) { return u < 18 ? 256u * 32u * 2u : 16u * 64u * 2u; }
 __host__ __device__ constexpr uint32_t unit_offset(int u) {
-  return chunk_offset(unit_chunk(u)) + (uint32_t)unit_half(u) * 16384u;
+  return u < 18 ? (uint32_t)u * 16384u : 18u * 16384u + (uint32_t)(u - 18) * 2048u;
 }
 // the units of a tile cover the tiled weights once, back to back
 __host__ __device__ constexpr bool units_tile_weights() {
@@ -1241,7 +1234,9 @@ __host__ __device__ constexpr bool units_tile_weights() {
 }
 static_assert(units_tile_weights(), "weight units");
 
-// bf16 parameter copy ([out][in] per layer) -> chunked K-major tiles
+// bf16 parameter copy ([out][in] per layer) -> the streamed units, each K-major in core matrices of 8 rows
+// x 8 columns: a W1-W3 unit (256 rows x 32 columns) has core matrix (row group, column group) at
+// (group * 4 + column group) * 128 bytes; a W4 chunk (16 x 64) at (group * 8 + column group) * 128.
 __global__ void mlp_tile_weights_kernel(const __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt) {
   const int n1 = 256 * 64, n2 = 256 * 256, n4 = 16 * 256;
   const int total = n1 + 2 * n2 + n4;
@@ -1256,9 +1251,13 @@ __global__ void mlp_tile_weights_kernel(const __nv_bfloat16* __restrict__ wb, __
     } else {
       layer = 3; K = 256; off = kOffW4; r = (idx - n1 - 2 * n2) / K; k = (idx - n1 - 2 * n2) % K;
     }
-    const int c = k / 64;
-    const int q = layer == 0 ? 0 : 1 + (layer - 1) * 4 + c;
-    const uint32_t byte = chunk_offset(q) + tc::kmajor_offset(r, k % 64, 64);
+    uint32_t byte;
+    if (layer < 3) {
+      const int u = (layer == 0 ? 0 : (layer == 1 ? 2 : 10)) + k / 32;
+      byte = unit_offset(u) + tc::kmajor_offset(r, k % 32, 32);
+    } else {
+      byte = unit_offset(18 + k / 64) + tc::kmajor_offset(r, k % 64, 64);
+    }
     wt[byte / 2] = wb[off + r * K + k];
   }
 }
@@ -1326,7 +1325,7 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
   tc::fence_after_sync();
   const uint32_t tmem = sm.tmem;
   const char* wsrc = reinterpret_cast<const char*>(wt);
-  uint32_t full_ph[2] = {0u, 0u}, done_ph[2] = {0u, 0u}, layer_ph = 0u;
+  uint32_t full_ph = 0u, done_ph = 0u, layer_ph = 0u;  // mbarrier phases, one bit per buffer
   if (tid == 0 && total_q > 0) {
     tc::mbar_expect_tx(&sm.full[0], unit_bytes(0));
     tc::bulk_g2s(sm.wbuf[0], wsrc + unit_offset(0), unit_bytes(0), &sm.full[0]);
@@ -1357,7 +1356,7 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
     __syncthreads();
     for (int lq = 0; lq < kUnitsPerTile; ++lq, ++q) {
       const int b = (int)(q & 1);
-      const int layer = unit_layer(lq), c = unit_col(lq), h = unit_half(lq);
+      const int layer = unit_layer(lq), k0 = unit_k0(lq);
       // warp 0 issues the copies and MMAs: lane 0 works while its warp-mates wait at the warp
       // barrier, so that their mbarrier polls below never hold up the issuing lane
       if (warp == 0) {
@@ -1366,28 +1365,34 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
           if (q + 1 < total_q) {
             const int nb = b ^ 1;
             if (q >= 1) {
-              if (!tc::mbar_wait(&sm.done[nb], done_ph[nb], kWaitTries)) sm.fail = 1;
-              done_ph[nb] ^= 1u;
+              if (!tc::mbar_wait(&sm.done[nb], (done_ph >> nb) & 1u, kWaitTries)) sm.fail = 1;
+              done_ph ^= 1u << nb;
             }
             const int nq = (lq + 1) % kUnitsPerTile;
             tc::mbar_expect_tx(&sm.full[nb], unit_bytes(nq));
             tc::bulk_g2s(sm.wbuf[nb], wsrc + unit_offset(nq), unit_bytes(nq), &sm.full[nb]);
           }
-          if (!tc::mbar_wait(&sm.full[b], full_ph[b], kWaitTries)) sm.fail = 1;
-          full_ph[b] ^= 1u;
+          if (!tc::mbar_wait(&sm.full[b], (full_ph >> b) & 1u, kWaitTries)) sm.fail = 1;
+          full_ph ^= 1u << b;
           tc::fence_after_sync();
           const uint32_t K_act = layer == 0 ? 64u : 256u;
           const uint32_t a0 = tc::smem_u32(sm.act), w0 = tc::smem_u32(sm.wbuf[b]);
           if (!sm.fail) {
             // the unit's first descriptors; each next K = 16 step starts 256 bytes further, i.e. 16 more
             // in the 14-bit start-address field (shared addresses stay below 2^18: the field never carries)
-            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(c * 8) * 128u, 128u, (K_act / 8u) * 128u);
-            const uint64_t bd = tc::smem_desc(w0, 128u, 8u * 128u);
-            const uint32_t idesc = layer == 3 ? tc::idesc_bf16(128, 16) : tc::idesc_bf16(128, 128);
-            const uint32_t d = tmem + (uint32_t)h * 128u;
-            tc::mma_bf16(d, ad, bd, idesc, c > 0 ? 1u : 0u);
+            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(k0 / 8) * 128u, 128u, (K_act / 8u) * 128u);
+            if (layer < 3) {  // 256 outputs x 32 columns: two MMAs with N = 256
+              const uint64_t bd = tc::smem_desc(w0, 128u, 4u * 128u);
+              const uint32_t idesc = tc::idesc_bf16(128, 256);
+              tc::mma_bf16(tmem, ad, bd, idesc, k0 > 0 ? 1u : 0u);
+              tc::mma_bf16(tmem, ad + 16u, bd + 16u, idesc, 1u);
+            } else {  // 16 outputs x 64 columns: four MMAs with N = 16
+              const uint64_t bd = tc::smem_desc(w0, 128u, 8u * 128u);
+              const uint32_t idesc = tc::idesc_bf16(128, 16);
+              tc::mma_bf16(tmem, ad, bd, idesc, k0 > 0 ? 1u : 0u);
 #pragma unroll
-            for (int kk = 1; kk < 4; ++kk) tc::mma_bf16(d, ad + 16u * kk, bd + 16u * kk, idesc, 1u);
+              for (int kk = 1; kk < 4; ++kk) tc::mma_bf16(tmem, ad + 16u * kk, bd + 16u * kk, idesc, 1u);
+            }
           }
           tc::mma_commit(&sm.done[b]);
           if (unit_ends_layer(lq)) tc::mma_commit(&sm.layer);
