@@ -1311,7 +1311,7 @@ static GemmArgs gemm_args(int M, int N, int K, const __nv_bfloat16* A, long long
   return g;
 }
 
-// forward pass of B rows of X; with `train`, keeps the pre-activations
+// forward pass of B rows of X; with `train`, keeps gelu' at each hidden layer's pre-activation (Z1..Z3)
 static fpt_status mlp_forward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16* X, uint64_t B, float* Y,
                                    bool train) {
   const int Bi = (int)B;

@@ -13,8 +13,8 @@
 // Other strides (and the atomic epilogue) take gemm_kernel, one tile per CTA with the operands gathered
 // element by element.  The training pass keeps every operand K-major: its epilogues also write the
 // transposes that the weight gradients read.  Epilogues: plain store, split-K partial store, atomic add,
-// bias + GELU with a BF16 activation (and its transpose), or the GELU derivative for the backward pass
-// (and its transpose).
+// bias + GELU with a BF16 activation (and its transpose) and, for training, the GELU derivative at the
+// pre-activation, or the backward's product with that derivative (and its transpose).
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -47,10 +47,15 @@ __device__ __forceinline__ float gelu(float z) {
   const float h = 0.5f * z;
   return fmaf(h, tanh_approx(z * fmaf(kGeluK01, z * z, kGeluK0)), h);
 }
-__device__ __forceinline__ float gelu_grad(float z) {
+// gelu(z) and, in d, its derivative gelu'(z) = (1 + th) / 2 + (z / 2) (1 - th^2) K0 (1 + 3 K1 z^2), from one
+// tanh.  The training forward keeps gelu'(Z) for the backward (dZ = dH gelu'(Z)), so the backward's
+// epilogue multiplies instead of evaluating the derivative again.
+__device__ __forceinline__ float gelu_with_grad(float z, float& d) {
   const float z2 = z * z;
   const float th = tanh_approx(z * fmaf(kGeluK01, z2, kGeluK0));
-  return 0.5f * (1.f + th) + 0.5f * z * (1.f - th * th) * kGeluK0 * fmaf(3.f * kGeluK1, z2, 1.f);
+  const float h = 0.5f * z;
+  d = 0.5f * (1.f + th) + 0.5f * z * (1.f - th * th) * kGeluK0 * fmaf(3.f * kGeluK1, z2, 1.f);
+  return fmaf(h, th, h);
 }
 
 // Gather rows [r0, r0 + 128) x k [k0, k0 + 64) of a strided bf16 matrix into a
@@ -166,13 +171,15 @@ __device__ __forceinline__ void gemm_epilogue_staged(const GemmArgs& g, uint32_t
           case EPI_SPLIT:
             g.C[((long long)split * g.M + m) * g.N + n] = x;
             break;
-          case EPI_BIAS_GELU:
-            if (g.C) g.C[(long long)m * g.scm + (long long)n * g.scn] = x;
-            y = __bfloat162float(__float2bfloat16(gelu(x)));
+          case EPI_BIAS_GELU: {
+            float d;
+            y = __bfloat162float(__float2bfloat16(gelu_with_grad(x, d)));
+            if (g.C) g.C[(long long)m * g.scm + (long long)n * g.scn] = d;
             g.H[(long long)m * g.shm + (long long)n * g.shn] = __float2bfloat16(y);
             break;
+          }
           case EPI_GELU_GRAD:
-            y = x * gelu_grad(g.Zin[(long long)m * g.szm + (long long)n * g.szn]);
+            y = x * g.Zin[(long long)m * g.szm + (long long)n * g.szn];
             if (g.C) g.C[(long long)m * g.scm + (long long)n * g.scn] = y;
             g.H[(long long)m * g.shm + (long long)n * g.shn] = __float2bfloat16(y);
             break;
@@ -517,7 +524,7 @@ __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev,
       for (int i = 0; i < 16; ++i) z[i] = zq[i];
       if (j + kWsGroupStride < n_groups) load_z16(g, ev, m, row, 16 * (j + kWsGroupStride), zq);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) x[i] = row ? x[i] * gelu_grad(z[i]) : 0.f;
+      for (int i = 0; i < 16; ++i) x[i] = row ? x[i] * z[i] : 0.f;
       if (s_col) {
         const float cs = warp_colsum16(x, lane);
         if ((lane & 1) == 0) {
@@ -528,8 +535,17 @@ __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev,
 #pragma unroll
       for (int i = 0; i < 16; ++i) h[i] = x[i];
     } else if (OP == EPI_BIAS_GELU) {
+      if (has_c) {  // training: the FP32 output is gelu'(Z) for the backward
 #pragma unroll
-      for (int i = 0; i < 16; ++i) h[i] = gelu(x[i]);
+        for (int i = 0; i < 16; ++i) {
+          float d;
+          h[i] = gelu_with_grad(x[i], d);
+          x[i] = d;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = gelu(x[i]);
+      }
     }
     // this lane's own stores for the outputs without a tensor map
     if (row) {

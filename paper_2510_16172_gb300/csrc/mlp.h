@@ -29,13 +29,13 @@ struct GemmArgs {
   long long sbn, sbk;
   int op;                 // EpilogueOp
   const float* bias;      // [N] (EPI_STORE, EPI_BIAS_GELU) or null
-  float* C;               // FP32 output D (+bias) / pre-activation / dZ, or null where optional
+  float* C;               // FP32 output: D (+bias) / gelu'(pre-activation) (EPI_BIAS_GELU) / dZ, or null where optional
   long long scm, scn;
   __nv_bfloat16* H;       // BF16 output: activation (EPI_BIAS_GELU) or dZ (EPI_GELU_GRAD)
   long long shm, shn;
   __nv_bfloat16* Ht;      // optional second copy of H with its own strides (the transpose, for the backward)
   long long shtm, shtn;
-  const float* Zin;       // pre-activation for EPI_GELU_GRAD
+  const float* Zin;       // EPI_GELU_GRAD: gelu' at the pre-activation, as the forward's EPI_BIAS_GELU wrote it
   long long szm, szn;
   float* colsum;          // EPI_GELU_GRAD: the column sums of the FP32 result are added here ([N]), or null
   int* err;               // device error word (MMA completion timeout)
