@@ -167,8 +167,6 @@ struct fpt_mlp {
   __nv_bfloat16* d_wt = nullptr;  // BF16 weights pre-tiled for the fused inference kernel
   bool wt_stale = true;
   __nv_bfloat16* d_wtT = nullptr;  // BF16 W^T of layers 2-4 (the backward's dH = dZ W), refreshed when stale
-  float* d_splitws = nullptr;      // split-K partial products of the weight gradients
-  size_t splitws_cap = 0;          // floats
   bool wtT_stale = true;
   float* d_loss = nullptr;
   // fpt_mlp_train: one shuffled mini-batch and the per-epoch mean losses
@@ -1353,13 +1351,12 @@ static fpt_status mlp_forward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat16
 // operands: the weight gradients dW = dZ^T act take the transposed copies written by the epilogues, the
 // back-propagation dH = dZ W the transposed BF16 weights.
 static int split_k(const fpt_ctx* ctx, int B, int m_tiles) {
-  // one (row tile, K split) item per SM (the persistent GEMM then keeps one partial product per CTA), at
-  // least four 64-wide K chunks per split
+  // one (row tile, K split) item per SM (each CTA adds one partial product into the gradient), at least
+  // four 64-wide K chunks per split
   int ks = ctx->n_sm / m_tiles;
   const int max_ks = B / 256 > 1 ? B / 256 : 1;
   ks = ks < 1 ? 1 : (ks > max_ks ? max_ks : ks);
-  // the GEMM gives each split ceil(B / (ks 64)) chunks of 64: count only the splits that get some,
-  // so that every split the reduction sums has written its partial product
+  // the GEMM gives each split ceil(B / (ks 64)) chunks of 64: count only the splits that get some
   const int per = (B + ks * 64 - 1) / (ks * 64) * 64;
   return (B + per - 1) / per;
 }
@@ -1376,22 +1373,16 @@ static fpt_status mlp_backward_impl(fpt_ctx* ctx, fpt_mlp* m, const __nv_bfloat1
   const __nv_bfloat16* Wt2 = m->d_wtT;
   const __nv_bfloat16* Wt3 = m->d_wtT + 256 * 256;
   const __nv_bfloat16* Wt4 = m->d_wtT + 2 * 256 * 256;
-  // weight gradients: split-K partial products in a workspace, then one reduction into m->d_g
+  // weight gradients: K (the batch) split into one slice per SM's item; each slice's partial product is
+  // added into m->d_g (zeroed above) by the GEMM's epilogue (TMA reduce-add, else atomics)
   const int ks = split_k(ctx, Bi, 2);
-  const size_t ws_need = (size_t)ks * kMlpHidden * kMlpHidden;
-  if (ws_need > m->splitws_cap) {
-    cudaFree(m->d_splitws);
-    m->d_splitws = nullptr;
-    m->splitws_cap = 0;
-    CUDA_OR_FAIL(ctx, cudaMalloc(&m->d_splitws, ws_need * sizeof(float)));
-    m->splitws_cap = ws_need;
-  }
   auto weight_grad = [&](int M, int N, const __nv_bfloat16* At, const __nv_bfloat16* Bt, float* dst, long long scm,
                          long long scn) -> fpt_status {
-    GemmArgs g = gemm_args(M, N, Bi, At, Bi, 1, Bt, Bi, 1, EPI_SPLIT, ctx->d_err);
-    g.C = m->d_splitws;
+    GemmArgs g = gemm_args(M, N, Bi, At, Bi, 1, Bt, Bi, 1, EPI_ATOMIC, ctx->d_err);
+    g.C = dst;
+    g.scm = scm;
+    g.scn = scn;
     CUDA_OR_FAIL(ctx, launch_gemm(g, ks, ctx->stream));
-    CUDA_OR_FAIL(ctx, launch_splitk_reduce(m->d_splitws, ks, M, N, dst, scm, scn, ctx->stream));
     return FPT_OK;
   };
   fpt_status st = mlp_forward_impl(ctx, m, X, B, m->d_Y, true);
@@ -1506,8 +1497,7 @@ void fpt_mlp_free(fpt_mlp* m) {
   if (m->ctx && m->ctx->init_mlp == m) m->ctx->init_mlp = nullptr;
   mlp_free_ws(m);
   for (void* p : {(void*)m->d_w, (void*)m->d_m, (void*)m->d_v, (void*)m->d_g, (void*)m->d_wb, (void*)m->d_wt,
-                  (void*)m->d_loss, (void*)m->d_Xb, (void*)m->d_Tb, (void*)m->d_Gb, (void*)m->d_hist, (void*)m->d_wtT,
-                  (void*)m->d_splitws})
+                  (void*)m->d_loss, (void*)m->d_Xb, (void*)m->d_Tb, (void*)m->d_Gb, (void*)m->d_hist, (void*)m->d_wtT})
     cudaFree(p);
   delete m;
 }

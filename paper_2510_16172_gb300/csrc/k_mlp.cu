@@ -10,11 +10,12 @@
 // K split) items, the chunks loaded by TMA into a two-stage ring (128-byte swizzled K-major tiles), one
 // thread issuing the MMAs into two TMEM accumulators, twelve epilogue warps staging the outputs in shared
 // memory for TMA tensor stores.
-// Other strides (and the atomic epilogue) take gemm_kernel, one tile per CTA with the operands gathered
-// element by element.  The training pass keeps every operand K-major: its epilogues also write the
-// transposes that the weight gradients read.  Epilogues: plain store, split-K partial store, atomic add,
-// bias + GELU with a BF16 activation (and its transpose) and, for training, the GELU derivative at the
-// pre-activation, or the backward's product with that derivative (and its transpose).
+// Other strides take gemm_kernel, one tile per CTA with the operands gathered element by element.  The
+// training pass keeps every operand K-major: its epilogues also write the transposes that the weight
+// gradients read.  Epilogues: plain store; addition into the output (the weight gradients' split-K
+// partial products, by TMA reduce-adds); bias + GELU with a BF16 activation (and its transpose) and, for
+// training, the GELU derivative at the pre-activation; or the backward's product with that derivative
+// (and its transpose).
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -138,7 +139,7 @@ static_assert(4 * 32 * kEpiStride * 4 <= kGemmSmem, "epilogue slabs");
 // (coalesced; Zin read the same way), and the final value is kept in the slab; (c) column by column,
 // consecutive lanes on consecutive rows, the transposed copy Ht is stored (coalesced too).
 __device__ __forceinline__ void gemm_epilogue_staged(const GemmArgs& g, uint32_t tmem_warp, int mrow0, int lane,
-                                                     int n_pad, float* slab, int split) {
+                                                     int n_pad, float* slab) {
   for (int c0 = 0; c0 < n_pad; c0 += kEpiCols) {
     const int cols = min(kEpiCols, n_pad - c0);
     for (int cc = 0; cc < cols; cc += 16) {
@@ -167,9 +168,6 @@ __device__ __forceinline__ void gemm_epilogue_staged(const GemmArgs& g, uint32_t
             break;
           case EPI_ATOMIC:
             atomicAdd(g.C + (long long)m * g.scm + (long long)n * g.scn, x);
-            break;
-          case EPI_SPLIT:
-            g.C[((long long)split * g.M + m) * g.N + n] = x;
             break;
           case EPI_BIAS_GELU: {
             float d;
@@ -320,7 +318,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
   } else if (n_chunks > 0) {
     // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31; the pipeline buffers are idle now
     float* slab = reinterpret_cast<float*>(gemm_smem) + warp * 32 * kEpiStride;
-    gemm_epilogue_staged(g, tmem + ((uint32_t)(warp * 32) << 16), m0 + warp * 32, lane, n_pad, slab, (int)blockIdx.y);
+    gemm_epilogue_staged(g, tmem + ((uint32_t)(warp * 32) << 16), m0 + warp * 32, lane, n_pad, slab);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -374,7 +372,7 @@ struct EpiVec {
 __device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 __device__ __forceinline__ EpiVec epi_vec(const GemmArgs& g) {
   EpiVec v;
-  v.c = g.op == EPI_SPLIT ? (g.N % 4 == 0 && aligned16(g.C)) : (g.scn == 1 && g.scm % 4 == 0 && aligned16(g.C));
+  v.c = g.scn == 1 && g.scm % 4 == 0 && aligned16(g.C);
   v.h = g.shn == 1 && g.shm % 8 == 0 && aligned16(g.H);
   v.z = g.szn == 1 && g.szm % 4 == 0 && aligned16(g.Zin);
   v.bias = aligned16(g.bias);
@@ -467,6 +465,7 @@ __device__ __forceinline__ void load_z16(const GemmArgs& g, const EpiVec& ev, in
 // in all three.
 constexpr int kStgC = 0, kStgH = 2048, kStgHt = 3072, kStgBytes = 4096;
 constexpr int kOutC = 1, kOutH = 2, kOutHt = 4;  // outputs that go through TMA stores
+constexpr int kOutCt = 8;  // EPI_ATOMIC into a column-major destination: the FP32 box staged transposed
 
 struct OutMaps {
   const CUtensorMap* c;
@@ -482,14 +481,14 @@ struct OutMaps {
 // loaded while the current one is worked on, and the column sums of dZ are added to s_col.
 template <int OP>
 __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev, uint32_t tacc, int m, int mrow0,
-                                            int j0, int n_groups, int split, float* s_col, const OutMaps& om,
+                                            int j0, int n_groups, float* s_col, const OutMaps& om,
                                             unsigned char* stg, int& gi) {
   const int lane = lane_id();
   const bool row = m < g.M;
-  const bool has_c = OP == EPI_STORE || OP == EPI_SPLIT || g.C != nullptr;
+  const bool has_c = OP == EPI_STORE || OP == EPI_ATOMIC || g.C != nullptr;
   const bool has_h = OP == EPI_BIAS_GELU || OP == EPI_GELU_GRAD;
   const bool has_ht = has_h && g.Ht != nullptr;
-  const bool tma_c = has_c && (om.flags & kOutC), tma_h = has_h && (om.flags & kOutH),
+  const bool tma_c = has_c && (om.flags & (kOutC | kOutCt)), tma_h = has_h && (om.flags & kOutH),
              tma_ht = has_ht && (om.flags & kOutHt);
   const bool any_tma = tma_c || tma_h || tma_ht;
   float zq[16];  // the pre-activations of the next column group (EPI_GELU_GRAD)
@@ -550,10 +549,13 @@ __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev,
     // this lane's own stores for the outputs without a tensor map
     if (row) {
       if (has_c && !tma_c) {
-        if (OP == EPI_SPLIT)
-          store16_f32(g.C + ((long long)split * g.M + m) * g.N + n0, x, full && ev.c, nv, 1);
-        else
+        if (OP == EPI_ATOMIC) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (i < nv) atomicAdd(g.C + (long long)m * g.scm + (long long)(n0 + i) * g.scn, x[i]);
+        } else {
           store16_f32(g.C + (long long)m * g.scm + (long long)n0 * g.scn, x, full && ev.c, nv, g.scn);
+        }
       }
       if (has_h && !tma_h) store16_bf16(g.H + (long long)m * g.shm + (long long)n0 * g.shn, h, full && ev.h, nv, g.shn);
       if (has_ht && !tma_ht) {
@@ -569,7 +571,11 @@ __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev,
     ++gi;
     if (lane == 0) tc::bulk_wait_read<1>();
     __syncwarp();
-    if (tma_c) {
+    if (tma_c && (om.flags & kOutCt)) {  // column n of the group at n 128 bytes, row r at 4 r
+      float* tb = reinterpret_cast<float*>(buf + kStgC) + lane;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) tb[32 * i] = x[i];
+    } else if (tma_c) {
       unsigned char* cb = buf + kStgC + lane * 64;
       const int sw = (lane >> 1) & 3;
 #pragma unroll
@@ -599,10 +605,14 @@ __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev,
     __syncwarp();
     if (lane == 0 && mrow0 < g.M) {
       if (tma_c) {
-        if (OP == EPI_SPLIT)
-          tc::tma_store_3d(om.c, buf + kStgC, n0, mrow0, split);
-        else
+        if (OP == EPI_ATOMIC) {
+          if (om.flags & kOutCt)
+            tc::tma_reduce_add_2d(om.c, buf + kStgC, mrow0, n0);
+          else
+            tc::tma_reduce_add_2d(om.c, buf + kStgC, n0, mrow0);
+        } else {
           tc::tma_store_2d(om.c, buf + kStgC, n0, mrow0);
+        }
       }
       if (tma_h) tc::tma_store_2d(om.h, buf + kStgH, n0, mrow0);
       if (tma_ht) tc::tma_store_2d(om.ht, buf + kStgHt, mrow0, n0);
@@ -735,16 +745,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       const int m = mrow0 + lane;
       switch (g.op) {
         case EPI_STORE:
-          ws_epilogue<EPI_STORE>(g, ev, tacc, m, mrow0, j0, n_groups, w.split, nullptr, om, stg, gi);
+          ws_epilogue<EPI_STORE>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, gi);
           break;
-        case EPI_SPLIT:
-          ws_epilogue<EPI_SPLIT>(g, ev, tacc, m, mrow0, j0, n_groups, w.split, nullptr, om, stg, gi);
+        case EPI_ATOMIC:
+          ws_epilogue<EPI_ATOMIC>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, gi);
           break;
         case EPI_BIAS_GELU:
-          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, mrow0, j0, n_groups, w.split, nullptr, om, stg, gi);
+          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, gi);
           break;
         default:
-          ws_epilogue<EPI_GELU_GRAD>(g, ev, tacc, m, mrow0, j0, n_groups, w.split, want_col ? s_col : nullptr, om,
+          ws_epilogue<EPI_GELU_GRAD>(g, ev, tacc, m, mrow0, j0, n_groups, want_col ? s_col : nullptr, om,
                                      stg, gi);
           break;
       }
@@ -810,14 +820,22 @@ static bool encode_operand(CUtensorMap* map, const __nv_bfloat16* base, int rows
 
 // Tensor maps of the epilogue's outputs (32-row x 16-column boxes, laid out as the staging buffers are);
 // returns the kOut* flags of the outputs that have one.
-static int encode_outputs(const GemmArgs& g, int splits, CUtensorMap* tmC, CUtensorMap* tmH, CUtensorMap* tmHt) {
+static int encode_outputs(const GemmArgs& g, CUtensorMap* tmC, CUtensorMap* tmH, CUtensorMap* tmHt) {
   int flags = 0;
-  if (g.op == EPI_SPLIT) {
-    const cuuint64_t dims[3] = {(cuuint64_t)g.N, (cuuint64_t)g.M, (cuuint64_t)splits};
-    const cuuint64_t strides[2] = {(cuuint64_t)g.N * 4u, (cuuint64_t)g.M * g.N * 4u};
-    const cuuint32_t box[3] = {16, 32, 1};
-    if (encode_map(tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g.C, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B))
-      flags |= kOutC;
+  if (g.op == EPI_ATOMIC) {
+    if (g.scn == 1) {  // row-major destination: boxes as the FP32 stores
+      const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
+      const cuuint64_t strides[1] = {(cuuint64_t)g.scm * 4u};
+      const cuuint32_t box[2] = {16, 32};
+      if (encode_map(tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g.C, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B))
+        flags |= kOutC;
+    } else if (g.scm == 1) {  // column-major destination: the transposed box
+      const cuuint64_t dims[2] = {(cuuint64_t)g.M, (cuuint64_t)g.N};
+      const cuuint64_t strides[1] = {(cuuint64_t)g.scn * 4u};
+      const cuuint32_t box[2] = {32, 16};
+      if (encode_map(tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g.C, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE))
+        flags |= kOutCt;
+    }
   } else if (g.C && g.scn == 1) {
     const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
     const cuuint64_t strides[1] = {(cuuint64_t)g.scm * 4u};
@@ -851,7 +869,7 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (gemm_vectorised(g) && g.op != EPI_ATOMIC) {
+  if (gemm_vectorised(g)) {
     const int n_pad = (g.N + 15) & ~15;
     CUtensorMap tmA, tmB;
     if (encode_operand(&tmA, g.A, g.M, g.K, g.sam, 128) && encode_operand(&tmB, g.B, g.N, g.K, g.sbn, n_pad)) {
@@ -866,7 +884,7 @@ cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream) {
       if (e != cudaSuccess) return e;
       const int grid = n_items < n_sm ? n_items : n_sm;
       CUtensorMap tmC{}, tmH{}, tmHt{};
-      const int out_flags = encode_outputs(g, splits, &tmC, &tmH, &tmHt);
+      const int out_flags = encode_outputs(g, &tmC, &tmH, &tmHt);
       gemm_ws_kernel<<<grid, kWsThreads, kWsSmem, stream>>>(tmA, tmB, tmC, tmH, tmHt, out_flags, g, m_tiles, n_items,
                                                             k_per);
       count_launch();
@@ -1639,62 +1657,6 @@ cudaError_t launch_colsum(const float* A, uint64_t B, int N, float* out, cudaStr
 cudaError_t launch_adam(float* w, float* m, float* v, const float* g, int n, float lr, float c1, float c2,
                         __nv_bfloat16* wb, cudaStream_t stream) {
   adam_kernel<<<grid_1d(n, 256, 1024), 256, 0, stream>>>(w, m, v, g, n, lr, c1, c2, wb);
-  count_launch();
-  return cudaGetLastError();
-}
-
-// dst[m][n] += sum over s of ws[s][m][n].  Each thread takes four consecutive entries (one 16-byte load per
-// split) over one of gridDim.y groups of splits, with two sums in flight, and adds its partial sums to dst.
-__global__ void splitk_reduce_kernel(const float* __restrict__ ws, int splits, int M, int N, float* dst, long long scm,
-                                     long long scn) {
-  const long long MN = (long long)M * N, n4 = MN / 4;
-  const int groups = gridDim.y;
-  const int s_lo = (int)((long long)blockIdx.y * splits / groups), s_hi = (int)((long long)(blockIdx.y + 1) * splits / groups);
-  const float4* w4 = reinterpret_cast<const float4*>(ws);
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-    int s = s_lo;
-    for (; s + 1 < s_hi; s += 2) {
-      const float4 u = w4[s * n4 + q], v = w4[(s + 1) * n4 + q];
-      a.x += u.x; a.y += u.y; a.z += u.z; a.w += u.w;
-      b.x += v.x; b.y += v.y; b.z += v.z; b.w += v.w;
-    }
-    if (s < s_hi) {
-      const float4 u = w4[s * n4 + q];
-      a.x += u.x; a.y += u.y; a.z += u.z; a.w += u.w;
-    }
-    const float r[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const long long e = 4 * q + i;
-      atomicAdd(dst + (e / N) * scm + (e % N) * scn, r[i]);
-    }
-  }
-}
-
-// The same for any M x N (one entry per thread, every split).
-__global__ void splitk_reduce1_kernel(const float* __restrict__ ws, int splits, int M, int N, float* dst, long long scm,
-                                      long long scn) {
-  const long long MN = (long long)M * N;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (long long)gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    for (int s = 0; s < splits; ++s) acc += ws[s * MN + e];
-    dst[(e / N) * scm + (e % N) * scn] += acc;
-  }
-}
-
-cudaError_t launch_splitk_reduce(const float* ws, int splits, int M, int N, float* dst, long long scm, long long scn,
-                                 cudaStream_t stream) {
-  const long long MN = (long long)M * N;
-  if (MN % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0) {
-    const long long n4 = MN / 4;
-    const unsigned gx = (unsigned)((n4 + 255) / 256 < 1024 ? (n4 + 255) / 256 : 1024);
-    const unsigned gy = splits < 8 ? (unsigned)splits : 8u;
-    splitk_reduce_kernel<<<dim3(gx, gy), 256, 0, stream>>>(ws, splits, M, N, dst, scm, scn);
-  } else {
-    const unsigned grid = (unsigned)((MN + 255) / 256 < 1024 ? (MN + 255) / 256 : 1024);
-    splitk_reduce1_kernel<<<grid, 256, 0, stream>>>(ws, splits, M, N, dst, scm, scn);
-  }
   count_launch();
   return cudaGetLastError();
 }

@@ -15,10 +15,9 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 256 * 64, kOffW2 = kOffB1 + 256, kOf
               kOffW3 = kOffB2 + 256, kOffB3 = kOffW3 + 256 * 256, kOffW4 = kOffB3 + 256, kOffB4 = kOffW4 + 16 * 256,
               kMlpParams = kOffB4 + 16;
 
-// EPI_SPLIT: split-K partial product, split s stored plainly at C + s M N ([M][N] row-major), summed by
-// launch_splitk_reduce (contended atomics on the same few outputs were the slowest part of the weight
-// gradients)
-enum EpilogueOp { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_GELU = 2, EPI_GELU_GRAD = 3, EPI_SPLIT = 4 };
+// EPI_ATOMIC adds the product into C: the split-K partial products of the weight gradients, one per
+// CTA, go in by TMA tensor reduce-adds (row- or column-major C), else by atomics.
+enum EpilogueOp { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_GELU = 2, EPI_GELU_GRAD = 3 };
 
 // D[M x N] = sum_k A(m, k) B(n, k); A(m, k) = A[m * sam + k * sak], B(n, k) = B[n * sbn + k * sbk].
 struct GemmArgs {
@@ -42,9 +41,6 @@ struct GemmArgs {
 };
 
 cudaError_t launch_gemm(const GemmArgs& g, int k_split, cudaStream_t stream);
-// dst[m * scm + n * scn] += sum over s < splits of ws[s][m][n]  (ws: splits x M x N floats)
-cudaError_t launch_splitk_reduce(const float* ws, int splits, int M, int N, float* dst, long long scm, long long scn,
-                                 cudaStream_t stream);
 // dst [C][R] = src [R][C]^T (bf16)
 cudaError_t launch_bf16_transpose(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t stream);
 // The transposed BF16 weights of layers 2-4 (W^T [in][out]) from the BF16 parameter copy.

@@ -109,9 +109,11 @@ __device__ __forceinline__ void tma_store_2d(const void* tmap, const void* src_s
                "r"(y), "r"(smem_u32(src_smem))
                : "memory");
 }
-__device__ __forceinline__ void tma_store_3d(const void* tmap, const void* src_smem, int x, int y, int z) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tmap), "r"(x),
-               "r"(y), "r"(z), "r"(smem_u32(src_smem))
+// The same box added element by element to global memory (the tensor map's element type; FP32 here) by the
+// TMA engine: a reduction in L2, with the store's completion and coordinate rules.
+__device__ __forceinline__ void tma_reduce_add_2d(const void* tmap, const void* src_smem, int x, int y) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group [%0, {%1, %2}], [%3];" ::"l"(tmap),
+               "r"(x), "r"(y), "r"(smem_u32(src_smem))
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
