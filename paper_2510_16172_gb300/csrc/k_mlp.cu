@@ -338,7 +338,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
 // The warps hand the accumulator back through `acc_empty`, so the MMAs of the tile after next may start
 // while this tile's epilogue runs.  Every wait is bounded; a timeout sets the CTA's fail flag, which every
 // role polls and leaves on.
-constexpr int kWsStages = 2;
+constexpr int kWsStages = 2;     // operand ring stages when the epilogue stages BF16 outputs
+constexpr int kWsStagesMax = 3;  // ... and when it stages only the FP32 box (plain stores, reduce-adds)
 constexpr int kWsEpiWarps = 12;
 constexpr int kWsGroupStride = kWsEpiWarps / 4;  // epilogue warps per 32-lane quarter of TMEM
 constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
@@ -346,6 +347,7 @@ constexpr int kWsTileA = 128 * 128;                       // 128 rows x 128 byte
 constexpr int kWsStageBytes = kWsTileA + 256 * 128;       // + B, up to 256 rows: 48 KB
 // the ring, two 4 KB output staging buffers per epilogue warp, slack to align the ring to 1024 bytes
 constexpr int kWsSmem = kWsStages * kWsStageBytes + kWsEpiWarps * 2 * 4096 + 1024;
+static_assert(kWsStagesMax * kWsStageBytes + kWsEpiWarps * 2 * 2048 + 1024 <= kWsSmem, "ring and staging");
 
 struct WsItem {
   int m0, kb, ke, split;
@@ -482,7 +484,7 @@ struct OutMaps {
 template <int OP>
 __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev, uint32_t tacc, int m, int mrow0,
                                             int j0, int n_groups, float* s_col, const OutMaps& om,
-                                            unsigned char* stg, int& gi) {
+                                            unsigned char* stg, int stg_bytes, int& gi) {
   const int lane = lane_id();
   const bool row = m < g.M;
   const bool has_c = OP == EPI_STORE || OP == EPI_ATOMIC || g.C != nullptr;
@@ -567,7 +569,7 @@ __device__ __forceinline__ void ws_epilogue(const GemmArgs& g, const EpiVec& ev,
     }
     if (!any_tma) continue;
     // the staged group: wait until the engine has read this buffer's previous group, fill it, store it
-    unsigned char* buf = stg + (gi & 1) * kStgBytes;
+    unsigned char* buf = stg + (gi & 1) * stg_bytes;
     ++gi;
     if (lane == 0) tc::bulk_wait_read<1>();
     __syncwarp();
@@ -627,18 +629,23 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                    const __grid_constant__ CUtensorMap tmHt, int out_flags, GemmArgs g, int m_tiles, int n_items,
                    int k_per) {
   extern __shared__ unsigned char ws_raw[];
-  __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t full[kWsStagesMax], empty[kWsStagesMax], acc_full[2], acc_empty[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   __shared__ int s_last_q;             // the MMA thread's last committed chunk (-1: none)
-  __shared__ int s_armed[kWsStages];   // each stage's last phase handed to the TMA engine (-1: none)
+  __shared__ int s_armed[kWsStagesMax];  // each stage's last phase handed to the TMA engine (-1: none)
   __shared__ float s_col[256];         // this CTA's column sums (EPI_GELU_GRAD with colsum)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned all = 0xffffffffu;
   const int n_pad = (g.N + 15) & ~15;
+  // outputs staged only in the FP32 slot leave room for a deeper operand ring (long K of the weight
+  // gradients); the BF16 outputs need the whole 4 KB staging buffers
+  const bool fp32_only = g.op == EPI_STORE || g.op == EPI_ATOMIC;
+  const int stages = fp32_only ? kWsStagesMax : kWsStages;
+  const int stg_bytes = fp32_only ? 2048 : kStgBytes;
   unsigned char* ring = ws_raw + ((1024u - (tc::smem_u32(ws_raw) & 1023u)) & 1023u);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWsStages; ++s) {
+    for (int s = 0; s < kWsStagesMax; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
       s_armed[s] = -1;
@@ -675,7 +682,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
         const WsItem w = ws_item(g, item, m_tiles, k_per);
         for (int k0 = w.kb; k0 < w.ke; k0 += kGemmKC, ++q) {
-          const int s = q % kWsStages, u = q / kWsStages;
+          const int s = q % stages, u = q / stages;
           if (u > 0) {  // the stage's previous chunk has been read by its MMAs
             ok = !failed() && tc::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), kWaitTries);
             if (!ok) break;
@@ -703,7 +710,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         tc::fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(b * 256);
         for (int k0 = w.kb, c = 0; k0 < w.ke; k0 += kGemmKC, ++q, ++c) {
-          const int s = q % kWsStages, u = q / kWsStages;
+          const int s = q % stages, u = q / stages;
           ok = !failed() && tc::mbar_wait(&full[s], (uint32_t)(u & 1), kWaitTries);
           if (!ok) break;
           tc::fence_after_sync();
@@ -728,7 +735,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     const int n_groups = n_pad / 16;
     const EpiVec ev = epi_vec(g);
     const OutMaps om{&tmC, &tmH, &tmHt, out_flags};
-    unsigned char* stg = ring + kWsStages * kWsStageBytes + (warp - 2) * 2 * kStgBytes;
+    unsigned char* stg = ring + stages * kWsStageBytes + (warp - 2) * 2 * stg_bytes;
     int gi = 0;
     int i = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++i) {
@@ -745,17 +752,17 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       const int m = mrow0 + lane;
       switch (g.op) {
         case EPI_STORE:
-          ws_epilogue<EPI_STORE>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, gi);
+          ws_epilogue<EPI_STORE>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, stg_bytes, gi);
           break;
         case EPI_ATOMIC:
-          ws_epilogue<EPI_ATOMIC>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, gi);
+          ws_epilogue<EPI_ATOMIC>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, stg_bytes, gi);
           break;
         case EPI_BIAS_GELU:
-          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, gi);
+          ws_epilogue<EPI_BIAS_GELU>(g, ev, tacc, m, mrow0, j0, n_groups, nullptr, om, stg, stg_bytes, gi);
           break;
         default:
           ws_epilogue<EPI_GELU_GRAD>(g, ev, tacc, m, mrow0, j0, n_groups, want_col ? s_col : nullptr, om,
-                                     stg, gi);
+                                     stg, stg_bytes, gi);
           break;
       }
       tc::fence_before_sync();
@@ -771,10 +778,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   if (s_fail && threadIdx.x == 0) {
     if (g.err) atomicCAS(g.err, 0, ERR_MMA_TIMEOUT);
     // let the copies and MMAs already issued finish (bounded) before shared and tensor memory go away
-    for (int s = 0; s < kWsStages; ++s)
+    for (int s = 0; s < stages; ++s)
       if (s_armed[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)(s_armed[s] & 1), kWaitTries);
     const int q = s_last_q;
-    if (q >= 0) tc::mbar_wait(&empty[q % kWsStages], (uint32_t)((q / kWsStages) & 1), kWaitTries);
+    if (q >= 0) tc::mbar_wait(&empty[q % stages], (uint32_t)((q / stages) & 1), kWaitTries);
   }
   __syncthreads();
   if (want_col && !s_fail)
