@@ -507,13 +507,15 @@ __global__ void __launch_bounds__(kThreads) bfgs_kernel(SceneDev S, BatchDev B, 
 
 // CTAs per SM that the register allocation of the refill kernels targets: four up to
 // order 3, whose kernels all fit 128 registers without spilling (left to itself, ptxas
-// gives some order-3 pattern kernels 137 and so only three CTAs per SM); no constraint
-// beyond kThreads for the longer orders, which need 168-255.
-template <int N>
-constexpr int kBfgsMinCtas = N <= 3 ? 4 : 1;
+// gives some order-3 pattern kernels 137 and so only three CTAs per SM); three for the
+// order-5 patterns with three or four reflectors (185-206 registers left alone, 165-168
+// and at most 8 bytes of spills bounded; the other order-5 patterns fit three CTAs or,
+// with five reflectors at 231 registers, would spill far more); no other constraint.
+template <int N, unsigned Q>
+constexpr int kBfgsMinCtas = N <= 3 ? 4 : (N == 5 && __builtin_popcount(Q) >= 3 && __builtin_popcount(Q) <= 4 ? 3 : 1);
 
 template <int N, unsigned Q, int kSrc>
-__global__ void __launch_bounds__(kThreads, kBfgsMinCtas<N>) bfgs_refill_kernel(SceneDev S, BatchDev B, SolveCfg cfg, uint64_t n_local,
+__global__ void __launch_bounds__(kThreads, kBfgsMinCtas<N, Q>) bfgs_refill_kernel(SceneDev S, BatchDev B, SolveCfg cfg, uint64_t n_local,
                                                                const PathRec* __restrict__ list,
                                                                float* __restrict__ T_out,
                                                                uint8_t* __restrict__ status_out,
