@@ -637,6 +637,14 @@ static void set_reciprocals(BatchDev& d) {
   d.fd_quad = make_fastdiv((uint64_t)d.n_alpha_quad);
   d.fd_edge = make_fastdiv((uint64_t)(d.n_alpha - d.n_alpha_quad));
   for (int n = 0; n <= kMaxOrder; ++n) d.fd_kpow[n] = make_fastdiv(d.kpow[n]);
+  const uint64_t range = d.hi >= d.lo ? (uint64_t)(d.hi - d.lo + 1) : 1u;
+  d.fd_alpha1 = make_fastdiv(d.n_alpha > 1 ? (uint64_t)(d.n_alpha - 1) : 1u);
+  d.fd_range = make_fastdiv(range);
+  d.fd_pp = make_fastdiv(d.per_pair);
+  auto t32 = [](uint64_t m) { return m >= 1 && m <= 65535 ? (uint32_t)((1ull << 32) % m) : 0u; };
+  d.t32_alpha = t32((uint64_t)d.n_alpha);
+  d.t32_alpha1 = t32(d.n_alpha > 1 ? (uint64_t)(d.n_alpha - 1) : 1u);
+  d.t32_range = t32(range);
 }
 
 static fpt_status check_orders(fpt_ctx* ctx, int lo, int hi) {

@@ -62,6 +62,14 @@ __host__ __device__ inline FastDiv make_fastdiv(uint64_t d) {
 __device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
   return f.d <= 1 ? x : (uint32_t)__umul64hi((unsigned long long)x, (unsigned long long)f.m);
 }
+// r mod d for a 64-bit r and 1 <= d <= 65535, with t32 = 2^32 mod d: r = 2^32 hi + lo, so
+// r mod d = ((hi mod d) t32 + lo mod d) mod d, every term below 2^32 (d^2 + d < 2^32).
+__device__ __forceinline__ uint32_t fmod64(uint64_t r, const FastDiv& f, uint32_t t32) {
+  const uint32_t hi = (uint32_t)(r >> 32), lo = (uint32_t)r;
+  const uint32_t a = hi - fdiv(hi, f) * f.d, b = lo - fdiv(lo, f) * f.d;
+  const uint32_t c = a * t32 + b;
+  return c - fdiv(c, f) * f.d;
+}
 
 struct BatchDev {
   int mode;
@@ -84,6 +92,10 @@ struct BatchDev {
   FastDiv fd_rx, fd_alpha, fd_quad, fd_edge;
   FastDiv fd_kpow[kMaxOrder + 1];
   FastDiv fd_pat;  // set per pattern launch: sequences of the launch's pattern per (tx, rx) pair
+  // seeded batches: K - 1, the number of orders and the sequences per pair (divisors of 2^16 or more, or 0,
+  // take the 64-bit operators), with 2^32 mod each of the first two
+  FastDiv fd_alpha1, fd_range, fd_pp;
+  uint32_t t32_alpha, t32_alpha1, t32_range;
 };
 
 // Interaction-type pattern of a sequence of order n: bit i set = slot i is a
@@ -131,14 +143,21 @@ __device__ __forceinline__ void load_rec(const PathRec* list, uint64_t j, PathDe
   d.flags = (uint8_t)(b.z >> 24);
 }
 
-__device__ __forceinline__ void store_rec(PathRec* list, uint64_t slot, const PathDesc& d) {
+// The record of a decoded path as two 16-byte words.
+__device__ __forceinline__ void pack_rec(const PathDesc& d, uint4& a, uint4& b) {
   uint32_t id[kMaxBfgsOrder];
 #pragma unroll
   for (int i = 0; i < kMaxBfgsOrder; ++i) id[i] = i < d.n && d.n <= kMaxBfgsOrder ? (uint32_t)d.ids[i] & 0xFFFFu : 0u;
+  a = make_uint4((uint32_t)d.g, (uint32_t)(d.g >> 32), (uint32_t)d.tx, (uint32_t)d.rx);
+  b = make_uint4(id[0] | (id[1] << 16), id[2] | (id[3] << 16), id[4] | ((uint32_t)d.n << 16) | ((uint32_t)d.flags << 24),
+                 0u);
+}
+__device__ __forceinline__ void store_rec(PathRec* list, uint64_t slot, const PathDesc& d) {
+  uint4 a, b;
+  pack_rec(d, a, b);
   uint4* p = reinterpret_cast<uint4*>(list + slot);
-  p[0] = make_uint4((uint32_t)d.g, (uint32_t)(d.g >> 32), (uint32_t)d.tx, (uint32_t)d.rx);
-  p[1] = make_uint4(id[0] | (id[1] << 16), id[2] | (id[3] << 16),
-                    id[4] | ((uint32_t)d.n << 16) | ((uint32_t)d.flags << 24), 0u);
+  p[0] = a;
+  p[1] = b;
 }
 
 // splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014).
@@ -255,19 +274,38 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
       }
     return;
   }
-  uint64_t pair = g / B.per_pair;
-  uint64_t r = g - pair * B.per_pair;
-  d.tx = (int)(pair / (uint64_t)B.n_rx);
+  uint64_t pair, r;
+  if (g <= 0xFFFFFFFFull && B.fd_pp.d > 1) {  // reciprocal multiplies: exact for 32-bit operands
+    pair = fdiv((uint32_t)g, B.fd_pp);
+    r = g - pair * B.per_pair;
+    d.tx = (int)fdiv((uint32_t)pair, B.fd_rx);
+  } else {
+    pair = g / B.per_pair;
+    r = g - pair * B.per_pair;
+    d.tx = (int)(pair / (uint64_t)B.n_rx);
+  }
   d.rx = (int)(pair - (uint64_t)d.tx * (uint64_t)B.n_rx);
   int digits[kMaxOrder];
   const uint64_t K = (uint64_t)B.n_alpha;
   if (B.mode == BATCH_SEEDED) {
-    int n = B.lo + (int)(seeded_draw(B.seed, g, 0) % (uint64_t)(B.hi - B.lo + 1));
+    // the draws of the seeded sampler, reduced with reciprocal multiplies when the divisors are below 2^16
+    const bool fast = K >= 2 && K <= 65535 && B.hi - B.lo + 1 <= 65535 && B.fd_alpha.d == (uint32_t)K &&
+                      B.fd_range.d == (uint32_t)(B.hi - B.lo + 1);
+    const uint64_t r0 = seeded_draw(B.seed, g, 0), r1 = seeded_draw(B.seed, g, 1);
+    int n = B.lo + (int)(fast ? fmod64(r0, B.fd_range, B.t32_range) : r0 % (uint64_t)(B.hi - B.lo + 1));
     d.n = n;
-    digits[0] = (int)(seeded_draw(B.seed, g, 1) % K);
+    digits[0] = (int)(fast ? fmod64(r1, B.fd_alpha, B.t32_alpha) : r1 % K);
 #pragma unroll
     for (int j = 1; j < kSlotsMax; ++j)
-      if (j < n) digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + seeded_draw(B.seed, g, j + 1) % (K - 1)) % K);
+      if (j < n) {
+        const uint64_t rj = seeded_draw(B.seed, g, j + 1);
+        if (fast) {
+          const uint32_t v = (uint32_t)digits[j - 1] + 1u + fmod64(rj, B.fd_alpha1, B.t32_alpha1);  // < 2 K
+          digits[j] = (int)(v >= (uint32_t)K ? v - (uint32_t)K : v);
+        } else {
+          digits[j] = (int)(((uint64_t)digits[j - 1] + 1ULL + rj % (K - 1)) % K);
+        }
+      }
   } else {
     int n = B.lo;
     while (n < B.hi && r >= B.offset[n + 1]) ++n;

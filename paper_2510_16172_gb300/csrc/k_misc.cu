@@ -49,15 +49,48 @@ __global__ void pattern_hist_kernel(SceneDev S, BatchDev B, unsigned long long* 
     if (s[k]) atomicAdd(&counts[k], s[k]);
 }
 
-// cursors[key] starts at the first slot of that bucket in `lists`; each slot
-// receives the decoded path.
+// cursors[key] starts at the first slot of that bucket in `lists`; each slot receives the decoded path.
+// A block takes tiles of 256 x kScatterPerThread paths: it counts the tile's paths per bucket in shared
+// memory (each path's rank within its bucket, its packed record kept in registers), reserves each
+// bucket's range with one global atomic, then writes the records.  One global atomic per (tile, bucket)
+// instead of one per path: with ~60 buckets, per-path atomics on the same few cursors serialised the kernel.
+constexpr int kScatterPerThread = 8;
 __global__ void pattern_scatter_kernel(SceneDev S, BatchDev B, unsigned long long* cursors, PathRec* lists) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < B.n_paths; g += stride) {
-    PathDesc d;
-    decode_global(B, g, d);
-    unsigned long long slot = atomicAdd(&cursors[path_key(S, d)], 1ULL);
-    store_rec(lists, slot, d);
+  __shared__ unsigned s_cnt[kPatternKeys];
+  __shared__ unsigned long long s_base[kPatternKeys];
+  const uint64_t tile = (uint64_t)blockDim.x * kScatterPerThread;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * tile; t0 < B.n_paths; t0 += (uint64_t)gridDim.x * tile) {
+    for (int k = threadIdx.x; k < kPatternKeys; k += blockDim.x) s_cnt[k] = 0u;
+    __syncthreads();
+    int key[kScatterPerThread];
+    unsigned rank[kScatterPerThread];
+    uint4 rec_a[kScatterPerThread], rec_b[kScatterPerThread];
+#pragma unroll
+    for (int i = 0; i < kScatterPerThread; ++i) {
+      const uint64_t g = t0 + (uint64_t)i * blockDim.x + threadIdx.x;
+      key[i] = -1;
+      rank[i] = 0u;
+      rec_a[i] = rec_b[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (g < B.n_paths) {
+        PathDesc d;
+        decode_global(B, g, d);
+        key[i] = path_key(S, d);
+        rank[i] = atomicAdd(&s_cnt[key[i]], 1u);
+        pack_rec(d, rec_a[i], rec_b[i]);
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kPatternKeys; k += blockDim.x)
+      if (s_cnt[k]) s_base[k] = atomicAdd(&cursors[k], (unsigned long long)s_cnt[k]);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kScatterPerThread; ++i) {
+      if (key[i] < 0) continue;
+      uint4* p = reinterpret_cast<uint4*>(lists + s_base[key[i]] + rank[i]);
+      p[0] = rec_a[i];
+      p[1] = rec_b[i];
+    }
+    __syncthreads();  // s_cnt and s_base are reused by the next tile
   }
 }
 
@@ -101,7 +134,7 @@ cudaError_t launch_pattern_histogram(const SceneDev& S, const BatchDev& B, unsig
 
 cudaError_t launch_pattern_scatter(const SceneDev& S, const BatchDev& B, unsigned long long* cursors, PathRec* lists,
                                    cudaStream_t stream, int n_sm) {
-  unsigned grid = grid_for(B.n_paths, 256, n_sm, 8);
+  unsigned grid = grid_for((B.n_paths + kScatterPerThread - 1) / kScatterPerThread, 256, n_sm, 8);
   if (grid == 0) return cudaSuccess;
   pattern_scatter_kernel<<<grid, 256, 0, stream>>>(S, B, cursors, lists);
   count_launch();
