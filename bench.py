@@ -450,8 +450,9 @@ def learned_vs_plain(ctx, fpt, epochs):
     from paper_2510_16172_gb300 import warmstart
 
     t0 = time.perf_counter()
-    net, ev = warmstart.run(ctx, per_pair_train=200_000, per_pair_eval=200_000, epochs=epochs)
-    res = {"workload": "train: 50 seeded 10 m scenes (8 quads + 4 edges) x 200,000 seeded order-1..4 sequences, "
+    # 285,000 sequences per scene give about 10 M solved paths as training samples
+    net, ev = warmstart.run(ctx, per_pair_train=285_000, per_pair_eval=200_000, epochs=epochs)
+    res = {"workload": "train: 50 seeded 10 m scenes (8 quads + 4 edges) x 285,000 seeded order-1..4 sequences, "
                        f"solved paths as targets, {epochs} epochs of Adam; eval: 10 unseen scenes x 200,000 "
                        "sequences",
            "train_samples": ev["train_samples"], "train_loss_per_epoch": ev["train_loss_per_epoch"],
