@@ -457,6 +457,20 @@ fpt_status fpt_set_init_mlp(fpt_ctx* ctx, fpt_mlp* mlp);
 fpt_status fpt_tc_gemm_bf16(fpt_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A, const void* W,
                             const float* bias, float* C);
 
+/* Check of the bounded waits.  Every tensor-core kernel (the GEMMs and the
+ * fused inference) gives up an mbarrier wait after 1 s of the GPU's global
+ * timer, sets the context's device error word and returns, so that a TMA copy
+ * or an MMA that never completes shows up as FPT_EDEVICE from the next
+ * fpt_sync (which clears the word) instead of a hung stream.  This call
+ * launches one CTA that waits, with the same helper and a limit of limit_us
+ * microseconds (1 <= limit_us <= 10^6, else FPT_EINVAL), on an mbarrier that
+ * receives its one expected arrival only when arrive != 0.  With arrive == 0
+ * the wait runs out and the following fpt_sync returns FPT_EDEVICE; with
+ * arrive != 0 it completes at once and the error word is left alone.
+ * elapsed_ns (host, optional) receives the wait's duration in nanoseconds;
+ * passing it makes the call synchronise the stream. */
+fpt_status fpt_check_bounded_wait(fpt_ctx* ctx, uint32_t limit_us, int arrive, uint64_t* elapsed_ns);
+
 /* Kernel timing.  While enabled, the kernels of each class that one call
  * launches are bracketed by CUDA events on the context's stream, and
  * fpt_profile_read() returns, per kernel class, the summed device time in

@@ -1769,6 +1769,28 @@ fpt_status fpt_tc_gemm_bf16(fpt_ctx* ctx, int32_t M, int32_t N, int32_t K, const
   return FPT_OK;
 }
 
+fpt_status fpt_check_bounded_wait(fpt_ctx* ctx, uint32_t limit_us, int arrive, uint64_t* elapsed_ns) {
+  if (!ctx) return FPT_EINVAL;
+  if (limit_us < 1 || limit_us > 1000000u) return fail(ctx, FPT_EINVAL, "limit %u us outside [1, 10^6]", limit_us);
+  CUDA_OR_FAIL(ctx, cudaSetDevice(ctx->device));
+  unsigned long long* d_ns = nullptr;
+  if (elapsed_ns) CUDA_OR_FAIL(ctx, cudaMalloc(&d_ns, sizeof(unsigned long long)));
+  cudaError_t e;
+  {
+    ProfScope ps(ctx, FPT_K_OTHER);
+    e = launch_bounded_wait_check(limit_us * 1000u, arrive, ctx->d_err, d_ns, ctx->stream);
+  }
+  unsigned long long h = 0;
+  if (e == cudaSuccess && elapsed_ns) {
+    e = cudaMemcpyAsync(&h, d_ns, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  if (d_ns) cudaFree(d_ns);
+  CUDA_OR_FAIL(ctx, e);
+  if (elapsed_ns) *elapsed_ns = h;
+  return FPT_OK;
+}
+
 fpt_status fpt_profile_enable(fpt_ctx* ctx, int on) {
   if (!ctx) return FPT_EINVAL;
   ctx->prof = on != 0;

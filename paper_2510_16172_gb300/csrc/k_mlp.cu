@@ -26,7 +26,7 @@
 namespace fpt {
 
 constexpr int kGemmKC = 64;                  // K per chunk
-constexpr uint32_t kWaitTries = 1u << 24;    // bounded mbarrier polls
+constexpr uint32_t kWaitNs = 1000000000u;   // mbarrier waits give up after 1 s
 constexpr int ERR_MMA_TIMEOUT = 3;
 
 // GELU in its tanh form (Hendrycks and Gimpel, arXiv:1606.08415):
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
   // chunk c's MMAs have completed: its stage barrier's phase number c / kGemmStages.  A thread whose
   // bounded wait runs out sets s_fail, which every thread reads only after the next barrier.
   auto wait_chunk = [&](int c) {
-    if (tc::mbar_wait(&bar[c % kGemmStages], (uint32_t)((c / kGemmStages) & 1), kWaitTries)) return true;
+    if (tc::mbar_wait(&bar[c % kGemmStages], (uint32_t)((c / kGemmStages) & 1), kWaitNs)) return true;
     atomicExch(&s_fail, 1);
     return false;
   };
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
     if (threadIdx.x == 0 && g.err) atomicCAS(g.err, 0, ERR_MMA_TIMEOUT);
     // give MMAs still in flight a (bounded) chance to finish before TMEM is freed
     if (n_chunks > 0) tc::mbar_wait(&bar[(n_chunks - 1) % kGemmStages], (uint32_t)(((n_chunks - 1) / kGemmStages) & 1),
-                                    kWaitTries);
+                                    kWaitNs);
   } else if (n_chunks > 0) {
     // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31; the pipeline buffers are idle now
     float* slab = reinterpret_cast<float*>(gemm_smem) + warp * 32 * kEpiStride;
@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         for (int k0 = w.kb; k0 < w.ke; k0 += kGemmKC, ++q) {
           const int s = q % stages, u = q / stages;
           if (u > 0) {  // the stage's previous chunk has been read by its MMAs
-            ok = !failed() && tc::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), kWaitTries);
+            ok = !failed() && tc::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), kWaitNs);
             if (!ok) break;
           }
           tc::mbar_expect_tx(&full[s], tx_bytes);
@@ -705,13 +705,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x, ++i) {
         const WsItem w = ws_item(g, item, m_tiles, k_per);
         const int b = i & 1, v = i >> 1;
-        if (v > 0) ok = !failed() && tc::mbar_wait(&acc_empty[b], (uint32_t)((v - 1) & 1), kWaitTries);
+        if (v > 0) ok = !failed() && tc::mbar_wait(&acc_empty[b], (uint32_t)((v - 1) & 1), kWaitNs);
         if (!ok) break;
         tc::fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(b * 256);
         for (int k0 = w.kb, c = 0; k0 < w.ke; k0 += kGemmKC, ++q, ++c) {
           const int s = q % stages, u = q / stages;
-          ok = !failed() && tc::mbar_wait(&full[s], (uint32_t)(u & 1), kWaitTries);
+          ok = !failed() && tc::mbar_wait(&full[s], (uint32_t)(u & 1), kWaitNs);
           if (!ok) break;
           tc::fence_after_sync();
           const uint64_t ad = tc::smem_desc_sw128(tc::smem_u32(stage_a(s)));
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++i) {
       const WsItem w = ws_item(g, item, m_tiles, k_per);
       const int b = i & 1, v = i >> 1;
-      const bool ok = __all_sync(all, !failed() && tc::mbar_wait(&acc_full[b], (uint32_t)(v & 1), kWaitTries));
+      const bool ok = __all_sync(all, !failed() && tc::mbar_wait(&acc_full[b], (uint32_t)(v & 1), kWaitNs));
       if (!ok) {
         if (lane == 0) atomicExch(&s_fail, 1);
         break;
@@ -779,9 +779,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (g.err) atomicCAS(g.err, 0, ERR_MMA_TIMEOUT);
     // let the copies and MMAs already issued finish (bounded) before shared and tensor memory go away
     for (int s = 0; s < stages; ++s)
-      if (s_armed[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)(s_armed[s] & 1), kWaitTries);
+      if (s_armed[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)(s_armed[s] & 1), kWaitNs);
     const int q = s_last_q;
-    if (q >= 0) tc::mbar_wait(&empty[q % stages], (uint32_t)((q / stages) & 1), kWaitTries);
+    if (q >= 0) tc::mbar_wait(&empty[q % stages], (uint32_t)((q / stages) & 1), kWaitNs);
   }
   __syncthreads();
   if (want_col && !s_fail)
@@ -1406,14 +1406,14 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
           if (q + 1 < total_q) {
             const int nb = b ^ 1;
             if (q >= 1) {
-              if (!tc::mbar_wait(&sm.done[nb], (done_ph >> nb) & 1u, kWaitTries)) sm.fail = 1;
+              if (!tc::mbar_wait(&sm.done[nb], (done_ph >> nb) & 1u, kWaitNs)) sm.fail = 1;
               done_ph ^= 1u << nb;
             }
             const int nq = (lq + 1) % kUnitsPerTile;
             tc::mbar_expect_tx(&sm.full[nb], unit_bytes(nq));
             tc::bulk_g2s(sm.wbuf[nb], wsrc + unit_offset(nq), unit_bytes(nq), &sm.full[nb]);
           }
-          if (!tc::mbar_wait(&sm.full[b], (full_ph >> b) & 1u, kWaitTries)) sm.fail = 1;
+          if (!tc::mbar_wait(&sm.full[b], (full_ph >> b) & 1u, kWaitNs)) sm.fail = 1;
           full_ph ^= 1u << b;
           tc::fence_after_sync();
           const uint32_t K_act = layer == 0 ? 64u : 256u;
@@ -1442,7 +1442,7 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
       }
       if (!unit_ends_layer(lq)) continue;
       // end of a layer: wait for its MMAs, then the epilogue
-      if (!tc::mbar_wait(&sm.layer, layer_ph, kWaitTries)) sm.fail = 1;
+      if (!tc::mbar_wait(&sm.layer, layer_ph, kWaitNs)) sm.fail = 1;
       layer_ph ^= 1u;
       tc::fence_after_sync();
       const int rg = warp & 3;  // TMEM lane group of this warp
@@ -1486,7 +1486,7 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
   }
   if (sm.fail && tid == 0) {
     if (err) atomicCAS(err, 0, ERR_MMA_TIMEOUT);
-    tc::mbar_wait(&sm.layer, layer_ph, kWaitTries);  // let MMAs in flight finish before TMEM is freed
+    tc::mbar_wait(&sm.layer, layer_ph, kWaitNs);  // let MMAs in flight finish before TMEM is freed
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -1684,6 +1684,32 @@ cudaError_t launch_mlp_transpose_weights(const __nv_bfloat16* wb, __nv_bfloat16*
 
 cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int n, cudaStream_t stream) {
   to_bf16_kernel<<<grid_1d(n, 256, 1024), 256, 0, stream>>>(src, dst, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Check of the bounded waits that every tensor-core kernel here relies on.  Thread 0 initialises an
+// mbarrier that expects one arrival; unless `arrive` is set, nothing ever arrives on it, so its phase
+// never completes.  The wait gives up after `limit_ns` and records ERR_MMA_TIMEOUT in the error word,
+// the same path a GEMM or inference CTA takes when an MMA or a TMA copy does not complete.
+// `elapsed` (optional) receives the nanoseconds the wait took.
+__global__ void bounded_wait_check_kernel(uint32_t limit_ns, int arrive, int* err, unsigned long long* elapsed) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (arrive) tc::mbar_arrive(&bar);
+  const uint64_t t0 = tc::global_ns();
+  const bool ok = tc::mbar_wait(&bar, 0u, limit_ns);
+  const uint64_t t1 = tc::global_ns();
+  if (!ok && err) atomicCAS(err, 0, ERR_MMA_TIMEOUT);
+  if (elapsed) *elapsed = (unsigned long long)(t1 - t0);
+}
+
+cudaError_t launch_bounded_wait_check(uint32_t limit_ns, int arrive, int* err, unsigned long long* elapsed,
+                                      cudaStream_t stream) {
+  if (limit_ns < 1 || limit_ns > kWaitNs) return cudaErrorInvalidValue;
+  bounded_wait_check_kernel<<<1, 32, 0, stream>>>(limit_ns, arrive, err, elapsed);
   count_launch();
   return cudaGetLastError();
 }

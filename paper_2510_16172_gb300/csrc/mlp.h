@@ -65,6 +65,11 @@ cudaError_t launch_mlp_gather(const __nv_bfloat16* X, const float* T, const floa
                               uint64_t B, uint64_t key, __nv_bfloat16* Xb, float* Tb, float* Gb, __nv_bfloat16* Xt,
                               cudaStream_t stream);
 cudaError_t launch_mlp_accumulate(float* dst, const float* src, float w, cudaStream_t stream);
+// One CTA waits, for at most `limit_ns` (1 ns .. 1 s), on an mbarrier that receives an arrival only
+// when `arrive` != 0; a wait that runs out sets *err (if 0) to the MMA-timeout code.  `elapsed`
+// (device, optional) receives the wait's duration in nanoseconds of the global timer.
+cudaError_t launch_bounded_wait_check(uint32_t limit_ns, int arrive, int* err, unsigned long long* elapsed,
+                                      cudaStream_t stream);
 cudaError_t launch_mlp_start(const SceneDev& S, const BatchDev& B, int n, const PathRec* list, uint64_t first,
                              uint64_t count, const float* Y, float* T, cudaStream_t stream);
 

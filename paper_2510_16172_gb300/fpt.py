@@ -99,6 +99,7 @@ _SIGS = {
     "fpt_mlp_train": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, C.POINTER(TrainParams), _vp]),
     "fpt_mlp_infer": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "fpt_set_init_mlp": (C.c_int, [_vp, _vp]),
+    "fpt_check_bounded_wait": (C.c_int, [_vp, C.c_uint32, C.c_int, C.POINTER(C.c_uint64)]),
     "fpt_profile_enable": (C.c_int, [_vp, C.c_int]),
     "fpt_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]),
 }
@@ -652,6 +653,15 @@ def tc_gemm_bf16(ctx: Context, A, W, bias=None, out=None):
     C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=A.device)
     _check(ctx.handle, library().fpt_tc_gemm_bf16(ctx.handle, M, N, K, _ptr(A), _ptr(W), _ptr(bias), _ptr(C)))
     return C
+
+
+def check_bounded_wait(ctx: Context, limit_us: int, arrive: bool) -> int:
+    """fpt_check_bounded_wait: one CTA waits at most `limit_us` on an mbarrier that gets its arrival only
+    if `arrive`; returns the wait's duration in ns.  Without the arrival the next ctx.sync() raises
+    FptError (FPT_EDEVICE)."""
+    ns = C.c_uint64(0)
+    _check(ctx.handle, library().fpt_check_bounded_wait(ctx.handle, int(limit_us), 1 if arrive else 0, C.byref(ns)))
+    return int(ns.value)
 
 
 def backward_dropped(ctx: Context) -> int:
