@@ -160,6 +160,7 @@ NCU_TRAFFIC = {
     # (profiles/launch_list_urban_canyon_33M.md)
     ("39df173948b3", "bfgs"): 570.1e6,
     ("f6467978743f", "bfgs"): 568.6e6,
+    ("886638d3c5ec", "bfgs"): 568.8e6,
 }
 
 
