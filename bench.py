@@ -197,6 +197,74 @@ def oracle_rate(sc, n_paths, seed, target_s=None, max_paths=None, decode=None):
     return solved / dt, m, dt, threads
 
 
+def sample_outputs(ctx, scene, batch, out, torch, fpt, dev, n_paths, m=100_000, seed=7):
+    """The timed step's outputs on a seeded uniform sample of paths, and the implicit backward of the sum
+    of the sample's valid solved lengths (fpt_backward with dL = 1 on those paths, 0 elsewhere).  The
+    comparison with the oracle is made on the host by oracle_agreement()."""
+    import numpy as np
+
+    g = np.sort(np.random.default_rng(seed).choice(n_paths, m, replace=False))
+    gi = torch.as_tensor(g, device=dev)
+    st = out["status"][gi]
+    both = fpt.ST_VALID | fpt.ST_SOLVED
+    w = (st & both) == both
+    dL = torch.zeros(n_paths, dtype=torch.float32, device=dev)
+    dL[gi] = w.float()
+    grads = fpt.backward(ctx, scene, batch, out["T"], out["status"], None, dL)
+    ctx.sync()
+    res = {"g": g, "T": out["T"][gi].double().cpu().numpy(), "L": out["L"][gi].double().cpu().numpy(),
+           "status": st.cpu().numpy().astype(np.int64), "w": w.cpu().numpy(),
+           "grads": [x.double().cpu().numpy() for x in grads]}
+    del dL
+    return res
+
+
+def oracle_agreement(sc, S, decode):
+    """Error of the timed step's results against the oracle on the sample of sample_outputs():
+    solved-set agreement, max |dX| and |dL|/L over the paths both solve, validity-mask mismatches, and
+    the relative error of the sample's TX/RX/vertex gradients against the oracle's FP64 implicit VJP
+    (Eq. 12-13) evaluated at the GPU's parameters."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    ids, order, ti, ri = decode(S["g"])
+    t0 = time.perf_counter()
+    ref = oracle.solve(sc, ids, order, ti, ri)
+    w = S["w"].astype(np.float64)
+    at = oracle.solve(sc, ids, order, ti, ri, solver=oracle.BFGS, max_iters=0, T_start=S["T"], dL=w)
+    dt = time.perf_counter() - t0
+    gs = (S["status"] & oracle.SOLVED) > 0
+    rs = (ref["status"] & oracle.SOLVED) > 0
+    both = gs & rs
+    slot = np.arange(ids.shape[1])[None, :] < np.asarray(order)[:, None]
+    dx = np.where(slot, np.linalg.norm(at["X"] - ref["X"], axis=2), 0.0).max(axis=1)
+    dl = np.abs(S["L"] - ref["L"]) / np.maximum(ref["L"], 1e-30)
+    vmis = ((S["status"] & oracle.VALID) > 0) != ((ref["status"] & oracle.VALID) > 0)
+    far = np.abs(ref["bdist"]) > 1e-5
+    want = oracle.reduce_gradients(sc, ids, order, ti, ri, at["dtheta"] * w[:, None])
+    rel = {}
+    for name, got, exp in zip(("tx", "rx", "vertices"), S["grads"], want):
+        rel[name] = float(np.abs(got - exp).max() / max(np.abs(exp).max(), 1e-30))
+    return {"sample_paths": int(len(S["g"])), "solved_both": int(both.sum()), "solved_gpu_only": int((gs & ~rs).sum()),
+            "solved_oracle_only": int((rs & ~gs).sum()),
+            "max_dX_m": float(dx[both].max()) if both.any() else None,
+            "max_rel_dL": float(dl[both].max()) if both.any() else None,
+            "mask_mismatches": int((vmis & both).sum()),
+            "mask_mismatches_beyond_1e-5_m_of_a_boundary": int((vmis & both & far).sum()),
+            "gradient_paths": int(w.sum()), "gradient_rel_err": rel,
+            "note": "oracle = FP64 damped Newton on the same paths; dX of the GPU's parameters mapped to points in "
+                    "FP64; gradients: fpt_backward with dL = 1 on the sample's valid solved paths vs the oracle's VJP "
+                    "at the GPU's parameters", "oracle_s": round(dt, 2)}
+
+
+def oracle_decode_canyon(sc, g):
+    import oracle
+
+    return oracle.exhaustive_paths(sc, 3, 3, g)
+
+
 def combine_ranks(total_ms, solved, dist, device):
     """Whole-job figures of a replicated run: the slowest rank's timed total and the sum of the ranks' solved
     paths (every rank solves its own copy of the workload; nothing else is exchanged)."""
@@ -339,6 +407,16 @@ def run_ours(args, world, rank, local_rank):
     run_paths = N - fpt.count_status(ctx, out["status"], fpt.ST_REPEAT)
     total_ms, solved_all = combine_ranks(total_ms, solved, dist, dev)
     value = solved_all * args.steps / (total_ms / 1e3)
+    # the step's run statistics: converged and FP64-polished fractions, BFGS steps (mean above, p99 here)
+    stats = {"converged_fraction": fpt.count_status(ctx, out["status"], fpt.ST_CONVERGED) / N,
+             "fp64_fraction": fpt.count_status(ctx, out["status"], fpt.ST_FP64) / N}
+    hist = torch.bincount(iters[(out["status"] & fpt.ST_REPEAT) == 0], minlength=256).double()
+    cdf = torch.cumsum(hist, 0) / hist.sum().clamp(min=1.0)
+    stats["bfgs_iters_p99"] = int((cdf < 0.99).sum().item())
+    del hist, cdf
+    sample = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sample = sample_outputs(ctx, scene, batch, out, torch, fpt, dev, N)
 
     # roofline of the dominant kernel (device time per launch from the library's event timing)
     peaks = measured_peaks()
@@ -397,6 +475,7 @@ def run_ours(args, world, rank, local_rank):
                        "polish": "1 Newton step, double-float gradient (FP64 for ill-conditioned Hessians)",
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "solved_per_step": solved, "solved_fraction": solved / N, "mean_bfgs_iters": total_iters / max(1, run_paths),
+            **stats,
             "kernel_ms_per_step": {names[k]: kms[k] / args.steps for k in range(fpt.K_COUNT) if klaunch[k]},
             "dominant_kernel": names[dom],
             "roofline": roof_bfgs,
@@ -418,6 +497,7 @@ def run_ours(args, world, rank, local_rank):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{m} seeded uniformly sampled paths of the workload, FP64 damped Newton "
                                           f"+ implicit VJP, {dt:.1f} s on {threads} threads"}
+        line["oracle_agreement"] = oracle_agreement(sc, sample, lambda g: oracle_decode_canyon(sc, g))
     if rank == 0 and world == 1 and not args.no_learned:
         line["learned_vs_plain"], net = learned_vs_plain(ctx, fpt, args.epochs)
         if not args.no_city:
