@@ -167,18 +167,18 @@ NCU_TRAFFIC = {
 # ---------------------------------------------------------------------------
 # the oracle (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rate(sc, n_paths, seed, target_s=None, max_paths=None, decode=None):
+def oracle_rate(sc, n_paths, seed, target_s=None, max_paths=None, decode=None, threads=None):
     """Oracle fwd+bwd on a seeded uniform sample of the workload: (solved/s, sample size, seconds, threads).
 
     decode(g) -> (ids, order, tx_idx, rx_idx) of global path indices g (default: the canyon's order-3
-    exhaustive enumeration)."""
+    exhaustive enumeration).  threads: host threads (default all cores)."""
     import numpy as np
 
     import oracle
 
     oracle.build()
     rng = np.random.default_rng(seed)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     decode = decode or (lambda g: oracle.exhaustive_paths(sc, 3, 3, g))
 
     def run(m):
@@ -494,9 +494,11 @@ def run_ours(args, world, rank, local_rank):
         line["e2e"] = e2e(args, sc, ctx, dev, torch, fpt)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, m, dt, threads = oracle_rate(sc, N, 1, target_s=args.cpu_seconds)
+        rate1, m1, dt1, _ = oracle_rate(sc, N, 2, threads=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{m} seeded uniformly sampled paths of the workload, FP64 damped Newton "
-                                          f"+ implicit VJP, {dt:.1f} s on {threads} threads"}
+                                          f"+ implicit VJP, {dt:.1f} s on {threads} threads",
+                                "value_1_core": rate1, "sample_1_core": f"{m1} paths, {dt1:.1f} s on 1 thread"}
         line["oracle_agreement"] = oracle_agreement(sc, sample, lambda g: oracle_decode_canyon(sc, g))
     if rank == 0 and world == 1 and not args.no_learned:
         line["learned_vs_plain"], net = learned_vs_plain(ctx, fpt, args.epochs)
