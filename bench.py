@@ -219,6 +219,31 @@ def sample_outputs(ctx, scene, batch, out, torch, fpt, dev, n_paths, m=100_000, 
     return res
 
 
+def residual_distribution(ctx, scene, batch, params, out, torch, fpt):
+    """The stationarity residual rho (the world-space size of the Newton step at the returned point) of one
+    more, untimed solve with the bench's settings: quantiles over the solved paths, and over the paths that
+    BFGS reported converged but the polish did not certify.  Overwrites the solve outputs in `out`."""
+    rho = torch.empty(batch.n_paths, dtype=torch.float32, device=out["T"].device)
+    o = dict(out)
+    o["rho"] = rho
+    fpt.solve(ctx, scene, batch, params, out=o)
+    ctx.sync()
+    st = o["status"]
+    groups = {"solved": (st & fpt.ST_SOLVED) != 0,
+              "converged_not_solved": ((st & fpt.ST_CONVERGED) != 0) & ((st & fpt.ST_SOLVED) == 0)}
+    res = {}
+    for name, m in groups.items():
+        r = rho[m]
+        r = torch.sort(r[torch.isfinite(r)]).values
+        n = r.numel()
+        res[name] = {"paths": int(n)}
+        if n:
+            res[name].update({"p50_m": float(r[(n - 1) // 2]), "p99_m": float(r[int(0.99 * (n - 1))]),
+                              "max_m": float(r[-1])})
+    del rho, o
+    return res
+
+
 def oracle_agreement(sc, S, decode):
     """Error of the timed step's results against the oracle on the sample of sample_outputs():
     solved-set agreement, max |dX| and |dL|/L over the paths both solve, validity-mask mismatches, and
@@ -485,6 +510,7 @@ def run_ours(args, world, rank, local_rank):
             "occlusion": occ}
     if dom != fpt.K_BFGS:
         line["roofline_note"] = f"dominant kernel is {names[dom]}; roofline reported for the FP32 solver kernel"
+    line["residual_m"] = residual_distribution(ctx, scene, batch, params, out, torch, fpt)
     if world == 1:
         line["at_library_defaults"] = library_defaults_leg(ctx, scene, batch, out, grads, mask, flush, stream, torch,
                                                            fpt, dev)
