@@ -164,16 +164,27 @@ __global__ void __launch_bounds__(kThreads) backward_kernel(SceneDev S, BatchDev
 }
 
 // List the paths of a slice that carry a cotangent (no dX: those with a non-zero length cotangent
-// and a status that the backward does not skip), by local index.
+// and a status that the backward does not skip), by local index.  A CTA takes kSelChunk consecutive
+// local indices at a time (kSelPer per thread), lists its chunk's paths in index order and claims
+// their place in the list with one atomic.  Consecutive list entries are then neighbouring
+// sequences, which mostly share their endpoints and leading objects, so the adjoint's warps find
+// uniform accumulator targets and sum them by shuffles.
+constexpr int kSelThreads = 256, kSelPer = 16, kSelChunk = kSelThreads * kSelPer;
 template <int N>
-__global__ void backward_select_kernel(BatchDev B, BackwardCfg cfg, uint64_t n_local, const PathRec* list,
-                                       const uint8_t* __restrict__ status, const float* __restrict__ dLv) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
-  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
-    const uint64_t j = j0 + threadIdx.x;
-    bool take = false;
-    if (j < n_local) {
+__global__ void __launch_bounds__(kSelThreads) backward_select_kernel(BatchDev B, BackwardCfg cfg, uint64_t n_local,
+                                                                      const PathRec* list,
+                                                                      const uint8_t* __restrict__ status,
+                                                                      const float* __restrict__ dLv) {
+  __shared__ unsigned s_warp[kSelThreads / 32];
+  __shared__ unsigned s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t c0 = (uint64_t)blockIdx.x * kSelChunk; c0 < n_local; c0 += (uint64_t)gridDim.x * kSelChunk) {
+    const uint64_t j0 = c0 + (uint64_t)threadIdx.x * kSelPer;
+    unsigned bits = 0;
+#pragma unroll 4
+    for (int k = 0; k < kSelPer; ++k) {
+      const uint64_t j = j0 + k;
+      if (j >= n_local) break;
       uint64_t g;
       uint8_t st;
       if (status) {  // the solver wrote the sequence's REPEAT / INVALID_INPUT bits into its status
@@ -185,14 +196,39 @@ __global__ void backward_select_kernel(BatchDev B, BackwardCfg cfg, uint64_t n_l
         g = d.g;
         st = d.flags;
       }
+      bool take = false;
       if (!(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE)))
         take = dLv ? dLv[g] != 0.f : (cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask);
+      bits |= (take ? 1u : 0u) << k;
     }
-    const unsigned ballot = __ballot_sync(0xffffffffu, take);
-    unsigned base = 0;
-    if (lane == 0 && ballot) base = atomicAdd(cfg.sel_count, (unsigned)__popc(ballot));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (take) cfg.sel[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)j;
+    // exclusive prefix of the per-thread counts over the CTA (thread order = index order)
+    const unsigned cnt = (unsigned)__popc(bits);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned run = 0;
+#pragma unroll
+      for (int w = 0; w < kSelThreads / 32; ++w) {
+        const unsigned c = s_warp[w];
+        s_warp[w] = run;
+        run += c;
+      }
+      s_base = run ? atomicAdd(cfg.sel_count, run) : 0u;
+    }
+    __syncthreads();
+    unsigned pos = s_base + s_warp[warp] + incl - cnt;
+    while (bits) {
+      const int k = __ffs(bits) - 1;
+      bits &= bits - 1u;
+      cfg.sel[pos++] = (uint32_t)(j0 + (uint64_t)k);
+    }
+    __syncthreads();  // s_warp and s_base are rewritten by the next chunk
   }
 }
 
@@ -291,10 +327,10 @@ cudaError_t launch_backward_n(const SceneDev& S, const BatchDev& B, const Backwa
   } else {
     cudaError_t e = cudaMemsetAsync(cfg.sel_count, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
-    const uint64_t want = (n_local + 255) / 256;
+    const uint64_t want = (n_local + kSelChunk - 1) / kSelChunk;
     const unsigned g = (unsigned)(want < (uint64_t)n_sm * 8 ? want : (uint64_t)n_sm * 8);
     if (g == 0) return cudaSuccess;
-    backward_select_kernel<N><<<g, 256, 0, stream>>>(B, cfg, n_local, list, status, dL);
+    backward_select_kernel<N><<<g, kSelThreads, 0, stream>>>(B, cfg, n_local, list, status, dL);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
