@@ -330,6 +330,10 @@ __device__ __forceinline__ uint64_t slice_global(const BatchDev& B, int n, const
     return (uint64_t)w.x | ((uint64_t)w.y << 32);
   }
   const uint64_t kn = B.kpow[n];
+  if (j <= 0xFFFFFFFFull && kn <= 0xFFFFFFFFull) {  // the usual case: a 32-bit reciprocal multiply
+    const uint32_t p32 = fdiv((uint32_t)j, B.fd_kpow[n]);
+    return (uint64_t)p32 * B.per_pair + B.offset[n] + ((uint32_t)j - p32 * (uint32_t)kn);
+  }
   const uint64_t pair = j / kn;
   return pair * B.per_pair + B.offset[n] + (j - pair * kn);
 }

@@ -26,21 +26,26 @@ __device__ __forceinline__ bool has_point_cotangent(const float* __restrict__ dX
 // Warp-aggregated accumulate of `cnt` values into acc[base + k] (or, without
 // shared accumulators, into gacc[gbase + k]).  Lanes with base < 0 add
 // nothing.  If every adding lane has the same base the warp sums its values
-// and one lane adds them (the common case: neighbouring paths share objects);
-// otherwise each adding lane adds its own.  CNT <= 32.
+// and one lane adds them (the common case: neighbouring paths share objects).
+// Otherwise the lanes that share a target are grouped and each group's values
+// are summed onto one lane first, so that no two lanes of the warp add to the
+// same address: a float atomic on shared memory is a compare-and-swap loop,
+// which every colliding lane would repeat.  Groups that are contiguous runs of
+// lanes (neighbouring entries of an index-ordered path list) are summed by a
+// segmented scan, other groups by pulling one member per round.  CNT <= 32.
 template <int CNT>
 __device__ __forceinline__ void warp_accumulate(float* acc, int base, const float (&v)[CNT], bool shared_acc,
                                                 double* gacc, int gbase) {
   const unsigned full = 0xffffffffu;
   const unsigned adding = __ballot_sync(full, base >= 0);
   if (!adding) return;
+  const int lane = (int)(threadIdx.x & 31);
   const int leader = __ffs(adding) - 1;
   const int b0 = __shfl_sync(full, base, leader);
   const bool uniform = __all_sync(full, base < 0 || base == b0);
   if (uniform) {
     // butterfly sums leave every lane with all CNT totals; lane k adds total k, so the CNT
     // additions are one warp instruction instead of CNT single-lane ones
-    const int lane = (int)(threadIdx.x & 31);
     const int g0 = __shfl_sync(full, gbase, leader);
     float mine = 0.f;
 #pragma unroll
@@ -56,13 +61,53 @@ __device__ __forceinline__ void warp_accumulate(float* acc, int base, const floa
       else
         atomicAdd(gacc + g0 + lane, (double)mine);
     }
-  } else if (base >= 0) {
+    return;
+  }
+  const unsigned peers = __match_any_sync(full, base);  // the lanes with this lane's target
+  const int first = __ffs(peers) - 1;
+  const unsigned gsize = (unsigned)__popc(peers);
+  const unsigned maxg = __reduce_max_sync(full, base >= 0 ? gsize : 1u);
+  float s[CNT];
+#pragma unroll
+  for (int k = 0; k < CNT; ++k) s[k] = v[k];
+  bool owner = base >= 0;  // the lane that adds its group's sum (every adding lane when all targets differ)
+  if (maxg > 1) {
+    const bool run = base < 0 || (peers >> first) == (gsize == 32u ? full : (1u << gsize) - 1u);
+    if (maxg > 4 && __all_sync(full, run)) {
+      // segmented inclusive scan: the last lane of each run ends with the run's sum
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const bool in = lane - o >= first;
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) {
+          const float y = __shfl_up_sync(full, s[k], o);
+          if (in) s[k] += y;
+        }
+      }
+      owner = base >= 0 && lane == 31 - __clz(peers);
+    } else {
+      // the first lane of each group pulls its other members' values, one member per round
+      unsigned rest = peers & (peers - 1u);
+      for (unsigned r = 1; r < maxg; ++r) {
+        const bool pull = lane == first && rest != 0u;
+        const int src = pull ? __ffs(rest) - 1 : lane;
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) {
+          const float y = __shfl_sync(full, v[k], src);
+          if (pull) s[k] += y;
+        }
+        if (pull) rest &= rest - 1u;
+      }
+      owner = base >= 0 && lane == first;
+    }
+  }
+  if (owner) {
 #pragma unroll
     for (int k = 0; k < CNT; ++k) {
       if (shared_acc)
-        atomicAdd(acc + base + k, v[k]);
+        atomicAdd(acc + base + k, s[k]);
       else
-        atomicAdd(gacc + gbase + k, (double)v[k]);
+        atomicAdd(gacc + gbase + k, (double)s[k]);
     }
   }
 }
