@@ -175,12 +175,10 @@ __global__ void __launch_bounds__(kSelThreads) backward_select_kernel(BatchDev B
                                                                       const PathRec* list,
                                                                       const uint8_t* __restrict__ status,
                                                                       const float* __restrict__ dLv) {
-  __shared__ unsigned s_warp[kSelThreads / 32];
-  __shared__ unsigned s_base;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t c0 = (uint64_t)blockIdx.x * kSelChunk; c0 < n_local; c0 += (uint64_t)gridDim.x * kSelChunk) {
     const uint64_t j0 = c0 + (uint64_t)threadIdx.x * kSelPer;
     unsigned bits = 0;
+    SliceWalk walk;
 #pragma unroll 4
     for (int k = 0; k < kSelPer; ++k) {
       const uint64_t j = j0 + k;
@@ -188,7 +186,7 @@ __global__ void __launch_bounds__(kSelThreads) backward_select_kernel(BatchDev B
       uint64_t g;
       uint8_t st;
       if (status) {  // the solver wrote the sequence's REPEAT / INVALID_INPUT bits into its status
-        g = slice_global(B, N, list, j);
+        g = list != nullptr ? slice_global(B, N, list, j) : walk.next(B, N, j);
         st = status[g];
       } else {
         PathDesc d;
@@ -201,34 +199,7 @@ __global__ void __launch_bounds__(kSelThreads) backward_select_kernel(BatchDev B
         take = dLv ? dLv[g] != 0.f : (cfg.dl_mask && (st & cfg.dl_mask) == cfg.dl_mask);
       bits |= (take ? 1u : 0u) << k;
     }
-    // exclusive prefix of the per-thread counts over the CTA (thread order = index order)
-    const unsigned cnt = (unsigned)__popc(bits);
-    unsigned incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned run = 0;
-#pragma unroll
-      for (int w = 0; w < kSelThreads / 32; ++w) {
-        const unsigned c = s_warp[w];
-        s_warp[w] = run;
-        run += c;
-      }
-      s_base = run ? atomicAdd(cfg.sel_count, run) : 0u;
-    }
-    __syncthreads();
-    unsigned pos = s_base + s_warp[warp] + incl - cnt;
-    while (bits) {
-      const int k = __ffs(bits) - 1;
-      bits &= bits - 1u;
-      cfg.sel[pos++] = (uint32_t)(j0 + (uint64_t)k);
-    }
-    __syncthreads();  // s_warp and s_base are rewritten by the next chunk
+    cta_append_ordered<kSelThreads>(bits, j0, cfg.sel, cfg.sel_count);
   }
 }
 

@@ -322,6 +322,69 @@ __device__ __forceinline__ void decode_global(const BatchDev& B, uint64_t g, Pat
   finish_desc<kN>(B, digits, d);
 }
 
+// Ordered list append of one CTA of kT threads: thread x flags local indices j0_x + k (bit k of
+// `bits`), with j0_x ascending in x; the flagged indices are written to sel in index order, after
+// the entries earlier CTAs claimed, with one atomic on sel_count for the whole CTA.  Every thread
+// of the CTA must call it (it synchronises the CTA).
+template <int kT>
+__device__ __forceinline__ void cta_append_ordered(unsigned bits, uint64_t j0, uint32_t* __restrict__ sel,
+                                                   unsigned* __restrict__ sel_count) {
+  __shared__ unsigned s_warp[kT / 32];
+  __shared__ unsigned s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned cnt = (unsigned)__popc(bits);
+  unsigned incl = cnt;  // inclusive prefix over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+#pragma unroll
+    for (int w = 0; w < kT / 32; ++w) {
+      const unsigned c = s_warp[w];
+      s_warp[w] = run;
+      run += c;
+    }
+    s_base = run ? atomicAdd(sel_count, run) : 0u;
+  }
+  __syncthreads();
+  unsigned pos = s_base + s_warp[warp] + incl - cnt;
+  while (bits) {
+    const int k = __ffs(bits) - 1;
+    bits &= bits - 1u;
+    sel[pos++] = (uint32_t)(j0 + (uint64_t)k);
+  }
+  __syncthreads();  // s_warp and s_base are rewritten by the next call
+}
+
+// Global indices of an exhaustive order-n slice, counted up from local index j: consecutive local
+// indices of one TX/RX pair have consecutive global indices, so g is derived once per pair.
+struct SliceWalk {
+  uint64_t g = 0, left = 0;
+  __device__ __forceinline__ uint64_t next(const BatchDev& B, int n, uint64_t j) {
+    if (left == 0) {
+      const uint64_t kn = B.kpow[n];
+      uint64_t pair, r;
+      if (j <= 0xFFFFFFFFull && kn <= 0xFFFFFFFFull) {
+        const uint32_t p32 = fdiv((uint32_t)j, B.fd_kpow[n]);
+        pair = p32;
+        r = (uint32_t)j - p32 * (uint32_t)kn;
+      } else {
+        pair = j / kn;
+        r = j - pair * kn;
+      }
+      g = pair * B.per_pair + B.offset[n] + r;
+      left = kn - r;  // paths of this pair from j on
+    }
+    --left;
+    return g++;
+  }
+};
+
 // Global index g of local index j of an order-n slice, without decoding the
 // sequence (the same g as decode_exhaustive_order / the record's).
 __device__ __forceinline__ uint64_t slice_global(const BatchDev& B, int n, const PathRec* list, uint64_t j) {

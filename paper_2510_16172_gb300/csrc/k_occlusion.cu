@@ -17,28 +17,32 @@
 
 namespace fpt {
 
-// List the paths of a slice that hold the status bits (local indices); zero the others' masks.
-__global__ void occlusion_select_kernel(BatchDev B, int n, const PathRec* list, uint64_t n_local,
-                                        const uint8_t* __restrict__ status, uint8_t mask,
-                                        uint16_t* __restrict__ blocked, uint32_t* __restrict__ sel,
-                                        unsigned* __restrict__ sel_count) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
-  for (uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x; j0 < n_local; j0 += stride) {
-    const uint64_t j = j0 + threadIdx.x;
-    bool take = false;
-    if (j < n_local) {
+// List the paths of a slice that hold the status bits (local indices); zero the others' masks.  A CTA
+// takes kOccSelPer consecutive local indices per thread and appends its chunk in index order with a
+// single atomic on the list counter, which one atomic per warp would turn into a serial hot spot.
+constexpr int kOccSelThreads = 256, kOccSelPer = 16, kOccSelChunk = kOccSelThreads * kOccSelPer;
+__global__ void __launch_bounds__(kOccSelThreads) occlusion_select_kernel(BatchDev B, int n, const PathRec* list,
+                                                                          uint64_t n_local,
+                                                                          const uint8_t* __restrict__ status,
+                                                                          uint8_t mask, uint16_t* __restrict__ blocked,
+                                                                          uint32_t* __restrict__ sel,
+                                                                          unsigned* __restrict__ sel_count) {
+  for (uint64_t c0 = (uint64_t)blockIdx.x * kOccSelChunk; c0 < n_local; c0 += (uint64_t)gridDim.x * kOccSelChunk) {
+    const uint64_t j0 = c0 + (uint64_t)threadIdx.x * kOccSelPer;
+    unsigned bits = 0;
+    SliceWalk walk;
+#pragma unroll 4
+    for (int k = 0; k < kOccSelPer; ++k) {
+      const uint64_t j = j0 + k;
+      if (j >= n_local) break;
       // the solver wrote the sequence's REPEAT / INVALID_INPUT bits into its status
-      const uint64_t g = slice_global(B, n, list, j);
+      const uint64_t g = list != nullptr ? slice_global(B, n, list, j) : walk.next(B, n, j);
       const uint8_t st = status[g];
-      take = !(st & ST_SKIP) && (st & mask) == mask;
+      const bool take = !(st & ST_SKIP) && (st & mask) == mask;
       if (!take) blocked[g] = 0;
+      bits |= (take ? 1u : 0u) << k;
     }
-    const unsigned ballot = __ballot_sync(0xffffffffu, take);
-    unsigned base = 0;
-    if (lane == 0 && ballot) base = atomicAdd(sel_count, (unsigned)__popc(ballot));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (take) sel[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)j;
+    cta_append_ordered<kOccSelThreads>(bits, j0, sel, sel_count);
   }
 }
 
@@ -109,10 +113,11 @@ cudaError_t launch_occlusion(const SceneDev& S, const BatchDev& B, int n, const 
     if (!sel || !sel_count) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(sel_count, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
-    const uint64_t want = (n_local + 255) / 256;
+    const uint64_t want = (n_local + kOccSelChunk - 1) / kOccSelChunk;
     const unsigned g = (unsigned)(want < (uint64_t)n_sm * 8 ? want : (uint64_t)n_sm * 8);
     if (g == 0) return cudaSuccess;
-    occlusion_select_kernel<<<g, 256, 0, stream>>>(B, n, list, n_local, status, mask, blocked, sel, sel_count);
+    occlusion_select_kernel<<<g, kOccSelThreads, 0, stream>>>(B, n, list, n_local, status, mask, blocked, sel,
+                                                              sel_count);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

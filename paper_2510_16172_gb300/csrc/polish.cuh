@@ -393,7 +393,12 @@ __global__ void __launch_bounds__(kThreads, kPolishMinBlocks<N>) polish_ff_kerne
               rho = r0;
               adj_ok = strict;
             } else {
-              const unsigned slot = atomicAdd(step_count, 1u);
+              // one atomic per group of lanes that list a path here together
+              const unsigned grp = __activemask();
+              const int lane = (int)(threadIdx.x & 31), first = __ffs(grp) - 1;
+              unsigned slot = 0;
+              if (lane == first) slot = atomicAdd(step_count, (unsigned)__popc(grp));
+              slot = __shfl_sync(grp, slot, first) + (unsigned)__popc(grp & ((1u << lane) - 1u));
               step_list[slot] = (uint32_t)j;
 #pragma unroll
               for (int q = 0; q < M; ++q) step_delta[(uint64_t)slot * M + q] = delta[q];
