@@ -169,7 +169,7 @@ __device__ __forceinline__ void load_geo(const PathDesc& d, const Tables& tb, Ge
 // g_i = A_i^T (u_i - u_{i+1}) with u_j = z_j / |z_j|.
 template <int N, unsigned Q>
 __device__ __forceinline__ void grad_eval(const Geo<N>& G, const float (&t)[N][2], float (&z)[N + 1][3],
-                                          float (&e)[N + 1], float (&g)[Pat<N, Q>::M]) {
+                                          float (&e)[N + 1], float (&g)[Pat<N, Q>::M], float (&rz)[N + 1]) {
   using P = Pat<N, Q>;
   float w[N][3];
 #pragma unroll
@@ -189,6 +189,7 @@ __device__ __forceinline__ void grad_eval(const Geo<N>& G, const float (&t)[N][2
     }
     e[j] = fmaf(z[j][2], z[j][2], fmaf(z[j][1], z[j][1], z[j][0] * z[j][0]));
     float r = rsqrtf(fmaxf(e[j], 1e-30f));
+    rz[j] = r;
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[j][c] = __fmul_rn(z[j][c], r);
   }
@@ -198,6 +199,13 @@ __device__ __forceinline__ void grad_eval(const Geo<N>& G, const float (&t)[N][2
     g[P::off(i)] = fmaf(G.a[i][0][2], d2, fmaf(G.a[i][0][1], d1, G.a[i][0][0] * d0));
     if (P::quad(i)) g[P::off(i) + 1] = fmaf(G.a[i][1][2], d2, fmaf(G.a[i][1][1], d1, G.a[i][1][0] * d0));
   }
+}
+
+template <int N, unsigned Q>
+__device__ __forceinline__ void grad_eval(const Geo<N>& G, const float (&t)[N][2], float (&z)[N + 1][3],
+                                          float (&e)[N + 1], float (&g)[Pat<N, Q>::M]) {
+  float rz[N + 1];
+  grad_eval<N, Q>(G, t, z, e, g, rz);
 }
 
 // Eq. 6: alpha <- -sum_j (q_j.z_j)/|z_j + alpha q_j| / sum_j (q_j.q_j)/|z_j + alpha q_j|,
@@ -241,6 +249,7 @@ struct PathState {
   // shared memory (one float per thread and entry) for the longer sequences
   std::conditional_t<(N <= kMaxBfgsOrder), float[HP], SmemH> H;
   float t[N][2], g[M], z[N + 1][3], e[N + 1];
+  float rz[N + 1];  // 1 / |z_j| at t, as the gradient evaluated it (the next step's alpha = 0 round reuses it)
   uint64_t gidx;
   int it;
   uint8_t st;
@@ -278,7 +287,7 @@ __device__ __forceinline__ bool path_start(PathState<N, Q>& P, const BatchDev& B
 #pragma unroll
     for (int c = r; c < M; ++c) P.H[hidx<M>(r, c)] = (r == c) ? 1.f : 0.f;
   if (P.st & ST_SKIP) return false;
-  grad_eval<N, Q>(P.G, P.t, P.z, P.e, P.g);
+  grad_eval<N, Q>(P.G, P.t, P.z, P.e, P.g, P.rz);
   return max_iters > 0;
 }
 
@@ -329,7 +338,13 @@ __device__ __forceinline__ bool bfgs_step(PathState<N, Q>& P, const SolveCfg& cf
 #pragma unroll
     for (int jj = 0; jj <= N; ++jj) {
       const float r1 = rsqrtf(fmaxf(fmaf(1.f, fmaf(1.f, qc[jj], 2.f * qa[jj]), P.e[jj]), 1e-30f));
-      const float r0 = rsqrtf(fmaxf(P.e[jj], 1e-30f));
+      // 1 / |z_j| at t: kept from the gradient evaluation up to order 4 (the same value), evaluated again
+      // for the longer sequences, where four or more reflectors would spill the extra registers
+      float r0;
+      if constexpr (N <= 4)
+        r0 = P.rz[jj];
+      else
+        r0 = rsqrtf(fmaxf(P.e[jj], 1e-30f));
       n1 = fmaf(qa[jj], r1, n1);
       d1 = fmaf(qc[jj], r1, d1);
       n0 = fmaf(qa[jj], r0, n0);
@@ -354,7 +369,7 @@ __device__ __forceinline__ bool bfgs_step(PathState<N, Q>& P, const SolveCfg& cf
         P.t[i][c] = __fadd_rn(P.t[i][c], s[r]);
       }
   float gn[M];
-  grad_eval<N, Q>(P.G, P.t, P.z, P.e, gn);
+  grad_eval<N, Q>(P.G, P.t, P.z, P.e, gn, P.rz);
   float y[M], sy = 0.f, ss = 0.f, yy = 0.f;
 #pragma unroll
   for (int r = 0; r < M; ++r) {

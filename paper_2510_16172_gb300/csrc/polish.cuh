@@ -197,9 +197,11 @@ __device__ __forceinline__ void newton_dir(const BlockTri<float, N>& F32, const 
 // double-float polish (default)
 // ---------------------------------------------------------------------------
 // Register budget of the double-float polish: up to order 3 the kernel fits in
-// 168 registers without spilling, which allows 3 CTAs per SM instead of 2.
+// 168 registers without spilling, which allows 3 CTAs per SM instead of 2; at
+// order 4 the same bound spills 48 bytes (left alone ptxas takes 231 registers,
+// two CTAs per SM).
 template <int N>
-constexpr int kPolishMinBlocks = N <= 3 ? 3 : 1;
+constexpr int kPolishMinBlocks = N <= 4 ? 3 : 1;
 
 // Output slots a kernel of order N writes in its unrolled loop (slots past N
 // get zeros); in batches with longer sequences the host clears the later slots
