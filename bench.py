@@ -161,6 +161,7 @@ NCU_TRAFFIC = {
     ("39df173948b3", "bfgs"): 570.1e6,
     ("f6467978743f", "bfgs"): 568.6e6,
     ("886638d3c5ec", "bfgs"): 568.8e6,
+    ("e1979203e5c7", "bfgs"): 567.1e6,
 }
 
 
