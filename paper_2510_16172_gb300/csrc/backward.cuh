@@ -179,8 +179,27 @@ __global__ void __launch_bounds__(kSelThreads) backward_select_kernel(BatchDev B
     const uint64_t j0 = c0 + (uint64_t)threadIdx.x * kSelPer;
     unsigned bits = 0;
     SliceWalk walk;
+    bool whole = false;  // the thread's 16 statuses read with one 16-byte load
+    if (status != nullptr && list == nullptr && dLv == nullptr && j0 + kSelPer <= n_local) {
+      // exhaustive batch, mask cotangent: 16 consecutive paths of one TX/RX pair whose statuses start on
+      // a 16-byte boundary
+      SliceWalk w0;
+      const uint64_t g0 = w0.next(B, N, j0);
+      if (w0.left + 1 >= (uint64_t)kSelPer && (reinterpret_cast<uintptr_t>(status + g0) & 15u) == 0) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(status + g0));
+        const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < kSelPer; ++k) {
+          const uint8_t st = (uint8_t)(wd[k >> 2] >> (8 * (k & 3)));
+          const bool take = !(st & (ST_REPEAT | ST_INVALID | ST_DEGENERATE | ST_NONFINITE)) && cfg.dl_mask &&
+                            (st & cfg.dl_mask) == cfg.dl_mask;
+          bits |= (take ? 1u : 0u) << k;
+        }
+        whole = true;
+      }
+    }
 #pragma unroll 4
-    for (int k = 0; k < kSelPer; ++k) {
+    for (int k = 0; k < kSelPer && !whole; ++k) {
       const uint64_t j = j0 + k;
       if (j >= n_local) break;
       uint64_t g;
