@@ -154,6 +154,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:12]
 
 
+# FP32 operations (FFMA counted as 2) the polish executes per path of the urban-canyon batch, both passes:
+# ncu SASS counters on the 8.4M-path canyon (profiles/polish_op_count_urban_canyon_8M.md).  Most are the
+# error-free transformations of its double-float gradient.
+POLISH_FP32_OPS_PER_PATH = 1674
+
 # DRAM traffic per launch from an ncu capture (profiles/), valid for the kernel sources with this hash.
 NCU_TRAFFIC = {
     # DRAM read + write of one step's bfgs_refill_kernel<3, Q> launches, ncu capture of these sources
@@ -333,6 +338,13 @@ def run_reference(args, world, rank):
     total = sum(times)
     value = solved / total
     sample = f"{per_step} uniformly sampled paths of the workload per step (seeded), FP64 damped Newton + VJP"
+    roof_polish = {"kernel": names[fpt.K_POLISH], "bound": "alu",
+                   "achieved": POLISH_FP32_OPS_PER_PATH * N / (kms[fpt.K_POLISH] / args.steps * 1e-3) / 1e12,
+                   "peak": fp32_peak, "unit": "TFLOP/s",
+                   "basis": f"executed FP32 operations, {POLISH_FP32_OPS_PER_PATH} per path of the batch (ncu SASS "
+                            "counters, both passes; mostly the double-float gradient's error-free sums)",
+                   "traffic": None}
+    roof_polish["frac"] = roof_polish["achieved"] / roof_polish["peak"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -492,6 +504,13 @@ def run_ours(args, world, rank, local_rank):
     roof_bfgs["frac"] = roof_bfgs["achieved"] / roof_bfgs["peak"]
     if clocks.get("sm_mhz"):
         roof_bfgs["frac_at_measured_clock"] = roof_bfgs["achieved"] / (fp32_peak * clocks["sm_mhz"] / sm_max)
+    roof_polish = {"kernel": names[fpt.K_POLISH], "bound": "alu",
+                   "achieved": POLISH_FP32_OPS_PER_PATH * N / (kms[fpt.K_POLISH] / args.steps * 1e-3) / 1e12,
+                   "peak": fp32_peak, "unit": "TFLOP/s",
+                   "basis": f"executed FP32 operations, {POLISH_FP32_OPS_PER_PATH} per path of the batch (ncu SASS "
+                            "counters, both passes; mostly the double-float gradient's error-free sums)",
+                   "traffic": None}
+    roof_polish["frac"] = roof_polish["achieved"] / roof_polish["peak"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -505,6 +524,7 @@ def run_ours(args, world, rank, local_rank):
             "kernel_ms_per_step": {names[k]: kms[k] / args.steps for k in range(fpt.K_COUNT) if klaunch[k]},
             "dominant_kernel": names[dom],
             "roofline": roof_bfgs,
+            "polish_roofline": roof_polish,
             "bfgs_flops_by_pattern": flops_by_pattern,
             "gpu_launches": int(sum(klaunch)),
             "clocks": clocks,
