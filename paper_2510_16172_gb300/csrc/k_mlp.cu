@@ -1237,11 +1237,13 @@ __global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const PathRec* l
 // with the accumulator in TMEM; each epilogue adds the bias, applies GELU and
 // writes the BF16 activations back into the same tile (K = 256) for the next
 // layer; the last one writes the starting parameters into T.  The weights are
-// pre-tiled in global memory as 22 units, each K-major in core matrices: for
+// pre-tiled in global memory as 19 units, each K-major in core matrices: for
 // layers 1-3 all 256 outputs x 32 input columns (16 KB, two MMAs with N = 256
 // into the whole TMEM accumulator; an MMA costs about the same time whatever
-// its N, so the widest one wastes least), for the output layer 16 outputs x 64
-// columns (2 KB, four MMAs).  They stream through two 16 KB shared buffers,
+// its N, so the widest one wastes least), for the output layer all of it, 16
+// outputs x 256 columns as four 64-column chunks (8 KB, sixteen MMAs with
+// N = 16: one unit instead of four, each unit paying a copy's latency).  They
+// stream through two 16 KB shared buffers,
 // prefetched one unit ahead: lane 0 of warp 0 waits for the MMAs that last read
 // a buffer before refilling it.  A CTA's steps are serial -- features,
 // MMAs, CUDA-core epilogue -- so the kernel is sized (103 KB of shared memory,
@@ -1250,22 +1252,22 @@ __global__ void mlp_start_kernel(SceneDev S, BatchDev B, int n, const PathRec* l
 // ---------------------------------------------------------------------------
 constexpr int kInferThreads = 256;
 constexpr int kInferCtasPerSm = 2;
-constexpr int kUnitsPerTile = 22;  // streamed units: W1 2 K-halves, W2 and W3 8 each, W4 4 chunks
+constexpr int kUnitsPerTile = 19;  // streamed units: W1 2 K-halves, W2 and W3 8 each, W4 whole
 
 // One K = 16 MMA (M = 128) occupies an SM's tensor pipe for about the same time whatever N is (measured on
 // the GB300: ~131 cycles for N = 64, 128 and 256), so the hidden layers run with N = 256: a unit of W1-W3
-// is all 256 outputs x 32 input columns (16 KB, two MMAs); the output layer (16 outputs) takes whole
-// 64-column chunks (2 KB, four MMAs).
+// is all 256 outputs x 32 input columns (16 KB, two MMAs); the output layer (16 outputs) is one unit of
+// four 64-column chunks (2 KB each, four MMAs each).
 __host__ __device__ constexpr int unit_layer(int u) { return u < 2 ? 0 : (u < 10 ? 1 : (u < 18 ? 2 : 3)); }
 // first input column of unit u within its layer
 __host__ __device__ constexpr int unit_k0(int u) {
-  return u < 2 ? 32 * u : (u < 10 ? 32 * (u - 2) : (u < 18 ? 32 * (u - 10) : 64 * (u - 18)));
+  return u < 2 ? 32 * u : (u < 10 ? 32 * (u - 2) : (u < 18 ? 32 * (u - 10) : 0));
 }
-__host__ __device__ constexpr bool unit_ends_layer(int u) { return u == 1 || u == 9 || u == 17 || u == 21; }
-__host__ __device__ constexpr uint32_t unit_bytes(int u) { return u < 18 ? 256u * 32u * 2u : 16u * 64u * 2u; }
-__host__ __device__ constexpr uint32_t unit_offset(int u) {
-  return u < 18 ? (uint32_t)u * 16384u : 18u * 16384u + (uint32_t)(u - 18) * 2048u;
-}
+__host__ __device__ constexpr bool unit_ends_layer(int u) { return u == 1 || u == 9 || u == 17 || u == 18; }
+__host__ __device__ constexpr uint32_t unit_bytes(int u) { return u < 18 ? 256u * 32u * 2u : 4u * 16u * 64u * 2u; }
+__host__ __device__ constexpr uint32_t unit_offset(int u) { return (uint32_t)(u < 18 ? u : 18) * 16384u; }
+// the output layer's 64-column chunk c (16 x 64, 2 KB) within the tiled weights
+__host__ __device__ constexpr uint32_t w4_chunk_offset(int c) { return unit_offset(18) + (uint32_t)c * 2048u; }
 // the units of a tile cover the tiled weights once, back to back
 __host__ __device__ constexpr bool units_tile_weights() {
   for (int u = 0; u + 1 < kUnitsPerTile; ++u)
@@ -1297,7 +1299,7 @@ __global__ void mlp_tile_weights_kernel(const __nv_bfloat16* __restrict__ wb, __
       const int u = (layer == 0 ? 0 : (layer == 1 ? 2 : 10)) + k / 32;
       byte = unit_offset(u) + tc::kmajor_offset(r, k % 32, 32);
     } else {
-      byte = unit_offset(18 + k / 64) + tc::kmajor_offset(r, k % 64, 64);
+      byte = w4_chunk_offset(k / 64) + tc::kmajor_offset(r, k % 64, 64);
     }
     wt[byte / 2] = wb[off + r * K + k];
   }
@@ -1427,12 +1429,18 @@ __global__ void __launch_bounds__(kInferThreads, kInferCtasPerSm) mlp_infer_kern
               const uint32_t idesc = tc::idesc_bf16(128, 256);
               tc::mma_bf16(tmem, ad, bd, idesc, k0 > 0 ? 1u : 0u);
               tc::mma_bf16(tmem, ad + 16u, bd + 16u, idesc, 1u);
-            } else {  // 16 outputs x 64 columns: four MMAs with N = 16
-              const uint64_t bd = tc::smem_desc(w0, 128u, 8u * 128u);
+            } else {  // 16 outputs x 256 columns: four 64-column chunks of four MMAs with N = 16
               const uint32_t idesc = tc::idesc_bf16(128, 16);
-              tc::mma_bf16(tmem, ad, bd, idesc, k0 > 0 ? 1u : 0u);
 #pragma unroll
-              for (int kk = 1; kk < 4; ++kk) tc::mma_bf16(tmem, ad + 16u * kk, bd + 16u * kk, idesc, 1u);
+              for (int c = 0; c < 4; ++c) {
+                // chunk c: activation columns 64 c .. 64 c + 63 (eight 8-column groups of 128 bytes on), and its
+                // 2 KB of weights
+                const uint64_t bd = tc::smem_desc(w0 + (uint32_t)c * 2048u, 128u, 8u * 128u);
+                const uint64_t adc = ad + 64u * (uint64_t)c;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                  tc::mma_bf16(tmem, adc + 16u * kk, bd + 16u * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              }
             }
           }
           tc::mma_commit(&sm.done[b]);
