@@ -338,13 +338,6 @@ def run_reference(args, world, rank):
     total = sum(times)
     value = solved / total
     sample = f"{per_step} uniformly sampled paths of the workload per step (seeded), FP64 damped Newton + VJP"
-    roof_polish = {"kernel": names[fpt.K_POLISH], "bound": "alu",
-                   "achieved": POLISH_FP32_OPS_PER_PATH * N / (kms[fpt.K_POLISH] / args.steps * 1e-3) / 1e12,
-                   "peak": fp32_peak, "unit": "TFLOP/s",
-                   "basis": f"executed FP32 operations, {POLISH_FP32_OPS_PER_PATH} per path of the batch (ncu SASS "
-                            "counters, both passes; mostly the double-float gradient's error-free sums)",
-                   "traffic": None}
-    roof_polish["frac"] = roof_polish["achieved"] / roof_polish["peak"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
